@@ -1,0 +1,104 @@
+/*
+ * nrr_oracle.h -- plain FP64 CPU oracle for the hyperbolic-relaxation solve of
+ * the binary-black-hole puncture Hamiltonian constraint (arXiv 2501.14030,
+ * Sec. 2, Eqs. for u and for the relaxation system; Alg. 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the independent checker of the
+ * CUDA path.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+ * leg may load it.  It shares no code, header, table or constant generator
+ * with the CUDA library; neither includes the other.
+ *
+ * Every array is a padded 3-D grid function of s0*s1*s2 doubles, index
+ * p = i0 + s0*(i1 + s1*i2), i0 fastest, s_d = n_d + 2*ng, ng = order/2.
+ * Cell-centred sampling: xx_d[i] = xxmin_d + (i - ng + 1/2) * dxx_d.
+ */
+#ifndef NRR_ORACLE_H
+#define NRR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_SINHSYMTP = 0, OR_SPHERICAL = 1, OR_CARTESIAN = 2 };
+enum { OR_INTERIOR = 0, OR_OUTER = 1, OR_INNER = 2 };
+enum { OR_CONVERGED = 0, OR_NOT_CONVERGED = 1, OR_DIVERGED = 2 };
+
+typedef struct {
+  int coord;       /* OR_SINHSYMTP / OR_SPHERICAL / OR_CARTESIAN        */
+  int n[3];        /* interior points per direction                      */
+  int order;       /* centred finite-difference order: 2,4,6,8,10,12     */
+  double amax;     /* SinhSymTP outer extent                              */
+  double bscale;   /* SinhSymTP focal half-distance                       */
+  double sinhwaa;  /* SinhSymTP sinh width                                */
+  double rmax;     /* Spherical outer radius                              */
+  double xmax;     /* Cartesian half-width                                */
+} or_desc;
+
+typedef struct {
+  double m;        /* bare mass                                           */
+  double x[3];     /* position                                            */
+  double P[3];     /* linear momentum                                     */
+  double S[3];     /* spin angular momentum                               */
+} or_puncture;
+
+typedef struct {
+  double eta;      /* damping factor of the relaxation system             */
+  double dt;       /* time step                                           */
+  double tol;      /* stop when the residual norm falls below this       */
+  double r_int;    /* radius of the norm's integration region             */
+  long max_iters;  /* RK4 steps allowed                                   */
+  int check_every; /* residual is evaluated every this many steps         */
+} or_relax_params;
+
+typedef struct {
+  long iters;
+  double norm;
+  int status;      /* OR_CONVERGED / OR_NOT_CONVERGED / OR_DIVERGED       */
+} or_relax_result;
+
+typedef struct or_grid or_grid;
+
+/* Geometry: coordinates, scale factors, Laplacian coefficients, wave speed,
+ * ghost classification and the inner-boundary image of every inner ghost,
+ * found by matching Cartesian coordinates.  NULL on error (message in err). */
+or_grid *or_grid_new(const or_desc *d, char *err, int errlen);
+void or_grid_free(or_grid *g);
+/* ints: ng, s0, s1, s2, npts(low 31 bits); dbls: xxmin[3], dxx[3], dsmin_global */
+void or_grid_info(const or_grid *g, int *ints, double *dbls);
+/* Named per-point arrays: "x","y","z","r","h0","h1","h2","g0","g1","g2",
+ * "jac","dsmin","c","drdxx0","xx0","xx1","xx2" (doubles); "kind","image"
+ * (ints).  Returns NULL for an unknown name. */
+void *or_grid_field(or_grid *g, const char *name);
+
+/* Centred FD weights at offsets -order/2..order/2 for derivative `deriv`. */
+int or_fd_weights(int order, int deriv, double *w);
+
+/* Bowen-York conformal extrinsic curvature contraction and psi_singular at x. */
+void or_bowen_york(int np, const or_puncture *p, const double *x,
+                   double *aa, double *psi_s);
+/* alpha = 1/psi_s and beta = aa * alpha^7 / 8 at every padded point. */
+int or_source(const or_grid *g, int np, const or_puncture *p,
+              double *alpha, double *beta);
+
+void or_fill_inner_ghosts(const or_grid *g, double *f);
+void or_laplacian(const or_grid *g, const double *u, double *lap);
+void or_rhs(const or_grid *g, const double *alpha, const double *beta,
+            double eta, const double *u, const double *v,
+            double *ku, double *kv);
+void or_rk4_step(const or_grid *g, const double *alpha, const double *beta,
+                 double eta, double dt, double *u, double *v);
+void or_residual(const or_grid *g, const double *alpha, const double *beta,
+                 const double *u, double *H);
+double or_residual_norm(const or_grid *g, const double *H, double r_int);
+int or_relax(const or_grid *g, const double *alpha, const double *beta,
+             const or_relax_params *prm, double *u, double *v,
+             or_relax_result *res);
+
+/* Newton's method with a dense LU on the discrete steady-state system. */
+int or_newton(const or_grid *g, const double *alpha, const double *beta,
+              double *u, int max_it, double step_tol, double *final_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
