@@ -1,0 +1,218 @@
+/*
+ * nrr.h -- C ABI of libnrr, a GB300 (sm_103a) solver for binary-black-hole
+ * puncture initial data by hyperbolic relaxation (arXiv 2501.14030).
+ *
+ * The method (paper Sec. 2): the non-singular part u of the conformal factor
+ * psi = psi_singular + u satisfies the Hamiltonian constraint
+ *     lap(u) + (1/8) A~_ij A~^ij (psi_singular + u)^-7 = 0,
+ * which is relaxed as the damped wave system
+ *     du/dt = v - eta u,   dv/dt = c^2 [lap(u) + (1/8) A~A~ (psi_s + u)^-7],
+ * with c proportional to the local grid spacing, by the method of lines with
+ * RK4 on a curvilinear reference-metric grid, until the L2 norm of the
+ * residual H (the left-hand side of the constraint) drops below a threshold
+ * (paper Alg. 1: RHS -> BC -> RK substeps, H and its norm, stop test).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an nrr_status.  On failure nrr_last_error() gives a
+ *    message for the calling thread.  No call aborts or prints.
+ *  - Grid functions are padded 3-D arrays of s0*s1*s2 values, flat index
+ *    p = i0 + s0*(i1 + s1*i2) (i0 fastest), s_d = n_d + 2*ng, ng = fd_order/2.
+ *    Sampling is cell-centred: xx_d = xxmin_d + (i_d - ng + 1/2) dxx_d.
+ *  - "Evolved" points are the interior plus the outer ghost shell (points
+ *    beyond the outer boundary, evolved by the radiation condition).  Inner
+ *    ghosts (xx0 < 0, theta outside [0,pi], phi outside [-pi,pi)) are images
+ *    of evolved points; the kernels read them through the image map and only
+ *    the calls that copy a grid function out fill them.
+ *  - Pointers flagged "on_device" are CUDA device pointers on the current
+ *    device; otherwise they are host pointers.  The caller owns every pointer
+ *    it passes; the library copies what it keeps.
+ *  - All device work is issued on the stream given to nrr_create_grid (NULL =
+ *    the legacy default stream).  Calls return after their results are
+ *    complete unless stated otherwise.
+ */
+#ifndef NRR_H
+#define NRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NRR_OK = 0,
+  NRR_ERR_INVALID_ARG = 1,   /* bad argument; nothing was changed          */
+  NRR_ERR_OOM = 2,           /* device memory would not fit; checked before */
+                             /* any allocation                              */
+  NRR_ERR_CUDA = 3,          /* a CUDA runtime call failed                  */
+  NRR_ERR_NOT_CONVERGED = 4, /* iteration limit reached above tolerance     */
+  NRR_ERR_DIVERGED = 5,      /* residual norm became non-finite             */
+  NRR_ERR_TIMEOUT = 6,       /* wall-clock limit of the solve reached       */
+  NRR_ERR_STATE = 7          /* call out of order (e.g. relax before        */
+                             /* punctures are set)                          */
+} nrr_status;
+
+enum { NRR_SINHSYMTP = 0, NRR_SPHERICAL = 1, NRR_CARTESIAN = 2 };
+enum { NRR_FP64 = 0, NRR_FP32 = 1, NRR_FP32_DC = 2 };
+enum { NRR_INIT_ZERO = 0, NRR_INIT_CURRENT = 1, NRR_INIT_HOST = 2,
+       NRR_INIT_DEVICE = 3 };
+
+/* Grid description (paper Sec. 2: SinhSymTP coordinates; Sec. 6: other
+ * coordinate families; Sec. 4: centred finite differences of selectable
+ * order).
+ *   coord     NRR_SINHSYMTP: xx0 in [0,1], xx1 = theta in [0,pi],
+ *             xx2 = phi in [-pi,pi); A = amax sinh(xx0/w)/sinh(1/w),
+ *             x = A sin(th) cos(ph), y = A sin(th) sin(ph),
+ *             z = sqrt(A^2 + bscale^2) cos(th), w = sinhwaa.
+ *             NRR_SPHERICAL: xx0 = r in [0,rmax].
+ *             NRR_CARTESIAN: [-xmax, xmax]^3.
+ *   n[3]      interior points per direction (n[2] even for curvilinear grids).
+ *   fd_order  4, 8 or 10.                                                    */
+typedef struct {
+  int coord;
+  int n[3];
+  int fd_order;
+  double amax, bscale, sinhwaa;
+  double rmax;
+  double xmax;
+} nrr_grid_desc;
+
+/* One puncture (paper Sec. 2, Brandt-Bruegmann data with Bowen-York
+ * curvature): bare mass m > 0, position x, momentum P, spin S. */
+typedef struct {
+  double m;
+  double x[3];
+  double P[3];
+  double S[3];
+} nrr_puncture;
+
+/* Options of one solve (paper Sec. 2 relaxation system; Alg. 1 loop).
+ *   mode         NRR_FP64, NRR_FP32 (whole relaxation in single precision)
+ *                or NRR_FP32_DC (single-precision relaxation of the linearised
+ *                correction equation inside an FP64 defect-correction loop;
+ *                FP64 residual, norm and update).
+ *   tol          stop when the residual norm < tol (e.g. 1e-10).
+ *   max_iters    RK4 steps allowed (all inner steps for NRR_FP32_DC).
+ *   check_every  residual norm evaluated every this many steps (>= 1).
+ *   cfl          dt = cfl * min over interior of the local spacing.
+ *   eta          damping factor; <= 0 selects 2 pi cfl / (n0 dt).
+ *   r_int        the norm integrates over interior points with r < r_int.
+ *   initial      NRR_INIT_ZERO (u = v = 0), NRR_INIT_CURRENT (continue from
+ *                the grid's state), NRR_INIT_HOST / NRR_INIT_DEVICE (u from
+ *                u0, padded FP64 layout; v = eta u).
+ *   u0           initial u for NRR_INIT_HOST/DEVICE, else ignored.
+ *   timeout_ms   wall-clock limit (<= 0: none); checked between norm checks.
+ *   inner_tol    NRR_FP32_DC: relative reduction of the inner residual.
+ *   max_outer    NRR_FP32_DC: defect-correction iterations allowed.        */
+typedef struct {
+  int mode;
+  double tol;
+  int64_t max_iters;
+  int check_every;
+  double cfl;
+  double eta;
+  double r_int;
+  int initial;
+  const double *u0;
+  int64_t timeout_ms;
+  double inner_tol;
+  int max_outer;
+} nrr_relax_opts;
+
+/* Result of one solve: RK4 steps taken, outer defect-correction iterations,
+ * last residual norm, wall seconds of the call, and its status code. */
+typedef struct {
+  int64_t iters;
+  int64_t outer_iters;
+  double final_norm;
+  double seconds;
+  int status;
+} nrr_relax_result;
+
+typedef struct nrr_grid nrr_grid;
+
+/* Fills *o with the defaults: FP64, tol 1e-10, max_iters 10^6,
+ * check_every 50, cfl 0.5, eta 0 (automatic), r_int 100, zero initial data,
+ * no timeout, inner_tol 1e-4, max_outer 20. */
+nrr_status nrr_default_opts(nrr_relax_opts *o);
+
+/* Creates a grid: computes the full device footprint, fails with
+ * NRR_ERR_OOM before allocating if it does not fit, allocates, and runs the
+ * coordinate and reference-metric set-up on the device (paper Alg. 1,
+ * set-up lines: coordinate arrays, reference-metric precompute, boundary
+ * containers, storage).  stream: a cudaStream_t, caller-owned, must outlive
+ * the grid.  *out receives a handle owned by the caller (nrr_destroy_grid).
+ * Errors: NRR_ERR_INVALID_ARG (unsupported coord/order, n < 1, odd n2 on a
+ * curvilinear grid, n1 < fd_order/2), NRR_ERR_OOM, NRR_ERR_CUDA. */
+nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
+                           nrr_grid **out);
+nrr_status nrr_destroy_grid(nrr_grid *g);
+
+/* Padded dims s[3], ghost width, and interior point count of a grid. */
+nrr_status nrr_grid_dims(const nrr_grid *g, int s[3], int *ng,
+                         int64_t *interior_points);
+
+/* Sets the punctures (1..8) and computes the constant source terms on the
+ * device (paper Sec. 2; Alg. 1 "compute constant source terms"):
+ * alpha = 1/psi_singular, beta = (1/8) A~_ij A~^ij alpha^7 at every padded
+ * point, with psi_singular = 1 + sum m_a/(2 r_a) and Bowen-York A~^ij.
+ * p: caller-owned host array, copied.  Errors: NRR_ERR_INVALID_ARG (n out of
+ * range, m <= 0, a puncture on a grid point). */
+nrr_status nrr_set_punctures(nrr_grid *g, int n, const nrr_puncture *p);
+
+/* Relaxes to tol (paper Alg. 1 relaxation loop).  Returns NRR_OK when the
+ * norm fell below tol, else NRR_ERR_NOT_CONVERGED / NRR_ERR_DIVERGED /
+ * NRR_ERR_TIMEOUT; *r (optional) is filled in every case.  The converged
+ * state stays on the grid (nrr_get_u). */
+nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
+                     nrr_relax_result *r);
+
+/* Residual H of the current u in FP64 (paper Eq. for u, the "H" of Alg. 1)
+ * and its L2 norm over r < r_int: sqrt(sum H^2 J / sum J) over interior
+ * points, J = h0 h1 h2 the reference-metric volume factor.
+ * h_out (nullable): padded array of s0*s1*s2 doubles, zero off the interior;
+ * device pointer when h_on_device, else host. */
+nrr_status nrr_residual(nrr_grid *g, double r_int, double *norm_out,
+                        double *h_out, int h_on_device);
+
+/* Copies the current u (and v) out, padded layout with inner ghosts filled,
+ * FP64 whatever the solve mode. */
+nrr_status nrr_get_state(nrr_grid *g, double *u, double *v, int on_device);
+
+/* Replaces the state (u, v) from padded FP64 arrays (inner ghosts ignored).
+ * v may be NULL (v = 0).  Used for checkpoint/resume and warm starts. */
+nrr_status nrr_set_state(nrr_grid *g, const double *u, const double *v,
+                         int on_device);
+
+/* One evaluation of the relaxation right-hand side with its boundary
+ * conditions (paper Sec. 2 system; Alg. 1 RHS then BC) on the given state,
+ * in the precision of `mode` (NRR_FP64 / NRR_FP32), with damping eta.
+ * u, v in: padded FP64; ku, kv out: padded FP64, values at evolved points
+ * and inner ghosts (copied from their images).  All device pointers. */
+nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
+                   const double *v, double *ku, double *kv);
+
+/* Takes `steps` RK4 steps (paper Alg. 1 inner loop) from the current state
+ * in precision `mode` with time step dt and damping eta, without norm checks.
+ * For trajectory comparisons and benchmarks. */
+nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
+                    int64_t steps);
+
+/* The time step the solver uses for a given CFL factor, and the default
+ * damping: dt = cfl * min ds over the interior, eta = 2 pi cfl / (n0 dt). */
+nrr_status nrr_timestep(const nrr_grid *g, double cfl, double *dt,
+                        double *eta_default);
+
+/* Host-side image map of the inner boundary: out[p] = flat index of the
+ * evolved point whose value ghost p copies, or p itself for evolved points.
+ * out: host array of s0*s1*s2 int32.  Pure host computation, no device. */
+nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
+
+const char *nrr_last_error(void);
+const char *nrr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,792 @@
+// nrr_api.cu -- the C ABI of libnrr (declared in include/nrr.h) and the host
+// driver of the relaxation loop (arXiv 2501.14030, Alg. 1).
+//
+// Set-up runs once per grid on the device; the relaxation loop is a CUDA
+// graph of `check_every` RK4 steps (4 fused stage kernels each) followed by
+// the residual and its norm, replayed until the norm falls below tol.  The
+// only host<->device traffic per chunk is the 8-byte norm.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/nrr.h"
+#include "nrr_internal.h"
+
+using namespace nrr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+nrr_status fail(nrr_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                     \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess)                                                 \
+      return fail(NRR_ERR_CUDA, "%s: %s (%s:%d)", #call,                   \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);             \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    nrr_status s_ = (expr);           \
+    if (s_ != NRR_OK) return s_;      \
+  } while (0)
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct GraphKey {
+  int mode, steps;
+  double dt, eta, r_int;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(mode, steps, dt, eta, r_int) <
+           std::tie(o.mode, o.steps, o.dt, o.eta, o.r_int);
+  }
+};
+
+struct nrr_grid {
+  nrr_grid_desc desc{};
+  Geo geo{};
+  cudaStream_t stream = nullptr;       // the grid's own work stream
+  cudaStream_t user_stream = nullptr;  // caller's stream (ordering only)
+  cudaEvent_t order_ev = nullptr;
+  int device = 0;
+  LaunchCfg cfg;
+  std::vector<void *> allocs;
+
+  FieldSet<double> f64;
+  FieldSet<float> f32;
+  ColumnSet<double> c64;
+  ColumnSet<float> c32;
+  CartCoef cart{};
+  // column geometry
+  double *h = nullptr, *gl = nullptr, *rad = nullptr, *drdxx0 = nullptr,
+         *jac = nullptr, *dsmin = nullptr;
+  double *scalars = nullptr;   // [0] dsmin_global, [1..3] norm out
+  double *partials = nullptr;
+  int *flag = nullptr;
+  double *host_pinned = nullptr;  // norm read-back
+  // defect correction
+  double *res64 = nullptr;
+  double *u_save = nullptr;
+  float *acoef32 = nullptr;
+  float *rhs32 = nullptr;
+
+  double dsmin_global = 0.0;
+  bool have_source = false;
+  int state_prec = 64;  // which FieldSet holds the current state
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+template <typename T>
+nrr_status dev_alloc(nrr_grid *g, T **p, size_t count) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  g->allocs.push_back(ptr);
+  *p = static_cast<T *>(ptr);
+  return NRR_OK;
+}
+
+size_t footprint_bytes(const Geo &geo) {
+  size_t n = (size_t)geo.npts, nc = (size_t)geo.ncol;
+  size_t b = 0;
+  b += n * (10 * 8 + 10 * 4);          // FP64 + FP32 field sets
+  b += n * (8 + 8 + 4 + 4);            // defect-correction buffers
+  b += nc * 8 * (3 + 2 + 4);           // column geometry
+  b += nc * (8 + 4) * (ncoef(geo.ng) + 4);
+  b += (size_t)(geo.ncol / 32 + 16) * 16 * ((geo.n2 + 1)) + (1 << 20);
+  return b;
+}
+
+nrr_status validate_desc(const nrr_grid_desc *d) {
+  if (!d) return fail(NRR_ERR_INVALID_ARG, "null grid descriptor");
+  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_CARTESIAN)
+    return fail(NRR_ERR_INVALID_ARG, "unknown coordinate system %d", d->coord);
+  if (d->fd_order != 4 && d->fd_order != 8 && d->fd_order != 10)
+    return fail(NRR_ERR_INVALID_ARG, "fd_order must be 4, 8 or 10 (got %d)",
+                d->fd_order);
+  int ng = d->fd_order / 2;
+  for (int i = 0; i < 3; i++)
+    if (d->n[i] < 1 || d->n[i] > (1 << 16))
+      return fail(NRR_ERR_INVALID_ARG, "n[%d] = %d out of range", i, d->n[i]);
+  if (d->coord != NRR_CARTESIAN) {
+    if (d->n[2] & 1)
+      return fail(NRR_ERR_INVALID_ARG, "n2 must be even on curvilinear grids");
+    if (d->n[1] < ng)
+      return fail(NRR_ERR_INVALID_ARG, "n1 must be >= fd_order/2");
+    if (d->n[0] < ng)
+      return fail(NRR_ERR_INVALID_ARG, "n0 must be >= fd_order/2");
+  } else {
+    for (int i = 0; i < 3; i++)
+      if (d->n[i] < 2)
+        return fail(NRR_ERR_INVALID_ARG, "Cartesian n must be >= 2");
+  }
+  if (d->coord == NRR_SINHSYMTP &&
+      !(d->amax > 0 && d->sinhwaa > 0 && d->bscale >= 0))
+    return fail(NRR_ERR_INVALID_ARG, "SinhSymTP needs amax > 0, sinhwaa > 0");
+  if (d->coord == NRR_SPHERICAL && !(d->rmax > 0))
+    return fail(NRR_ERR_INVALID_ARG, "Spherical needs rmax > 0");
+  if (d->coord == NRR_CARTESIAN && !(d->xmax > 0))
+    return fail(NRR_ERR_INVALID_ARG, "Cartesian needs xmax > 0");
+  return NRR_OK;
+}
+
+Geo make_geo(const nrr_grid_desc *d) {
+  Geo g{};
+  g.coord = d->coord;
+  g.n0 = d->n[0];
+  g.n1 = d->n[1];
+  g.n2 = d->n[2];
+  g.ng = d->fd_order / 2;
+  g.s0 = g.n0 + 2 * g.ng;
+  g.s1 = g.n1 + 2 * g.ng;
+  g.s2 = g.n2 + 2 * g.ng;
+  g.ncol = g.s0 * g.s1;
+  g.npts = (int64_t)g.ncol * g.s2;
+  double xmin[3], xmax[3];
+  if (d->coord == NRR_CARTESIAN) {
+    for (int i = 0; i < 3; i++) {
+      xmin[i] = -d->xmax;
+      xmax[i] = d->xmax;
+    }
+  } else {
+    xmin[0] = 0.0;
+    xmax[0] = d->coord == NRR_SINHSYMTP ? 1.0 : d->rmax;
+    xmin[1] = 0.0;
+    xmax[1] = M_PI;
+    xmin[2] = -M_PI;
+    xmax[2] = M_PI;
+  }
+  int n[3] = {g.n0, g.n1, g.n2};
+  for (int i = 0; i < 3; i++) {
+    g.xxmin[i] = xmin[i];
+    g.dxx[i] = (xmax[i] - xmin[i]) / n[i];
+  }
+  g.amax = d->amax;
+  g.bscale = d->bscale;
+  g.sinhwaa = d->sinhwaa;
+  return g;
+}
+
+template <typename R>
+StageArgs<R> stage_args(const nrr_grid *g, const FieldSet<R> &f,
+                        const ColumnSet<R> &c, int stage, double dt,
+                        double eta) {
+  // Classical RK4: k1 = F(y); k2 = F(y + dt/2 k1); k3 = F(y + dt/2 k2);
+  // k4 = F(y + dt k3); y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
+  StageArgs<R> a{};
+  a.alpha = f.alpha;
+  a.bc2 = f.bc2;
+  a.col = c;
+  a.cart = g->cart;
+  a.eta = (R)eta;
+  a.au = f.a[0];
+  a.av = f.a[1];
+  a.bu = f.y[0];
+  a.bv = f.y[1];
+  switch (stage) {
+    case 0:  // in y; acc = y + dt/6 k1; s = y + dt/2 k1
+      a.su = f.y[0]; a.sv = f.y[1];
+      a.ou = f.s[0]; a.ov = f.s[1];
+      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 6.0);
+      break;
+    case 1:  // in s; acc += dt/3 k2; t = y + dt/2 k2
+      a.su = f.s[0]; a.sv = f.s[1];
+      a.ou = f.t[0]; a.ov = f.t[1];
+      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 3.0);
+      break;
+    case 2:  // in t; acc += dt/3 k3; s = y + dt k3
+      a.su = f.t[0]; a.sv = f.t[1];
+      a.ou = f.s[0]; a.ov = f.s[1];
+      a.wa = (R)dt; a.wb = (R)(dt / 3.0);
+      break;
+    default:  // in s; y = acc + dt/6 k4
+      a.su = f.s[0]; a.sv = f.s[1];
+      a.ou = f.y[0]; a.ov = f.y[1];
+      a.wa = (R)0; a.wb = (R)(dt / 6.0);
+      break;
+  }
+  return a;
+}
+
+template <typename R>
+void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
+                      const ColumnSet<R> &c, double dt, double eta,
+                      int64_t steps) {
+  static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
+  for (int64_t s = 0; s < steps; s++)
+    for (int k = 0; k < 4; k++)
+      launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta),
+                      g->cfg, g->stream);
+}
+
+// Residual + norm of the current state in precision R into scalars[1..3].
+template <typename R>
+void launch_norm(const nrr_grid *g, const FieldSet<R> &f, const ColumnSet<R> &c,
+                 double r_int, double *h_out) {
+  int nb = 0;
+  launch_residual<R>(g->geo, f.y[0], f.alpha, f.bc2, c, g->cart, g->jac,
+                     g->rad, r_int, h_out, g->partials, &nb, g->cfg, g->stream);
+  launch_norm_finalize(g->partials, nb, g->scalars + 1, g->stream);
+}
+
+nrr_status sync_read_norm(nrr_grid *g, double *out) {
+  CUDA_TRY(cudaMemcpyAsync(g->host_pinned, g->scalars + 1, sizeof(double),
+                           cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  *out = g->host_pinned[0];
+  return NRR_OK;
+}
+
+// Make the requested precision hold the current state.
+nrr_status ensure_state(nrr_grid *g, int prec) {
+  if (g->state_prec == prec) return NRR_OK;
+  int64_t n = g->geo.npts;
+  for (int c = 0; c < 2; c++) {
+    if (prec == 32)
+      launch_convert(g->f64.y[c], g->f32.y[c], n, g->stream);
+    else
+      launch_convert(g->f32.y[c], g->f64.y[c], n, g->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  g->state_prec = prec;
+  return NRR_OK;
+}
+
+nrr_status get_graph(nrr_grid *g, int mode, int steps, double dt, double eta,
+                     double r_int, cudaGraphExec_t *out) {
+  GraphKey key{mode, steps, dt, eta, r_int};
+  auto it = g->graphs.find(key);
+  if (it != g->graphs.end()) {
+    *out = it->second;
+    return NRR_OK;
+  }
+  cudaGraph_t graph;
+  CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+  if (mode == NRR_FP32) {
+    launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, steps);
+    launch_norm<float>(g, g->f32, g->c32, r_int, nullptr);
+  } else {
+    launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, steps);
+    launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
+  }
+  cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+  if (e != cudaSuccess)
+    return fail(NRR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return fail(NRR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  g->graphs[key] = exec;
+  *out = exec;
+  return NRR_OK;
+}
+
+nrr_status check_grid(const nrr_grid *g) {
+  if (!g) return fail(NRR_ERR_INVALID_ARG, "null grid");
+  return NRR_OK;
+}
+
+// Every call starts by making the grid's work stream wait for the work the
+// caller has queued on its own stream (inputs produced there), and ends
+// after the work stream has drained.
+nrr_status set_device(const nrr_grid *g) {
+  CUDA_TRY(cudaSetDevice(g->device));
+  CUDA_TRY(cudaEventRecord(g->order_ev, g->user_stream));
+  CUDA_TRY(cudaStreamWaitEvent(g->stream, g->order_ev, 0));
+  return NRR_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *nrr_last_error(void) { return g_last_error.c_str(); }
+const char *nrr_version(void) { return "nrr 0.1 (sm_103a)"; }
+
+nrr_status nrr_default_opts(nrr_relax_opts *o) {
+  if (!o) return fail(NRR_ERR_INVALID_ARG, "null opts");
+  memset(o, 0, sizeof *o);
+  o->mode = NRR_FP64;
+  o->tol = 1e-10;
+  o->max_iters = 1000000;
+  o->check_every = 50;
+  o->cfl = 0.5;
+  o->eta = 0.0;
+  o->r_int = 100.0;
+  o->initial = NRR_INIT_ZERO;
+  o->u0 = nullptr;
+  o->timeout_ms = 0;
+  o->inner_tol = 1e-4;
+  o->max_outer = 20;
+  return NRR_OK;
+}
+
+nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out) {
+  TRY(validate_desc(d));
+  if (!out) return fail(NRR_ERR_INVALID_ARG, "null output");
+  Geo g = make_geo(d);
+  for (int i2 = 0; i2 < g.s2; i2++)
+    for (int i1 = 0; i1 < g.s1; i1++)
+      for (int i0 = 0; i0 < g.s0; i0++) {
+        int64_t p = flat(g, i0, i1, i2);
+        int j0 = i0, j1 = i1, j2 = i2;
+        if (g.coord != CARTESIAN) image_of(g, j0, j1, j2);
+        out[p] = (int32_t)flat(g, j0, j1, j2);
+      }
+  return NRR_OK;
+}
+
+nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
+                           nrr_grid **out) {
+  if (!out) return fail(NRR_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  TRY(validate_desc(d));
+  Geo geo = make_geo(d);
+  if (geo.npts > (int64_t)1 << 31)
+    return fail(NRR_ERR_INVALID_ARG, "grid of %lld points exceeds 2^31",
+                (long long)geo.npts);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  size_t need = footprint_bytes(geo), free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (need + (size_t)(256u << 20) > free_b)
+    return fail(NRR_ERR_OOM, "grid needs %zu bytes, %zu free", need, free_b);
+
+  nrr_grid *g = new (std::nothrow) nrr_grid();
+  if (!g) return fail(NRR_ERR_OOM, "host allocation failed");
+  g->desc = *d;
+  g->geo = geo;
+  g->user_stream = static_cast<cudaStream_t>(stream);
+  g->device = dev;
+  nrr_status st = [&]() -> nrr_status {
+    CUDA_TRY(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&g->order_ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(g->order_ev, g->user_stream));
+    CUDA_TRY(cudaStreamWaitEvent(g->stream, g->order_ev, 0));
+    const int64_t n = geo.npts;
+    const int nc = geo.ncol, nco = ncoef(geo.ng);
+    for (int c = 0; c < 2; c++) {
+      TRY(dev_alloc(g, &g->f64.y[c], n));
+      TRY(dev_alloc(g, &g->f64.s[c], n));
+      TRY(dev_alloc(g, &g->f64.t[c], n));
+      TRY(dev_alloc(g, &g->f64.a[c], n));
+      TRY(dev_alloc(g, &g->f32.y[c], n));
+      TRY(dev_alloc(g, &g->f32.s[c], n));
+      TRY(dev_alloc(g, &g->f32.t[c], n));
+      TRY(dev_alloc(g, &g->f32.a[c], n));
+    }
+    TRY(dev_alloc(g, &g->f64.alpha, n));
+    TRY(dev_alloc(g, &g->f64.bc2, n));
+    TRY(dev_alloc(g, &g->f32.alpha, n));
+    TRY(dev_alloc(g, &g->f32.bc2, n));
+    TRY(dev_alloc(g, &g->res64, n));
+    TRY(dev_alloc(g, &g->u_save, n));
+    TRY(dev_alloc(g, &g->acoef32, n));
+    TRY(dev_alloc(g, &g->rhs32, n));
+    TRY(dev_alloc(g, &g->h, 3 * (size_t)nc));
+    TRY(dev_alloc(g, &g->gl, 2 * (size_t)nc));
+    TRY(dev_alloc(g, &g->rad, nc));
+    TRY(dev_alloc(g, &g->drdxx0, nc));
+    TRY(dev_alloc(g, &g->jac, nc));
+    TRY(dev_alloc(g, &g->dsmin, nc));
+    TRY(dev_alloc(g, &g->c64.coef, (size_t)nco * nc));
+    TRY(dev_alloc(g, &g->c64.somm, 3 * (size_t)nc));
+    TRY(dev_alloc(g, &g->c64.c2inv, nc));
+    TRY(dev_alloc(g, &g->c32.coef, (size_t)nco * nc));
+    TRY(dev_alloc(g, &g->c32.somm, 3 * (size_t)nc));
+    TRY(dev_alloc(g, &g->c32.c2inv, nc));
+    TRY(dev_alloc(g, &g->scalars, 8));
+    int nb = residual_blocks(geo, g->cfg);
+    TRY(dev_alloc(g, &g->partials, 2 * (size_t)nb + 64));
+    TRY(dev_alloc(g, &g->flag, 4));
+    CUDA_TRY(cudaMallocHost(&g->host_pinned, 8 * sizeof(double)));
+    // zero all state so unset regions are finite
+    for (int c = 0; c < 2; c++) {
+      double *f64s[4] = {g->f64.y[c], g->f64.s[c], g->f64.t[c], g->f64.a[c]};
+      float *f32s[4] = {g->f32.y[c], g->f32.s[c], g->f32.t[c], g->f32.a[c]};
+      for (int k = 0; k < 4; k++) {
+        CUDA_TRY(cudaMemsetAsync(f64s[k], 0, n * sizeof(double), g->stream));
+        CUDA_TRY(cudaMemsetAsync(f32s[k], 0, n * sizeof(float), g->stream));
+      }
+    }
+    CUDA_TRY(cudaMemsetAsync(g->f64.alpha, 0, n * sizeof(double), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->f64.bc2, 0, n * sizeof(double), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->f32.alpha, 0, n * sizeof(float), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->f32.bc2, 0, n * sizeof(float), g->stream));
+
+    // FD weights, closed forms.
+    int m = geo.ng;
+    double w1[7] = {0}, w2[7] = {0};
+    for (int k = 0; k <= m; k++) {
+      w1[k] = k == 0 ? 0.0 : fd_first(m, k);
+      w2[k] = fd_second(m, k);
+    }
+    if (geo.coord == CARTESIAN) {
+      // Uniform spacing: dt from the smallest spacing, c = 1 when the
+      // spacings agree (the wave speed follows the local spacing).
+      double ds = fmin(geo.dxx[0], fmin(geo.dxx[1], geo.dxx[2]));
+      g->dsmin_global = ds;
+      CartCoef cc{};
+      cc.cc = 0.0;
+      for (int dd = 0; dd < 3; dd++) {
+        double inv = 1.0 / (geo.dxx[dd] * geo.dxx[dd]);
+        cc.cc += w2[0] * inv;
+        for (int k = 1; k <= m; k++) cc.a[dd][k - 1] = w2[k] * inv;
+      }
+      g->cart = cc;
+      double host_s[1] = {ds};
+      CUDA_TRY(cudaMemcpyAsync(g->scalars, host_s, sizeof(double),
+                               cudaMemcpyHostToDevice, g->stream));
+    } else {
+      launch_column_geometry(geo, g->h, g->gl, g->rad, g->drdxx0, g->jac,
+                             g->dsmin, g->stream);
+      launch_min_interior(geo, g->dsmin, g->scalars, g->stream);
+      launch_column_coefs(geo, g->h, g->gl, g->rad, g->drdxx0, g->dsmin,
+                          g->scalars, w1, w2, g->c64, g->c32, g->stream);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemcpyAsync(g->host_pinned, g->scalars, sizeof(double),
+                               cudaMemcpyDeviceToHost, g->stream));
+      CUDA_TRY(cudaStreamSynchronize(g->stream));
+      g->dsmin_global = g->host_pinned[0];
+      if (!(g->dsmin_global > 0.0) || !std::isfinite(g->dsmin_global))
+        return fail(NRR_ERR_INVALID_ARG, "degenerate grid spacing %g",
+                    g->dsmin_global);
+    }
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return NRR_OK;
+  }();
+  if (st != NRR_OK) {
+    std::string msg = g_last_error;
+    nrr_destroy_grid(g);
+    g_last_error = msg;
+    return st;
+  }
+  *out = g;
+  return NRR_OK;
+}
+
+nrr_status nrr_destroy_grid(nrr_grid *g) {
+  if (!g) return NRR_OK;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  for (void *p : g->allocs) cudaFree(p);
+  if (g->host_pinned) cudaFreeHost(g->host_pinned);
+  if (g->order_ev) cudaEventDestroy(g->order_ev);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return NRR_OK;
+}
+
+nrr_status nrr_grid_dims(const nrr_grid *g, int s[3], int *ng,
+                         int64_t *interior_points) {
+  TRY(check_grid(g));
+  if (s) {
+    s[0] = g->geo.s0;
+    s[1] = g->geo.s1;
+    s[2] = g->geo.s2;
+  }
+  if (ng) *ng = g->geo.ng;
+  if (interior_points)
+    *interior_points = (int64_t)g->geo.n0 * g->geo.n1 * g->geo.n2;
+  return NRR_OK;
+}
+
+nrr_status nrr_timestep(const nrr_grid *g, double cfl, double *dt,
+                        double *eta_default) {
+  TRY(check_grid(g));
+  if (!(cfl > 0.0)) return fail(NRR_ERR_INVALID_ARG, "cfl must be positive");
+  double d = cfl * g->dsmin_global;
+  if (dt) *dt = d;
+  if (eta_default) *eta_default = 2.0 * M_PI * cfl / (g->geo.n0 * d);
+  return NRR_OK;
+}
+
+nrr_status nrr_set_punctures(nrr_grid *g, int n, const nrr_puncture *p) {
+  TRY(check_grid(g));
+  if (n < 1 || n > 8 || !p)
+    return fail(NRR_ERR_INVALID_ARG, "need 1..8 punctures (got %d)", n);
+  PunctureSet ps{};
+  ps.n = n;
+  for (int i = 0; i < n; i++) {
+    if (!(p[i].m > 0.0) || !std::isfinite(p[i].m))
+      return fail(NRR_ERR_INVALID_ARG, "puncture %d: mass must be positive", i);
+    ps.p[i].m = p[i].m;
+    for (int k = 0; k < 3; k++) {
+      ps.p[i].x[k] = p[i].x[k];
+      ps.p[i].P[k] = p[i].P[k];
+      ps.p[i].S[k] = p[i].S[k];
+      if (!std::isfinite(p[i].x[k]) || !std::isfinite(p[i].P[k]) ||
+          !std::isfinite(p[i].S[k]))
+        return fail(NRR_ERR_INVALID_ARG, "puncture %d: non-finite input", i);
+    }
+  }
+  TRY(set_device(g));
+  CUDA_TRY(cudaMemsetAsync(g->flag, 0, sizeof(int), g->stream));
+  launch_source(g->geo, ps, g->dsmin, g->scalars, g->f64.alpha, g->f64.bc2,
+                g->f32.alpha, g->f32.bc2, g->flag, g->stream);
+  CUDA_TRY(cudaGetLastError());
+  int bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, g->flag, sizeof(int), cudaMemcpyDeviceToHost,
+                           g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (bad) {
+    g->have_source = false;
+    return fail(NRR_ERR_INVALID_ARG, "a puncture lies on a grid point");
+  }
+  g->have_source = true;
+  return NRR_OK;
+}
+
+nrr_status nrr_set_state(nrr_grid *g, const double *u, const double *v,
+                         int on_device) {
+  TRY(check_grid(g));
+  if (!u) return fail(NRR_ERR_INVALID_ARG, "null u");
+  TRY(set_device(g));
+  size_t bytes = (size_t)g->geo.npts * sizeof(double);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(g->f64.y[0], u, bytes, kind, g->stream));
+  if (v)
+    CUDA_TRY(cudaMemcpyAsync(g->f64.y[1], v, bytes, kind, g->stream));
+  else
+    CUDA_TRY(cudaMemsetAsync(g->f64.y[1], 0, bytes, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  g->state_prec = 64;
+  return NRR_OK;
+}
+
+nrr_status nrr_get_state(nrr_grid *g, double *u, double *v, int on_device) {
+  TRY(check_grid(g));
+  TRY(set_device(g));
+  TRY(ensure_state(g, 64));
+  size_t bytes = (size_t)g->geo.npts * sizeof(double);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int c = 0; c < 2; c++) launch_fill_ghosts<double>(g->geo, g->f64.y[c], g->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (u) CUDA_TRY(cudaMemcpyAsync(u, g->f64.y[0], bytes, kind, g->stream));
+  if (v) CUDA_TRY(cudaMemcpyAsync(v, g->f64.y[1], bytes, kind, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return NRR_OK;
+}
+
+nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
+                   const double *v, double *ku, double *kv) {
+  TRY(check_grid(g));
+  if (!u || !v || !ku || !kv) return fail(NRR_ERR_INVALID_ARG, "null pointer");
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  if (mode != NRR_FP64 && mode != NRR_FP32)
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  TRY(set_device(g));
+  int64_t n = g->geo.npts;
+  if (mode == NRR_FP64) {
+    StageArgs<double> a{};
+    a.su = u; a.sv = v; a.ou = ku; a.ov = kv;
+    a.alpha = g->f64.alpha; a.bc2 = g->f64.bc2; a.col = g->c64; a.cart = g->cart;
+    a.eta = eta;
+    CUDA_TRY(cudaMemsetAsync(ku, 0, n * sizeof(double), g->stream));
+    CUDA_TRY(cudaMemsetAsync(kv, 0, n * sizeof(double), g->stream));
+    launch_stage<double>(g->geo, STAGE_RAW, a, g->cfg, g->stream);
+  } else {
+    // Round the inputs to FP32 in the grid's stage buffers, evaluate in
+    // FP32, widen the result.
+    TRY(ensure_state(g, 64));  // keep any FP32 state safe from the scratch use
+    float *us = g->f32.s[0], *vs = g->f32.s[1], *ko = g->f32.t[0], *kw = g->f32.t[1];
+    launch_convert(u, us, n, g->stream);
+    launch_convert(v, vs, n, g->stream);
+    CUDA_TRY(cudaMemsetAsync(ko, 0, n * sizeof(float), g->stream));
+    CUDA_TRY(cudaMemsetAsync(kw, 0, n * sizeof(float), g->stream));
+    StageArgs<float> a{};
+    a.su = us; a.sv = vs; a.ou = ko; a.ov = kw;
+    a.alpha = g->f32.alpha; a.bc2 = g->f32.bc2; a.col = g->c32; a.cart = g->cart;
+    a.eta = (float)eta;
+    launch_stage<float>(g->geo, STAGE_RAW, a, g->cfg, g->stream);
+    launch_convert(ko, ku, n, g->stream);
+    launch_convert(kw, kv, n, g->stream);
+  }
+  launch_fill_ghosts<double>(g->geo, ku, g->stream);
+  launch_fill_ghosts<double>(g->geo, kv, g->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return NRR_OK;
+}
+
+nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
+                    int64_t steps) {
+  TRY(check_grid(g));
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  if (steps < 0 || !(dt > 0.0))
+    return fail(NRR_ERR_INVALID_ARG, "need steps >= 0 and dt > 0");
+  TRY(set_device(g));
+  if (mode == NRR_FP32) {
+    TRY(ensure_state(g, 32));
+    launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, steps);
+  } else if (mode == NRR_FP64) {
+    TRY(ensure_state(g, 64));
+    launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, steps);
+  } else {
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return NRR_OK;
+}
+
+nrr_status nrr_residual(nrr_grid *g, double r_int, double *norm_out,
+                        double *h_out, int h_on_device) {
+  TRY(check_grid(g));
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  TRY(set_device(g));
+  TRY(ensure_state(g, 64));
+  double *hdev = nullptr;
+  size_t bytes = (size_t)g->geo.npts * sizeof(double);
+  if (h_out) {
+    hdev = h_on_device ? h_out : g->res64;
+    CUDA_TRY(cudaMemsetAsync(hdev, 0, bytes, g->stream));
+  }
+  launch_norm<double>(g, g->f64, g->c64, r_int, hdev);
+  CUDA_TRY(cudaGetLastError());
+  if (h_out && !h_on_device)
+    CUDA_TRY(cudaMemcpyAsync(h_out, hdev, bytes, cudaMemcpyDeviceToHost, g->stream));
+  double nrm = 0.0;
+  TRY(sync_read_norm(g, &nrm));
+  if (norm_out) *norm_out = nrm;
+  return NRR_OK;
+}
+
+nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
+                     nrr_relax_result *r) {
+  double t_start = now_s();
+  TRY(check_grid(g));
+  if (!o) return fail(NRR_ERR_INVALID_ARG, "null opts");
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  if (o->mode != NRR_FP64 && o->mode != NRR_FP32 && o->mode != NRR_FP32_DC)
+    return fail(NRR_ERR_INVALID_ARG, "unknown mode %d", o->mode);
+  if (!(o->tol > 0.0) || o->check_every < 1 || o->max_iters < 0 ||
+      !(o->cfl > 0.0) || !(o->r_int > 0.0))
+    return fail(NRR_ERR_INVALID_ARG, "invalid relax options");
+  if (o->mode == NRR_FP32_DC)
+    return fail(NRR_ERR_INVALID_ARG, "NRR_FP32_DC not available in this build");
+  TRY(set_device(g));
+  double dt = 0.0, eta_def = 0.0;
+  TRY(nrr_timestep(g, o->cfl, &dt, &eta_def));
+  double eta = o->eta > 0.0 ? o->eta : eta_def;
+  size_t bytes = (size_t)g->geo.npts * sizeof(double);
+  switch (o->initial) {
+    case NRR_INIT_ZERO:
+      for (int c = 0; c < 2; c++)
+        CUDA_TRY(cudaMemsetAsync(g->f64.y[c], 0, bytes, g->stream));
+      g->state_prec = 64;
+      break;
+    case NRR_INIT_CURRENT:
+      break;
+    case NRR_INIT_HOST:
+    case NRR_INIT_DEVICE:
+      if (!o->u0) return fail(NRR_ERR_INVALID_ARG, "u0 required");
+      CUDA_TRY(cudaMemcpyAsync(g->f64.y[0], o->u0, bytes,
+                               o->initial == NRR_INIT_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice,
+                               g->stream));
+      // v = eta u: the steady-state relation of the relaxation system.
+      CUDA_TRY(cudaMemcpyAsync(g->f64.y[1], g->f64.y[0], bytes,
+                               cudaMemcpyDeviceToDevice, g->stream));
+      launch_scale(g->f64.y[1], eta, g->geo.npts, g->stream);
+      g->state_prec = 64;
+      break;
+    default:
+      return fail(NRR_ERR_INVALID_ARG, "unknown initial mode %d", o->initial);
+  }
+  int prec = o->mode == NRR_FP32 ? 32 : 64;
+  TRY(ensure_state(g, prec));
+
+  nrr_relax_result res{};
+  int64_t it = 0;
+  double nrm = 0.0;
+  if (prec == 32)
+    launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
+  else
+    launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+  CUDA_TRY(cudaGetLastError());
+  TRY(sync_read_norm(g, &nrm));
+  nrr_status status = NRR_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (!std::isfinite(nrm)) {
+      status = NRR_ERR_DIVERGED;
+      break;
+    }
+    if (nrm < o->tol) {
+      status = NRR_OK;
+      break;
+    }
+    if (it >= o->max_iters) break;
+    if (o->timeout_ms > 0 && (now_s() - t_start) * 1e3 > (double)o->timeout_ms) {
+      status = NRR_ERR_TIMEOUT;
+      break;
+    }
+    int64_t m = o->check_every;
+    if (o->max_iters - it < m) m = o->max_iters - it;
+    if (m == o->check_every) {
+      cudaGraphExec_t exec;
+      TRY(get_graph(g, o->mode, (int)m, dt, eta, o->r_int, &exec));
+      CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+    } else if (prec == 32) {
+      launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, m);
+      launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
+    } else {
+      launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, m);
+      launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+    }
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_read_norm(g, &nrm));
+    it += m;
+  }
+  res.iters = it;
+  res.outer_iters = 0;
+  res.final_norm = nrm;
+  res.status = status;
+  res.seconds = now_s() - t_start;
+  if (r) *r = res;
+  if (status == NRR_ERR_NOT_CONVERGED)
+    return fail(status, "not converged after %lld steps (norm %.3e)",
+                (long long)it, nrm);
+  if (status == NRR_ERR_DIVERGED)
+    return fail(status, "residual norm not finite after %lld steps",
+                (long long)it);
+  if (status == NRR_ERR_TIMEOUT)
+    return fail(status, "timeout after %lld steps (norm %.3e)", (long long)it,
+                nrm);
+  return NRR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// nrr_internal.h -- device buffers of one grid and the kernel launchers that
+// the C-ABI layer (nrr_api.cu) drives.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nrr_common.cuh"
+
+namespace nrr {
+
+// Stage kinds of the fused RK4 stage kernel (classical RK4: k1..k4 with
+// weights 1/6, 1/3, 1/3, 1/6 and stage offsets 1/2, 1/2, 1):
+//   FIRST: acc = y + b dt k;  out = y + a dt k        (input state: y)
+//   MID:   acc += b dt k;     out = y + a dt k        (input: stage state)
+//   LAST:  out = acc + b dt k                         (out is y's buffer)
+//   RAW:   out = k                                    (one RHS evaluation)
+enum StageKind { STAGE_FIRST = 0, STAGE_MID = 1, STAGE_LAST = 2, STAGE_RAW = 3 };
+
+// Number of folded stencil coefficients per column: one centre weight, ng
+// forward and ng backward weights in xx0 and xx1, ng symmetric weights in xx2.
+inline int ncoef(int ng) { return 5 * ng + 1; }
+
+// Per-column arrays of a curvilinear grid in one precision.
+template <typename R>
+struct ColumnSet {
+  R *coef = nullptr;   // [ncoef][ncol] c^2-scaled Laplacian weights
+  R *somm = nullptr;   // [3][ncol]: c, 1/(2 dxx0 dr/dxx0), 1/r
+  R *c2inv = nullptr;  // [ncol] 1/c^2
+};
+
+// Grid functions of one precision: RK4 state y, two stage states s/t, the
+// accumulator a (each u and v), and the constant sources alpha and
+// c^2 beta.
+template <typename R>
+struct FieldSet {
+  R *y[2] = {nullptr, nullptr};
+  R *s[2] = {nullptr, nullptr};
+  R *t[2] = {nullptr, nullptr};
+  R *a[2] = {nullptr, nullptr};
+  R *alpha = nullptr;
+  R *bc2 = nullptr;
+};
+
+struct LaunchCfg {
+  int block = 128;  // threads per block (columns)
+  int zc = 2;       // phi planes per thread
+};
+
+// Cartesian grids use constant coefficients (uniform spacing, c = 1).
+struct CartCoef {
+  double cc;          // centre weight, all three directions
+  double a[3][6];     // a[dir][k] for k = 1..ng, symmetric
+};
+
+// ----------------------------------------------------------------- set-up
+// Column geometry (curvilinear): scale factors, Laplacian first-derivative
+// coefficients, radius, dr/dxx0, volume factor and local spacing.
+void launch_column_geometry(const Geo &g, double *h, double *gl, double *rad,
+                            double *drdxx0, double *jac, double *dsmin,
+                            cudaStream_t st);
+void launch_min_interior(const Geo &g, const double *dsmin, double *out,
+                         cudaStream_t st);
+// Folded, c^2-scaled coefficients and boundary factors.  w1/w2 = FD weights
+// for k = 0..ng (closed forms).
+void launch_column_coefs(const Geo &g, const double *h, const double *gl,
+                         const double *rad, const double *drdxx0,
+                         const double *dsmin, const double *dsmin_global,
+                         const double *w1, const double *w2,
+                         ColumnSet<double> c64, ColumnSet<float> c32,
+                         cudaStream_t st);
+
+struct PunctureDev {
+  double m, x[3], P[3], S[3];
+};
+struct PunctureSet {
+  int n;
+  PunctureDev p[8];
+};
+// alpha = 1/psi_s, c^2 beta at every padded point (FP64 and FP32 copies);
+// sets *bad if a puncture coincides with a grid point.
+void launch_source(const Geo &g, const PunctureSet &ps, const double *dsmin,
+                   const double *dsmin_global, double *alpha, double *bc2,
+                   float *alpha32, float *bc2_32, int *bad, cudaStream_t st);
+
+// ---------------------------------------------------------------- stencil
+template <typename R>
+struct StageArgs {
+  const R *su, *sv;  // stage input state (u is differentiated)
+  const R *bu, *bv;  // base state y (FIRST/MID)
+  R *au, *av;        // accumulator
+  R *ou, *ov;        // stage output (or k for RAW)
+  const R *alpha, *bc2;
+  ColumnSet<R> col;
+  CartCoef cart;
+  R eta, wa, wb;     // damping, a_s dt, b_s dt
+};
+
+template <typename R>
+void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
+                  const LaunchCfg &cfg, cudaStream_t st);
+
+// Residual H (c^-2 times the scaled operator) at interior points and the
+// per-block partial sums of H^2 J and J over r < r_int.  h_out nullable.
+template <typename R>
+void launch_residual(const Geo &g, const R *u, const R *alpha, const R *bc2,
+                     ColumnSet<R> col, const CartCoef &cart, const double *jac,
+                     const double *rad, double r_int, double *h_out,
+                     double *partials, int *nblocks_out, const LaunchCfg &cfg,
+                     cudaStream_t st);
+int residual_blocks(const Geo &g, const LaunchCfg &cfg);
+// sqrt(sum num / sum den) of nblocks partial pairs into out[0]; out[1] = num,
+// out[2] = den.  Fixed summation order.
+void launch_norm_finalize(const double *partials, int nblocks, double *out,
+                          cudaStream_t st);
+
+// Fill inner ghosts of a padded grid function from their images.
+template <typename R>
+void launch_fill_ghosts(const Geo &g, R *f, cudaStream_t st);
+// Precision conversion of whole padded arrays.
+void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t st);
+void launch_convert(const float *src, double *dst, int64_t n, cudaStream_t st);
+void launch_scale(double *f, double s, int64_t n, cudaStream_t st);
+
+}  // namespace nrr

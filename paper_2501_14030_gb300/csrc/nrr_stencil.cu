@@ -1,0 +1,500 @@
+// nrr_stencil.cu -- the relaxation hot path on sm_103a (arXiv 2501.14030,
+// Sec. 2 relaxation system; Alg. 1 RHS -> BC -> RK substep, residual H and
+// its L2 norm).
+//
+// One launch per RK4 stage evaluates the right-hand side at every evolved
+// point -- the damped-wave RHS at interior points, the radiation condition on
+// the outer ghost shell -- and applies the stage's RK4 update in the same
+// pass.  Inner ghosts are never stored during a solve: the stencil reads the
+// image point directly (phi periodicity, the xx0 < 0 and theta reflections),
+// which is the inner boundary condition of Alg. 1 applied on read.
+//
+// Curvilinear grids: the reference metric, c^2 and the FD weights are folded
+// into per-column weights (the metric is phi-independent), so the operator is
+// 5*ng+1 fused multiply-adds on u plus the source term.
+#include <cuda_runtime.h>
+
+#include "nrr_internal.h"
+
+namespace nrr {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ R ld(const R *p) {
+  return __ldg(p);
+}
+
+template <int NG>
+__device__ __forceinline__ int wrap2(const Geo &g, int i2) {
+  // phi index into [NG, NG+n2); |offset| <= NG so one correction suffices
+  // when n2 >= NG, else fall back to a modulo.
+  if (g.n2 >= NG) {
+    if (i2 < NG) return i2 + g.n2;
+    if (i2 >= NG + g.n2) return i2 - g.n2;
+    return i2;
+  }
+  return wrap_phi(g, i2);
+}
+
+// beta c^2 (1 + alpha u)^-7 added to acc.
+template <typename R>
+__device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2) {
+  R s = fma(al, u0, R(1));
+  R t = R(1) / s;
+  R t2 = t * t;
+  R t4 = t2 * t2;
+  R q = bc2 * t;
+  q = q * t2;
+  return fma(q, t4, acc);
+}
+
+// c^2 [lap(u) + source] at an interior point of a curvilinear grid.
+template <typename R, int NG>
+__device__ __forceinline__ R curvi_operator(const Geo &g, const R *__restrict__ su,
+                                            const R (&w)[5 * NG + 1], int col,
+                                            int i0, int i1, int i2, int64_t p,
+                                            R u0, R al, R bc2) {
+  const int64_t nc = g.ncol;
+  const int s0 = g.s0;
+  const int half = g.n2 / 2;
+  R lap = w[0] * u0;
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+    // xx0: the + side stays inside the padded box; the - side may cross
+    // xx0 = 0 and read the reflected point at phi + pi.
+    R up = ld(su + p + k);
+    R um;
+    int im = i0 - k;
+    if (im >= NG) {
+      um = ld(su + p - k);
+    } else {
+      int j0 = 2 * NG - 1 - im;
+      int j1 = g.coord == SPHERICAL ? g.n1 + 2 * NG - 1 - i1 : i1;
+      int j2 = wrap2<NG>(g, i2 + half);
+      um = ld(su + j0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
+    }
+    lap = fma(w[k], up, lap);
+    lap = fma(w[NG + k], um, lap);
+  }
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+    // theta: reflections through the axis, again with phi + pi.
+    R up, um;
+    int ip = i1 + k, im = i1 - k;
+    if (ip < g.n1 + NG) {
+      up = ld(su + p + (int64_t)k * s0);
+    } else {
+      int j1 = 2 * g.n1 + 2 * NG - 1 - ip;
+      int j2 = wrap2<NG>(g, i2 + half);
+      up = ld(su + i0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
+    }
+    if (im >= NG) {
+      um = ld(su + p - (int64_t)k * s0);
+    } else {
+      int j1 = 2 * NG - 1 - im;
+      int j2 = wrap2<NG>(g, i2 + half);
+      um = ld(su + i0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
+    }
+    lap = fma(w[2 * NG + k], up, lap);
+    lap = fma(w[3 * NG + k], um, lap);
+  }
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+    // phi: periodic.
+    R sp = ld(su + col + nc * wrap2<NG>(g, i2 + k));
+    R sm = ld(su + col + nc * wrap2<NG>(g, i2 - k));
+    lap = fma(w[4 * NG + k], sp + sm, lap);
+  }
+  return add_source(lap, u0, al, bc2);
+}
+
+template <typename R, int KIND>
+__device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
+                                               R ku, R kv) {
+  if (KIND == STAGE_FIRST) {
+    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    a.au[p] = fma(a.wb, ku, yu);
+    a.av[p] = fma(a.wb, kv, yv);
+    a.ou[p] = fma(a.wa, ku, yu);
+    a.ov[p] = fma(a.wa, kv, yv);
+  } else if (KIND == STAGE_MID) {
+    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    a.au[p] = fma(a.wb, ku, a.au[p]);
+    a.av[p] = fma(a.wb, kv, a.av[p]);
+    a.ou[p] = fma(a.wa, ku, yu);
+    a.ov[p] = fma(a.wa, kv, yv);
+  } else if (KIND == STAGE_LAST) {
+    a.ou[p] = fma(a.wb, ku, a.au[p]);
+    a.ov[p] = fma(a.wb, kv, a.av[p]);
+  } else {
+    a.ou[p] = ku;
+    a.ov[p] = kv;
+  }
+}
+
+// Curvilinear stage kernel.  Thread = one (i0, i1) column of evolved points
+// (interior plus the outer shell i0 >= n0+ng) and zc consecutive phi planes.
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(128)
+    stage_curvi_kernel(Geo g, StageArgs<R> a, int zc) {
+  const int ne0 = g.n0 + NG;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne0 * g.n1) return;
+  const int i0 = e % ne0 + NG, i1 = e / ne0 + NG;
+  const int col = i0 + g.s0 * i1;
+  const int nc = g.ncol;
+  const int z0 = NG + blockIdx.y * zc;
+  const int z1 = min(z0 + zc, NG + g.n2);
+  if (i0 >= g.n0 + NG) {
+    // Radiation condition, df/dt = -c (d_r f + f/r), d_r from the
+    // second-order backward difference along xx0.
+    R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
+      rinv = ld(a.col.somm + 2 * nc + col);
+    for (int i2 = z0; i2 < z1; i2++) {
+      int64_t p = col + (int64_t)nc * i2;
+      R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
+      R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+      R du = fma(R(3), u0, fma(R(-4), u1, u2));
+      R dv = fma(R(3), v0, fma(R(-4), v1, v2));
+      R ku = -c * fma(kdb, du, rinv * u0);
+      R kv = -c * fma(kdb, dv, rinv * v0);
+      stage_epilogue<R, KIND>(a, p, ku, kv);
+    }
+    return;
+  }
+  R w[5 * NG + 1];
+#pragma unroll
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+  for (int i2 = z0; i2 < z1; i2++) {
+    int64_t p = col + (int64_t)nc * i2;
+    R u0 = ld(a.su + p), v0 = ld(a.sv + p);
+    R kv = curvi_operator<R, NG>(g, a.su, w, col, i0, i1, i2, p, u0,
+                                 ld(a.alpha + p), ld(a.bc2 + p));
+    R ku = fma(-a.eta, u0, v0);
+    stage_epilogue<R, KIND>(a, p, ku, kv);
+  }
+}
+
+// Cartesian: uniform spacing, c = 1, every ghost is an outer ghost evolved by
+// the radiation condition with d_r f = sum_i (x^i/r) D_i f (one-sided inward
+// along directions in which the point lies outside, centred otherwise).
+template <typename R, int NG>
+__device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ f,
+                                            int i0, int i1, int i2, int64_t p) {
+  const int ii[3] = {i0, i1, i2};
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
+  R x[3], r2 = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    x[d] = R(g.xxmin[d] + (ii[d] - NG + 0.5) * g.dxx[d]);
+    r2 = fma(x[d], x[d], r2);
+  }
+  R rinv = R(1) / sqrt(r2);
+  R f0 = ld(f + p);
+  R dr = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    R D;
+    R inv2 = R(0.5 / g.dxx[d]);
+    if (ii[d] >= nn[d] + NG)
+      D = (R(3) * f0 - R(4) * ld(f + p - st[d]) + ld(f + p - 2 * st[d])) * inv2;
+    else if (ii[d] < NG)
+      D = -(R(3) * f0 - R(4) * ld(f + p + st[d]) + ld(f + p + 2 * st[d])) * inv2;
+    else
+      D = (ld(f + p + st[d]) - ld(f + p - st[d])) * inv2;
+    dr = fma(x[d] * rinv, D, dr);
+  }
+  return -(dr + f0 * rinv);
+}
+
+template <typename R, int NG>
+__device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ su,
+                                           const CartCoef &cc, int64_t p, R u0,
+                                           R al, R bc2) {
+  const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
+  R lap = R(cc.cc) * u0;
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+#pragma unroll
+    for (int k = 1; k <= NG; k++)
+      lap = fma(R(cc.a[d][k - 1]), ld(su + p + k * st[d]) + ld(su + p - k * st[d]),
+                lap);
+  return add_source(lap, u0, al, bc2);
+}
+
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(128)
+    stage_cart_kernel(Geo g, StageArgs<R> a, int zc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ncol) return;
+  const int i0 = e % g.s0, i1 = e / g.s0;
+  const int z0 = blockIdx.y * zc;
+  const int z1 = min(z0 + zc, g.s2);
+  const bool in01 = i0 >= NG && i0 < g.n0 + NG && i1 >= NG && i1 < g.n1 + NG;
+  for (int i2 = z0; i2 < z1; i2++) {
+    int64_t p = e + (int64_t)g.ncol * i2;
+    R ku, kv;
+    if (in01 && i2 >= NG && i2 < g.n2 + NG) {
+      R u0 = ld(a.su + p), v0 = ld(a.sv + p);
+      kv = cart_operator<R, NG>(g, a.su, a.cart, p, u0, ld(a.alpha + p),
+                                ld(a.bc2 + p));
+      ku = fma(-a.eta, u0, v0);
+    } else {
+      ku = cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
+      kv = cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
+    }
+    stage_epilogue<R, KIND>(a, p, ku, kv);
+  }
+}
+
+// Deterministic block sum of two FP64 values (warp shuffles in a fixed
+// pattern, then the warps in order).
+__device__ __forceinline__ void block_sum2(double &x, double &y, double *out) {
+  __shared__ double sx[32], sy[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sx[wid] = x;
+    sy[wid] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tx = 0.0, ty = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      tx += sx[i];
+      ty += sy[i];
+    }
+    out[0] = tx;
+    out[1] = ty;
+  }
+}
+
+// Residual H at interior points and the block partials of H^2 J, J over
+// r < r_int (the volume-weighted L2 norm of Alg. 1's residual).
+template <typename R, int NG>
+__global__ void __launch_bounds__(128)
+    residual_curvi_kernel(Geo g, const R *__restrict__ su,
+                          const R *__restrict__ alpha, const R *__restrict__ bc2,
+                          ColumnSet<R> col_set, const double *__restrict__ jac,
+                          const double *__restrict__ rad, double r_int,
+                          double *h_out, double *partials, int zc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double num = 0.0, den = 0.0;
+  if (e < g.n0 * g.n1) {
+    const int i0 = e % g.n0 + NG, i1 = e / g.n0 + NG;
+    const int col = i0 + g.s0 * i1;
+    const int nc = g.ncol;
+    R w[5 * NG + 1];
+#pragma unroll
+    for (int j = 0; j < 5 * NG + 1; j++)
+      w[j] = ld(col_set.coef + (int64_t)j * nc + col);
+    R c2inv = ld(col_set.c2inv + col);
+    double wt = rad[col] < r_int ? jac[col] : 0.0;
+    const int z0 = NG + blockIdx.y * zc;
+    const int z1 = min(z0 + zc, NG + g.n2);
+    for (int i2 = z0; i2 < z1; i2++) {
+      int64_t p = col + (int64_t)nc * i2;
+      R u0 = ld(su + p);
+      R op = curvi_operator<R, NG>(g, su, w, col, i0, i1, i2, p, u0,
+                                   ld(alpha + p), ld(bc2 + p));
+      double H = (double)(op * c2inv);
+      if (h_out) h_out[p] = H;
+      num += H * H * wt;
+      den += wt;
+    }
+  }
+  block_sum2(num, den, partials + 2 * (blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+template <typename R, int NG>
+__global__ void __launch_bounds__(128)
+    residual_cart_kernel(Geo g, const R *__restrict__ su,
+                         const R *__restrict__ alpha, const R *__restrict__ bc2,
+                         CartCoef cc, double r_int, double *h_out,
+                         double *partials, int zc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double num = 0.0, den = 0.0;
+  if (e < g.n0 * g.n1) {
+    const int i0 = e % g.n0 + NG, i1 = e / g.n0 + NG;
+    const int z0 = NG + blockIdx.y * zc;
+    const int z1 = min(z0 + zc, NG + g.n2);
+    double x0 = g.xxmin[0] + (i0 - NG + 0.5) * g.dxx[0];
+    double x1 = g.xxmin[1] + (i1 - NG + 0.5) * g.dxx[1];
+    for (int i2 = z0; i2 < z1; i2++) {
+      int64_t p = i0 + (int64_t)g.s0 * (i1 + (int64_t)g.s1 * i2);
+      R u0 = ld(su + p);
+      double H = (double)cart_operator<R, NG>(g, su, cc, p, u0, ld(alpha + p),
+                                              ld(bc2 + p));
+      if (h_out) h_out[p] = H;
+      double x2 = g.xxmin[2] + (i2 - NG + 0.5) * g.dxx[2];
+      double wt = sqrt(x0 * x0 + x1 * x1 + x2 * x2) < r_int ? 1.0 : 0.0;
+      num += H * H * wt;
+      den += wt;
+    }
+  }
+  block_sum2(num, den, partials + 2 * (blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+__global__ void norm_finalize_kernel(const double *partials, int nblocks,
+                                     double *out) {
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    x += partials[2 * i];
+    y += partials[2 * i + 1];
+  }
+  __shared__ double res[2];
+  block_sum2(x, y, res);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = res[1] > 0.0 ? sqrt(res[0] / res[1]) : 0.0;
+    out[1] = res[0];
+    out[2] = res[1];
+  }
+}
+
+template <typename R>
+__global__ void fill_ghosts_kernel(Geo g, R *f) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.npts) return;
+  int i0 = (int)(p % g.s0);
+  int i1 = (int)((p / g.s0) % g.s1);
+  int i2 = (int)(p / g.ncol);
+  bool evolved = i0 >= g.ng && i1 >= g.ng && i1 < g.n1 + g.ng && i2 >= g.ng &&
+                 i2 < g.n2 + g.ng;
+  if (evolved) return;
+  int j0 = i0, j1 = i1, j2 = i2;
+  image_of(g, j0, j1, j2);
+  f[p] = f[flat(g, j0, j1, j2)];
+}
+
+__global__ void convert_d2f_kernel(const double *s, float *d, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+__global__ void convert_f2d_kernel(const float *s, double *d, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (double)s[i];
+}
+__global__ void scale_kernel(double *f, double s, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] *= s;
+}
+
+template <typename R, int NG>
+void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
+                     const LaunchCfg &cfg, cudaStream_t st) {
+  if (g.coord == CARTESIAN) {
+    dim3 grid((g.ncol + cfg.block - 1) / cfg.block, (g.s2 + cfg.zc - 1) / cfg.zc);
+    switch (kind) {
+      case STAGE_FIRST: stage_cart_kernel<R, NG, STAGE_FIRST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+      case STAGE_MID: stage_cart_kernel<R, NG, STAGE_MID><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+      case STAGE_LAST: stage_cart_kernel<R, NG, STAGE_LAST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+      default: stage_cart_kernel<R, NG, STAGE_RAW><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+    }
+    return;
+  }
+  int ncols = (g.n0 + NG) * g.n1;
+  dim3 grid((ncols + cfg.block - 1) / cfg.block, (g.n2 + cfg.zc - 1) / cfg.zc);
+  switch (kind) {
+    case STAGE_FIRST: stage_curvi_kernel<R, NG, STAGE_FIRST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+    case STAGE_MID: stage_curvi_kernel<R, NG, STAGE_MID><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+    case STAGE_LAST: stage_curvi_kernel<R, NG, STAGE_LAST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+    default: stage_curvi_kernel<R, NG, STAGE_RAW><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+  }
+}
+
+template <typename R, int NG>
+void launch_residual_ng(const Geo &g, const R *u, const R *alpha, const R *bc2,
+                        ColumnSet<R> col, const CartCoef &cart,
+                        const double *jac, const double *rad, double r_int,
+                        double *h_out, double *partials, const LaunchCfg &cfg,
+                        cudaStream_t st) {
+  dim3 grid((g.n0 * g.n1 + cfg.block - 1) / cfg.block,
+            (g.n2 + cfg.zc - 1) / cfg.zc);
+  if (g.coord == CARTESIAN)
+    residual_cart_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
+        g, u, alpha, bc2, cart, r_int, h_out, partials, cfg.zc);
+  else
+    residual_curvi_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
+        g, u, alpha, bc2, col, jac, rad, r_int, h_out, partials, cfg.zc);
+}
+
+}  // namespace
+
+template <typename R>
+void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
+                  const LaunchCfg &cfg, cudaStream_t st) {
+  switch (g.ng) {
+    case 2: launch_stage_ng<R, 2>(g, kind, a, cfg, st); break;
+    case 4: launch_stage_ng<R, 4>(g, kind, a, cfg, st); break;
+    case 5: launch_stage_ng<R, 5>(g, kind, a, cfg, st); break;
+    default: break;
+  }
+}
+template void launch_stage<double>(const Geo &, int, const StageArgs<double> &,
+                                   const LaunchCfg &, cudaStream_t);
+template void launch_stage<float>(const Geo &, int, const StageArgs<float> &,
+                                  const LaunchCfg &, cudaStream_t);
+
+int residual_blocks(const Geo &g, const LaunchCfg &cfg) {
+  return ((g.n0 * g.n1 + cfg.block - 1) / cfg.block) *
+         ((g.n2 + cfg.zc - 1) / cfg.zc);
+}
+
+template <typename R>
+void launch_residual(const Geo &g, const R *u, const R *alpha, const R *bc2,
+                     ColumnSet<R> col, const CartCoef &cart, const double *jac,
+                     const double *rad, double r_int, double *h_out,
+                     double *partials, int *nblocks_out, const LaunchCfg &cfg,
+                     cudaStream_t st) {
+  switch (g.ng) {
+    case 2: launch_residual_ng<R, 2>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
+    case 4: launch_residual_ng<R, 4>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
+    case 5: launch_residual_ng<R, 5>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
+    default: break;
+  }
+  if (nblocks_out) *nblocks_out = residual_blocks(g, cfg);
+}
+template void launch_residual<double>(const Geo &, const double *, const double *,
+                                      const double *, ColumnSet<double>,
+                                      const CartCoef &, const double *,
+                                      const double *, double, double *,
+                                      double *, int *, const LaunchCfg &,
+                                      cudaStream_t);
+template void launch_residual<float>(const Geo &, const float *, const float *,
+                                     const float *, ColumnSet<float>,
+                                     const CartCoef &, const double *,
+                                     const double *, double, double *, double *,
+                                     int *, const LaunchCfg &, cudaStream_t);
+
+void launch_norm_finalize(const double *partials, int nblocks, double *out,
+                          cudaStream_t st) {
+  norm_finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, out);
+}
+
+template <typename R>
+void launch_fill_ghosts(const Geo &g, R *f, cudaStream_t st) {
+  if (g.coord == CARTESIAN) return;
+  int64_t nb = (g.npts + 255) / 256;
+  fill_ghosts_kernel<R><<<(unsigned)nb, 256, 0, st>>>(g, f);
+}
+template void launch_fill_ghosts<double>(const Geo &, double *, cudaStream_t);
+template void launch_fill_ghosts<float>(const Geo &, float *, cudaStream_t);
+
+void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t st) {
+  convert_d2f_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+}
+void launch_convert(const float *src, double *dst, int64_t n, cudaStream_t st) {
+  convert_f2d_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+}
+void launch_scale(double *f, double s, int64_t n, cudaStream_t st) {
+  scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, s, n);
+}
+
+}  // namespace nrr

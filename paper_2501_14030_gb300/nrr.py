@@ -1,0 +1,244 @@
+"""Python binding of libnrr (include/nrr.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; this module converts Python
+values to the C structs, passes torch tensor pointers (device memory and the
+current CUDA stream come from PyTorch) or numpy buffers, and turns status codes
+into exceptions.  The library must have been built (``__graft_entry__.build()``
+or ``python -m paper_2501_14030_gb300.build``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnrr.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA = 0, 1, 2, 3
+ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = 4, 5, 6, 7
+FP64, FP32, FP32_DC = 0, 1, 2
+INIT_ZERO, INIT_CURRENT, INIT_HOST, INIT_DEVICE = 0, 1, 2, 3
+MODES = {"fp64": FP64, "fp32": FP32, "fp32_dc": FP32_DC}
+
+# Every entry point declared in include/nrr.h.
+EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
+           "nrr_grid_dims", "nrr_set_punctures", "nrr_relax", "nrr_residual",
+           "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
+           "nrr_timestep", "nrr_image_map", "nrr_last_error", "nrr_version")
+
+
+class NrrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("nrr status %d: %s" % (status, msg))
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("coord", C.c_int), ("n", C.c_int * 3), ("fd_order", C.c_int),
+                ("amax", C.c_double), ("bscale", C.c_double),
+                ("sinhwaa", C.c_double), ("rmax", C.c_double),
+                ("xmax", C.c_double)]
+
+
+class Puncture(C.Structure):
+    _fields_ = [("m", C.c_double), ("x", C.c_double * 3),
+                ("P", C.c_double * 3), ("S", C.c_double * 3)]
+
+
+class RelaxOpts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("tol", C.c_double),
+                ("max_iters", C.c_int64), ("check_every", C.c_int),
+                ("cfl", C.c_double), ("eta", C.c_double),
+                ("r_int", C.c_double), ("initial", C.c_int),
+                ("u0", C.POINTER(C.c_double)), ("timeout_ms", C.c_int64),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int)]
+
+
+class RelaxResult(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("outer_iters", C.c_int64),
+                ("final_norm", C.c_double), ("seconds", C.c_double),
+                ("status", C.c_int)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libnrr.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libnrr.so is missing (%s): build it with __graft_entry__.build()"
+            % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    V, D, I = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "nrr_default_opts": [C.POINTER(RelaxOpts)],
+        "nrr_create_grid": [C.POINTER(GridDesc), V, C.POINTER(V)],
+        "nrr_destroy_grid": [V],
+        "nrr_grid_dims": [V, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                          C.POINTER(C.c_int64)],
+        "nrr_set_punctures": [V, I, C.POINTER(Puncture)],
+        "nrr_relax": [V, C.POINTER(RelaxOpts), C.POINTER(RelaxResult)],
+        "nrr_residual": [V, C.c_double, D, V, I],
+        "nrr_get_state": [V, V, V, I],
+        "nrr_set_state": [V, V, V, I],
+        "nrr_rhs": [V, I, C.c_double, V, V, V, V],
+        "nrr_step": [V, I, C.c_double, C.c_double, C.c_int64],
+        "nrr_timestep": [V, C.c_double, D, D],
+        "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.nrr_last_error.restype = C.c_char_p
+    L.nrr_last_error.argtypes = []
+    L.nrr_version.restype = C.c_char_p
+    L.nrr_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        raise NrrError(status, lib().nrr_last_error().decode())
+
+
+def make_desc(desc: dict) -> GridDesc:
+    return GridDesc(workloads.COORDS[desc["coord"]],
+                    (C.c_int * 3)(*desc["n"]), int(desc["order"]),
+                    float(desc["amax"]), float(desc["bscale"]),
+                    float(desc["sinhwaa"]), float(desc["rmax"]),
+                    float(desc["xmax"]))
+
+
+def make_punctures(punctures) -> C.Array:
+    arr = (Puncture * len(punctures))()
+    for i, p in enumerate(punctures):
+        arr[i].m = p["m"]
+        for k in range(3):
+            arr[i].x[k] = p["x"][k]
+            arr[i].P[k] = p["P"][k]
+            arr[i].S[k] = p["S"][k]
+    return arr
+
+
+def image_map(desc: dict) -> np.ndarray:
+    """Inner-boundary image index of every padded point (host computation)."""
+    shape = workloads.padded_shape(desc)
+    out = np.zeros(shape, dtype=np.int32)
+    d = make_desc(desc)
+    _check(lib().nrr_image_map(C.byref(d),
+                               out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out
+
+
+def _ptr(x):
+    """(pointer, on_device) of a torch tensor or numpy array of float64."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data), 0
+    assert x.dtype.is_floating_point and x.is_contiguous()
+    return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+
+
+class Grid:
+    """One grid on the current CUDA device, driven through the C ABI."""
+
+    def __init__(self, desc: dict, stream=None):
+        import torch
+        self.desc = dict(desc)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        handle = C.c_void_p()
+        d = make_desc(desc)
+        _check(lib().nrr_create_grid(C.byref(d), C.c_void_p(stream.cuda_stream),
+                                     C.byref(handle)))
+        self._h = handle
+        s = (C.c_int * 3)()
+        ng = C.c_int()
+        ni = C.c_int64()
+        _check(lib().nrr_grid_dims(handle, s, C.byref(ng), C.byref(ni)))
+        self.s = (s[0], s[1], s[2])
+        self.ng = ng.value
+        self.interior_points = ni.value
+        self.shape = (s[2], s[1], s[0])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrr_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_punctures(self, punctures):
+        arr = make_punctures(punctures)
+        _check(lib().nrr_set_punctures(self._h, len(punctures), arr))
+
+    def timestep(self, cfl: float = 0.5):
+        dt, eta = C.c_double(), C.c_double()
+        _check(lib().nrr_timestep(self._h, cfl, C.byref(dt), C.byref(eta)))
+        return dt.value, eta.value
+
+    def relax(self, mode="fp64", tol=1e-10, max_iters=1_000_000,
+              check_every=50, cfl=0.5, eta=0.0, r_int=100.0, initial=None,
+              u0=None, timeout_ms=0, inner_tol=1e-4, max_outer=20,
+              raise_on_error=True) -> dict:
+        o = RelaxOpts()
+        _check(lib().nrr_default_opts(C.byref(o)))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.tol, o.max_iters, o.check_every = tol, max_iters, check_every
+        o.cfl, o.eta, o.r_int = cfl, eta, r_int
+        o.timeout_ms, o.inner_tol, o.max_outer = timeout_ms, inner_tol, max_outer
+        if u0 is not None:
+            p, on_dev = _ptr(u0)
+            o.initial = INIT_DEVICE if on_dev else INIT_HOST
+            o.u0 = C.cast(p, C.POINTER(C.c_double))
+        else:
+            o.initial = INIT_ZERO if initial is None else int(initial)
+        r = RelaxResult()
+        st = lib().nrr_relax(self._h, C.byref(o), C.byref(r))
+        if raise_on_error:
+            _check(st)
+        return {"iters": r.iters, "outer_iters": r.outer_iters,
+                "norm": r.final_norm, "seconds": r.seconds, "status": st}
+
+    def residual(self, r_int: float = 100.0, h_out=None) -> float:
+        nrm = C.c_double()
+        if h_out is None:
+            _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), None, 0))
+        else:
+            p, on_dev = _ptr(h_out)
+            _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), p, on_dev))
+        return nrm.value
+
+    def get_state(self, u_out, v_out=None):
+        pu, on_dev = _ptr(u_out)
+        pv = _ptr(v_out)[0] if v_out is not None else None
+        _check(lib().nrr_get_state(self._h, pu, pv, on_dev))
+
+    def set_state(self, u, v=None):
+        pu, on_dev = _ptr(u)
+        pv = _ptr(v)[0] if v is not None else None
+        _check(lib().nrr_set_state(self._h, pu, pv, on_dev))
+
+    def rhs(self, u, v, ku, kv, eta: float, mode="fp64"):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().nrr_rhs(self._h, m, eta, _ptr(u)[0], _ptr(v)[0],
+                             _ptr(ku)[0], _ptr(kv)[0]))
+
+    def step(self, steps: int, dt: float, eta: float, mode="fp64"):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().nrr_step(self._h, m, dt, eta, int(steps)))

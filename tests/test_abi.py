@@ -1,0 +1,87 @@
+"""The C ABI without a GPU: the library loads, exports every entry point that
+include/*.h declares, validates arguments on the host, and its host-side
+inner-boundary map agrees with the oracle's Cartesian matching."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2501_14030_gb300 import nrr, workloads as W
+from tests.helpers import oracle_grid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_14030_gb300 import build
+    build.build()
+    return nrr.lib()
+
+
+def declared_functions() -> set[str]:
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"\b(nrr_\w+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = declared_functions()
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(nrr.EXPORTS) <= declared
+
+
+def test_version_and_defaults(lib):
+    assert b"sm_103a" in lib.nrr_version()
+    o = nrr.RelaxOpts()
+    assert lib.nrr_default_opts(C.byref(o)) == nrr.OK
+    assert (o.mode, o.tol, o.check_every, o.cfl, o.r_int) == (
+        nrr.FP64, 1e-10, 50, 0.5, 100.0)
+    assert lib.nrr_default_opts(None) == nrr.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bad", [
+    dict(coord="sinhsymtp", n=(32, 16, 3), order=4),   # odd n2
+    dict(coord="sinhsymtp", n=(32, 16, 2), order=6),   # unsupported order
+    dict(coord="sinhsymtp", n=(32, 3, 2), order=8),    # n1 < ng
+    dict(coord="spherical", n=(0, 16, 2), order=4),    # empty
+    dict(coord="cartesian", n=(1, 16, 16), order=4),   # too small
+])
+def test_create_grid_rejects_bad_descriptors_on_host(lib, bad):
+    desc = W.grid_desc(bad["coord"], bad["n"], bad["order"])
+    d = nrr.make_desc(desc)
+    h = C.c_void_p()
+    st = lib.nrr_create_grid(C.byref(d), None, C.byref(h))
+    assert st == nrr.ERR_INVALID_ARG
+    assert not h.value
+    assert lib.nrr_last_error()
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.nrr_relax(None, None, None) == nrr.ERR_INVALID_ARG
+    assert lib.nrr_residual(None, 100.0, None, None, 0) == nrr.ERR_INVALID_ARG
+    assert lib.nrr_destroy_grid(None) == nrr.OK
+
+
+@pytest.mark.parametrize("desc", [
+    W.grid_desc("sinhsymtp", (32, 16, 2), 4),
+    W.grid_desc("sinhsymtp", (44, 26, 6), 8),
+    W.grid_desc("sinhsymtp", (20, 5, 4), 10),
+    W.grid_desc("spherical", (40, 22, 8), 8, rmax=64.0),
+    W.grid_desc("spherical", (12, 6, 2), 10, rmax=9.0),
+    W.grid_desc("cartesian", (10, 12, 14), 4),
+])
+def test_host_image_map_matches_oracle_cartesian_matching(lib, oracle_mod,
+                                                          desc):
+    og = oracle_grid(desc)
+    assert np.array_equal(nrr.image_map(desc), og.field("image"))

@@ -1,0 +1,165 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+FP64 tolerances: 1e-12 relative per RHS evaluation and per trajectory
+(max-norm relative to the oracle field's maximum, per region), 1e-10
+relative on converged u.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2501_14030_gb300 import nrr, workloads as W
+from tests.helpers import default_dt_eta, oracle_grid, rel_err, region_masks
+
+pytestmark = pytest.mark.gpu
+
+Q4 = W.spinning_q4_pair()
+CASES = {
+    # small equal-mass case, 4th order
+    "sinh_32x16x2_o4": W.small_equal_mass(),
+    # several tiles with ragged edges, 8th and 10th order
+    "sinh_44x26x6_o8": (W.grid_desc("sinhsymtp", (44, 26, 6), 8), Q4),
+    "sinh_36x20x10_o10": (W.grid_desc("sinhsymtp", (36, 20, 10), 10), Q4),
+    "sph_40x22x8_o8": (W.grid_desc("spherical", (40, 22, 8), 8, rmax=64.0), Q4),
+    "cart_26x20x22_o4": (W.grid_desc("cartesian", (26, 20, 22), 4, xmax=32.0), Q4),
+    "cart_20x18x24_o8": (W.grid_desc("cartesian", (20, 18, 24), 8, xmax=32.0), Q4),
+    # full-size q=4 grid
+    "sinh_128x128x16_o8": W.q4_sinhsymtp_128(),
+}
+
+
+def _dev(a: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _setup(name):
+    desc, punc = CASES[name]
+    og = oracle_grid(desc)
+    alpha, beta = og.source(punc)
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    return desc, punc, og, alpha, beta, g
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_timestep_matches_oracle(gpu, name):
+    desc, punc, og, alpha, beta, g = _setup(name)
+    dt, eta = g.timestep(0.5)
+    dto, etao = default_dt_eta(og)
+    assert abs(dt - dto) <= 1e-13 * dto
+    assert abs(eta - etao) <= 1e-13 * etao
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_parity_fp64(gpu, name):
+    desc, punc, og, alpha, beta, g = _setup(name)
+    u = W.smooth_random_field(desc, seed=11, amplitude=0.2, noise=0.01)
+    v = W.smooth_random_field(desc, seed=12, amplitude=0.1, noise=0.01)
+    dt, eta = default_dt_eta(og)
+    ku_o, kv_o = og.rhs(alpha, beta, eta, og.fill_inner_ghosts(u),
+                        og.fill_inner_ghosts(v))
+    # The device gets the raw fields: inner ghosts hold unrelated values, so
+    # any read of ghost memory instead of the image shows up as a mismatch.
+    ku, kv = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+    g.rhs(_dev(u), _dev(v), ku, kv, eta, mode="fp64")
+    ku, kv = ku.cpu().numpy(), kv.cpu().numpy()
+    for region, m in region_masks(og).items():
+        assert rel_err(ku, ku_o, m) <= 1e-12, (region, rel_err(ku, ku_o, m))
+        assert rel_err(kv, kv_o, m) <= 1e-12, (region, rel_err(kv, kv_o, m))
+
+
+@pytest.mark.parametrize("name", ["sinh_32x16x2_o4", "sinh_44x26x6_o8",
+                                  "cart_26x20x22_o4", "sinh_128x128x16_o8"])
+def test_source_parity(gpu, name):
+    """At u = v = 0 the RHS is c^2 beta: the Bowen-York source on device."""
+    desc, punc, og, alpha, beta, g = _setup(name)
+    z = np.zeros(og.shape)
+    ku_o, kv_o = og.rhs(alpha, beta, 1.0, z, z)
+    ku, kv = torch.empty_like(_dev(z)), torch.empty_like(_dev(z))
+    g.rhs(_dev(z), _dev(z), ku, kv, 1.0, mode="fp64")
+    m = region_masks(og)["interior"]
+    assert rel_err(kv.cpu().numpy(), kv_o, m) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_norm_parity(gpu, name):
+    desc, punc, og, alpha, beta, g = _setup(name)
+    u = W.smooth_random_field(desc, seed=21, amplitude=0.2, noise=0.01)
+    H_o = og.residual(alpha, beta, og.fill_inner_ghosts(u))
+    for r_int in (100.0, 1.0e9):
+        n_o = og.norm(H_o, r_int)
+        g.set_state(_dev(u))
+        H = torch.empty_like(_dev(u))
+        n = g.residual(r_int, H)
+        assert abs(n - n_o) <= 1e-12 * n_o, (r_int, n, n_o)
+        m = region_masks(og)["interior"]
+        assert rel_err(H.cpu().numpy(), H_o, m) <= 1e-12
+
+
+@pytest.mark.parametrize("name,steps", [("sinh_32x16x2_o4", 200),
+                                        ("sinh_44x26x6_o8", 60),
+                                        ("sinh_36x20x10_o10", 40),
+                                        ("sph_40x22x8_o8", 60),
+                                        ("cart_26x20x22_o4", 60),
+                                        ("sinh_128x128x16_o8", 8)])
+def test_trajectory_parity_fp64(gpu, name, steps):
+    """Fixed-step trajectories from the same state agree to 1e-12."""
+    desc, punc, og, alpha, beta, g = _setup(name)
+    dt, eta = default_dt_eta(og)
+    u = og.fill_inner_ghosts(W.smooth_random_field(desc, seed=31, amplitude=0.1))
+    v = og.zeros()
+    g.set_state(_dev(u), _dev(v))
+    g.step(steps, dt, eta, mode="fp64")
+    for _ in range(steps):
+        og.rk4_step(alpha, beta, eta, dt, u, v)
+    ug, vg = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+    g.get_state(ug, vg)
+    assert rel_err(ug.cpu().numpy(), u) <= 1e-12
+    assert rel_err(vg.cpu().numpy(), v) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["sinh_32x16x2_o4", "sph_40x22x8_o8",
+                                  "cart_26x20x22_o4"])
+def test_relax_converged_parity(gpu, name):
+    """Full solves to 1e-10: same step count, u within 1e-10."""
+    desc, punc, og, alpha, beta, g = _setup(name)
+    dt, eta = default_dt_eta(og)
+    res = g.relax(mode="fp64", tol=1e-10, check_every=50)
+    uo, vo = og.zeros(), og.zeros()
+    it, n_o, st = og.relax(alpha, beta, uo, vo, eta=eta, dt=dt, tol=1e-10,
+                           check_every=50)
+    assert st == 0 and res["status"] == 0
+    assert it == res["iters"], (it, res)
+    u = np.zeros(og.shape)
+    g.get_state(u)
+    assert rel_err(u, uo) <= 1e-10
+    assert og.norm(og.residual(alpha, beta, u)) < 1e-10
+
+
+def test_relax_full_size_residual_checked_by_oracle(gpu):
+    """128x128x16 FP64 solve to 1e-10; the oracle re-evaluates the residual
+    of the returned u (a size-independent check)."""
+    desc, punc, og, alpha, beta, g = _setup("sinh_128x128x16_o8")
+    res = g.relax(mode="fp64", tol=1e-10, check_every=50)
+    u = np.zeros(og.shape)
+    g.get_state(u)
+    n_o = og.norm(og.residual(alpha, beta, u))
+    assert res["norm"] < 1e-10
+    assert n_o < 1.02e-10, n_o
+    assert abs(n_o - res["norm"]) <= 1e-3 * n_o + 1e-14
+
+
+def test_brill_lindquist_is_exactly_zero(gpu):
+    """Zero momentum and spin: beta = 0, so u = v = 0 for all time."""
+    desc = W.grid_desc("sinhsymtp", (32, 16, 4), 4)
+    g = nrr.Grid(desc)
+    g.set_punctures(W.brill_lindquist_pair())
+    res = g.relax(mode="fp64", tol=1e-10)
+    assert res["iters"] == 0 and res["norm"] == 0.0
+    dt, eta = g.timestep(0.5)
+    g.step(50, dt, eta)
+    u = np.ones(g.shape)
+    g.get_state(u)
+    assert not u.any()
