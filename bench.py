@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the puncture-data relaxation solve on GB300.
+
+One step = one complete FP64 solve of the mass-ratio-4 spinning Bowen-York
+pair on SinhSymTP 128x128x16 (8th-order FD, RK4): the source set-up, the
+relaxation to residual L2 norm < 1e-10 and the final residual, all on the
+device through the C ABI.  `value` is gridpoint-RHS/s = interior points x 4
+RHS evaluations per RK4 step x steps / device seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (launched by torchrun) every rank solves its own copy (the solves
+are independent; no collective on the data path) and rank 0 prints the
+whole-job rate over the slowest rank's time.  `--impl reference` times the
+CPU oracle on the host cores instead, on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gridpoint-RHS/s, FP64 relaxation of a BBH puncture solve to residual 1e-10"
+UNIT = "gridpoint-RHS/s"
+WORKLOAD = ("q=4 spinning Bowen-York pair (m 0.8/0.2, z=+-5, P=+-0.09x, "
+            "chi=(0.3,-0.2,0.5)/(0,0.4,-0.1)); SinhSymTP 128x128x16, AMAX 1e4, "
+            "bScale 5, SINHWAA 0.07; 8th-order FD; RK4 CFL 0.5; "
+            "FP64 relaxation to residual L2 < 1e-10 (r < 100, checked every 50 steps)")
+CHECK_EVERY = 50
+# FP64 peak of the GB300 from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop
+SMS, FP64_FMA_PER_CLK = 152, 2
+
+
+def flops_per_point(ng: int) -> int:
+    """Algorithmic FP64 flops per interior point per fused stage launch, as
+    the folded operator is evaluated: centre weight (1 mul), 2*ng FMAs in
+    each of xx0 and xx1 (8 ng), ng adds + ng FMAs in phi (3 ng), the source
+    term (fma, divide, 4 mul, fma: 9), k_u (fma: 2) and the RK4 update
+    (7 on average over the four stages)."""
+    return 11 * ng + 1 + 9 + 2 + 7
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.index = vis.split(",")[local_rank] if vis else str(local_rank)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_rate(desc, punc, seconds: float):
+    """Gridpoint-RHS/s of the CPU oracle on a bounded sample: RK4 steps of the
+    same grid from zero data, sized to about `seconds` of host time."""
+    import numpy as np  # noqa: F401
+    import oracle as O
+    from tests.helpers import default_dt_eta, oracle_grid
+    og = oracle_grid(desc)
+    alpha, beta = og.source(punc)
+    dt, eta = default_dt_eta(og)
+    u, v = og.zeros(), og.zeros()
+    t = time.perf_counter()
+    og.rk4_step(alpha, beta, eta, dt, u, v)
+    one = time.perf_counter() - t
+    steps = max(2, int(seconds / max(one, 1e-6)))
+    t = time.perf_counter()
+    for _ in range(steps):
+        og.rk4_step(alpha, beta, eta, dt, u, v)
+    H = og.residual(alpha, beta, u)
+    og.norm(H)
+    el = time.perf_counter() - t
+    n_int = desc["n"][0] * desc["n"][1] * desc["n"][2]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_int * 4 * steps / el, el, steps, cores
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_2501_14030_gb300 import workloads as W
+    desc, punc = W.q4_sinhsymtp_128()
+    for _ in range(args.warmup):
+        oracle_rate(desc, punc, 2.0)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, el, steps, cores = oracle_rate(desc, punc, 4.0)
+        rates.append(r)
+        times.append(el)
+    value = sum(rates) / len(rates)
+    sample = ("%d RK4 steps + one residual of the 128x128x16 FP64 workload "
+              "per timed step" % steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+
+    desc, punc = W.q4_sinhsymtp_128()
+    g = nrr.Grid(desc)
+    n_int = g.interior_points
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def solve():
+        g.set_punctures(punc)
+        r = g.relax(mode="fp64", tol=1e-10, check_every=CHECK_EVERY)
+        nrm = g.residual(100.0)
+        return r, nrm
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = nrr.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, iters, results = 0.0, 0, []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 (129 MB) between steps; not timed
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, nrm = solve()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters += r["iters"]
+        results.append((r, nrm))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    launches = nrr.kernel_launches() - launches0
+    clk = clocks.stop()
+
+    # whole job: every rank solved the same number of RHS evaluations
+    my = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(my, op=dist.ReduceOp.MAX)
+    t_max_s = my.item() / 1e3
+    rhs_evals = n_int * 4 * iters
+    value = world * rhs_evals / t_max_s
+
+    # ---- dominant kernel: the fused RK4 stage, timed on its own stream
+    dt, eta = g.timestep(0.5)
+    g.set_punctures(punc)
+    g.relax(mode="fp64", tol=1e-10, check_every=CHECK_EVERY)
+    ms_launch = g.profile_stages(200, dt, eta, mode="fp64")
+    ng = g.ng
+    flops = flops_per_point(ng) * n_int
+    achieved = flops / (ms_launch * 1e-3) / 1e12
+    peak = SMS * FP64_FMA_PER_CLK * 2 * 2070e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "stage_curvi_kernel<double,4,*> (fused RHS + BC + RK4 stage)",
+                "ms_per_launch": ms_launch,
+                "flops_per_launch": flops,
+                "peak_basis": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz "
+                              "(unit counts and max clock)"}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (
+            SMS * FP64_FMA_PER_CLK * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    # ---- end to end through the public API with host buffers
+    pinned_u = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_ms = 0.0
+    e2e_iters = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.set_punctures(punc)  # host puncture array -> device
+        r = g.relax(mode="fp64", tol=1e-10, check_every=CHECK_EVERY)
+        g.get_state(pinned_u)  # converged u -> pinned host memory
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_iters += r["iters"]
+    e2e_value = world * n_int * 4 * e2e_iters / (e2e_ms / 1e3)
+    h2d = 2 * (10 * 8)  # two nrr_puncture structs
+    d2h = int(np.prod(g.shape)) * 8
+
+    # ---- plain FP32 relaxation (context: its stall level), untimed
+    r32 = g.relax(mode="fp32", tol=1e-10, check_every=CHECK_EVERY,
+                  max_iters=iters // max(1, args.steps), raise_on_error=False)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            rate, el, steps, cores = oracle_rate(desc, punc, args.cpu_seconds)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d RK4 steps (+ one residual) of the same FP64 "
+                             "workload from zero data, %.1f s" % (steps, el)}
+        r0, n0 = results[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "SinhSymTP 128x128x16",
+                       "fd_order": 8, "global_batch": world,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed before each step (256 MiB write, untimed)"},
+            "sec_to_residual": {"fp64": t_max_s / args.steps,
+                                "rk4_steps": r0["iters"],
+                                "final_norm": r0["norm"],
+                                "residual_after": n0},
+            "fp32_plain": {"rk4_steps": r32["iters"], "final_norm": r32["norm"],
+                           "seconds": r32["seconds"], "status": r32["status"]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_steps(args):
+    """A short fixed workload for profiler captures: set-up, then
+    `--profile-steps` RK4 steps (4 fused stage launches each) and one
+    residual, in the precision given by --mode.  Prints nothing timed."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    desc, punc = W.q4_sinhsymtp_128()
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    dt, eta = g.timestep(0.5)
+    g.step(args.profile_steps, dt, eta, mode=args.mode)
+    print(json.dumps({"profile_steps": args.profile_steps, "mode": args.mode,
+                      "residual": g.residual(100.0)}))
+    g.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run only this many RK4 steps (profiler captures)")
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
+    args = ap.parse_args()
+    if args.profile_steps > 0:
+        return run_profile_steps(args)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

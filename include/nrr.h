@@ -27,9 +27,10 @@
  *  - Pointers flagged "on_device" are CUDA device pointers on the current
  *    device; otherwise they are host pointers.  The caller owns every pointer
  *    it passes; the library copies what it keeps.
- *  - All device work is issued on the stream given to nrr_create_grid (NULL =
- *    the legacy default stream).  Calls return after their results are
- *    complete unless stated otherwise.
+ *  - Each grid owns a non-blocking work stream.  Every call first orders
+ *    that stream after the work already queued on the caller's stream (the
+ *    one given to nrr_create_grid; NULL = the legacy default stream), and
+ *    returns after its device work is complete.
  */
 #ifndef NRR_H
 #define NRR_H
@@ -208,6 +209,17 @@ nrr_status nrr_timestep(const nrr_grid *g, double cfl, double *dt,
  * evolved point whose value ghost p copies, or p itself for evolved points.
  * out: host array of s0*s1*s2 int32.  Pure host computation, no device. */
 nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
+
+/* Measurement hook: takes `steps` RK4 steps exactly as nrr_step does, with
+ * CUDA events recorded on the grid's work stream around them, and returns
+ * the average device time of one fused stage launch in *ms_per_launch
+ * (4 launches per step).  The state advances. */
+nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
+                              int64_t steps, double *ms_per_launch);
+
+/* Cumulative number of kernels this library has launched in this process
+ * (graph replays count every kernel node). */
+int64_t nrr_kernel_launches(void);
 
 const char *nrr_last_error(void);
 const char *nrr_version(void);

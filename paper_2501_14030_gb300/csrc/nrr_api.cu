@@ -7,6 +7,7 @@
 // only host<->device traffic per chunk is the 8-byte norm.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -26,6 +27,7 @@ using namespace nrr;
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
 
 nrr_status fail(nrr_status s, const char *fmt, ...) {
   char buf[512];
@@ -99,6 +101,7 @@ struct nrr_grid {
   bool have_source = false;
   int state_prec = 64;  // which FieldSet holds the current state
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, int64_t> graph_kernels;
 };
 
 namespace {
@@ -242,6 +245,7 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
                       const ColumnSet<R> &c, double dt, double eta,
                       int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
+  g_launches += 4 * steps;
   for (int64_t s = 0; s < steps; s++)
     for (int k = 0; k < 4; k++)
       launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta),
@@ -253,6 +257,7 @@ template <typename R>
 void launch_norm(const nrr_grid *g, const FieldSet<R> &f, const ColumnSet<R> &c,
                  double r_int, double *h_out) {
   int nb = 0;
+  g_launches += 2;
   launch_residual<R>(g->geo, f.y[0], f.alpha, f.bc2, c, g->cart, g->jac,
                      g->rad, r_int, h_out, g->partials, &nb, g->cfg, g->stream);
   launch_norm_finalize(g->partials, nb, g->scalars + 1, g->stream);
@@ -290,6 +295,7 @@ nrr_status get_graph(nrr_grid *g, int mode, int steps, double dt, double eta,
     return NRR_OK;
   }
   cudaGraph_t graph;
+  int64_t before = g_launches.load();
   CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
   if (mode == NRR_FP32) {
     launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, steps);
@@ -307,6 +313,9 @@ nrr_status get_graph(nrr_grid *g, int mode, int steps, double dt, double eta,
   if (e != cudaSuccess)
     return fail(NRR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   g->graphs[key] = exec;
+  // captured launches are not executed: count them once per replay instead
+  g->graph_kernels[key] = g_launches.load() - before;
+  g_launches -= g->graph_kernels[key];
   *out = exec;
   return NRR_OK;
 }
@@ -333,6 +342,7 @@ nrr_status set_device(const nrr_grid *g) {
 extern "C" {
 
 const char *nrr_last_error(void) { return g_last_error.c_str(); }
+int64_t nrr_kernel_launches(void) { return g_launches.load(); }
 const char *nrr_version(void) { return "nrr 0.1 (sm_103a)"; }
 
 nrr_status nrr_default_opts(nrr_relax_opts *o) {
@@ -555,6 +565,7 @@ nrr_status nrr_set_punctures(nrr_grid *g, int n, const nrr_puncture *p) {
   }
   TRY(set_device(g));
   CUDA_TRY(cudaMemsetAsync(g->flag, 0, sizeof(int), g->stream));
+  g_launches += 1;
   launch_source(g->geo, ps, g->dsmin, g->scalars, g->f64.alpha, g->f64.bc2,
                 g->f32.alpha, g->f32.bc2, g->flag, g->stream);
   CUDA_TRY(cudaGetLastError());
@@ -663,6 +674,34 @@ nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
   return NRR_OK;
 }
 
+nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
+                              int64_t steps, double *ms_per_launch) {
+  TRY(check_grid(g));
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  if (steps < 1 || !(dt > 0.0) || !ms_per_launch)
+    return fail(NRR_ERR_INVALID_ARG, "need steps >= 1, dt > 0, output");
+  if (mode != NRR_FP64 && mode != NRR_FP32)
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  TRY(set_device(g));
+  TRY(ensure_state(g, mode == NRR_FP32 ? 32 : 64));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  CUDA_TRY(cudaEventRecord(e0, g->stream));
+  if (mode == NRR_FP32)
+    launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, steps);
+  else
+    launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, steps);
+  CUDA_TRY(cudaEventRecord(e1, g->stream));
+  CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = (double)ms / (4.0 * (double)steps);
+  return NRR_OK;
+}
+
 nrr_status nrr_residual(nrr_grid *g, double r_int, double *norm_out,
                         double *h_out, int h_on_device) {
   TRY(check_grid(g));
@@ -760,6 +799,7 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
       cudaGraphExec_t exec;
       TRY(get_graph(g, o->mode, (int)m, dt, eta, o->r_int, &exec));
       CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+      g_launches += g->graph_kernels[GraphKey{o->mode, (int)m, dt, eta, o->r_int}];
     } else if (prec == 32) {
       launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, m);
       launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);

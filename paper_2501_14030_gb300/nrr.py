@@ -28,7 +28,8 @@ MODES = {"fp64": FP64, "fp32": FP32, "fp32_dc": FP32_DC}
 EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_grid_dims", "nrr_set_punctures", "nrr_relax", "nrr_residual",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
-           "nrr_timestep", "nrr_image_map", "nrr_last_error", "nrr_version")
+           "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
+           "nrr_kernel_launches", "nrr_last_error", "nrr_version")
 
 
 class NrrError(RuntimeError):
@@ -93,6 +94,7 @@ def lib() -> C.CDLL:
         "nrr_step": [V, I, C.c_double, C.c_double, C.c_int64],
         "nrr_timestep": [V, C.c_double, D, D],
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
+        "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -100,6 +102,8 @@ def lib() -> C.CDLL:
         fn.restype = C.c_int
     L.nrr_last_error.restype = C.c_char_p
     L.nrr_last_error.argtypes = []
+    L.nrr_kernel_launches.restype = C.c_int64
+    L.nrr_kernel_launches.argtypes = []
     L.nrr_version.restype = C.c_char_p
     L.nrr_version.argtypes = []
     _lib = L
@@ -138,6 +142,11 @@ def image_map(desc: dict) -> np.ndarray:
     _check(lib().nrr_image_map(C.byref(d),
                                out.ctypes.data_as(C.POINTER(C.c_int32))))
     return out
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libnrr so far in this process."""
+    return int(lib().nrr_kernel_launches())
 
 
 def _ptr(x):
@@ -238,6 +247,16 @@ class Grid:
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         _check(lib().nrr_rhs(self._h, m, eta, _ptr(u)[0], _ptr(v)[0],
                              _ptr(ku)[0], _ptr(kv)[0]))
+
+    def profile_stages(self, steps: int, dt: float, eta: float,
+                       mode="fp64") -> float:
+        """Average ms of one fused stage launch over `steps` RK4 steps,
+        timed with CUDA events on the library's work stream."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        ms = C.c_double()
+        _check(lib().nrr_profile_stages(self._h, m, dt, eta, int(steps),
+                                        C.byref(ms)))
+        return ms.value
 
     def step(self, steps: int, dt: float, eta: float, mode="fp64"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
