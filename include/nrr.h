@@ -221,6 +221,35 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * (graph replays count every kernel node). */
 int64_t nrr_kernel_launches(void);
 
+/* Residual norm without any device allocation.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc,
+ * for instance an application whose memory manager already owns the whole
+ * device, or an embedding whose policy allows no allocation calls after
+ * start-up.  No grid object is needed: for the grid described by d and the
+ * punctures p (host array, 1..8), it evaluates H = lap(u) + (1/8) A~A~
+ * (psi_s + u)^-7 at interior points of the caller's u (device pointer,
+ * padded FP64 layout, inner ghosts ignored) and writes the L2 norm over
+ * r < r_int, sqrt(sum H^2 J / sum J), to norm_out[0] (device pointer), and H
+ * to h_out (device pointer, padded, nullable; only interior points are
+ * written).  Geometry and source are recomputed per point.
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default); the
+ * results are ready when that stream has reached this point.
+ * Scratch: the per-block partial sums live in one static device array of
+ * 32768 pairs of doubles (512 KiB), held by every GPU that loads the
+ * library until exit.  Grids with n0*n1 > 32768*128 are rejected with
+ * NRR_ERR_INVALID_ARG.  Every call reuses that array and each launch writes
+ * every slot it reads, so nothing needs clearing between calls; calls that
+ * overlap on the GPU (on different streams, or from several host threads)
+ * race on it and must be serialised by the caller.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before capturing any stream.
+ * Errors: NRR_ERR_INVALID_ARG (bad descriptor, punctures or size),
+ * NRR_ERR_CUDA (lookup or launch failure). */
+nrr_status nrr_residual_noalloc(const nrr_grid_desc *d, int npunct,
+                                const nrr_puncture *p, const double *u,
+                                double r_int, double *norm_out, double *h_out,
+                                void *stream);
+
 const char *nrr_last_error(void);
 const char *nrr_version(void);
 

@@ -60,6 +60,8 @@ double now_s() {
 
 }  // namespace
 
+void nrr::set_last_error(const char *msg) { g_last_error = msg; }
+
 struct GraphKey {
   int mode, steps;
   double dt, eta, r_int;

@@ -29,7 +29,8 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_grid_dims", "nrr_set_punctures", "nrr_relax", "nrr_residual",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
-           "nrr_kernel_launches", "nrr_last_error", "nrr_version")
+           "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_last_error",
+           "nrr_version")
 
 
 class NrrError(RuntimeError):
@@ -95,6 +96,8 @@ def lib() -> C.CDLL:
         "nrr_timestep": [V, C.c_double, D, D],
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
+        "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
+                                 V, C.c_double, V, V, V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -142,6 +145,22 @@ def image_map(desc: dict) -> np.ndarray:
     _check(lib().nrr_image_map(C.byref(d),
                                out.ctypes.data_as(C.POINTER(C.c_int32))))
     return out
+
+
+def residual_noalloc(desc: dict, punctures, u, norm_out, h_out=None,
+                     r_int: float = 100.0, stream=None) -> None:
+    """Residual norm of a device u without device allocation (queued on
+    `stream`, default the current torch stream); writes norm_out[0] and,
+    if given, H into h_out.  All tensors on the current device."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    d = make_desc(desc)
+    arr = make_punctures(punctures)
+    h = C.c_void_p(h_out.data_ptr()) if h_out is not None else None
+    _check(lib().nrr_residual_noalloc(
+        C.byref(d), len(punctures), arr, C.c_void_p(u.data_ptr()), r_int,
+        C.c_void_p(norm_out.data_ptr()), h, C.c_void_p(stream.cuda_stream)))
 
 
 def kernel_launches() -> int:
