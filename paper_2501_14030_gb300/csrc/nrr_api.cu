@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <tuple>
@@ -78,7 +79,8 @@ struct nrr_grid {
   cudaStream_t user_stream = nullptr;  // caller's stream (ordering only)
   cudaEvent_t order_ev = nullptr;
   int device = 0;
-  LaunchCfg cfg;
+  LaunchCfg res_cfg;       // residual kernels (fixed: sizes the partials)
+  LaunchCfg stage_cfg[2];  // stage kernels, [0] FP64, [1] FP32 (autotuned)
   std::vector<void *> allocs;
 
   FieldSet<double> f64;
@@ -107,6 +109,28 @@ struct nrr_grid {
 };
 
 namespace {
+
+// Autotuned launch shapes, remembered per (coordinates, n, order, precision)
+// for the life of the process.
+struct TuneKey {
+  int coord, n0, n1, n2, ng, prec;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(coord, n0, n1, n2, ng, prec) <
+           std::tie(o.coord, o.n0, o.n1, o.n2, o.ng, o.prec);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchCfg> g_tuned;
+
+TuneKey tune_key(const Geo &g, int prec) {
+  return TuneKey{g.coord, g.n0, g.n1, g.n2, g.ng, prec};
+}
+
+LaunchCfg tuned_or_default(const Geo &g, int prec) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(tune_key(g, prec));
+  return it != g_tuned.end() ? it->second : LaunchCfg{};
+}
 
 template <typename T>
 nrr_status dev_alloc(nrr_grid *g, T **p, size_t count) {
@@ -251,7 +275,7 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
   for (int64_t s = 0; s < steps; s++)
     for (int k = 0; k < 4; k++)
       launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta),
-                      g->cfg, g->stream);
+                      g->stage_cfg[sizeof(R) == 4], g->stream);
 }
 
 // Residual + norm of the current state in precision R into scalars[1..3].
@@ -261,7 +285,8 @@ void launch_norm(const nrr_grid *g, const FieldSet<R> &f, const ColumnSet<R> &c,
   int nb = 0;
   g_launches += 2;
   launch_residual<R>(g->geo, f.y[0], f.alpha, f.bc2, c, g->cart, g->jac,
-                     g->rad, r_int, h_out, g->partials, &nb, g->cfg, g->stream);
+                     g->rad, r_int, h_out, g->partials, &nb, g->res_cfg,
+                     g->stream);
   launch_norm_finalize(g->partials, nb, g->scalars + 1, g->stream);
 }
 
@@ -440,7 +465,8 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
     TRY(dev_alloc(g, &g->c32.somm, 3 * (size_t)nc));
     TRY(dev_alloc(g, &g->c32.c2inv, nc));
     TRY(dev_alloc(g, &g->scalars, 8));
-    int nb = residual_blocks(geo, g->cfg);
+    int nb = residual_blocks(geo, g->res_cfg);
+    for (int k = 0; k < 2; k++) g->stage_cfg[k] = tuned_or_default(geo, k);
     TRY(dev_alloc(g, &g->partials, 2 * (size_t)nb + 64));
     TRY(dev_alloc(g, &g->flag, 4));
     CUDA_TRY(cudaMallocHost(&g->host_pinned, 8 * sizeof(double)));
@@ -630,7 +656,7 @@ nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
     a.eta = eta;
     CUDA_TRY(cudaMemsetAsync(ku, 0, n * sizeof(double), g->stream));
     CUDA_TRY(cudaMemsetAsync(kv, 0, n * sizeof(double), g->stream));
-    launch_stage<double>(g->geo, STAGE_RAW, a, g->cfg, g->stream);
+    launch_stage<double>(g->geo, STAGE_RAW, a, g->stage_cfg[0], g->stream);
   } else {
     // Round the inputs to FP32 in the grid's stage buffers, evaluate in
     // FP32, widen the result.
@@ -644,7 +670,7 @@ nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
     a.su = us; a.sv = vs; a.ou = ko; a.ov = kw;
     a.alpha = g->f32.alpha; a.bc2 = g->f32.bc2; a.col = g->c32; a.cart = g->cart;
     a.eta = (float)eta;
-    launch_stage<float>(g->geo, STAGE_RAW, a, g->cfg, g->stream);
+    launch_stage<float>(g->geo, STAGE_RAW, a, g->stage_cfg[1], g->stream);
     launch_convert(ko, ku, n, g->stream);
     launch_convert(kw, kv, n, g->stream);
   }
@@ -701,6 +727,83 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms_per_launch = (double)ms / (4.0 * (double)steps);
+  return NRR_OK;
+}
+
+nrr_status nrr_set_launch(nrr_grid *g, int mode, int zc) {
+  TRY(check_grid(g));
+  if (mode != NRR_FP64 && mode != NRR_FP32)
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  if (zc != 1 && zc != 2 && zc != 4)
+    return fail(NRR_ERR_INVALID_ARG, "zc must be 1, 2 or 4");
+  g->stage_cfg[mode == NRR_FP32].zc = zc;
+  return NRR_OK;
+}
+
+nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
+                        int *best_zc, double *best_ms_per_launch) {
+  TRY(check_grid(g));
+  if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
+  if (mode != NRR_FP64 && mode != NRR_FP32)
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  if (trial_steps < 1) return fail(NRR_ERR_INVALID_ARG, "trial_steps >= 1");
+  TRY(set_device(g));
+  const int prec = mode == NRR_FP32 ? 32 : 64;
+  TRY(ensure_state(g, prec));
+  double dt = 0.0, eta = 0.0;
+  TRY(nrr_timestep(g, 0.5, &dt, &eta));
+  // Keep the state: trials run from it and it is restored afterwards.
+  size_t bytes = (size_t)g->geo.npts * (prec == 32 ? sizeof(float) : sizeof(double));
+  void *save_u = prec == 32 ? (void *)g->acoef32 : (void *)g->res64;
+  void *save_v = prec == 32 ? (void *)g->rhs32 : (void *)g->u_save;
+  void *yu = prec == 32 ? (void *)g->f32.y[0] : (void *)g->f64.y[0];
+  void *yv = prec == 32 ? (void *)g->f32.y[1] : (void *)g->f64.y[1];
+  CUDA_TRY(cudaMemcpyAsync(save_u, yu, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(save_v, yv, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  LaunchCfg &cfg = g->stage_cfg[prec == 32];
+  const LaunchCfg keep = cfg;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int best = keep.zc;
+  double best_ms = 1e30;
+  const int cands[3] = {1, 2, 4};
+  for (int zc : cands) {
+    cfg.zc = zc;
+    for (int rep = 0; rep < 2; rep++) {  // first repetition warms up
+      CUDA_TRY(cudaEventRecord(e0, g->stream));
+      if (prec == 32)
+        launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, trial_steps);
+      else
+        launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, trial_steps);
+      CUDA_TRY(cudaEventRecord(e1, g->stream));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      double per = ms / (4.0 * (double)trial_steps);
+      if (rep == 1 && per < best_ms) {
+        best_ms = per;
+        best = zc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cfg = keep;
+  cfg.zc = best;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[tune_key(g->geo, prec == 32)] = cfg;
+  }
+  CUDA_TRY(cudaMemcpyAsync(yu, save_u, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(yv, save_v, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  // cached relaxation graphs hold the old shape
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  g->graphs.clear();
+  g->graph_kernels.clear();
+  if (best_zc) *best_zc = best;
+  if (best_ms_per_launch) *best_ms_per_launch = best_ms;
   return NRR_OK;
 }
 

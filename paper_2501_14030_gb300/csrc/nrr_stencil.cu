@@ -25,23 +25,29 @@ __device__ __forceinline__ R ld(const R *p) {
   return __ldg(p);
 }
 
-template <int NG>
-__device__ __forceinline__ int wrap2(const Geo &g, int i2) {
-  // phi index into [NG, NG+n2); |offset| <= NG so one correction suffices
-  // when n2 >= NG, else fall back to a modulo.
-  if (g.n2 >= NG) {
-    if (i2 < NG) return i2 + g.n2;
-    if (i2 >= NG + g.n2) return i2 - g.n2;
-    return i2;
-  }
-  return wrap_phi(g, i2);
+// Reciprocal of s = 1 + alpha u (a normal number near 1) by Newton-Raphson
+// refinement of the hardware approximation: t <- t + t (1 - s t) converges
+// quadratically, so two steps from the approximate seed reach full double
+// precision and one step suffices in single precision.
+__device__ __forceinline__ double recip(double s) {
+  double t;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(t) : "d"(s));
+  double e = fma(-s, t, 1.0);
+  t = fma(t, e, t);
+  e = fma(-s, t, 1.0);
+  return fma(t, e, t);
+}
+__device__ __forceinline__ float recip(float s) {
+  float t;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(s));
+  float e = fmaf(-s, t, 1.0f);
+  return fmaf(t, e, t);
 }
 
 // beta c^2 (1 + alpha u)^-7 added to acc.
 template <typename R>
 __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2) {
-  R s = fma(al, u0, R(1));
-  R t = R(1) / s;
+  R t = recip(fma(al, u0, R(1)));
   R t2 = t * t;
   R t4 = t2 * t2;
   R q = bc2 * t;
@@ -49,64 +55,81 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2) {
   return fma(q, t4, acc);
 }
 
-// c^2 [lap(u) + source] at an interior point of a curvilinear grid.
-template <typename R, int NG>
-__device__ __forceinline__ R curvi_operator(const Geo &g, const R *__restrict__ su,
-                                            const R (&w)[5 * NG + 1], int col,
-                                            int i0, int i1, int i2, int64_t p,
-                                            R u0, R al, R bc2) {
+// c^2 [lap(u) + source] at ZC interior points of one column (i0, i1) of a
+// curvilinear grid, planes pl[0..ZC).  wp[] holds the wrapped phi planes
+// pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  Two
+// independent accumulation chains per point (xx0 + phi, xx1) and ZC points
+// interleaved give the FP64 pipe independent work.
+template <typename R, int NG, int ZC>
+__device__ __forceinline__ void curvi_operator(
+    const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
+    int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
+    const R (&u0)[ZC], const R (&al)[ZC], const R (&bc)[ZC], R (&out)[ZC]) {
   const int64_t nc = g.ncol;
   const int s0 = g.s0;
-  const int half = g.n2 / 2;
-  R lap = w[0] * u0;
+  R a0[ZC], a1[ZC];
+#pragma unroll
+  for (int j = 0; j < ZC; j++) a0[j] = w[0] * u0[j];
+  // xx0: the + side stays inside the padded box; the - side may cross
+  // xx0 = 0 and read the reflected point at phi + pi.
 #pragma unroll
   for (int k = 1; k <= NG; k++) {
-    // xx0: the + side stays inside the padded box; the - side may cross
-    // xx0 = 0 and read the reflected point at phi + pi.
-    R up = ld(su + p + k);
-    R um;
-    int im = i0 - k;
-    if (im >= NG) {
-      um = ld(su + p - k);
-    } else {
-      int j0 = 2 * NG - 1 - im;
-      int j1 = g.coord == SPHERICAL ? g.n1 + 2 * NG - 1 - i1 : i1;
-      int j2 = wrap2<NG>(g, i2 + half);
-      um = ld(su + j0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
+    const int im = i0 - k;
+    const bool refl = im < NG;
+    const int rcol = (2 * NG - 1 - im) +
+                     s0 * (g.coord == SPHERICAL ? g.n1 + 2 * NG - 1 - i1 : i1);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      const int64_t p = col + nc * wp[NG + j];
+      R up = ld(su + p + k);
+      R um = refl ? ld(su + rcol + nc * wh[j]) : ld(su + p - k);
+      a0[j] = fma(w[k], up, a0[j]);
+      a0[j] = fma(w[NG + k], um, a0[j]);
     }
-    lap = fma(w[k], up, lap);
-    lap = fma(w[NG + k], um, lap);
   }
+  // theta: reflections through the axis, again with phi + pi.
 #pragma unroll
   for (int k = 1; k <= NG; k++) {
-    // theta: reflections through the axis, again with phi + pi.
-    R up, um;
-    int ip = i1 + k, im = i1 - k;
-    if (ip < g.n1 + NG) {
-      up = ld(su + p + (int64_t)k * s0);
-    } else {
-      int j1 = 2 * g.n1 + 2 * NG - 1 - ip;
-      int j2 = wrap2<NG>(g, i2 + half);
-      up = ld(su + i0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
+    const int ip = i1 + k, im = i1 - k;
+    const bool rp = ip >= g.n1 + NG, rm = im < NG;
+    const int cp = i0 + s0 * (rp ? 2 * g.n1 + 2 * NG - 1 - ip : ip);
+    const int cm = i0 + s0 * (rm ? 2 * NG - 1 - im : im);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      R up = ld(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
+      R um = ld(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
+      a1[j] = k == 1 ? w[2 * NG + k] * up : fma(w[2 * NG + k], up, a1[j]);
+      a1[j] = fma(w[3 * NG + k], um, a1[j]);
     }
-    if (im >= NG) {
-      um = ld(su + p - (int64_t)k * s0);
-    } else {
-      int j1 = 2 * NG - 1 - im;
-      int j2 = wrap2<NG>(g, i2 + half);
-      um = ld(su + i0 + (int64_t)s0 * (j1 + (int64_t)g.s1 * j2));
-    }
-    lap = fma(w[2 * NG + k], up, lap);
-    lap = fma(w[3 * NG + k], um, lap);
   }
+  // phi: periodic.
 #pragma unroll
   for (int k = 1; k <= NG; k++) {
-    // phi: periodic.
-    R sp = ld(su + col + nc * wrap2<NG>(g, i2 + k));
-    R sm = ld(su + col + nc * wrap2<NG>(g, i2 - k));
-    lap = fma(w[4 * NG + k], sp + sm, lap);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      R sp = ld(su + col + nc * wp[NG + j + k]);
+      R sm = ld(su + col + nc * wp[NG + j - k]);
+      a0[j] = fma(w[4 * NG + k], sp + sm, a0[j]);
+    }
   }
-  return add_source(lap, u0, al, bc2);
+#pragma unroll
+  for (int j = 0; j < ZC; j++) out[j] = add_source(a0[j] + a1[j], u0[j], al[j], bc[j]);
+}
+
+// Plane tables of one thread: wp[] = wrapped phi planes z0-NG .. z0+ZC-1+NG
+// (planes past the last one are clamped so that loads stay in range), wh[] =
+// the plane at phi + pi of each of the ZC planes.
+template <int NG, int ZC>
+__device__ __forceinline__ void plane_tables(const Geo &g, int z0, int (&wp)[ZC + 2 * NG],
+                                             int (&wh)[ZC]) {
+  const int last = NG + g.n2 - 1;
+#pragma unroll
+  for (int j = 0; j < ZC + 2 * NG; j++) {
+    int z = min(z0 - NG + j, last + NG);
+    wp[j] = wrap_phi(g, z);
+  }
+#pragma unroll
+  for (int j = 0; j < ZC; j++) wh[j] = wrap_phi(g, min(z0 + j, last) + g.n2 / 2);
 }
 
 template <typename R, int KIND>
@@ -134,25 +157,27 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
 }
 
 // Curvilinear stage kernel.  Thread = one (i0, i1) column of evolved points
-// (interior plus the outer shell i0 >= n0+ng) and zc consecutive phi planes.
-template <typename R, int NG, int KIND>
+// (interior plus the outer shell i0 >= n0+ng) and ZC consecutive phi planes.
+template <typename R, int NG, int KIND, int ZC>
 __global__ void __launch_bounds__(128)
-    stage_curvi_kernel(Geo g, StageArgs<R> a, int zc) {
+    stage_curvi_kernel(Geo g, StageArgs<R> a) {
   const int ne0 = g.n0 + NG;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne0 * g.n1) return;
   const int i0 = e % ne0 + NG, i1 = e / ne0 + NG;
   const int col = i0 + g.s0 * i1;
   const int nc = g.ncol;
-  const int z0 = NG + blockIdx.y * zc;
-  const int z1 = min(z0 + zc, NG + g.n2);
+  const int z0 = NG + blockIdx.y * ZC;
+  const int zend = NG + g.n2;
   if (i0 >= g.n0 + NG) {
     // Radiation condition, df/dt = -c (d_r f + f/r), d_r from the
     // second-order backward difference along xx0.
     R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
       rinv = ld(a.col.somm + 2 * nc + col);
-    for (int i2 = z0; i2 < z1; i2++) {
-      int64_t p = col + (int64_t)nc * i2;
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      if (z0 + j >= zend) break;
+      int64_t p = col + (int64_t)nc * (z0 + j);
       R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
       R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
       R du = fma(R(3), u0, fma(R(-4), u1, u2));
@@ -166,13 +191,24 @@ __global__ void __launch_bounds__(128)
   R w[5 * NG + 1];
 #pragma unroll
   for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
-  for (int i2 = z0; i2 < z1; i2++) {
-    int64_t p = col + (int64_t)nc * i2;
-    R u0 = ld(a.su + p), v0 = ld(a.sv + p);
-    R kv = curvi_operator<R, NG>(g, a.su, w, col, i0, i1, i2, p, u0,
-                                 ld(a.alpha + p), ld(a.bc2 + p));
-    R ku = fma(-a.eta, u0, v0);
-    stage_epilogue<R, KIND>(a, p, ku, kv);
+  int wp[ZC + 2 * NG], wh[ZC];
+  plane_tables<NG, ZC>(g, z0, wp, wh);
+  R u0[ZC], v0[ZC], al[ZC], bc[ZC], kv[ZC];
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    int64_t p = col + (int64_t)nc * wp[NG + j];
+    u0[j] = ld(a.su + p);
+    v0[j] = ld(a.sv + p);
+    al[j] = ld(a.alpha + p);
+    bc[j] = ld(a.bc2 + p);
+  }
+  curvi_operator<R, NG, ZC>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv);
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    if (z0 + j >= zend) break;
+    int64_t p = col + (int64_t)nc * (z0 + j);
+    R ku = fma(-a.eta, u0[j], v0[j]);
+    stage_epilogue<R, KIND>(a, p, ku, kv[j]);
   }
 }
 
@@ -299,11 +335,12 @@ __global__ void __launch_bounds__(128)
     const int z0 = NG + blockIdx.y * zc;
     const int z1 = min(z0 + zc, NG + g.n2);
     for (int i2 = z0; i2 < z1; i2++) {
+      int wp[1 + 2 * NG], wh[1];
+      plane_tables<NG, 1>(g, i2, wp, wh);
       int64_t p = col + (int64_t)nc * i2;
-      R u0 = ld(su + p);
-      R op = curvi_operator<R, NG>(g, su, w, col, i0, i1, i2, p, u0,
-                                   ld(alpha + p), ld(bc2 + p));
-      double H = (double)(op * c2inv);
+      R u0[1] = {ld(su + p)}, al[1] = {ld(alpha + p)}, bc[1] = {ld(bc2 + p)}, op[1];
+      curvi_operator<R, NG, 1>(g, su, w, col, i0, i1, wp, wh, u0, al, bc, op);
+      double H = (double)(op[0] * c2inv);
       if (h_out) h_out[p] = H;
       num += H * H * wt;
       den += wt;
@@ -386,6 +423,18 @@ __global__ void scale_kernel(double *f, double s, int64_t n) {
   if (i < n) f[i] *= s;
 }
 
+template <typename R, int NG, int ZC>
+void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
+                  const LaunchCfg &cfg, int ncols, cudaStream_t st) {
+  dim3 grid((ncols + 127) / 128, (g.n2 + ZC - 1) / ZC);
+  switch (kind) {
+    case STAGE_FIRST: stage_curvi_kernel<R, NG, STAGE_FIRST, ZC><<<grid, 128, 0, st>>>(g, a); break;
+    case STAGE_MID: stage_curvi_kernel<R, NG, STAGE_MID, ZC><<<grid, 128, 0, st>>>(g, a); break;
+    case STAGE_LAST: stage_curvi_kernel<R, NG, STAGE_LAST, ZC><<<grid, 128, 0, st>>>(g, a); break;
+    default: stage_curvi_kernel<R, NG, STAGE_RAW, ZC><<<grid, 128, 0, st>>>(g, a); break;
+  }
+}
+
 template <typename R, int NG>
 void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
                      const LaunchCfg &cfg, cudaStream_t st) {
@@ -400,12 +449,10 @@ void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
     return;
   }
   int ncols = (g.n0 + NG) * g.n1;
-  dim3 grid((ncols + cfg.block - 1) / cfg.block, (g.n2 + cfg.zc - 1) / cfg.zc);
-  switch (kind) {
-    case STAGE_FIRST: stage_curvi_kernel<R, NG, STAGE_FIRST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-    case STAGE_MID: stage_curvi_kernel<R, NG, STAGE_MID><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-    case STAGE_LAST: stage_curvi_kernel<R, NG, STAGE_LAST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-    default: stage_curvi_kernel<R, NG, STAGE_RAW><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+  switch (cfg.zc) {
+    case 1: launch_curvi<R, NG, 1>(g, kind, a, cfg, ncols, st); break;
+    case 4: launch_curvi<R, NG, 4>(g, kind, a, cfg, ncols, st); break;
+    default: launch_curvi<R, NG, 2>(g, kind, a, cfg, ncols, st); break;
   }
 }
 

@@ -29,7 +29,8 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_grid_dims", "nrr_set_punctures", "nrr_relax", "nrr_residual",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
-           "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_last_error",
+           "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
+           "nrr_autotune", "nrr_last_error",
            "nrr_version")
 
 
@@ -96,6 +97,8 @@ def lib() -> C.CDLL:
         "nrr_timestep": [V, C.c_double, D, D],
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
+        "nrr_set_launch": [V, I, I],
+        "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
     }
@@ -276,6 +279,18 @@ class Grid:
         _check(lib().nrr_profile_stages(self._h, m, dt, eta, int(steps),
                                         C.byref(ms)))
         return ms.value
+
+    def set_launch(self, zc: int, mode="fp64"):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().nrr_set_launch(self._h, m, int(zc)))
+
+    def autotune(self, mode="fp64", trial_steps: int = 20):
+        """Pick the fastest stage launch shape; returns (zc, ms/launch)."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        zc, ms = C.c_int(), C.c_double()
+        _check(lib().nrr_autotune(self._h, m, int(trial_steps), C.byref(zc),
+                                  C.byref(ms)))
+        return zc.value, ms.value
 
     def step(self, steps: int, dt: float, eta: float, mode="fp64"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
