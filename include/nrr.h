@@ -90,9 +90,12 @@ typedef struct {
 
 /* Options of one solve (paper Sec. 2 relaxation system; Alg. 1 loop).
  *   mode         NRR_FP64, NRR_FP32 (whole relaxation in single precision)
- *                or NRR_FP32_DC (single-precision relaxation of the linearised
- *                correction equation inside an FP64 defect-correction loop;
- *                FP64 residual, norm and update).
+ *                or NRR_FP32_DC (defect correction: every outer iteration
+ *                evaluates in FP64 the relaxation system's right-hand side
+ *                at the current state, then integrates in FP32 the
+ *                increment of the state under the system linearised there
+ *                and forced by that FP64 defect, adds the increment in FP64
+ *                and checks the FP64 residual norm).
  *   tol          stop when the residual norm < tol (e.g. 1e-10).
  *   max_iters    RK4 steps allowed (all inner steps for NRR_FP32_DC).
  *   check_every  residual norm evaluated every this many steps (>= 1).
@@ -104,8 +107,10 @@ typedef struct {
  *                u0, padded FP64 layout; v = eta u).
  *   u0           initial u for NRR_INIT_HOST/DEVICE, else ignored.
  *   timeout_ms   wall-clock limit (<= 0: none); checked between norm checks.
- *   inner_tol    NRR_FP32_DC: relative reduction of the inner residual.
- *   max_outer    NRR_FP32_DC: defect-correction iterations allowed.        */
+ *   inner_steps  NRR_FP32_DC: FP32 RK4 steps per outer iteration (0: use
+ *                check_every).
+ *   max_outer    NRR_FP32_DC: outer iterations allowed (0: no limit other
+ *                than max_iters, which counts FP32 steps).                 */
 typedef struct {
   int mode;
   double tol;
@@ -117,7 +122,7 @@ typedef struct {
   int initial;
   const double *u0;
   int64_t timeout_ms;
-  double inner_tol;
+  int64_t inner_steps;
   int max_outer;
 } nrr_relax_opts;
 
@@ -135,7 +140,7 @@ typedef struct nrr_grid nrr_grid;
 
 /* Fills *o with the defaults: FP64, tol 1e-10, max_iters 10^6,
  * check_every 50, cfl 0.5, eta 0 (automatic), r_int 100, zero initial data,
- * no timeout, inner_tol 1e-4, max_outer 20. */
+ * no timeout, inner_steps 0 (= check_every), max_outer 0 (no limit). */
 nrr_status nrr_default_opts(nrr_relax_opts *o);
 
 /* Creates a grid: computes the full device footprint, fails with

@@ -106,6 +106,9 @@ def lib():
         _lib.or_residual_norm.argtypes = [C.c_void_p, D, C.c_double]
         _lib.or_relax.argtypes = [C.c_void_p, D, D, C.POINTER(_RelaxParams),
                                   D, D, C.POINTER(_RelaxResult)]
+        _lib.or_linear_coefficient.argtypes = [C.c_void_p, D, D, D, D]
+        _lib.or_linear_rhs.argtypes = [C.c_void_p, D, D, C.c_double, D, D,
+                                       D, D]
         _lib.or_newton.argtypes = [C.c_void_p, D, D, D, C.c_int, C.c_double,
                                    D]
     return _lib
@@ -215,6 +218,19 @@ class Grid:
                      _dp(np.ascontiguousarray(u)),
                      _dp(np.ascontiguousarray(v)), _dp(ku), _dp(kv))
         return ku, kv
+
+    def linear_coefficient(self, alpha, beta, u):
+        a = self.zeros()
+        lib().or_linear_coefficient(self._h, _dp(alpha), _dp(beta),
+                                    _dp(np.ascontiguousarray(u)), _dp(a))
+        return a
+
+    def linear_rhs(self, a, rhat, eta, d, w):
+        kd, kw = self.zeros(), self.zeros()
+        lib().or_linear_rhs(self._h, _dp(a), _dp(np.ascontiguousarray(rhat)),
+                            float(eta), _dp(np.ascontiguousarray(d)),
+                            _dp(np.ascontiguousarray(w)), _dp(kd), _dp(kw))
+        return kd, kw
 
     def rk4_step(self, alpha, beta, eta, dt, u, v):
         """One RK4 step in place on (u, v)."""

@@ -522,6 +522,40 @@ void or_rhs(const or_grid *g, const double *alpha, const double *beta,
     }
 }
 
+/* a = -d/du of the source term beta (1 + alpha u)^-7, i.e.
+ * 7 alpha beta (1 + alpha u)^-8, at every point. */
+void or_linear_coefficient(const or_grid *g, const double *alpha,
+                           const double *beta, const double *u, double *a) {
+  for (long p = 0; p < g->npts; p++)
+    a[p] = 7.0 * alpha[p] * beta[p] * pow(1.0 + alpha[p] * u[p], -8.0);
+}
+
+/* Right-hand side of the relaxation system of the correction equation with
+ * the same boundary handling as or_rhs. */
+void or_linear_rhs(const or_grid *g, const double *a, const double *rhat,
+                   double eta, const double *d, const double *w, double *kd,
+                   double *kw) {
+#pragma omp parallel for collapse(2)
+  for (int i2 = 0; i2 < g->s[2]; i2++)
+    for (int i1 = 0; i1 < g->s[1]; i1++)
+      for (int i0 = 0; i0 < g->s[0]; i0++) {
+        long p = pidx(g, i0, i1, i2);
+        if (g->kind[p] == OR_INTERIOR) {
+          double lap = laplacian_at(g, d, i0, i1, i2);
+          kd[p] = w[p] - eta * d[p];
+          kw[p] = g->c[p] * g->c[p] * (lap - a[p] * d[p] + rhat[p]);
+        } else if (g->kind[p] == OR_OUTER) {
+          kd[p] = -g->c[p] * radiation_df(g, d, i0, i1, i2);
+          kw[p] = -g->c[p] * radiation_df(g, w, i0, i1, i2);
+        }
+      }
+  for (long p = 0; p < g->npts; p++)
+    if (g->kind[p] == OR_INNER) {
+      kd[p] = kd[g->image[p]];
+      kw[p] = kw[g->image[p]];
+    }
+}
+
 /* Classical RK4 (method of lines), the substep loop of Alg. 1. */
 void or_rk4_step(const or_grid *g, const double *alpha, const double *beta,
                  double eta, double dt, double *u, double *v) {

@@ -94,6 +94,18 @@ int or_relax(const or_grid *g, const double *alpha, const double *beta,
              const or_relax_params *prm, double *u, double *v,
              or_relax_result *res);
 
+/* Defect correction (FP32 relaxation inside an FP64 outer loop): the
+ * linearisation of H at u, H(u + d) ~ H(u) + lap(d) - a d, with
+ * a = 7 alpha beta (1 + alpha u)^-8, and the relaxation system of the
+ * correction equation lap(d) - a d + rhat = 0:
+ *   dd/dt = w - eta d,  dw/dt = c^2 [lap(d) - a d + rhat]
+ * with the same boundary conditions as (u, v). */
+void or_linear_coefficient(const or_grid *g, const double *alpha,
+                           const double *beta, const double *u, double *a);
+void or_linear_rhs(const or_grid *g, const double *a, const double *rhat,
+                   double eta, const double *d, const double *w,
+                   double *kd, double *kw);
+
 /* Newton's method with a dense LU on the discrete steady-state system. */
 int or_newton(const or_grid *g, const double *alpha, const double *beta,
               double *u, int max_it, double step_tol, double *final_step);

@@ -100,6 +100,7 @@ struct nrr_grid {
   double *u_save = nullptr;
   float *acoef32 = nullptr;
   float *rhs32 = nullptr;
+  float *fu32 = nullptr;
 
   double dsmin_global = 0.0;
   bool have_source = false;
@@ -148,7 +149,7 @@ size_t footprint_bytes(const Geo &geo) {
   size_t n = (size_t)geo.npts, nc = (size_t)geo.ncol;
   size_t b = 0;
   b += n * (10 * 8 + 10 * 4);          // FP64 + FP32 field sets
-  b += n * (8 + 8 + 4 + 4);            // defect-correction buffers
+  b += n * (8 + 8 + 4 + 4 + 4);        // defect-correction buffers
   b += nc * 8 * (3 + 2 + 4);           // column geometry
   b += nc * (8 + 4) * (ncoef(geo.ng) + 4);
   b += (size_t)(geo.ncol / 32 + 16) * 16 * ((geo.n2 + 1)) + (1 << 20);
@@ -237,6 +238,8 @@ StageArgs<R> stage_args(const nrr_grid *g, const FieldSet<R> &f,
   a.col = c;
   a.cart = g->cart;
   a.eta = (R)eta;
+  a.lin = f.lin;
+  a.fu = f.fu;
   a.au = f.a[0];
   a.av = f.a[1];
   a.bu = f.y[0];
@@ -286,7 +289,7 @@ void launch_norm(const nrr_grid *g, const FieldSet<R> &f, const ColumnSet<R> &c,
   g_launches += 2;
   launch_residual<R>(g->geo, f.y[0], f.alpha, f.bc2, c, g->cart, g->jac,
                      g->rad, r_int, h_out, g->partials, &nb, g->res_cfg,
-                     g->stream);
+                     g->stream, f.lin);
   launch_norm_finalize(g->partials, nb, g->scalars + 1, g->stream);
 }
 
@@ -313,6 +316,18 @@ nrr_status ensure_state(nrr_grid *g, int prec) {
   return NRR_OK;
 }
 
+// The FP32 field set of the defect correction's increment equation: (d, w)
+// in the FP32 state buffers, with c^2 a in place of alpha and the FP64
+// defect (f_u, f_v) as forcing.
+FieldSet<float> dc_fields(const nrr_grid *g) {
+  FieldSet<float> dc = g->f32;
+  dc.alpha = g->acoef32;
+  dc.bc2 = g->rhs32;
+  dc.fu = g->fu32;
+  dc.lin = 1;
+  return dc;
+}
+
 nrr_status get_graph(nrr_grid *g, int mode, int steps, double dt, double eta,
                      double r_int, cudaGraphExec_t *out) {
   GraphKey key{mode, steps, dt, eta, r_int};
@@ -327,6 +342,14 @@ nrr_status get_graph(nrr_grid *g, int mode, int steps, double dt, double eta,
   if (mode == NRR_FP32) {
     launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, steps);
     launch_norm<float>(g, g->f32, g->c32, r_int, nullptr);
+  } else if (mode == NRR_FP32_DC) {
+    // defect-correction inner steps, FP64 update, FP64 norm
+    FieldSet<float> dc = dc_fields(g);
+    launch_rk4_steps<float>(g, dc, g->c32, dt, eta, steps);
+    launch_dc_update(g->f64.y[0], g->f64.y[1], g->f32.y[0], g->f32.y[1],
+                     g->geo.npts, g->stream);
+    g_launches += 1;
+    launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
   } else {
     launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, steps);
     launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
@@ -362,6 +385,135 @@ nrr_status set_device(const nrr_grid *g) {
   return NRR_OK;
 }
 
+// Relaxes the current state chunk by chunk (check_every steps, then the norm)
+// in the given mode; *norm holds the last norm.  Stops below tol, at
+// max_steps, on a non-finite norm or at the wall-clock limit.
+nrr_status relax_chunks(nrr_grid *g, int mode, double dt, double eta,
+                        double tol, double r_int, int check_every,
+                        int64_t max_steps, double t_start, int64_t timeout_ms,
+                        int64_t *steps_done, double *norm, nrr_status *why) {
+  int64_t it = 0;
+  *why = NRR_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (!std::isfinite(*norm)) {
+      *why = NRR_ERR_DIVERGED;
+      break;
+    }
+    if (*norm < tol) {
+      *why = NRR_OK;
+      break;
+    }
+    if (it >= max_steps) break;
+    if (timeout_ms > 0 && (now_s() - t_start) * 1e3 > (double)timeout_ms) {
+      *why = NRR_ERR_TIMEOUT;
+      break;
+    }
+    int64_t m = check_every;
+    if (max_steps - it < m) m = max_steps - it;
+    if (m == check_every) {
+      cudaGraphExec_t exec;
+      TRY(get_graph(g, mode, (int)m, dt, eta, r_int, &exec));
+      CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+      g_launches += g->graph_kernels[GraphKey{mode, (int)m, dt, eta, r_int}];
+    } else if (mode == NRR_FP32) {
+      launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, m);
+      launch_norm<float>(g, g->f32, g->c32, r_int, nullptr);
+    } else {
+      launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, m);
+      launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
+    }
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_read_norm(g, norm));
+    it += m;
+  }
+  *steps_done = it;
+  return NRR_OK;
+}
+
+// Defect correction of the relaxation itself.  Outer iteration, in FP64:
+// the full right-hand side F of the relaxation system (with its boundary
+// conditions) at the current state (u, v) -- the defect -- and the
+// linearisation coefficient a of the source at u.  Inner, in FP32: the
+// increment (d, w) from rest by `inner_steps` RK4 steps of
+//   dd/dt = w - eta d + F_u,   dw/dt = c^2 (lap d - a d) + F_v
+// (radiation condition plus F on the outer shell).  Then (u, v) += (d, w) in
+// FP64 and the FP64 residual norm decides whether to stop.  The fixed point
+// has F = 0, i.e. the FP64 discrete solution; FP32 rounding enters only
+// through the increments.
+nrr_status relax_defect_correction(nrr_grid *g, const nrr_relax_opts *o,
+                                   double dt, double eta, double t_start,
+                                   nrr_relax_result *res) {
+  const Geo &geo = g->geo;
+  const size_t n = (size_t)geo.npts;
+  TRY(ensure_state(g, 64));
+  const int64_t inner = o->inner_steps > 0 ? o->inner_steps : o->check_every;
+  launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+  double norm64 = 0.0;
+  TRY(sync_read_norm(g, &norm64));
+  int64_t steps_total = 0;
+  int64_t outer = 0;
+  nrr_status status = NRR_ERR_NOT_CONVERGED;
+  FieldSet<float> dc = dc_fields(g);
+  double *Fu = g->f64.t[0], *Fv = g->f64.t[1];  // FP64 defect (scratch)
+  for (;;) {
+    if (!std::isfinite(norm64)) {
+      status = NRR_ERR_DIVERGED;
+      break;
+    }
+    if (norm64 < o->tol) {
+      status = NRR_OK;
+      break;
+    }
+    if ((o->max_outer > 0 && outer >= o->max_outer) || steps_total >= o->max_iters)
+      break;
+    if (o->timeout_ms > 0 && (now_s() - t_start) * 1e3 > (double)o->timeout_ms) {
+      status = NRR_ERR_TIMEOUT;
+      break;
+    }
+    int64_t m = inner;
+    if (o->max_iters - steps_total < m) m = o->max_iters - steps_total;
+    // FP64 defect at (u, v), then the FP32 forcing and coefficient
+    StageArgs<double> ra{};
+    ra.su = g->f64.y[0];
+    ra.sv = g->f64.y[1];
+    ra.ou = Fu;
+    ra.ov = Fv;
+    ra.alpha = g->f64.alpha;
+    ra.bc2 = g->f64.bc2;
+    ra.col = g->c64;
+    ra.cart = g->cart;
+    ra.eta = eta;
+    launch_stage<double>(geo, STAGE_RAW, ra, g->stage_cfg[0], g->stream);
+    launch_dc_prepare(geo, g->f64.y[0], g->f64.alpha, g->f64.bc2, Fu, Fv,
+                      g->acoef32, g->fu32, g->rhs32, g->stream);
+    CUDA_TRY(cudaMemsetAsync(g->f32.y[0], 0, n * sizeof(float), g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->f32.y[1], 0, n * sizeof(float), g->stream));
+    g_launches += 2;
+    if (m == inner) {
+      cudaGraphExec_t exec;
+      TRY(get_graph(g, NRR_FP32_DC, (int)m, dt, eta, o->r_int, &exec));
+      CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+      g_launches += g->graph_kernels[GraphKey{NRR_FP32_DC, (int)m, dt, eta, o->r_int}];
+    } else {
+      launch_rk4_steps<float>(g, dc, g->c32, dt, eta, m);
+      launch_dc_update(g->f64.y[0], g->f64.y[1], g->f32.y[0], g->f32.y[1],
+                       geo.npts, g->stream);
+      launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+      g_launches += 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    TRY(sync_read_norm(g, &norm64));
+    steps_total += m;
+    outer++;
+  }
+  g->state_prec = 64;
+  res->iters = steps_total;
+  res->outer_iters = outer;
+  res->final_norm = norm64;
+  res->status = status;
+  return NRR_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
@@ -385,8 +537,8 @@ nrr_status nrr_default_opts(nrr_relax_opts *o) {
   o->initial = NRR_INIT_ZERO;
   o->u0 = nullptr;
   o->timeout_ms = 0;
-  o->inner_tol = 1e-4;
-  o->max_outer = 20;
+  o->inner_steps = 0;
+  o->max_outer = 0;
   return NRR_OK;
 }
 
@@ -452,6 +604,7 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
     TRY(dev_alloc(g, &g->u_save, n));
     TRY(dev_alloc(g, &g->acoef32, n));
     TRY(dev_alloc(g, &g->rhs32, n));
+    TRY(dev_alloc(g, &g->fu32, n));
     TRY(dev_alloc(g, &g->h, 3 * (size_t)nc));
     TRY(dev_alloc(g, &g->gl, 2 * (size_t)nc));
     TRY(dev_alloc(g, &g->rad, nc));
@@ -840,8 +993,8 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
   if (!(o->tol > 0.0) || o->check_every < 1 || o->max_iters < 0 ||
       !(o->cfl > 0.0) || !(o->r_int > 0.0))
     return fail(NRR_ERR_INVALID_ARG, "invalid relax options");
-  if (o->mode == NRR_FP32_DC)
-    return fail(NRR_ERR_INVALID_ARG, "NRR_FP32_DC not available in this build");
+  if (o->inner_steps < 0 || o->max_outer < 0)
+    return fail(NRR_ERR_INVALID_ARG, "inner_steps and max_outer must be >= 0");
   TRY(set_device(g));
   double dt = 0.0, eta_def = 0.0;
   TRY(nrr_timestep(g, o->cfl, &dt, &eta_def));
@@ -871,55 +1024,33 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
     default:
       return fail(NRR_ERR_INVALID_ARG, "unknown initial mode %d", o->initial);
   }
-  int prec = o->mode == NRR_FP32 ? 32 : 64;
-  TRY(ensure_state(g, prec));
-
   nrr_relax_result res{};
-  int64_t it = 0;
+  nrr_status status;
   double nrm = 0.0;
-  if (prec == 32)
-    launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
-  else
-    launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
-  CUDA_TRY(cudaGetLastError());
-  TRY(sync_read_norm(g, &nrm));
-  nrr_status status = NRR_ERR_NOT_CONVERGED;
-  for (;;) {
-    if (!std::isfinite(nrm)) {
-      status = NRR_ERR_DIVERGED;
-      break;
-    }
-    if (nrm < o->tol) {
-      status = NRR_OK;
-      break;
-    }
-    if (it >= o->max_iters) break;
-    if (o->timeout_ms > 0 && (now_s() - t_start) * 1e3 > (double)o->timeout_ms) {
-      status = NRR_ERR_TIMEOUT;
-      break;
-    }
-    int64_t m = o->check_every;
-    if (o->max_iters - it < m) m = o->max_iters - it;
-    if (m == o->check_every) {
-      cudaGraphExec_t exec;
-      TRY(get_graph(g, o->mode, (int)m, dt, eta, o->r_int, &exec));
-      CUDA_TRY(cudaGraphLaunch(exec, g->stream));
-      g_launches += g->graph_kernels[GraphKey{o->mode, (int)m, dt, eta, o->r_int}];
-    } else if (prec == 32) {
-      launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, m);
+  int64_t it = 0;
+  if (o->mode == NRR_FP32_DC) {
+    TRY(relax_defect_correction(g, o, dt, eta, t_start, &res));
+    status = (nrr_status)res.status;
+    nrm = res.final_norm;
+    it = res.iters;
+  } else {
+    int prec = o->mode == NRR_FP32 ? 32 : 64;
+    TRY(ensure_state(g, prec));
+    if (prec == 32)
       launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
-    } else {
-      launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, m);
+    else
       launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
-    }
     CUDA_TRY(cudaGetLastError());
     TRY(sync_read_norm(g, &nrm));
-    it += m;
+    TRY(relax_chunks(g, o->mode, dt, eta, o->tol, o->r_int, o->check_every,
+                     o->max_iters, t_start, o->timeout_ms, &it, &nrm,
+                     &status));
+    res.iters = it;
+    res.outer_iters = 0;
+    res.final_norm = nrm;
+    res.status = status;
   }
-  res.iters = it;
-  res.outer_iters = 0;
-  res.final_norm = nrm;
-  res.status = status;
+
   res.seconds = now_s() - t_start;
   if (r) *r = res;
   if (status == NRR_ERR_NOT_CONVERGED)

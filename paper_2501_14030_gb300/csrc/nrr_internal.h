@@ -42,6 +42,9 @@ struct FieldSet {
   R *a[2] = {nullptr, nullptr};
   R *alpha = nullptr;
   R *bc2 = nullptr;
+  R *fu = nullptr;  // forcing of the u equation (linear mode only)
+  int lin = 0;      // 1: increment equation of the defect correction, with
+                    // (alpha, bc2, fu) = (c^2 a, f_v, f_u)
 };
 
 struct LaunchCfg {
@@ -96,6 +99,11 @@ struct StageArgs {
   ColumnSet<R> col;
   CartCoef cart;
   R eta, wa, wb;     // damping, a_s dt, b_s dt
+  const R *fu;       // forcing of the u equation (lin only)
+  int lin;           // 1: increment equation of the defect correction:
+                     //    k_u = v - eta u + f_u, k_v = c^2 lap u - alpha u + bc2
+                     //    with alpha = c^2 a, bc2 = f_v (forcings also added
+                     //    on the outer shell)
 };
 
 template <typename R>
@@ -109,7 +117,7 @@ void launch_residual(const Geo &g, const R *u, const R *alpha, const R *bc2,
                      ColumnSet<R> col, const CartCoef &cart, const double *jac,
                      const double *rad, double r_int, double *h_out,
                      double *partials, int *nblocks_out, const LaunchCfg &cfg,
-                     cudaStream_t st);
+                     cudaStream_t st, int lin = 0);
 int residual_blocks(const Geo &g, const LaunchCfg &cfg);
 // sqrt(sum num / sum den) of nblocks partial pairs into out[0]; out[1] = num,
 // out[2] = den.  Fixed summation order.
@@ -123,5 +131,12 @@ void launch_fill_ghosts(const Geo &g, R *f, cudaStream_t st);
 void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t st);
 void launch_convert(const float *src, double *dst, int64_t n, cudaStream_t st);
 void launch_scale(double *f, double s, int64_t n, cudaStream_t st);
+// Defect correction: FP32 coefficient c^2 a and forcings (f_u, f_v) = the
+// FP64 right-hand side at (u, v); and the FP64 update (u, v) += (d, w).
+void launch_dc_prepare(const Geo &g, const double *u, const double *alpha,
+                       const double *bc2, const double *ku, const double *kv,
+                       float *ac2, float *fu, float *fv, cudaStream_t st);
+void launch_dc_update(double *u, double *v, const float *d, const float *w,
+                      int64_t n, cudaStream_t st);
 
 }  // namespace nrr

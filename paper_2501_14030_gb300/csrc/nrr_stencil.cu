@@ -44,9 +44,13 @@ __device__ __forceinline__ float recip(float s) {
   return fmaf(t, e, t);
 }
 
-// beta c^2 (1 + alpha u)^-7 added to acc.
+// The source term added to acc (both c^2-scaled).  Nonlinear:
+// beta c^2 (1 + alpha u)^-7 with (al, bc2) = (alpha, c^2 beta).  Linear (the
+// increment equation of the defect correction): f_v - c^2 a d with
+// (al, bc2) = (c^2 a, f_v).  `lin` is uniform across the launch.
 template <typename R>
-__device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2) {
+__device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
+  if (lin) return acc + fma(-al, u0, bc2);
   R t = recip(fma(al, u0, R(1)));
   R t2 = t * t;
   R t4 = t2 * t2;
@@ -64,7 +68,8 @@ template <typename R, int NG, int ZC>
 __device__ __forceinline__ void curvi_operator(
     const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
     int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
-    const R (&u0)[ZC], const R (&al)[ZC], const R (&bc)[ZC], R (&out)[ZC]) {
+    const R (&u0)[ZC], const R (&al)[ZC], const R (&bc)[ZC], R (&out)[ZC],
+    int lin) {
   const int64_t nc = g.ncol;
   const int s0 = g.s0;
   R a0[ZC], a1[ZC];
@@ -113,7 +118,8 @@ __device__ __forceinline__ void curvi_operator(
     }
   }
 #pragma unroll
-  for (int j = 0; j < ZC; j++) out[j] = add_source(a0[j] + a1[j], u0[j], al[j], bc[j]);
+  for (int j = 0; j < ZC; j++)
+    out[j] = add_source(a0[j] + a1[j], u0[j], al[j], bc[j], lin);
 }
 
 // Plane tables of one thread: wp[] = wrapped phi planes z0-NG .. z0+ZC-1+NG
@@ -184,6 +190,10 @@ __global__ void __launch_bounds__(128)
       R dv = fma(R(3), v0, fma(R(-4), v1, v2));
       R ku = -c * fma(kdb, du, rinv * u0);
       R kv = -c * fma(kdb, dv, rinv * v0);
+      if (a.lin) {
+        ku += ld(a.fu + p);
+        kv += ld(a.bc2 + p);
+      }
       stage_epilogue<R, KIND>(a, p, ku, kv);
     }
     return;
@@ -202,12 +212,14 @@ __global__ void __launch_bounds__(128)
     al[j] = ld(a.alpha + p);
     bc[j] = ld(a.bc2 + p);
   }
-  curvi_operator<R, NG, ZC>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv);
+  curvi_operator<R, NG, ZC>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv,
+                            a.lin);
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
     if (z0 + j >= zend) break;
     int64_t p = col + (int64_t)nc * (z0 + j);
     R ku = fma(-a.eta, u0[j], v0[j]);
+    if (a.lin) ku += ld(a.fu + p);
     stage_epilogue<R, KIND>(a, p, ku, kv[j]);
   }
 }
@@ -248,7 +260,7 @@ __device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ 
 template <typename R, int NG>
 __device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ su,
                                            const CartCoef &cc, int64_t p, R u0,
-                                           R al, R bc2) {
+                                           R al, R bc2, int lin) {
   const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
   R lap = R(cc.cc) * u0;
 #pragma unroll
@@ -257,7 +269,7 @@ __device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ s
     for (int k = 1; k <= NG; k++)
       lap = fma(R(cc.a[d][k - 1]), ld(su + p + k * st[d]) + ld(su + p - k * st[d]),
                 lap);
-  return add_source(lap, u0, al, bc2);
+  return add_source(lap, u0, al, bc2, lin);
 }
 
 template <typename R, int NG, int KIND>
@@ -275,11 +287,16 @@ __global__ void __launch_bounds__(128)
     if (in01 && i2 >= NG && i2 < g.n2 + NG) {
       R u0 = ld(a.su + p), v0 = ld(a.sv + p);
       kv = cart_operator<R, NG>(g, a.su, a.cart, p, u0, ld(a.alpha + p),
-                                ld(a.bc2 + p));
+                                ld(a.bc2 + p), a.lin);
       ku = fma(-a.eta, u0, v0);
+      if (a.lin) ku += ld(a.fu + p);
     } else {
       ku = cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
       kv = cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
+      if (a.lin) {
+        ku += ld(a.fu + p);
+        kv += ld(a.bc2 + p);
+      }
     }
     stage_epilogue<R, KIND>(a, p, ku, kv);
   }
@@ -319,7 +336,7 @@ __global__ void __launch_bounds__(128)
                           const R *__restrict__ alpha, const R *__restrict__ bc2,
                           ColumnSet<R> col_set, const double *__restrict__ jac,
                           const double *__restrict__ rad, double r_int,
-                          double *h_out, double *partials, int zc) {
+                          double *h_out, double *partials, int zc, int lin) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   double num = 0.0, den = 0.0;
   if (e < g.n0 * g.n1) {
@@ -339,7 +356,8 @@ __global__ void __launch_bounds__(128)
       plane_tables<NG, 1>(g, i2, wp, wh);
       int64_t p = col + (int64_t)nc * i2;
       R u0[1] = {ld(su + p)}, al[1] = {ld(alpha + p)}, bc[1] = {ld(bc2 + p)}, op[1];
-      curvi_operator<R, NG, 1>(g, su, w, col, i0, i1, wp, wh, u0, al, bc, op);
+      curvi_operator<R, NG, 1>(g, su, w, col, i0, i1, wp, wh, u0, al, bc, op,
+                               lin);
       double H = (double)(op[0] * c2inv);
       if (h_out) h_out[p] = H;
       num += H * H * wt;
@@ -354,7 +372,7 @@ __global__ void __launch_bounds__(128)
     residual_cart_kernel(Geo g, const R *__restrict__ su,
                          const R *__restrict__ alpha, const R *__restrict__ bc2,
                          CartCoef cc, double r_int, double *h_out,
-                         double *partials, int zc) {
+                         double *partials, int zc, int lin) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   double num = 0.0, den = 0.0;
   if (e < g.n0 * g.n1) {
@@ -367,7 +385,7 @@ __global__ void __launch_bounds__(128)
       int64_t p = i0 + (int64_t)g.s0 * (i1 + (int64_t)g.s1 * i2);
       R u0 = ld(su + p);
       double H = (double)cart_operator<R, NG>(g, su, cc, p, u0, ld(alpha + p),
-                                              ld(bc2 + p));
+                                              ld(bc2 + p), lin);
       if (h_out) h_out[p] = H;
       double x2 = g.xxmin[2] + (i2 - NG + 0.5) * g.dxx[2];
       double wt = sqrt(x0 * x0 + x1 * x1 + x2 * x2) < r_int ? 1.0 : 0.0;
@@ -408,6 +426,35 @@ __global__ void fill_ghosts_kernel(Geo g, R *f) {
   int j0 = i0, j1 = i1, j2 = i2;
   image_of(g, j0, j1, j2);
   f[p] = f[flat(g, j0, j1, j2)];
+}
+
+// Defect correction, set-up of one outer iteration at the FP64 state (u, v)
+// whose FP64 right-hand side (with boundary conditions) is (ku, kv):
+//   c^2 a = 7 alpha (c^2 beta) (1 + alpha u)^-8   (linearised source)
+//   f_u = ku, f_v = kv                            (the defect, as forcing)
+__global__ void dc_prepare_kernel(Geo g, const double *__restrict__ u,
+                                  const double *__restrict__ alpha,
+                                  const double *__restrict__ bc2,
+                                  const double *__restrict__ ku,
+                                  const double *__restrict__ kv, float *ac2,
+                                  float *fu, float *fv) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.npts) return;
+  double t = 1.0 / (1.0 + alpha[p] * u[p]);
+  double t2 = t * t, t4 = t2 * t2;
+  ac2[p] = (float)(7.0 * alpha[p] * bc2[p] * (t4 * t4));
+  fu[p] = (float)ku[p];
+  fv[p] = (float)kv[p];
+}
+
+// (u, v) += (d, w): the FP64 update with the FP32 increments.
+__global__ void dc_update_kernel(double *u, double *v, const float *d,
+                                 const float *w, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    u[i] += (double)d[i];
+    v[i] += (double)w[i];
+  }
 }
 
 __global__ void convert_d2f_kernel(const double *s, float *d, int64_t n) {
@@ -461,15 +508,15 @@ void launch_residual_ng(const Geo &g, const R *u, const R *alpha, const R *bc2,
                         ColumnSet<R> col, const CartCoef &cart,
                         const double *jac, const double *rad, double r_int,
                         double *h_out, double *partials, const LaunchCfg &cfg,
-                        cudaStream_t st) {
+                        cudaStream_t st, int lin) {
   dim3 grid((g.n0 * g.n1 + cfg.block - 1) / cfg.block,
             (g.n2 + cfg.zc - 1) / cfg.zc);
   if (g.coord == CARTESIAN)
     residual_cart_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
-        g, u, alpha, bc2, cart, r_int, h_out, partials, cfg.zc);
+        g, u, alpha, bc2, cart, r_int, h_out, partials, cfg.zc, lin);
   else
     residual_curvi_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
-        g, u, alpha, bc2, col, jac, rad, r_int, h_out, partials, cfg.zc);
+        g, u, alpha, bc2, col, jac, rad, r_int, h_out, partials, cfg.zc, lin);
 }
 
 }  // namespace
@@ -499,11 +546,11 @@ void launch_residual(const Geo &g, const R *u, const R *alpha, const R *bc2,
                      ColumnSet<R> col, const CartCoef &cart, const double *jac,
                      const double *rad, double r_int, double *h_out,
                      double *partials, int *nblocks_out, const LaunchCfg &cfg,
-                     cudaStream_t st) {
+                     cudaStream_t st, int lin) {
   switch (g.ng) {
-    case 2: launch_residual_ng<R, 2>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
-    case 4: launch_residual_ng<R, 4>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
-    case 5: launch_residual_ng<R, 5>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st); break;
+    case 2: launch_residual_ng<R, 2>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st, lin); break;
+    case 4: launch_residual_ng<R, 4>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st, lin); break;
+    case 5: launch_residual_ng<R, 5>(g, u, alpha, bc2, col, cart, jac, rad, r_int, h_out, partials, cfg, st, lin); break;
     default: break;
   }
   if (nblocks_out) *nblocks_out = residual_blocks(g, cfg);
@@ -513,12 +560,12 @@ template void launch_residual<double>(const Geo &, const double *, const double 
                                       const CartCoef &, const double *,
                                       const double *, double, double *,
                                       double *, int *, const LaunchCfg &,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 template void launch_residual<float>(const Geo &, const float *, const float *,
                                      const float *, ColumnSet<float>,
                                      const CartCoef &, const double *,
                                      const double *, double, double *, double *,
-                                     int *, const LaunchCfg &, cudaStream_t);
+                                     int *, const LaunchCfg &, cudaStream_t, int);
 
 void launch_norm_finalize(const double *partials, int nblocks, double *out,
                           cudaStream_t st) {
@@ -540,6 +587,17 @@ void launch_convert(const double *src, float *dst, int64_t n, cudaStream_t st) {
 void launch_convert(const float *src, double *dst, int64_t n, cudaStream_t st) {
   convert_f2d_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
 }
+void launch_dc_prepare(const Geo &g, const double *u, const double *alpha,
+                       const double *bc2, const double *ku, const double *kv,
+                       float *ac2, float *fu, float *fv, cudaStream_t st) {
+  dc_prepare_kernel<<<(unsigned)((g.npts + 255) / 256), 256, 0, st>>>(
+      g, u, alpha, bc2, ku, kv, ac2, fu, fv);
+}
+void launch_dc_update(double *u, double *v, const float *d, const float *w,
+                      int64_t n, cudaStream_t st) {
+  dc_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, v, d, w, n);
+}
+
 void launch_scale(double *f, double s, int64_t n, cudaStream_t st) {
   scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, s, n);
 }

@@ -58,7 +58,7 @@ class RelaxOpts(C.Structure):
                 ("cfl", C.c_double), ("eta", C.c_double),
                 ("r_int", C.c_double), ("initial", C.c_int),
                 ("u0", C.POINTER(C.c_double)), ("timeout_ms", C.c_int64),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int)]
+                ("inner_steps", C.c_int64), ("max_outer", C.c_int)]
 
 
 class RelaxResult(C.Structure):
@@ -225,14 +225,14 @@ class Grid:
 
     def relax(self, mode="fp64", tol=1e-10, max_iters=1_000_000,
               check_every=50, cfl=0.5, eta=0.0, r_int=100.0, initial=None,
-              u0=None, timeout_ms=0, inner_tol=1e-4, max_outer=20,
+              u0=None, timeout_ms=0, inner_steps=0, max_outer=0,
               raise_on_error=True) -> dict:
         o = RelaxOpts()
         _check(lib().nrr_default_opts(C.byref(o)))
         o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
         o.tol, o.max_iters, o.check_every = tol, max_iters, check_every
         o.cfl, o.eta, o.r_int = cfl, eta, r_int
-        o.timeout_ms, o.inner_tol, o.max_outer = timeout_ms, inner_tol, max_outer
+        o.timeout_ms, o.inner_steps, o.max_outer = timeout_ms, inner_steps, max_outer
         if u0 is not None:
             p, on_dev = _ptr(u0)
             o.initial = INIT_DEVICE if on_dev else INIT_HOST

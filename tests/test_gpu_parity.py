@@ -163,3 +163,74 @@ def test_brill_lindquist_is_exactly_zero(gpu):
     u = np.ones(g.shape)
     g.get_state(u)
     assert not u.any()
+
+
+# ------------------------------------------------ FP32 and defect correction
+FP32_RHS_TOL = 2e-5  # see test docstring
+
+
+@pytest.mark.parametrize("name", ["sinh_32x16x2_o4", "sinh_44x26x6_o8",
+                                  "sph_40x22x8_o8", "cart_26x20x22_o4",
+                                  "sinh_128x128x16_o8"])
+def test_rhs_parity_fp32(gpu, name):
+    """Single-precision RHS against the FP64 oracle.  Tolerance from the
+    arithmetic: inputs and the ~5*ng+1 folded weights are rounded to FP32
+    (unit roundoff 6e-8) and summed over 25-31 terms whose magnitudes exceed
+    the result by at most ~10 for these smooth-plus-noise states, so the
+    norm-relative error stays below 31 x 10 x 6e-8 ~ 2e-5."""
+    desc, punc, og, alpha, beta, g = _setup(name)
+    u = W.smooth_random_field(desc, seed=11, amplitude=0.2, noise=0.01)
+    v = W.smooth_random_field(desc, seed=12, amplitude=0.1, noise=0.01)
+    dt, eta = default_dt_eta(og)
+    ku_o, kv_o = og.rhs(alpha, beta, eta, og.fill_inner_ghosts(u),
+                        og.fill_inner_ghosts(v))
+    ku, kv = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+    g.rhs(_dev(u), _dev(v), ku, kv, eta, mode="fp32")
+    ku, kv = ku.cpu().numpy(), kv.cpu().numpy()
+    for region, m in region_masks(og).items():
+        assert rel_err(ku, ku_o, m) <= FP32_RHS_TOL, (region, rel_err(ku, ku_o, m))
+        assert rel_err(kv, kv_o, m) <= FP32_RHS_TOL, (region, rel_err(kv, kv_o, m))
+
+
+@pytest.mark.parametrize("name", ["sinh_32x16x2_o4", "sinh_44x26x6_o8",
+                                  "sph_40x22x8_o8", "cart_26x20x22_o4"])
+def test_defect_correction_reaches_fp64_solution(gpu, name):
+    """FP32 relaxation inside the FP64 defect-correction loop reaches the
+    1e-10 residual (confirmed by the oracle) in about as many steps as the
+    FP64 relaxation.  A residual of 1e-10 fixes u only up to the conditioning
+    of the discrete operator, and the two paths round differently, so u is
+    compared after both have been driven to 1e-12: agreement to 1e-10."""
+    desc, punc, og, alpha, beta, g = _setup(name)
+    dt, eta = default_dt_eta(og)
+    res = g.relax(mode="fp32_dc", tol=1e-10, check_every=50)
+    assert res["status"] == 0 and res["norm"] < 1e-10
+    u = np.zeros(og.shape)
+    g.get_state(u)
+    assert og.norm(og.residual(alpha, beta, u)) < 1.02e-10
+    uo, vo = og.zeros(), og.zeros()
+    it, _, st = og.relax(alpha, beta, uo, vo, eta=eta, dt=dt, tol=1e-10,
+                         check_every=50)
+    assert st == 0
+    assert abs(res["iters"] - it) <= 100, (res, it)
+    res = g.relax(mode="fp32_dc", tol=1e-12, check_every=50)
+    assert res["status"] == 0
+    g.get_state(u)
+    _, _, st = og.relax(alpha, beta, uo, vo, eta=eta, dt=dt, tol=1e-12,
+                        check_every=50)
+    assert st == 0
+    assert rel_err(u, uo) <= 1e-10, rel_err(u, uo)
+
+
+def test_defect_correction_full_size_matches_fp64(gpu):
+    """128x128x16: the defect-correction solve and the FP64 solve agree to
+    1e-9 and the oracle re-evaluates the residual of both."""
+    desc, punc, og, alpha, beta, g = _setup("sinh_128x128x16_o8")
+    r64 = g.relax(mode="fp64", tol=1e-10, check_every=50)
+    u64 = np.zeros(og.shape)
+    g.get_state(u64)
+    rdc = g.relax(mode="fp32_dc", tol=1e-10, check_every=50)
+    udc = np.zeros(og.shape)
+    g.get_state(udc)
+    assert rdc["status"] == 0 and abs(rdc["iters"] - r64["iters"]) <= 100
+    assert og.norm(og.residual(alpha, beta, udc)) < 1.02e-10
+    assert rel_err(udc, u64) <= 1e-9

@@ -368,3 +368,34 @@ def test_relaxation_agrees_with_dense_newton(oracle_mod, desc):
                          r_int=1e30, check_every=1000, max_iters=4000)
     assert nrm < 1e-16, nrm
     assert np.abs(u - un).max() <= 1e-13 * np.abs(un).max()
+
+
+# -------------------------------------------- defect-correction operator
+def test_linearisation_is_the_derivative_of_the_residual(oracle_mod):
+    """H(u + e d) - H(u - e d) = 2 e (lap d - a d) + O(e^3): the correction
+    equation's coefficient a is minus the derivative of the source term."""
+    desc, punc = W.small_equal_mass()
+    g = oracle_grid(desc)
+    alpha, beta = g.source(punc)
+    u = g.fill_inner_ghosts(W.smooth_random_field(desc, seed=5, amplitude=0.1))
+    d = g.fill_inner_ghosts(W.smooth_random_field(desc, seed=6, amplitude=0.1))
+    a = g.linear_coefficient(alpha, beta, u)
+    eps = 1e-4
+    fd = (g.residual(alpha, beta, u + eps * d)
+          - g.residual(alpha, beta, u - eps * d)) / (2 * eps)
+    lin = g.laplacian(d) - a * d
+    m = g.field("kind") == 0
+    assert np.abs(fd - lin)[m].max() <= 1e-7 * np.abs(lin)[m].max()
+
+
+def test_linear_rhs_matches_relaxation_rhs_structure(oracle_mod):
+    """With a = 0 and rhat = beta (1 + alpha u)^-7 evaluated at u = 0 the
+    correction system's RHS at d = 0 equals the nonlinear RHS at u = 0."""
+    desc, punc = W.small_equal_mass()
+    g = oracle_grid(desc)
+    alpha, beta = g.source(punc)
+    z = g.zeros()
+    ku, kv = g.rhs(alpha, beta, 0.3, z, z)
+    kd, kw = g.linear_rhs(z, beta, 0.3, z, z)
+    assert np.array_equal(ku, kd)
+    np.testing.assert_allclose(kw, kv, rtol=1e-15, atol=0)
