@@ -237,6 +237,47 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int zc);
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
                         int *best_zc, double *best_ms_per_launch);
 
+/* ---- Batches of independent solves (paper Sec. 5, N independent grids,
+ * there on several streams; here one graph launch for all of them) ------- */
+typedef struct nrr_batch nrr_batch;
+
+/* Creates a batch of n solves of uneven sizes: descs[i] (SinhSymTP or
+ * Spherical, one fd_order for the whole batch), npunct[i] punctures at
+ * punct[i] (host arrays, copied).  Computes the footprint first
+ * (NRR_ERR_OOM before any allocation), then allocates one arena per field
+ * and runs the set-up of every solve on the device.  flags bit 0: also
+ * allocate FP64 stage buffers so that NRR_FP64 batch relaxations are
+ * possible (NRR_FP32_DC needs no extra storage).  stream: as for
+ * nrr_create_grid. */
+nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
+                            const int *npunct, const nrr_puncture *const *punct,
+                            int flags, void *stream, nrr_batch **out);
+nrr_status nrr_batch_destroy(nrr_batch *b);
+nrr_status nrr_batch_info(const nrr_batch *b, int64_t *total_points,
+                          int64_t *interior_points);
+
+/* Relaxes every solve of the batch to o->tol (modes NRR_FP64 or
+ * NRR_FP32_DC; initial NRR_INIT_ZERO or NRR_INIT_CURRENT) as one CUDA graph
+ * launch: each RK4 stage is one kernel over all solves still above tol; the
+ * per-solve norms and the stop test run on the device every check_every
+ * steps (every inner_steps for NRR_FP32_DC) and a conditional WHILE node
+ * repeats the chunk until no solve is left, max_iters steps have been taken
+ * or timeout_ms has passed (measured on the device).  per_solve (nullable,
+ * n entries) receives each solve's steps, norm and status; total (nullable)
+ * the largest step count, the number of chunks and the largest norm.
+ * Returns NRR_OK when every solve converged. */
+nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
+                           nrr_relax_result *per_solve,
+                           nrr_relax_result *total);
+
+/* Copies u of solve i out (padded FP64 layout, inner ghosts filled). */
+nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device);
+
+/* Autotuner for the batch's stage launch shape (phi planes per thread),
+ * timed over all solves; keeps the fastest for later relaxations. */
+nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
+                              int *best_zc, double *best_ms_per_launch);
+
 /* Cumulative number of kernels this library has launched in this process
  * (graph replays count every kernel node). */
 int64_t nrr_kernel_launches(void);

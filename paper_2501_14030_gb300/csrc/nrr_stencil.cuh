@@ -1,0 +1,314 @@
+// nrr_stencil.cuh -- device building blocks of the relaxation hot path
+// (arXiv 2501.14030, Sec. 2 relaxation system; Alg. 1 RHS, BC, RK, H), shared
+// by the single-grid kernels (nrr_stencil.cu) and the batched kernels
+// (nrr_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nrr_internal.h"
+
+namespace nrr {
+namespace dev {
+
+template <typename R>
+__device__ __forceinline__ R ld(const R *p) {
+  return __ldg(p);
+}
+
+// Reciprocal of s = 1 + alpha u (a normal number near 1) by Newton-Raphson
+// refinement of the hardware approximation: t <- t + t (1 - s t) converges
+// quadratically, so two steps from the approximate seed reach full double
+// precision and one step suffices in single precision.
+__device__ __forceinline__ double recip(double s) {
+  double t;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(t) : "d"(s));
+  double e = fma(-s, t, 1.0);
+  t = fma(t, e, t);
+  e = fma(-s, t, 1.0);
+  return fma(t, e, t);
+}
+__device__ __forceinline__ float recip(float s) {
+  float t;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(s));
+  float e = fmaf(-s, t, 1.0f);
+  return fmaf(t, e, t);
+}
+
+// The source term added to acc (both c^2-scaled).  Nonlinear:
+// beta c^2 (1 + alpha u)^-7 with (al, bc2) = (alpha, c^2 beta).  Linear (the
+// increment equation of the defect correction): f_v - c^2 a d with
+// (al, bc2) = (c^2 a, f_v).  `lin` is uniform across the launch.
+template <typename R>
+__device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
+  if (lin) return acc + fma(-al, u0, bc2);
+  R t = recip(fma(al, u0, R(1)));
+  R t2 = t * t;
+  R t4 = t2 * t2;
+  R q = bc2 * t;
+  q = q * t2;
+  return fma(q, t4, acc);
+}
+
+// c^2 [lap(u) + source] at ZC interior points of one column (i0, i1) of a
+// curvilinear grid, planes pl[0..ZC).  wp[] holds the wrapped phi planes
+// pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  Two
+// independent accumulation chains per point (xx0 + phi, xx1) and ZC points
+// interleaved give the FP64 pipe independent work.
+template <typename R, int NG, int ZC>
+__device__ __forceinline__ void curvi_operator(
+    const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
+    int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
+    const R (&u0)[ZC], const R (&al)[ZC], const R (&bc)[ZC], R (&out)[ZC],
+    int lin) {
+  const int64_t nc = g.ncol;
+  const int s0 = g.s0;
+  R a0[ZC], a1[ZC];
+#pragma unroll
+  for (int j = 0; j < ZC; j++) a0[j] = w[0] * u0[j];
+  // xx0: the + side stays inside the padded box; the - side may cross
+  // xx0 = 0 and read the reflected point at phi + pi.
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+    const int im = i0 - k;
+    const bool refl = im < NG;
+    const int rcol = (2 * NG - 1 - im) +
+                     s0 * (g.coord == SPHERICAL ? g.n1 + 2 * NG - 1 - i1 : i1);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      const int64_t p = col + nc * wp[NG + j];
+      R up = ld(su + p + k);
+      R um = refl ? ld(su + rcol + nc * wh[j]) : ld(su + p - k);
+      a0[j] = fma(w[k], up, a0[j]);
+      a0[j] = fma(w[NG + k], um, a0[j]);
+    }
+  }
+  // theta: reflections through the axis, again with phi + pi.
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+    const int ip = i1 + k, im = i1 - k;
+    const bool rp = ip >= g.n1 + NG, rm = im < NG;
+    const int cp = i0 + s0 * (rp ? 2 * g.n1 + 2 * NG - 1 - ip : ip);
+    const int cm = i0 + s0 * (rm ? 2 * NG - 1 - im : im);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      R up = ld(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
+      R um = ld(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
+      a1[j] = k == 1 ? w[2 * NG + k] * up : fma(w[2 * NG + k], up, a1[j]);
+      a1[j] = fma(w[3 * NG + k], um, a1[j]);
+    }
+  }
+  // phi: periodic.
+#pragma unroll
+  for (int k = 1; k <= NG; k++) {
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      R sp = ld(su + col + nc * wp[NG + j + k]);
+      R sm = ld(su + col + nc * wp[NG + j - k]);
+      a0[j] = fma(w[4 * NG + k], sp + sm, a0[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < ZC; j++)
+    out[j] = add_source(a0[j] + a1[j], u0[j], al[j], bc[j], lin);
+}
+
+// phi index into [NG, NG+n2) by adding or subtracting periods (offsets are a
+// few planes, so this is one or two compare-and-adds, no division).
+template <int NG>
+__device__ __forceinline__ int wrap_plane(const Geo &g, int z) {
+  while (z < NG) z += g.n2;
+  while (z >= NG + g.n2) z -= g.n2;
+  return z;
+}
+
+// Plane tables of one thread: wp[] = wrapped phi planes z0-NG .. z0+ZC-1+NG
+// (planes past the last one are clamped so that loads stay in range), wh[] =
+// the plane at phi + pi of each of the ZC planes.
+template <int NG, int ZC>
+__device__ __forceinline__ void plane_tables(const Geo &g, int z0, int (&wp)[ZC + 2 * NG],
+                                             int (&wh)[ZC]) {
+  const int last = NG + g.n2 - 1;
+#pragma unroll
+  for (int j = 0; j < ZC + 2 * NG; j++) {
+    int z = min(z0 - NG + j, last + NG);
+    wp[j] = wrap_plane<NG>(g, z);
+  }
+#pragma unroll
+  for (int j = 0; j < ZC; j++) wh[j] = wrap_plane<NG>(g, min(z0 + j, last) + g.n2 / 2);
+}
+
+template <typename R, int KIND>
+__device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
+                                               R ku, R kv) {
+  if (KIND == STAGE_FIRST) {
+    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    a.au[p] = fma(a.wb, ku, yu);
+    a.av[p] = fma(a.wb, kv, yv);
+    a.ou[p] = fma(a.wa, ku, yu);
+    a.ov[p] = fma(a.wa, kv, yv);
+  } else if (KIND == STAGE_MID) {
+    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    a.au[p] = fma(a.wb, ku, a.au[p]);
+    a.av[p] = fma(a.wb, kv, a.av[p]);
+    a.ou[p] = fma(a.wa, ku, yu);
+    a.ov[p] = fma(a.wa, kv, yv);
+  } else if (KIND == STAGE_LAST) {
+    a.ou[p] = fma(a.wb, ku, a.au[p]);
+    a.ov[p] = fma(a.wb, kv, a.av[p]);
+  } else {
+    a.ou[p] = ku;
+    a.ov[p] = kv;
+  }
+}
+
+// One work item of the curvilinear stage kernel: column e of the evolved
+// points (interior plus the outer shell i0 >= n0+ng), counted i0 fastest, on
+// ZC consecutive phi planes from z0.
+template <typename R, int NG, int KIND, int ZC>
+__device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R> &a,
+                                                 int e, int z0) {
+  const int ne0 = g.n0 + NG;
+  const int i0 = e % ne0 + NG, i1 = e / ne0 + NG;
+  const int col = i0 + g.s0 * i1;
+  const int nc = g.ncol;
+  const int zend = NG + g.n2;
+  if (i0 >= g.n0 + NG) {
+    // Radiation condition, df/dt = -c (d_r f + f/r), d_r from the
+    // second-order backward difference along xx0.
+    R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
+      rinv = ld(a.col.somm + 2 * nc + col);
+#pragma unroll
+    for (int j = 0; j < ZC; j++) {
+      if (z0 + j >= zend) break;
+      int64_t p = col + (int64_t)nc * (z0 + j);
+      R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
+      R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+      R du = fma(R(3), u0, fma(R(-4), u1, u2));
+      R dv = fma(R(3), v0, fma(R(-4), v1, v2));
+      R ku = -c * fma(kdb, du, rinv * u0);
+      R kv = -c * fma(kdb, dv, rinv * v0);
+      if (a.lin) {
+        ku += ld(a.fu + p);
+        kv += ld(a.bc2 + p);
+      }
+      stage_epilogue<R, KIND>(a, p, ku, kv);
+    }
+    return;
+  }
+  R w[5 * NG + 1];
+#pragma unroll
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+  int wp[ZC + 2 * NG], wh[ZC];
+  plane_tables<NG, ZC>(g, z0, wp, wh);
+  R u0[ZC], v0[ZC], al[ZC], bc[ZC], kv[ZC];
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    int64_t p = col + (int64_t)nc * wp[NG + j];
+    u0[j] = ld(a.su + p);
+    v0[j] = ld(a.sv + p);
+    al[j] = ld(a.alpha + p);
+    bc[j] = ld(a.bc2 + p);
+  }
+  // Operands of the RK4 update, loaded before any store so that the loads
+  // overlap the stencil's.
+  R yb[2][ZC], ac[2][ZC], fu[ZC];
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    int64_t p = col + (int64_t)nc * wp[NG + j];
+    if (KIND == STAGE_FIRST || KIND == STAGE_MID) {
+      yb[0][j] = ld(a.bu + p);
+      yb[1][j] = ld(a.bv + p);
+    }
+    if (KIND == STAGE_MID || KIND == STAGE_LAST) {
+      ac[0][j] = a.au[p];
+      ac[1][j] = a.av[p];
+    }
+    fu[j] = a.lin ? ld(a.fu + p) : R(0);
+  }
+  curvi_operator<R, NG, ZC>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv,
+                            a.lin);
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    if (z0 + j >= zend) break;
+    int64_t p = col + (int64_t)nc * (z0 + j);
+    R ku = fma(-a.eta, u0[j], v0[j]) + fu[j];
+    if (KIND == STAGE_FIRST) {
+      a.au[p] = fma(a.wb, ku, yb[0][j]);
+      a.av[p] = fma(a.wb, kv[j], yb[1][j]);
+      a.ou[p] = fma(a.wa, ku, yb[0][j]);
+      a.ov[p] = fma(a.wa, kv[j], yb[1][j]);
+    } else if (KIND == STAGE_MID) {
+      a.au[p] = fma(a.wb, ku, ac[0][j]);
+      a.av[p] = fma(a.wb, kv[j], ac[1][j]);
+      a.ou[p] = fma(a.wa, ku, yb[0][j]);
+      a.ov[p] = fma(a.wa, kv[j], yb[1][j]);
+    } else if (KIND == STAGE_LAST) {
+      a.ou[p] = fma(a.wb, ku, ac[0][j]);
+      a.ov[p] = fma(a.wb, kv[j], ac[1][j]);
+    } else {
+      a.ou[p] = ku;
+      a.ov[p] = kv[j];
+    }
+  }
+}
+
+
+// Deterministic block sum of two FP64 values (warp shuffles in a fixed
+// pattern, then the warps in order).
+__device__ __forceinline__ void block_sum2(double &x, double &y, double *out) {
+  __shared__ double sx[32], sy[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sx[wid] = x;
+    sy[wid] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tx = 0.0, ty = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+      tx += sx[i];
+      ty += sy[i];
+    }
+    out[0] = tx;
+    out[1] = ty;
+  }
+}
+
+// Residual of the curvilinear operator at one interior column e (counted i0
+// fastest over the n0 x n1 interior columns) on planes [z0, z1): H at each
+// point (written to h_out if given) and the sums of H^2 wt and wt with the
+// column's norm weight wt.
+template <typename R, int NG>
+__device__ __forceinline__ void residual_curvi_item(
+    const Geo &g, const R *__restrict__ su, const R *__restrict__ alpha,
+    const R *__restrict__ bc2, const ColumnSet<R> &col_set, double wt, int e,
+    int z0, int z1, int lin, double *h_out, double &num, double &den) {
+  const int i0 = e % g.n0 + NG, i1 = e / g.n0 + NG;
+  const int col = i0 + g.s0 * i1;
+  const int nc = g.ncol;
+  R w[5 * NG + 1];
+#pragma unroll
+  for (int j = 0; j < 5 * NG + 1; j++)
+    w[j] = ld(col_set.coef + (int64_t)j * nc + col);
+  R c2inv = ld(col_set.c2inv + col);
+  for (int i2 = z0; i2 < z1; i2++) {
+    int wp[1 + 2 * NG], wh[1];
+    plane_tables<NG, 1>(g, i2, wp, wh);
+    int64_t p = col + (int64_t)nc * i2;
+    R u0[1] = {ld(su + p)}, al[1] = {ld(alpha + p)}, bc[1] = {ld(bc2 + p)}, op[1];
+    curvi_operator<R, NG, 1>(g, su, w, col, i0, i1, wp, wh, u0, al, bc, op, lin);
+    double H = (double)(op[0] * c2inv);
+    if (h_out) h_out[p] = H;
+    num += H * H * wt;
+    den += wt;
+  }
+}
+
+}  // namespace dev
+}  // namespace nrr

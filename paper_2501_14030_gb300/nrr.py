@@ -30,7 +30,9 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
-           "nrr_autotune", "nrr_last_error",
+           "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
+           "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
+           "nrr_batch_autotune", "nrr_last_error",
            "nrr_version")
 
 
@@ -99,6 +101,15 @@ def lib() -> C.CDLL:
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
         "nrr_set_launch": [V, I, I],
         "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
+        "nrr_batch_create": [I, C.POINTER(GridDesc), C.POINTER(C.c_int),
+                             C.POINTER(C.POINTER(Puncture)), I, V,
+                             C.POINTER(V)],
+        "nrr_batch_destroy": [V],
+        "nrr_batch_info": [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "nrr_batch_relax": [V, C.POINTER(RelaxOpts), C.POINTER(RelaxResult),
+                            C.POINTER(RelaxResult)],
+        "nrr_batch_get_u": [V, I, V, I],
+        "nrr_batch_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
     }
@@ -295,3 +306,78 @@ class Grid:
     def step(self, steps: int, dt: float, eta: float, mode="fp64"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         _check(lib().nrr_step(self._h, m, dt, eta, int(steps)))
+
+
+def _result(r: RelaxResult, st: int | None = None) -> dict:
+    return {"iters": r.iters, "outer_iters": r.outer_iters,
+            "norm": r.final_norm, "seconds": r.seconds,
+            "status": r.status if st is None else st}
+
+
+class Batch:
+    """Independent solves of uneven sizes relaxed together on the current
+    CUDA device (one graph launch per relaxation)."""
+
+    def __init__(self, descs, punctures, with_fp64: bool = False,
+                 stream=None):
+        import torch
+        n = len(descs)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.descs = [dict(d) for d in descs]
+        self.n = n
+        self.shapes = [workloads.padded_shape(d) for d in descs]
+        d_arr = (GridDesc * n)(*[make_desc(d) for d in descs])
+        self._punc = [make_punctures(p) for p in punctures]
+        np_arr = (C.c_int * n)(*[len(p) for p in punctures])
+        pp = (C.POINTER(Puncture) * n)(*[C.cast(a, C.POINTER(Puncture))
+                                         for a in self._punc])
+        h = C.c_void_p()
+        _check(lib().nrr_batch_create(n, d_arr, np_arr, pp, int(with_fp64),
+                                      C.c_void_p(stream.cuda_stream),
+                                      C.byref(h)))
+        self._h = h
+        tp, ip = C.c_int64(), C.c_int64()
+        _check(lib().nrr_batch_info(h, C.byref(tp), C.byref(ip)))
+        self.total_points, self.interior_points = tp.value, ip.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def relax(self, mode="fp32_dc", tol=1e-10, max_iters=1_000_000,
+              check_every=50, cfl=0.5, eta=0.0, r_int=100.0, initial=None,
+              timeout_ms=0, inner_steps=0, raise_on_error=True):
+        """Returns (per-solve result dicts, total result dict)."""
+        o = RelaxOpts()
+        _check(lib().nrr_default_opts(C.byref(o)))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.tol, o.max_iters, o.check_every = tol, max_iters, check_every
+        o.cfl, o.eta, o.r_int = cfl, eta, r_int
+        o.initial = INIT_ZERO if initial is None else int(initial)
+        o.timeout_ms, o.inner_steps = timeout_ms, inner_steps
+        per = (RelaxResult * self.n)()
+        tot = RelaxResult()
+        st = lib().nrr_batch_relax(self._h, C.byref(o), per, C.byref(tot))
+        if raise_on_error:
+            _check(st)
+        return [_result(r) for r in per], _result(tot, st)
+
+    def get_u(self, i: int, out):
+        p, on_dev = _ptr(out)
+        _check(lib().nrr_batch_get_u(self._h, int(i), p, on_dev))
+
+    def autotune(self, mode="fp32_dc", trial_steps: int = 5):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        zc, ms = C.c_int(), C.c_double()
+        _check(lib().nrr_batch_autotune(self._h, m, int(trial_steps),
+                                        C.byref(zc), C.byref(ms)))
+        return zc.value, ms.value
