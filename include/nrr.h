@@ -278,6 +278,15 @@ nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device);
 nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
                               int *best_zc, double *best_ms_per_launch);
 
+/* BF16 tensor-core GEMM used by the surrogate network (tcgen05 MMA with an
+ * FP32 accumulator in tensor memory, TMA-fed 128-byte-swizzled tiles):
+ * D[m][n] = sum_k A[m][k] B[n][k] for row-major BF16 A (M x K) and B
+ * (N x K) -- both K-major -- and row-major FP32 D (M x N).  All device
+ * pointers, 16-byte aligned; M % 128 == 0, N % 64 == 0, K % 64 == 0.
+ * Synchronous on `stream`; NRR_ERR_TIMEOUT if a pipeline wait expired. */
+nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
+                            int N, int K, void *stream);
+
 /* Cumulative number of kernels this library has launched in this process
  * (graph replays count every kernel node). */
 int64_t nrr_kernel_launches(void);

@@ -1,0 +1,385 @@
+// nrr_gemm.cu -- BF16 tensor-core GEMM on sm_103a (tcgen05 + TMA + TMEM) for
+// the surrogate network: D[M,N] (FP32) = sum_k A[m,k] B[n,k], both operands
+// K-major BF16 in global memory.
+//
+// One CTA computes a 128 x BN tile.  Warp 0 (one lane) streams 128x64 and
+// BNx64 operand tiles into a 4-stage shared-memory ring with TMA
+// (128-byte swizzle); warp 1 (one lane) issues tcgen05.mma (M=128, N=BN,
+// K=16 per instruction) into an FP32 accumulator in tensor memory and
+// releases each stage with tcgen05.commit; then all four warps read the
+// accumulator back with tcgen05.ld (warp w owns rows 32w..32w+31) and store
+// it.  Every mbarrier wait is bounded: on expiry the kernel records an error,
+// skips the remaining work, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/nrr.h"
+#include "nrr_internal.h"
+
+namespace nrr {
+
+namespace {
+
+constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr long long kWaitLimit = 1ll << 22;  // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on one phase of an mbarrier; false (and *err set) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          int *err, int code) {
+  for (long long i = 0; i < kWaitLimit; i++)
+    if (mbar_try(bar, parity)) return true;
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
+                                            uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 64 BF16 (128 B), 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major.
+template <int N>
+__device__ __forceinline__ uint32_t mma_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap map_a,
+                        const __grid_constant__ CUtensorMap map_b, float *D,
+                        int M, int N, int K, int ldd, int *err) {
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + STAGES * A_BYTES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *done = empty + STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *issued = reinterpret_cast<int *>(tmem_slot + 1);  // k-blocks loaded
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_addr(tmem_slot)),
+        "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; kb++) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES &&
+          !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err, 1))
+        break;
+      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      tma_load_2d(sA + s * A_BYTES, &map_a, &full[s], kb * BK, m0);
+      tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], kb * BK, n0);
+      *issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = mma_idesc<BN>();
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; kb++) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, err, 2)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = sw128_desc(smem_addr(sA + s * A_BYTES));
+      const uint64_t db = sw128_desc(smem_addr(sB + s * B_BYTES));
+#pragma unroll
+      for (int k = 0; k < BK / 16; k++) {
+        // +32 bytes along K per instruction (encoded >> 4)
+        const uint64_t off = (uint64_t)(k * 2);
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                tmem),
+            "l"(da + off), "l"(db + off), "r"(idesc), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+          "[%0];" ::"r"(smem_addr(&empty[s]))
+          : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+        "[%0];" ::"r"(smem_addr(done))
+        : "memory");
+  }
+  __syncwarp();
+
+  // Epilogue: accumulator rows 32*warp + lane, BN columns.
+  const bool ready = mbar_wait(done, 0, err, 3);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // tcgen05.ld is warp-collective: decide per warp, not per thread
+  if (__all_sync(0xffffffffu, ready && *((volatile int *)err) == 0)) {
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+    for (int c = 0; c < BN; c += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, "
+          "%7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+            "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+            "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15])
+          : "r"(taddr + (uint32_t)c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        float4 *dst = reinterpret_cast<float4 *>(D + (int64_t)row * ldd + n0 + c);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                               __uint_as_float(r[4 * q + 2]),
+                               __uint_as_float(r[4 * q + 3]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // No copy may still be landing in this CTA's shared memory when it exits:
+    // wait (bounded) for the last phase issued on every stage.
+    const int n_iss = *issued;
+    for (int kb = n_iss - STAGES < 0 ? 0 : n_iss - STAGES; kb < n_iss; kb++)
+      mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err, 4);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(BN));
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
+                              void *, const cuuint64_t *, const cuuint64_t *,
+                              const cuuint32_t *, const cuuint32_t *,
+                              CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a row-major [rows][cols] BF16 matrix read in tiles of
+// box_rows x 64 with 128-byte swizzle.
+bool make_map(CUtensorMap *m, const void *base, int rows, int cols,
+              int box_rows) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
+             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct MapKey {
+  const void *p;
+  int rows, cols, box;
+  bool operator<(const MapKey &o) const {
+    return std::tie(p, rows, cols, box) < std::tie(o.p, o.rows, o.cols, o.box);
+  }
+};
+std::mutex g_map_mu;
+std::map<MapKey, CUtensorMap> g_maps;
+
+bool cached_map(CUtensorMap *out, const void *base, int rows, int cols,
+                int box) {
+  std::lock_guard<std::mutex> lock(g_map_mu);
+  MapKey k{base, rows, cols, box};
+  auto it = g_maps.find(k);
+  if (it != g_maps.end()) {
+    *out = it->second;
+    return true;
+  }
+  CUtensorMap m;
+  if (!make_map(&m, base, rows, cols, box)) return false;
+  g_maps[k] = m;
+  *out = m;
+  return true;
+}
+
+int *g_err = nullptr;
+std::once_flag g_err_once;
+
+template <int BN>
+cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, float *D,
+                        int M, int N, int K, int ldd, cudaStream_t st) {
+  constexpr int smem = STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(N / BN, M / BM);
+  gemm_bf16_tn_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, D, M, N, K, ldd, g_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int *gemm_error_flag() {
+  std::call_once(g_err_once, [] {
+    if (cudaMalloc(&g_err, sizeof(int)) == cudaSuccess) cudaMemset(g_err, 0, sizeof(int));
+  });
+  return g_err;
+}
+
+nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
+                        int K, int ldd, cudaStream_t st, char *msg, int msglen) {
+  if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || M % BM || K % BK ||
+      (N % 64) || ldd < N || (ldd % 4) ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
+      (reinterpret_cast<uintptr_t>(D) & 15)) {
+    snprintf(msg, msglen,
+             "gemm: need M %% 128 == 0, N %% 64 == 0, K %% 64 == 0, ldd >= N, "
+             "ldd %% 4 == 0 and 16-byte aligned operands (M=%d N=%d K=%d ldd=%d)",
+             M, N, K, ldd);
+    return NRR_ERR_INVALID_ARG;
+  }
+  if (!gemm_error_flag()) {
+    snprintf(msg, msglen, "gemm: error flag allocation failed");
+    return NRR_ERR_OOM;
+  }
+  const int bn = (N % 128 == 0) ? 128 : 64;
+  CUtensorMap ma, mb;
+  if (!cached_map(&ma, A, M, K, BM) || !cached_map(&mb, B, N, K, bn)) {
+    snprintf(msg, msglen, "gemm: tensor map encoding failed");
+    return NRR_ERR_CUDA;
+  }
+  cudaError_t e = bn == 128 ? launch_gemm<128>(ma, mb, D, M, N, K, ldd, st)
+                            : launch_gemm<64>(ma, mb, D, M, N, K, ldd, st);
+  if (e != cudaSuccess) {
+    snprintf(msg, msglen, "gemm launch: %s", cudaGetErrorString(e));
+    return NRR_ERR_CUDA;
+  }
+  return NRR_OK;
+}
+
+nrr_status gemm_check_error(cudaStream_t st, char *msg, int msglen) {
+  int h = 0;
+  int *f = gemm_error_flag();
+  if (!f) return NRR_OK;
+  if (cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    snprintf(msg, msglen, "gemm: status read-back failed");
+    return NRR_ERR_CUDA;
+  }
+  if (h) {
+    snprintf(msg, msglen, "gemm: a pipeline wait expired (code %d)", h);
+    cudaMemsetAsync(f, 0, sizeof(int), st);
+    return NRR_ERR_TIMEOUT;
+  }
+  return NRR_OK;
+}
+
+}  // namespace nrr
+
+extern "C" nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D,
+                                       int M, int N, int K, void *stream) {
+  char msg[256] = {0};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  nrr_status s = nrr::gemm_bf16_tn(A, B, D, M, N, K, N, st, msg, sizeof msg);
+  if (s != NRR_OK) {
+    nrr::set_last_error(msg);
+    return s;
+  }
+  s = nrr::gemm_check_error(st, msg, sizeof msg);
+  if (s != NRR_OK) nrr::set_last_error(msg);
+  return s;
+}

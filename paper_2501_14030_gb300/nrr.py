@@ -32,7 +32,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
-           "nrr_batch_autotune", "nrr_last_error",
+           "nrr_batch_autotune", "nrr_gemm_bf16_tn", "nrr_last_error",
            "nrr_version")
 
 
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
                             C.POINTER(RelaxResult)],
         "nrr_batch_get_u": [V, I, V, I],
         "nrr_batch_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
+        "nrr_gemm_bf16_tn": [V, V, V, I, I, I, V],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
     }
@@ -175,6 +176,19 @@ def residual_noalloc(desc: dict, punctures, u, norm_out, h_out=None,
     _check(lib().nrr_residual_noalloc(
         C.byref(d), len(punctures), arr, C.c_void_p(u.data_ptr()), r_int,
         C.c_void_p(norm_out.data_ptr()), h, C.c_void_p(stream.cuda_stream)))
+
+
+def gemm_bf16_tn(A, B, D, stream=None) -> None:
+    """D (float32, M x N) = A (bf16, M x K) @ B (bf16, N x K)^T on device."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().nrr_gemm_bf16_tn(C.c_void_p(A.data_ptr()),
+                                  C.c_void_p(B.data_ptr()),
+                                  C.c_void_p(D.data_ptr()), M, N, K,
+                                  C.c_void_p(stream.cuda_stream)))
 
 
 def kernel_launches() -> int:

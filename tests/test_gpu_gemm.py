@@ -1,0 +1,46 @@
+"""The tcgen05 BF16 GEMM against an FP64 product of the same BF16 operands."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2501_14030_gb300 import nrr
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round float32 to the nearest BF16 (ties to even); returns float32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return (u.astype(np.uint32) << 16).view(np.float32)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (128, 128, 128),
+                                   (256, 512, 512), (384, 192, 320),
+                                   (256, 16384, 512), (512, 64, 256)])
+def test_gemm_matches_fp64_product(gpu, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = bf16_round(rng.standard_normal((M, K)).astype(np.float32))
+    B = bf16_round(rng.standard_normal((N, K)).astype(np.float32))
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    nrr.gemm_bf16_tn(Ad, Bd, D)
+    torch.cuda.synchronize()
+    out = D.cpu().numpy().astype(np.float64)
+    # FP32 accumulation of K exact BF16 products: |err| <= K eps32 sum|a b|
+    bound = K * 6e-8 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T)
+    assert np.all(np.isfinite(out))
+    assert np.all(np.abs(out - ref) <= bound + 1e-30)
+
+
+def test_gemm_rejects_bad_shapes(gpu):
+    A = torch.zeros((100, 64), dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros((64, 64), dtype=torch.bfloat16, device="cuda")
+    D = torch.zeros((100, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(nrr.NrrError) as e:
+        nrr.gemm_bf16_tn(A, B, D)
+    assert e.value.status == nrr.ERR_INVALID_ARG
