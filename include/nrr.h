@@ -287,6 +287,50 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
 nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
                             int N, int K, void *stream);
 
+/* ---- Warm-start surrogate (trained on solutions the solver generates) ---- */
+typedef struct nrr_surrogate nrr_surrogate;
+
+/* A multilayer perceptron n_in -> hidden x depth (GELU) -> n_out (linear)
+ * with BF16 weights and activations, FP32 accumulation on the tensor cores
+ * and FP32 master weights (AdamW).  init_params: host array in the logical
+ * packed layout -- for each layer l, W_l as [out][in] row-major then b_l
+ * [out] -- of nrr_surrogate_num_params() floats (the caller draws them).
+ * Limits: n_in <= 64, hidden and n_out multiples of 128, batch a multiple
+ * of 128.  Output scaling starts as the identity (mean 0, std 1). */
+nrr_status nrr_surrogate_create(int n_in, int hidden, int depth, int n_out,
+                                int batch, const float *init_params,
+                                void *stream, nrr_surrogate **out);
+nrr_status nrr_surrogate_destroy(nrr_surrogate *s);
+int64_t nrr_surrogate_num_params(const nrr_surrogate *s);
+
+/* Sets the output scaling to the per-output mean and standard deviation of
+ * Y (device, [n][n_out] FP32); the network learns (Y - mean)/std. */
+nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
+                                     int64_t n);
+
+/* `steps` AdamW steps (beta 0.9/0.999, eps 1e-8, decoupled weight decay on
+ * weights) on minibatches of `batch` rows: step t uses the sample indices
+ * order[t*batch .. (t+1)*batch) (device int32; the caller draws the
+ * shuffles).  X: device [n][n_in], Y: device [n][n_out].  loss_out
+ * (nullable, host, steps floats) receives each step's mean squared error of
+ * the scaled outputs. */
+nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
+                               int64_t n, const int32_t *order, int64_t steps,
+                               double lr, double weight_decay, float *loss_out);
+
+/* out (device [n][n_out]) = network(X) mapped back through the scaling. */
+nrr_status nrr_surrogate_predict(nrr_surrogate *s, const float *X, int64_t n,
+                                 float *out);
+
+/* Loss and parameter gradients of one minibatch (the first `batch` rows of
+ * X, Y; device) without updating: grads is a host array in the logical
+ * packed layout.  For gradient checks. */
+nrr_status nrr_surrogate_gradients(nrr_surrogate *s, const float *X,
+                                   const float *Y, float *grads, double *loss);
+
+/* Current parameters in the logical packed layout (host). */
+nrr_status nrr_surrogate_get_params(nrr_surrogate *s, float *params);
+
 /* Cumulative number of kernels this library has launched in this process
  * (graph replays count every kernel node). */
 int64_t nrr_kernel_launches(void);

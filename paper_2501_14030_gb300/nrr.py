@@ -32,7 +32,11 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
-           "nrr_batch_autotune", "nrr_gemm_bf16_tn", "nrr_last_error",
+           "nrr_batch_autotune", "nrr_gemm_bf16_tn", "nrr_surrogate_create",
+           "nrr_surrogate_destroy", "nrr_surrogate_num_params",
+           "nrr_surrogate_fit_scaling", "nrr_surrogate_train",
+           "nrr_surrogate_predict", "nrr_surrogate_gradients",
+           "nrr_surrogate_get_params", "nrr_last_error",
            "nrr_version")
 
 
@@ -111,6 +115,15 @@ def lib() -> C.CDLL:
         "nrr_batch_get_u": [V, I, V, I],
         "nrr_batch_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
         "nrr_gemm_bf16_tn": [V, V, V, I, I, I, V],
+        "nrr_surrogate_create": [I, I, I, I, I, C.POINTER(C.c_float), V,
+                                 C.POINTER(V)],
+        "nrr_surrogate_destroy": [V],
+        "nrr_surrogate_fit_scaling": [V, V, C.c_int64],
+        "nrr_surrogate_train": [V, V, V, C.c_int64, V, C.c_int64, C.c_double,
+                                C.c_double, C.POINTER(C.c_float)],
+        "nrr_surrogate_predict": [V, V, C.c_int64, V],
+        "nrr_surrogate_gradients": [V, V, V, C.POINTER(C.c_float), D],
+        "nrr_surrogate_get_params": [V, C.POINTER(C.c_float)],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
     }
@@ -120,6 +133,8 @@ def lib() -> C.CDLL:
         fn.restype = C.c_int
     L.nrr_last_error.restype = C.c_char_p
     L.nrr_last_error.argtypes = []
+    L.nrr_surrogate_num_params.restype = C.c_int64
+    L.nrr_surrogate_num_params.argtypes = [V]
     L.nrr_kernel_launches.restype = C.c_int64
     L.nrr_kernel_launches.argtypes = []
     L.nrr_version.restype = C.c_char_p
@@ -395,3 +410,68 @@ class Batch:
         _check(lib().nrr_batch_autotune(self._h, m, int(trial_steps),
                                         C.byref(zc), C.byref(ms)))
         return zc.value, ms.value
+
+
+class Surrogate:
+    """The warm-start network on the current CUDA device."""
+
+    def __init__(self, dims, init_params: np.ndarray, batch: int = 256,
+                 stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.dims = list(dims)
+        n_in, hidden, depth, n_out = dims[0], dims[1], len(dims) - 2, dims[-1]
+        self.batch = batch
+        p = np.ascontiguousarray(init_params, dtype=np.float32)
+        h = C.c_void_p()
+        _check(lib().nrr_surrogate_create(
+            n_in, hidden, depth, n_out, batch,
+            p.ctypes.data_as(C.POINTER(C.c_float)),
+            C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.num_params = int(lib().nrr_surrogate_num_params(h))
+        assert self.num_params == p.size
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrr_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fit_scaling(self, Y):
+        _check(lib().nrr_surrogate_fit_scaling(self._h, C.c_void_p(Y.data_ptr()),
+                                               Y.shape[0]))
+
+    def train(self, X, Y, order, steps: int, lr: float = 1e-3,
+              weight_decay: float = 0.0) -> np.ndarray:
+        losses = np.zeros(steps, dtype=np.float32)
+        _check(lib().nrr_surrogate_train(
+            self._h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+            X.shape[0], C.c_void_p(order.data_ptr()), steps, lr, weight_decay,
+            losses.ctypes.data_as(C.POINTER(C.c_float))))
+        return losses
+
+    def predict(self, X, out):
+        _check(lib().nrr_surrogate_predict(self._h, C.c_void_p(X.data_ptr()),
+                                           X.shape[0], C.c_void_p(out.data_ptr())))
+
+    def gradients(self, X, Y):
+        g = np.zeros(self.num_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().nrr_surrogate_gradients(
+            self._h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+            g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return loss.value, g
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().nrr_surrogate_get_params(
+            self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p

@@ -142,3 +142,44 @@ def batch_parameters(count: int, seed: int) -> list[dict]:
                     "n": n, "punctures": punct,
                     "desc": grid_desc("sinhsymtp", n, 8, bscale=d / 2)})
     return out
+
+
+def mlp_dims(n_in: int = 12, hidden: int = 512, depth: int = 4,
+             n_out: int = 64 * 32 * 8) -> list[int]:
+    return [n_in] + [hidden] * depth + [n_out]
+
+
+def mlp_init_params(dims, seed: int) -> np.ndarray:
+    """Seeded initial parameters in the logical packed layout (per layer W
+    [out][in] then b [out]): normal weights with variance 2/in on hidden
+    layers and 1/in on the output layer, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (din, dout) in enumerate(zip(dims[:-1], dims[1:])):
+        scale = np.sqrt((1.0 if l == len(dims) - 2 else 2.0) / din)
+        parts.append((rng.standard_normal((dout, din)) * scale).ravel())
+        parts.append(np.zeros(dout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_inputs(params: list[dict]) -> np.ndarray:
+    """The 12 network inputs of each parameter draw, scaled to [-1, 1]:
+    q in [1,8], d in [6,16], P (|P| <= 0.15), chi1, chi2 (|chi| <= 0.8),
+    total mass (1)."""
+    rows = []
+    for p in params:
+        rows.append([(p["q"] - 4.5) / 3.5, (p["d"] - 11.0) / 5.0,
+                     *(c / 0.15 for c in p["P"]), *(c / 0.8 for c in p["chi1"]),
+                     *(c / 0.8 for c in p["chi2"]), 1.0])
+    return np.asarray(rows, dtype=np.float32)
+
+
+def minibatch_order(n: int, batch: int, steps: int, seed: int) -> np.ndarray:
+    """Sample indices for `steps` minibatches: concatenated seeded
+    permutations of range(n), cut into batches."""
+    rng = np.random.default_rng(seed)
+    need = steps * batch
+    out = []
+    while sum(len(o) for o in out) < need:
+        out.append(rng.permutation(n))
+    return np.concatenate(out)[:need].astype(np.int32)
