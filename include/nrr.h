@@ -273,6 +273,16 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
 /* Copies u of solve i out (padded FP64 layout, inner ghosts filled). */
 nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device);
 
+/* Sets u of solve i (padded FP64 layout; inner ghosts ignored) for a warm
+ * start: a following nrr_batch_relax with initial = NRR_INIT_DEVICE starts
+ * from the u of every solve with v = eta u. */
+nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device);
+
+/* Interior u of every solve as FP32, dst (device) [n][n0*n1*n2] with i0
+ * fastest; all solves must have the same size.  Training targets of the
+ * surrogate. */
+nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
+
 /* Autotuner for the batch's stage launch shape (phi planes per thread),
  * timed over all solves; keeps the fastest for later relaxations. */
 nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
@@ -330,6 +340,15 @@ nrr_status nrr_surrogate_gradients(nrr_surrogate *s, const float *X,
 
 /* Current parameters in the logical packed layout (host). */
 nrr_status nrr_surrogate_get_params(nrr_surrogate *s, float *params);
+
+/* Warm-start prolongation: u on the fine grid (device, padded FP64, every
+ * point written) interpolated trilinearly in the coordinates xx from the
+ * coarse interior values uc (device, [n2][n1][n0] FP32) of a grid of the
+ * same curvilinear family and parameters; coarse neighbours across the inner
+ * boundary come from their images, beyond the outer boundary the last
+ * interior plane is used.  Synchronous on `stream`. */
+nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
+                       const nrr_grid_desc *fine, double *uf, void *stream);
 
 /* Cumulative number of kernels this library has launched in this process
  * (graph replays count every kernel node). */

@@ -291,6 +291,29 @@ __global__ void batch_update_kernel(const SolveDev *__restrict__ sds,
   sd.v[p] += (double)sd.w[p];
 }
 
+// dst[s][interior point] = (float) u of solve s (all solves of one size).
+__global__ void batch_interior_kernel(const SolveDev *__restrict__ sds, int n,
+                                      int64_t per, float *dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * per) return;
+  const int s = (int)(i / per);
+  const int64_t q = i % per;
+  const Geo g = sds[s].g;
+  const int i0 = (int)(q % g.n0), i1 = (int)((q / g.n0) % g.n1),
+            i2 = (int)(q / ((int64_t)g.n0 * g.n1));
+  dst[i] = (float)sds[s].u[flat(g, i0 + g.ng, i1 + g.ng, i2 + g.ng)];
+}
+
+// v = eta u for every point of every solve (warm starts).
+__global__ void batch_warm_v_kernel(const SolveDev *__restrict__ sds,
+                                    const int2 *__restrict__ map) {
+  const int2 bm = map[blockIdx.x];
+  const SolveDev &sd = sds[bm.x];
+  const int64_t p = (int64_t)bm.y + threadIdx.x;
+  if (p >= sd.g.npts) return;
+  sd.v[p] = sd.eta * sd.u[p];
+}
+
 __global__ void batch_zero_kernel(const SolveDev *__restrict__ sds,
                                   const int2 *__restrict__ map) {
   const int2 bm = map[blockIdx.x];
@@ -773,8 +796,10 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
   if (!(o->tol > 0.0) || o->check_every < 1 || o->max_iters < 0 ||
       !(o->cfl > 0.0) || !(o->r_int > 0.0))
     return bfail(NRR_ERR_INVALID_ARG, "invalid relax options");
-  if (o->initial != NRR_INIT_ZERO && o->initial != NRR_INIT_CURRENT)
-    return bfail(NRR_ERR_INVALID_ARG, "batches start from zero or the current state");
+  if (o->initial != NRR_INIT_ZERO && o->initial != NRR_INIT_CURRENT &&
+      o->initial != NRR_INIT_DEVICE)
+    return bfail(NRR_ERR_INVALID_ARG,
+                 "batches start from zero, the current state or set u (v = eta u)");
   auto t0 = std::chrono::steady_clock::now();
   BTRY(bbegin(b));
   const int every = (int)(o->mode == NRR_FP32_DC && o->inner_steps > 0
@@ -789,6 +814,8 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
                         cudaMemcpyHostToDevice, b->stream));
   if (o->initial == NRR_INIT_ZERO)
     batch_zero_kernel<<<b->nblk_pts, 256, 0, b->stream>>>(b->d_sd, b->d_map_pts);
+  else if (o->initial == NRR_INIT_DEVICE)
+    batch_warm_v_kernel<<<b->nblk_pts, 256, 0, b->stream>>>(b->d_sd, b->d_map_pts);
   std::vector<int> act(b->n, 1);
   BCUDA(cudaMemcpyAsync(b->d_active, act.data(), b->n * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream));
@@ -862,6 +889,35 @@ nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device) {
   BCUDA(cudaMemcpyAsync(dst, b->host_sd[i].u, (size_t)g.npts * sizeof(double),
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         b->stream));
+  BCUDA(cudaStreamSynchronize(b->stream));
+  return NRR_OK;
+}
+
+nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device) {
+  if (!b || !u) return bfail(NRR_ERR_INVALID_ARG, "null argument");
+  if (i < 0 || i >= b->n) return bfail(NRR_ERR_INVALID_ARG, "solve %d out of range", i);
+  BTRY(bbegin(b));
+  BCUDA(cudaMemcpyAsync(b->host_sd[i].u, u, (size_t)b->geos[i].npts * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        b->stream));
+  BCUDA(cudaStreamSynchronize(b->stream));
+  return NRR_OK;
+}
+
+nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst) {
+  if (!b || !dst) return bfail(NRR_ERR_INVALID_ARG, "null argument");
+  for (int s = 1; s < b->n; s++)
+    if (b->geos[s].n0 != b->geos[0].n0 || b->geos[s].n1 != b->geos[0].n1 ||
+        b->geos[s].n2 != b->geos[0].n2)
+      return bfail(NRR_ERR_INVALID_ARG, "solves differ in size");
+  BTRY(bbegin(b));
+  const Geo &g = b->geos[0];
+  const int64_t per = (int64_t)g.n0 * g.n1 * g.n2;
+  BCUDA(cudaMemcpyAsync(b->d_sd, b->host_sd.data(), b->n * sizeof(SolveDev),
+                        cudaMemcpyHostToDevice, b->stream));
+  batch_interior_kernel<<<(unsigned)((b->n * per + 255) / 256), 256, 0, b->stream>>>(
+      b->d_sd, b->n, per, dst);
+  BCUDA(cudaGetLastError());
   BCUDA(cudaStreamSynchronize(b->stream));
   return NRR_OK;
 }

@@ -36,7 +36,8 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_surrogate_destroy", "nrr_surrogate_num_params",
            "nrr_surrogate_fit_scaling", "nrr_surrogate_train",
            "nrr_surrogate_predict", "nrr_surrogate_gradients",
-           "nrr_surrogate_get_params", "nrr_last_error",
+           "nrr_surrogate_get_params", "nrr_batch_set_u",
+           "nrr_batch_get_interior", "nrr_prolong", "nrr_last_error",
            "nrr_version")
 
 
@@ -124,6 +125,9 @@ def lib() -> C.CDLL:
         "nrr_surrogate_predict": [V, V, C.c_int64, V],
         "nrr_surrogate_gradients": [V, V, V, C.POINTER(C.c_float), D],
         "nrr_surrogate_get_params": [V, C.POINTER(C.c_float)],
+        "nrr_batch_set_u": [V, I, V, I],
+        "nrr_batch_get_interior": [V, V],
+        "nrr_prolong": [C.POINTER(GridDesc), V, C.POINTER(GridDesc), V, V],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
     }
@@ -204,6 +208,18 @@ def gemm_bf16_tn(A, B, D, stream=None) -> None:
                                   C.c_void_p(B.data_ptr()),
                                   C.c_void_p(D.data_ptr()), M, N, K,
                                   C.c_void_p(stream.cuda_stream)))
+
+
+def prolong(coarse: dict, uc, fine: dict, uf, stream=None) -> None:
+    """Trilinear prolongation of coarse interior u (float32 tensor) onto the
+    padded fine grid (float64 tensor)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    dc, df = make_desc(coarse), make_desc(fine)
+    _check(lib().nrr_prolong(C.byref(dc), C.c_void_p(uc.data_ptr()), C.byref(df),
+                             C.c_void_p(uf.data_ptr()),
+                             C.c_void_p(stream.cuda_stream)))
 
 
 def kernel_launches() -> int:
@@ -403,6 +419,14 @@ class Batch:
     def get_u(self, i: int, out):
         p, on_dev = _ptr(out)
         _check(lib().nrr_batch_get_u(self._h, int(i), p, on_dev))
+
+    def set_u(self, i: int, u):
+        p, on_dev = _ptr(u)
+        _check(lib().nrr_batch_set_u(self._h, int(i), p, on_dev))
+
+    def get_interior(self, out):
+        """Interior u of every solve (equal sizes) into a float32 tensor."""
+        _check(lib().nrr_batch_get_interior(self._h, C.c_void_p(out.data_ptr())))
 
     def autotune(self, mode="fp32_dc", trial_steps: int = 5):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
