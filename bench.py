@@ -301,6 +301,8 @@ def run_ours(args):
     r32 = g.relax(mode="fp32", tol=1e-10, check_every=CHECK_EVERY,
                   max_iters=iters // max(1, args.steps), raise_on_error=False)
 
+    batch = None if args.no_batch else run_batch(args, nrr, W, torch)
+
     line = None
     if rank == 0:
         cpu = None
@@ -335,6 +337,7 @@ def run_ours(args):
                 "max_rel_diff_u_vs_fp64_solution": dc_err,
                 "fp32_stage_us_per_launch": ms32 * 1e3,
                 "fp32_stage_GBps_algorithmic": bytes32 / (ms32 * 1e-3) / 1e9},
+            "batch_512": batch,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -371,6 +374,142 @@ def run_profile_steps(args):
     return 0
 
 
+def run_batch(args, nrr, W, torch):
+    """The 512-solve parameter sweep (uneven SinhSymTP grids, order 8) as one
+    graph launch in defect-correction mode; returns a summary dict."""
+    import numpy as np
+    params = W.batch_parameters(512, 20250124)
+    descs = [p["desc"] for p in params]
+    b = nrr.Batch(descs, [p["punctures"] for p in params])
+    zc, ms = b.autotune("fp32_dc", 3)
+    b.relax(mode="fp32_dc", tol=1e-10, max_iters=100, raise_on_error=False)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    per, tot = b.relax(mode="fp32_dc", tol=1e-10, raise_on_error=False)
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    its = np.array([r["iters"] for r in per])
+    rhs = sum(4 * r["iters"] * int(np.prod(d["n"])) for r, d in zip(per, descs))
+    b.close()
+    return {"solves": len(descs), "converged": int(sum(r["status"] == 0 for r in per)),
+            "seconds": secs, "solves_per_s": len(descs) / secs,
+            "gridpoint_rhs_per_s": rhs / secs,
+            "rk4_steps_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())],
+            "stage_zc": zc, "fp32_stage_ms_all_solves": ms,
+            "graph_launches": 1, "chunks": tot["outer_iters"],
+            "grids": "SinhSymTP N0 in {64,96,128}, N1 in {32,64,96,128}, N2 in {8,16}, order 8"}
+
+
+def run_surrogate(args):
+    """Surrogate pipeline: 8192 solver-generated coarse solutions (64x32x8),
+    device training of the 12 -> 512x4 -> 16384 network, then 1024 held-out
+    solves at 128x128x16 started cold and from the network's prediction."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    coarse_n, fine_n = (64, 32, 8), (128, 128, 16)
+    n_train, n_held = args.surrogate_train, args.surrogate_held
+    train = W.batch_parameters(n_train, seed=1)
+    cdesc = [W.grid_desc("sinhsymtp", coarse_n, 8, bscale=p["d"] / 2) for p in train]
+    b = nrr.Batch(cdesc, [p["punctures"] for p in train])
+    (per, tot), t_gen = timed(lambda: b.relax(mode="fp32_dc", tol=1e-10,
+                                              raise_on_error=False))
+    n_out = int(np.prod(coarse_n))
+    Y = torch.empty((n_train, n_out), dtype=torch.float32, device="cuda")
+    b.get_interior(Y)
+    b.close()
+    X = torch.from_numpy(W.surrogate_inputs(train)).cuda()
+    dims = W.mlp_dims(n_out=n_out)
+    net = nrr.Surrogate(dims, W.mlp_init_params(dims, seed=3), batch=256)
+    net.fit_scaling(Y)
+    steps = args.surrogate_epochs * (n_train // 256)
+    order = torch.from_numpy(W.minibatch_order(n_train, 256, steps, seed=4)).cuda()
+    losses, t_train = timed(lambda: net.train(X, Y, order, steps, lr=1e-3))
+    flops_step = 6 * 256 * sum(a * b_ for a, b_ in zip(dims[:-1], dims[1:]))
+
+    held = W.batch_parameters(n_held, seed=2)
+    fdesc = [W.grid_desc("sinhsymtp", fine_n, 8, bscale=p["d"] / 2) for p in held]
+    cold = nrr.Batch(fdesc, [p["punctures"] for p in held])
+    cold.relax(mode="fp32_dc", tol=1e-10, max_iters=50, raise_on_error=False)
+    (per_c, tot_c), t_cold = timed(lambda: cold.relax(mode="fp32_dc", tol=1e-10,
+                                                      raise_on_error=False))
+    cold.close()
+    warm = nrr.Batch(fdesc, [p["punctures"] for p in held])
+    warm.relax(mode="fp32_dc", tol=1e-10, max_iters=50, raise_on_error=False)
+    Xh = torch.from_numpy(W.surrogate_inputs(held)).cuda()
+    shape = W.padded_shape(fdesc[0])
+
+    def predict_and_start():
+        pred = torch.empty((n_held, n_out), dtype=torch.float32, device="cuda")
+        net.predict(Xh, pred)
+        uf = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        for i, p in enumerate(held):
+            cd = W.grid_desc("sinhsymtp", coarse_n, 8, bscale=p["d"] / 2)
+            nrr.prolong(cd, pred[i].contiguous(), fdesc[i], uf)
+            warm.set_u(i, uf)
+    _, t_pred = timed(predict_and_start)
+    (per_w, tot_w), t_warm = timed(lambda: warm.relax(
+        mode="fp32_dc", tol=1e-10, initial=nrr.INIT_DEVICE, raise_on_error=False))
+    warm.close()
+    it_c = np.array([r["iters"] for r in per_c])
+    it_w = np.array([r["iters"] for r in per_w])
+    line = {"surrogate": {
+        "train_solves": n_train, "train_grid": "SinhSymTP 64x32x8, order 8",
+        "train_data_seconds": t_gen,
+        "train_converged": int(sum(r["status"] == 0 for r in per)),
+        "network": dims, "batch": 256, "steps": steps,
+        "train_seconds": t_train, "train_tflops": flops_step * steps / t_train / 1e12,
+        "loss_first_last": [float(losses[:10].mean()), float(losses[-10:].mean())],
+        "held_out_solves": n_held, "held_out_grid": "SinhSymTP 128x128x16, order 8",
+        "cold": {"seconds": t_cold, "status": tot_c["status"],
+                 "mean_rk4_steps": float(it_c.mean()), "max_rk4_steps": int(it_c.max())},
+        "warm": {"seconds": t_warm, "predict_prolong_seconds": t_pred,
+                 "status": tot_w["status"], "mean_rk4_steps": float(it_w.mean()),
+                 "max_rk4_steps": int(it_w.max())},
+        "step_reduction": float(1.0 - it_w.mean() / it_c.mean()),
+        "time_reduction": float(1.0 - (t_warm + t_pred) / t_cold)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_batch(args):
+    """A short fixed workload for profiler captures of the batched kernels:
+    `--profile-batch` solves of 128x128x16 (held-out parameter draws) and
+    100 defect-correction steps."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    held = W.batch_parameters(args.profile_batch, seed=2)
+    descs = [W.grid_desc("sinhsymtp", (128, 128, 16), 8, bscale=p["d"] / 2)
+             for p in held]
+    b = nrr.Batch(descs, [p["punctures"] for p in held])
+    per, tot = b.relax(mode="fp32_dc", tol=1e-10, max_iters=100,
+                       raise_on_error=False)
+    print(json.dumps({"profile_batch": args.profile_batch,
+                      "steps": tot["iters"], "seconds": tot["seconds"]}))
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +521,21 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many RK4 steps (profiler captures)")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--surrogate", action="store_true",
+                    help="run the learned warm-start pipeline instead")
+    ap.add_argument("--surrogate-train", type=int, default=8192)
+    ap.add_argument("--surrogate-held", type=int, default=1024)
+    ap.add_argument("--surrogate-epochs", type=int, default=100)
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="run only a short batch of this many 128x128x16 "
+                         "solves (profiler captures)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 512-solve batch in the default run")
     args = ap.parse_args()
+    if args.surrogate:
+        return run_surrogate(args)
+    if args.profile_batch > 0:
+        return run_profile_batch(args)
     if args.profile_steps > 0:
         return run_profile_steps(args)
     if args.warmup < 3:
