@@ -320,7 +320,8 @@ def run_ours(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "SinhSymTP 128x128x16",
                        "fd_order": 8, "global_batch": world,
-                       "stage_zc": {m: z for m, (z, _) in tuned.items()},
+                       "stage_launch": {m: {"variant": ["column", "tiled"][v], "zc": z}
+                                        for m, (v, z, _) in tuned.items()},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed before each step (256 MiB write, untimed)"},
             "sec_to_residual": {"fp64": t_max_s / args.steps,
@@ -502,9 +503,14 @@ def run_profile_batch(args):
     descs = [W.grid_desc("sinhsymtp", (128, 128, 16), 8, bscale=p["d"] / 2)
              for p in held]
     b = nrr.Batch(descs, [p["punctures"] for p in held])
+    # the autotuner launches the stage kernels outside graphs (kernels inside
+    # conditional graph nodes cannot be captured one by one): 3 trial steps
+    # x 4 stages x 2 repetitions for each of zc = 1, 2, 4
+    zc, ms = b.autotune("fp32_dc", 3)
     per, tot = b.relax(mode="fp32_dc", tol=1e-10, max_iters=100,
                        raise_on_error=False)
-    print(json.dumps({"profile_batch": args.profile_batch,
+    print(json.dumps({"profile_batch": args.profile_batch, "zc": zc,
+                      "fp32_stage_ms": ms,
                       "steps": tot["iters"], "seconds": tot["seconds"]}))
     b.close()
     return 0

@@ -222,20 +222,24 @@ nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
 nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
                               int64_t steps, double *ms_per_launch);
 
-/* Launch shape of the fused stage kernels: zc = phi planes per thread
- * (1, 2 or 4) for the precision of `mode` (NRR_FP64 / NRR_FP32).
- * Curvilinear grids only; other grids ignore it. */
-nrr_status nrr_set_launch(nrr_grid *g, int mode, int zc);
+/* Launch shape of the fused stage kernels for the precision of `mode`
+ * (NRR_FP64 / NRR_FP32): variant 0 = one thread per (i0, i1) column and zc
+ * (1, 2 or 4) phi planes, neighbours read through the caches; variant 1 =
+ * tiles of 32 x 4 columns staged plane by plane in shared memory, zc (2, 4,
+ * 8 or 16) planes per block.  Curvilinear grids only. */
+nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc);
 
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
- * events on the grid's work stream, keeps the fastest for this grid and for
+ * events on the grid's work stream (both stage-kernel variants, each over
+ * its zc values), keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the
  * punctures set.  *best_zc and *best_ms_per_launch (nullable) report the
  * choice and its average time per stage launch. */
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
-                        int *best_zc, double *best_ms_per_launch);
+                        int *best_variant, int *best_zc,
+                        double *best_ms_per_launch);
 
 /* ---- Batches of independent solves (paper Sec. 5, N independent grids,
  * there on several streams; here one graph launch for all of them) ------- */

@@ -79,7 +79,7 @@ struct nrr_grid {
   cudaStream_t user_stream = nullptr;  // caller's stream (ordering only)
   cudaEvent_t order_ev = nullptr;
   int device = 0;
-  LaunchCfg res_cfg;       // residual kernels (fixed: sizes the partials)
+  LaunchCfg res_cfg{128, 2};  // residual kernels (fixed: sizes the partials)
   LaunchCfg stage_cfg[2];  // stage kernels, [0] FP64, [1] FP32 (autotuned)
   std::vector<void *> allocs;
 
@@ -883,18 +883,27 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
   return NRR_OK;
 }
 
-nrr_status nrr_set_launch(nrr_grid *g, int mode, int zc) {
+nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc) {
   TRY(check_grid(g));
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (zc != 1 && zc != 2 && zc != 4)
-    return fail(NRR_ERR_INVALID_ARG, "zc must be 1, 2 or 4");
+  if (variant != 0 && variant != 1)
+    return fail(NRR_ERR_INVALID_ARG, "variant must be 0 (column) or 1 (tiled)");
+  if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
+      (variant == 1 && zc != 2 && zc != 4 && zc != 8 && zc != 16))
+    return fail(NRR_ERR_INVALID_ARG,
+                "zc must be 1, 2 or 4 (column) or 2, 4, 8 or 16 (tiled)");
+  g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  g->graphs.clear();
+  g->graph_kernels.clear();
   return NRR_OK;
 }
 
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
-                        int *best_zc, double *best_ms_per_launch) {
+                        int *best_variant, int *best_zc,
+                        double *best_ms_per_launch) {
   TRY(check_grid(g));
   if (!g->have_source) return fail(NRR_ERR_STATE, "punctures not set");
   if (mode != NRR_FP64 && mode != NRR_FP32)
@@ -918,11 +927,12 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  int best = keep.zc;
+  LaunchCfg best = keep;
   double best_ms = 1e30;
-  const int cands[3] = {1, 2, 4};
-  for (int zc : cands) {
-    cfg.zc = zc;
+  const LaunchCfg cands[7] = {{128, 1, 0}, {128, 2, 0}, {128, 4, 0}, {128, 2, 1},
+                              {128, 4, 1}, {128, 8, 1}, {128, 16, 1}};
+  for (const LaunchCfg &cand : cands) {
+    cfg = cand;
     for (int rep = 0; rep < 2; rep++) {  // first repetition warms up
       CUDA_TRY(cudaEventRecord(e0, g->stream));
       if (prec == 32)
@@ -936,14 +946,13 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
       double per = ms / (4.0 * (double)trial_steps);
       if (rep == 1 && per < best_ms) {
         best_ms = per;
-        best = zc;
+        best = cand;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cfg = keep;
-  cfg.zc = best;
+  cfg = best;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[tune_key(g->geo, prec == 32)] = cfg;
@@ -955,7 +964,8 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
-  if (best_zc) *best_zc = best;
+  if (best_variant) *best_variant = best.variant;
+  if (best_zc) *best_zc = best.zc;
   if (best_ms_per_launch) *best_ms_per_launch = best_ms;
   return NRR_OK;
 }

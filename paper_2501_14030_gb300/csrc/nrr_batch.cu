@@ -58,6 +58,9 @@ nrr_status bfail(nrr_status s, const char *fmt, ...) {
 struct SolveDev {
   Geo g;
   double dt, eta;
+  // RK4 stage weights a_s dt and b_s dt, computed on the host per relax
+  double wa[4], wb[4];
+  float wa32[4], wb32[4], eta32;
   double *u, *v;                 // FP64 state
   double *ku, *kv;               // FP64 right-hand side (the defect)
   double *s64[2], *t64[2], *a64[2];  // FP64 stage buffers (FP64 mode)
@@ -105,23 +108,20 @@ __device__ __forceinline__ StageArgs<double> batch_stage_args<double>(
     a.ov = sd.kv;
     return a;
   }
-  const double dt = sd.dt;
   a.bu = sd.u;
   a.bv = sd.v;
   a.au = sd.a64[0];
   a.av = sd.a64[1];
-  const double *in[4][2] = {{sd.u, sd.v}, {sd.s64[0], sd.s64[1]},
-                            {sd.t64[0], sd.t64[1]}, {sd.s64[0], sd.s64[1]}};
-  double *out[4][2] = {{sd.s64[0], sd.s64[1]}, {sd.t64[0], sd.t64[1]},
-                       {sd.s64[0], sd.s64[1]}, {sd.u, sd.v}};
-  const double wa[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-  const double wb[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
-  a.su = in[stage][0];
-  a.sv = in[stage][1];
-  a.ou = out[stage][0];
-  a.ov = out[stage][1];
-  a.wa = wa[stage];
-  a.wb = wb[stage];
+  switch (stage) {
+    case 0: a.su = sd.u; a.sv = sd.v; a.ou = sd.s64[0]; a.ov = sd.s64[1];
+            a.wa = sd.wa[0]; a.wb = sd.wb[0]; break;
+    case 1: a.su = sd.s64[0]; a.sv = sd.s64[1]; a.ou = sd.t64[0]; a.ov = sd.t64[1];
+            a.wa = sd.wa[1]; a.wb = sd.wb[1]; break;
+    case 2: a.su = sd.t64[0]; a.sv = sd.t64[1]; a.ou = sd.s64[0]; a.ov = sd.s64[1];
+            a.wa = sd.wa[2]; a.wb = sd.wb[2]; break;
+    default: a.su = sd.s64[0]; a.sv = sd.s64[1]; a.ou = sd.u; a.ov = sd.v;
+             a.wa = sd.wa[3]; a.wb = sd.wb[3]; break;
+  }
   return a;
 }
 
@@ -134,45 +134,44 @@ __device__ __forceinline__ StageArgs<float> batch_stage_args<float>(
   a.fu = sd.fu;
   a.lin = 1;
   a.col = sd.c32;
-  a.eta = (float)sd.eta;
-  const double dt = sd.dt;
+  a.eta = sd.eta32;
   a.bu = sd.d;
   a.bv = sd.w;
   a.au = sd.a32[0];
   a.av = sd.a32[1];
-  const float *in[4][2] = {{sd.d, sd.w}, {sd.s32[0], sd.s32[1]},
-                           {sd.t32[0], sd.t32[1]}, {sd.s32[0], sd.s32[1]}};
-  float *out[4][2] = {{sd.s32[0], sd.s32[1]}, {sd.t32[0], sd.t32[1]},
-                      {sd.s32[0], sd.s32[1]}, {sd.d, sd.w}};
-  const double wa[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-  const double wb[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
-  a.su = in[stage][0];
-  a.sv = in[stage][1];
-  a.ou = out[stage][0];
-  a.ov = out[stage][1];
-  a.wa = (float)wa[stage];
-  a.wb = (float)wb[stage];
+  switch (stage) {
+    case 0: a.su = sd.d; a.sv = sd.w; a.ou = sd.s32[0]; a.ov = sd.s32[1];
+            a.wa = sd.wa32[0]; a.wb = sd.wb32[0]; break;
+    case 1: a.su = sd.s32[0]; a.sv = sd.s32[1]; a.ou = sd.t32[0]; a.ov = sd.t32[1];
+            a.wa = sd.wa32[1]; a.wb = sd.wb32[1]; break;
+    case 2: a.su = sd.t32[0]; a.sv = sd.t32[1]; a.ou = sd.s32[0]; a.ov = sd.s32[1];
+            a.wa = sd.wa32[2]; a.wb = sd.wb32[2]; break;
+    default: a.su = sd.s32[0]; a.sv = sd.s32[1]; a.ou = sd.d; a.ov = sd.w;
+             a.wa = sd.wa32[3]; a.wb = sd.wb32[3]; break;
+  }
   (void)mode;
   return a;
 }
 
 // --- kernels ----------------------------------------------------------------
-// Stage kernel over all solves: block b works on solve map[b].x, items
-// map[b].y .. +127 of it (item = column e + ncols * chunk, column fastest).
-template <typename R, int NG, int KIND, int ZC>
-__global__ void __launch_bounds__(128)
+constexpr int kTileY = 4;
+
+// Stage kernel over all solves: block b works on solve map[b].x, tile
+// map[b].y of it (tiles counted i0 fastest, then i1, then phi chunks, with
+// one extra i0 tile per row for the outer shell).
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(32 * kTileY)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
-                       const int *__restrict__ active, int stage, int mode) {
+                       const int *__restrict__ active, int stage, int mode, int zc) {
+  __shared__ R tile[2][kTileY + 2 * NG][32 + 2 * NG];
   const int2 bm = map[blockIdx.x];
   if (!active[bm.x]) return;
   const SolveDev &sd = sds[bm.x];
   const Geo g = sd.g;
-  const int ncols = (g.n0 + NG) * g.n1;
-  const int item = bm.y + threadIdx.x;
-  if (item >= ncols * ((g.n2 + ZC - 1) / ZC)) return;
+  const int nx = dev::tiles_x(g) + 1, ny = dev::tiles_y<kTileY>(g);
   const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
-  dev::stage_curvi_item<R, NG, KIND, ZC>(g, a, item % ncols,
-                                         NG + (item / ncols) * ZC);
+  dev::stage_tile_block<R, NG, KIND, kTileY>(g, a, bm.y % nx, (bm.y / nx) % ny,
+                                             bm.y / (nx * ny), zc, tile);
 }
 
 // FP64 residual partial sums over all solves (2 phi planes per item).
@@ -347,7 +346,7 @@ struct nrr_batch {
   int nblk_res = 0, nblk_pts = 0;
   int2 *d_map_stage[5] = {};
   int nblk_stage[5] = {};
-  int zc[2] = {2, 2};  // [0] FP64 stages, [1] FP32 stages
+  int zc[2] = {4, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
   int64_t total_points = 0, interior_points = 0;
   // relaxation graph and its key
   cudaGraphExec_t exec = nullptr;
@@ -356,6 +355,21 @@ struct nrr_batch {
 };
 
 namespace {
+
+// Classical RK4 weights of one solve: stage offsets a = (1/2, 1/2, 1, 0) and
+// update weights b = (1/6, 1/3, 1/3, 1/6), times dt.
+void set_stage_weights(SolveDev &sd) {
+  const double dt = sd.dt;
+  const double wa[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  const double wb[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+  for (int k = 0; k < 4; k++) {
+    sd.wa[k] = wa[k];
+    sd.wb[k] = wb[k];
+    sd.wa32[k] = (float)wa[k];
+    sd.wb32[k] = (float)wb[k];
+  }
+  sd.eta32 = (float)sd.eta;
+}
 
 template <typename T>
 nrr_status balloc(nrr_batch *b, T **p, size_t count) {
@@ -417,15 +431,19 @@ nrr_status build_map(nrr_batch *b, int bs, F per_solve, int2 **d_map, int *nblk,
   return NRR_OK;
 }
 
-int zc_index(int zc) { return zc; }  // launch shapes 1, 2, 4 use slots 1, 2, 4
+int zc_index(int zc) {  // planes per chunk 1, 2, 4, 8, 16 -> slots 0..4
+  return zc <= 1 ? 0 : zc == 2 ? 1 : zc == 4 ? 2 : zc == 8 ? 3 : 4;
+}
 
 nrr_status stage_map(nrr_batch *b, int zc) {
   if (b->d_map_stage[zc_index(zc)]) return NRR_OK;
   const int ng = b->ng;
+  (void)ng;
   return build_map(
-      b, 128,
-      [ng, zc](const Geo &g) {
-        return (int64_t)(g.n0 + ng) * g.n1 * ((g.n2 + zc - 1) / zc);
+      b, 1,
+      [zc](const Geo &g) {
+        return (int64_t)(dev::tiles_x(g) + 1) * dev::tiles_y<kTileY>(g) *
+               dev::chunks_z(g, zc);
       },
       &b->d_map_stage[zc_index(zc)], &b->nblk_stage[zc_index(zc)], nullptr);
 }
@@ -435,11 +453,8 @@ void launch_bstage_kind(nrr_batch *b, int zc, int stage, int mode,
                         cudaStream_t st) {
   const int2 *map = b->d_map_stage[zc_index(zc)];
   const int nb = b->nblk_stage[zc_index(zc)];
-  switch (zc) {
-    case 1: batch_stage_kernel<R, NG, KIND, 1><<<nb, 128, 0, st>>>(b->d_sd, map, b->d_active, stage, mode); break;
-    case 4: batch_stage_kernel<R, NG, KIND, 4><<<nb, 128, 0, st>>>(b->d_sd, map, b->d_active, stage, mode); break;
-    default: batch_stage_kernel<R, NG, KIND, 2><<<nb, 128, 0, st>>>(b->d_sd, map, b->d_active, stage, mode); break;
-  }
+  batch_stage_kernel<R, NG, KIND><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
+                                                          stage, mode, zc);
 }
 
 template <typename R, int NG>
@@ -809,6 +824,7 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
   for (int s = 0; s < b->n; s++) {
     sd[s].dt = o->cfl * b->host_sd[s].dt;
     sd[s].eta = o->eta > 0.0 ? o->eta : 2.0 * M_PI * o->cfl / (b->geos[s].n0 * sd[s].dt);
+    set_stage_weights(sd[s]);
   }
   BCUDA(cudaMemcpyAsync(b->d_sd, sd.data(), sd.size() * sizeof(SolveDev),
                         cudaMemcpyHostToDevice, b->stream));
@@ -937,6 +953,7 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
   for (int s = 0; s < b->n; s++) {
     sd[s].dt = 0.5 * b->host_sd[s].dt;
     sd[s].eta = 2.0 * M_PI * 0.5 / (b->geos[s].n0 * sd[s].dt);
+    set_stage_weights(sd[s]);
   }
   BCUDA(cudaMemcpyAsync(b->d_sd, sd.data(), sd.size() * sizeof(SolveDev),
                         cudaMemcpyHostToDevice, b->stream));
@@ -958,7 +975,7 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
   const int keep = b->zc[slot];
   int best = keep;
   double best_ms = 1e30;
-  for (int zc : {1, 2, 4}) {
+  for (int zc : {2, 4, 8, 16}) {
     b->zc[slot] = zc;
     BTRY(stage_map(b, zc));
     for (int rep = 0; rep < 2; rep++) {

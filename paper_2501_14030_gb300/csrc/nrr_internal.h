@@ -48,8 +48,10 @@ struct FieldSet {
 };
 
 struct LaunchCfg {
-  int block = 128;  // threads per block (columns)
-  int zc = 2;       // phi planes per thread
+  int block = 128;  // threads per block (Cartesian and residual kernels)
+  int zc = 2;       // curvilinear stages: phi planes per thread (variant 0)
+                    // or per block chunk (variant 1)
+  int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel
 };
 
 // Cartesian grids use constant coefficients (uniform spacing, c = 1).

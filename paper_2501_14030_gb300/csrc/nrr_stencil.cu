@@ -24,8 +24,20 @@ namespace {
 using namespace dev;
 
 
-// Curvilinear stage kernel.  Thread = one (i0, i1) column of evolved points
-// and ZC consecutive phi planes (grid y).
+// Tiled curvilinear stage kernel (see stage_tile_block): grid (tiles in i0
+// + 1 outer-shell column of blocks, tiles in i1, phi chunks of zc planes).
+template <typename R, int NG, int KIND, int TY>
+__global__ void __launch_bounds__(32 * TY)
+    stage_tile_kernel(Geo g, StageArgs<R> a, int zc) {
+  __shared__ R tile[2][TY + 2 * NG][32 + 2 * NG];
+  stage_tile_block<R, NG, KIND, TY>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, zc,
+                                    tile);
+}
+
+// Column curvilinear stage kernel.  Thread = one (i0, i1) column of evolved
+// points and ZC consecutive phi planes (grid y); all neighbours come from
+// global memory (L1/L2).  Faster than the tiled kernel on small grids with
+// few phi planes.
 template <typename R, int NG, int KIND, int ZC>
 __global__ void __launch_bounds__(128)
     stage_curvi_kernel(Geo g, StageArgs<R> a) {
@@ -236,15 +248,47 @@ __global__ void scale_kernel(double *f, double s, int64_t n) {
   if (i < n) f[i] *= s;
 }
 
-template <typename R, int NG, int ZC>
+constexpr int kTileY = 4;
+
+template <typename R, int NG, int KIND>
+void launch_tile_kind(const Geo &g, const StageArgs<R> &a, int zc, cudaStream_t st) {
+  dim3 grid(tiles_x(g) + 1, tiles_y<kTileY>(g), chunks_z(g, zc));
+  stage_tile_kernel<R, NG, KIND, kTileY><<<grid, 32 * kTileY, 0, st>>>(g, a, zc);
+}
+
+template <typename R, int NG, int KIND, int ZC>
+void launch_column_zc(const Geo &g, const StageArgs<R> &a, cudaStream_t st) {
+  dim3 grid(((g.n0 + NG) * g.n1 + 127) / 128, (g.n2 + ZC - 1) / ZC);
+  stage_curvi_kernel<R, NG, KIND, ZC><<<grid, 128, 0, st>>>(g, a);
+}
+
+template <typename R, int NG, int KIND>
+void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, cudaStream_t st) {
+  switch (zc) {
+    case 1: launch_column_zc<R, NG, KIND, 1>(g, a, st); break;
+    case 4: launch_column_zc<R, NG, KIND, 4>(g, a, st); break;
+    default: launch_column_zc<R, NG, KIND, 2>(g, a, st); break;
+  }
+}
+
+template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
-                  const LaunchCfg &cfg, int ncols, cudaStream_t st) {
-  dim3 grid((ncols + 127) / 128, (g.n2 + ZC - 1) / ZC);
+                  const LaunchCfg &cfg, cudaStream_t st) {
+  const int zc = cfg.zc;
+  if (cfg.variant == 0) {
+    switch (kind) {
+      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, st); break;
+      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, st); break;
+      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, st); break;
+      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, st); break;
+    }
+    return;
+  }
   switch (kind) {
-    case STAGE_FIRST: stage_curvi_kernel<R, NG, STAGE_FIRST, ZC><<<grid, 128, 0, st>>>(g, a); break;
-    case STAGE_MID: stage_curvi_kernel<R, NG, STAGE_MID, ZC><<<grid, 128, 0, st>>>(g, a); break;
-    case STAGE_LAST: stage_curvi_kernel<R, NG, STAGE_LAST, ZC><<<grid, 128, 0, st>>>(g, a); break;
-    default: stage_curvi_kernel<R, NG, STAGE_RAW, ZC><<<grid, 128, 0, st>>>(g, a); break;
+    case STAGE_FIRST: launch_tile_kind<R, NG, STAGE_FIRST>(g, a, zc, st); break;
+    case STAGE_MID: launch_tile_kind<R, NG, STAGE_MID>(g, a, zc, st); break;
+    case STAGE_LAST: launch_tile_kind<R, NG, STAGE_LAST>(g, a, zc, st); break;
+    default: launch_tile_kind<R, NG, STAGE_RAW>(g, a, zc, st); break;
   }
 }
 
@@ -261,12 +305,7 @@ void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
     }
     return;
   }
-  int ncols = (g.n0 + NG) * g.n1;
-  switch (cfg.zc) {
-    case 1: launch_curvi<R, NG, 1>(g, kind, a, cfg, ncols, st); break;
-    case 4: launch_curvi<R, NG, 4>(g, kind, a, cfg, ncols, st); break;
-    default: launch_curvi<R, NG, 2>(g, kind, a, cfg, ncols, st); break;
-  }
+  launch_curvi<R, NG>(g, kind, a, cfg, st);
 }
 
 template <typename R, int NG>

@@ -312,3 +312,157 @@ __device__ __forceinline__ void residual_curvi_item(
 
 }  // namespace dev
 }  // namespace nrr
+
+namespace nrr {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Tiled stage: one block = a tile of 32 (i0) x TY (i1) interior columns and a
+// chunk of ZC phi planes.  Per plane the block stages the tile with its
+// NG-wide halo into shared memory (inner-boundary halo cells read from their
+// images, so the phi + pi planes of reflected cells come in here), each
+// thread keeps the 2NG+1 phi neighbours of its column in a register queue,
+// and the folded column weights are loaded once per thread.  Extra blocks
+// (tile_x == number of interior tiles) evolve the outer shell with the
+// radiation condition.
+// ---------------------------------------------------------------------------
+template <int TY, int NG>
+struct TileDims {
+  static constexpr int W = 32 + 2 * NG;  // staged width (i0)
+  static constexpr int H = TY + 2 * NG;  // staged height (i1)
+};
+
+__host__ __device__ __forceinline__ int tiles_x(const Geo &g) { return (g.n0 + 31) / 32; }
+template <int TY>
+__host__ __device__ __forceinline__ int tiles_y(const Geo &g) { return (g.n1 + TY - 1) / TY; }
+__host__ __device__ __forceinline__ int chunks_z(const Geo &g, int zc) { return (g.n2 + zc - 1) / zc; }
+
+template <typename R, int NG, int KIND, int TY>
+__device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R> &a,
+                                                 int tile_x, int tile_y, int chunk,
+                                                 int zc, R (*tile)[TY + 2 * NG][32 + 2 * NG]) {
+  constexpr int TW = 32 + 2 * NG, TH = TY + 2 * NG;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nc = g.ncol;
+  const int z0 = NG + chunk * zc;
+  const int z1 = min(z0 + zc, NG + g.n2);
+  const int i1 = NG + tile_y * TY + ty;
+  if (tile_x == tiles_x(g)) {
+    // outer shell: radiation condition, df/dt = -c (d_r f + f/r)
+    if (tx >= NG || i1 >= g.n1 + NG) return;
+    const int i0 = g.n0 + NG + tx;
+    const int col = i0 + g.s0 * i1;
+    const R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
+            rinv = ld(a.col.somm + 2 * nc + col);
+    for (int i2 = z0; i2 < z1; i2++) {
+      const int64_t p = col + (int64_t)nc * i2;
+      R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
+      R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+      R ku = -c * fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), rinv * u0);
+      R kv = -c * fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), rinv * v0);
+      if (a.lin) {
+        ku += ld(a.fu + p);
+        kv += ld(a.bc2 + p);
+      }
+      stage_epilogue<R, KIND>(a, p, ku, kv);
+    }
+    return;
+  }
+  const int i0 = NG + tile_x * 32 + tx;
+  const bool active = i0 < g.n0 + NG && i1 < g.n1 + NG;
+  const int col = i0 + g.s0 * i1;
+  R w[5 * NG + 1];
+  R q[2 * NG + 1];
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+#pragma unroll
+    for (int k = 0; k < 2 * NG; k++)
+      q[k + 1] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
+  }
+  const int j0b = NG + tile_x * 32 - NG, j1b = NG + tile_y * TY - NG;
+  int buf = 0;
+  for (int i2 = z0; i2 < z1; i2++, buf ^= 1) {
+    // stage plane i2 (tile + halo) into shared memory
+    for (int cidx = threadIdx.x; cidx < TW * TH; cidx += 32 * TY) {
+      const int cy = cidx / TW, cx = cidx - cy * TW;
+      int j0 = j0b + cx, j1 = j1b + cy, j2 = i2;
+      if (j0 >= g.s0 || j1 >= g.s1) continue;
+      if (j0 < NG || j1 < NG || j1 >= g.n1 + NG) {
+        // inner-boundary halo cell: its image, on the plane phi + pi
+        int flip = 0;
+        if (j0 < NG) {
+          j0 = 2 * NG - 1 - j0;
+          flip = 1;
+          if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
+        }
+        if (j1 < NG) {
+          j1 = 2 * NG - 1 - j1;
+          flip ^= 1;
+        } else if (j1 >= g.n1 + NG) {
+          j1 = 2 * g.n1 + 2 * NG - 1 - j1;
+          flip ^= 1;
+        }
+        if (flip) j2 = wrap_plane<NG>(g, j2 + g.n2 / 2);
+      }
+      tile[buf][cy][cx] = ld(a.su + j0 + g.s0 * (j1 + g.s1 * j2));
+    }
+    __syncthreads();
+    if (active) {
+      const int64_t p = col + (int64_t)nc * i2;
+#pragma unroll
+      for (int k = 0; k < 2 * NG; k++) q[k] = q[k + 1];
+      q[2 * NG] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + NG));
+      const R v0 = ld(a.sv + p), al = ld(a.alpha + p), bc = ld(a.bc2 + p);
+      R yb0 = R(0), yb1 = R(0), ac0 = R(0), ac1 = R(0);
+      if (KIND == STAGE_FIRST || KIND == STAGE_MID) {
+        yb0 = ld(a.bu + p);
+        yb1 = ld(a.bv + p);
+      }
+      if (KIND == STAGE_MID || KIND == STAGE_LAST) {
+        ac0 = a.au[p];
+        ac1 = a.av[p];
+      }
+      const R fu = a.lin ? ld(a.fu + p) : R(0);
+      const R(&t)[TH][TW] = tile[buf];
+      const R u0 = t[ty + NG][tx + NG];
+      R a0 = w[0] * u0, a1;
+#pragma unroll
+      for (int k = 1; k <= NG; k++) {
+        a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
+        a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
+      }
+      a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
+      a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
+#pragma unroll
+      for (int k = 2; k <= NG; k++) {
+        a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
+        a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
+      }
+#pragma unroll
+      for (int k = 1; k <= NG; k++) a0 = fma(w[4 * NG + k], q[NG + k] + q[NG - k], a0);
+      const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
+      const R ku = fma(-a.eta, u0, v0) + fu;
+      if (KIND == STAGE_FIRST) {
+        a.au[p] = fma(a.wb, ku, yb0);
+        a.av[p] = fma(a.wb, kv, yb1);
+        a.ou[p] = fma(a.wa, ku, yb0);
+        a.ov[p] = fma(a.wa, kv, yb1);
+      } else if (KIND == STAGE_MID) {
+        a.au[p] = fma(a.wb, ku, ac0);
+        a.av[p] = fma(a.wb, kv, ac1);
+        a.ou[p] = fma(a.wa, ku, yb0);
+        a.ov[p] = fma(a.wa, kv, yb1);
+      } else if (KIND == STAGE_LAST) {
+        a.ou[p] = fma(a.wb, ku, ac0);
+        a.ov[p] = fma(a.wb, kv, ac1);
+      } else {
+        a.ou[p] = ku;
+        a.ov[p] = kv;
+      }
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace nrr

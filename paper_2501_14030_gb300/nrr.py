@@ -104,8 +104,9 @@ def lib() -> C.CDLL:
         "nrr_timestep": [V, C.c_double, D, D],
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
-        "nrr_set_launch": [V, I, I],
-        "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
+        "nrr_set_launch": [V, I, I, I],
+        "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int),
+                         C.POINTER(C.c_int), D],
         "nrr_batch_create": [I, C.POINTER(GridDesc), C.POINTER(C.c_int),
                              C.POINTER(C.POINTER(Puncture)), I, V,
                              C.POINTER(V)],
@@ -336,17 +337,18 @@ class Grid:
                                         C.byref(ms)))
         return ms.value
 
-    def set_launch(self, zc: int, mode="fp64"):
+    def set_launch(self, zc: int, mode="fp64", variant: int = 0):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        _check(lib().nrr_set_launch(self._h, m, int(zc)))
+        _check(lib().nrr_set_launch(self._h, m, int(variant), int(zc)))
 
     def autotune(self, mode="fp64", trial_steps: int = 20):
-        """Pick the fastest stage launch shape; returns (zc, ms/launch)."""
+        """Pick the fastest stage kernel and launch shape; returns
+        (variant, zc, ms/launch)."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        zc, ms = C.c_int(), C.c_double()
-        _check(lib().nrr_autotune(self._h, m, int(trial_steps), C.byref(zc),
-                                  C.byref(ms)))
-        return zc.value, ms.value
+        var, zc, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().nrr_autotune(self._h, m, int(trial_steps), C.byref(var),
+                                  C.byref(zc), C.byref(ms)))
+        return var.value, zc.value, ms.value
 
     def step(self, steps: int, dt: float, eta: float, mode="fp64"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
