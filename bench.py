@@ -368,6 +368,8 @@ def run_profile_steps(args):
     g = nrr.Grid(desc)
     g.set_punctures(punc)
     dt, eta = g.timestep(0.5)
+    if args.profile_zc > 0:
+        g.set_launch(args.profile_zc, args.mode, args.profile_variant)
     g.step(args.profile_steps, dt, eta, mode=args.mode)
     print(json.dumps({"profile_steps": args.profile_steps, "mode": args.mode,
                       "residual": g.residual(100.0)}))
@@ -490,6 +492,34 @@ def run_surrogate(args):
     return 0
 
 
+def run_profile_gemm(args):
+    """The surrogate's largest GEMM shapes once each (profiler captures):
+    forward/backward of the 512 -> 16384 layer at batch 256 and a larger
+    M for the tensor-core rate."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for (M, N, K) in [(256, 16384, 512), (16384, 512, 256), (8192, 16384, 512)]:
+        A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        nrr.gemm_bf16_tn(A, B, D)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            nrr.gemm_bf16_tn(A, B, D)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        print(json.dumps({"gemm": [M, N, K], "ms": ms,
+                          "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}))
+    return 0
+
+
 def run_profile_batch(args):
     """A short fixed workload for profiler captures of the batched kernels:
     `--profile-batch` solves of 128x128x16 (held-out parameter draws) and
@@ -516,6 +546,69 @@ def run_profile_batch(args):
     return 0
 
 
+def run_configs2(args):
+    """The q=4 spinning pair on SinhSymTP 256x256x32, Spherical 128x64x32 and
+    Cartesian 256^3 (order 8): FP32 relaxation inside the FP64
+    defect-correction loop against the plain FP64 relaxation, with the
+    difference of the two solutions and the oracle's residual of the
+    defect-corrected one (r < 100)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    from tests.helpers import oracle_grid
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, mk in [("sinhsymtp_256x256x32", W.q4_sinhsymtp_256),
+                     ("spherical_128x64x32", W.q4_spherical_128),
+                     ("cartesian_256^3", W.q4_cartesian_256)]:
+        desc, punc = mk()
+        g = nrr.Grid(desc)
+        g.set_punctures(punc)
+        tuned = {m: g.autotune(m, 10)[:2] for m in ("fp64", "fp32")}
+        res = {}
+        for mode in ("fp32_dc", "fp64"):
+            g.relax(mode=mode, tol=1e-10, max_iters=100, raise_on_error=False)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = g.relax(mode=mode, tol=1e-10, max_iters=200000,
+                        raise_on_error=False)
+            e1.record(stream)
+            e1.synchronize()
+            u = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+            g.get_state(u)
+            res[mode] = (r, e0.elapsed_time(e1) / 1e3, u)
+        udc, u64 = res["fp32_dc"][2], res["fp64"][2]
+        diff = float((udc - u64).abs().max() / u64.abs().max())
+        entry = {"launch": tuned,
+                 "fp32_dc": {"seconds": res["fp32_dc"][1],
+                             "rk4_steps": res["fp32_dc"][0]["iters"],
+                             "norm": res["fp32_dc"][0]["norm"],
+                             "status": res["fp32_dc"][0]["status"]},
+                 "fp64": {"seconds": res["fp64"][1],
+                          "rk4_steps": res["fp64"][0]["iters"],
+                          "norm": res["fp64"][0]["norm"],
+                          "status": res["fp64"][0]["status"]},
+                 "speedup_dc_vs_fp64": res["fp64"][1] / res["fp32_dc"][1],
+                 "max_rel_diff_u_dc_vs_fp64": diff,
+                 "gridpoint_rhs_per_s_fp64": g.interior_points * 4 *
+                 res["fp64"][0]["iters"] / res["fp64"][1]}
+        if g.interior_points <= 4_000_000:
+            og = oracle_grid(desc)
+            alpha, beta = og.source(punc)
+            entry["oracle_residual_of_dc_u"] = og.norm(
+                og.residual(alpha, beta, udc.cpu().numpy()))
+        out[name] = entry
+        g.close()
+        del udc, u64, res
+        torch.cuda.empty_cache()
+    print(json.dumps({"configs2": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -527,11 +620,19 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many RK4 steps (profiler captures)")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--profile-variant", type=int, default=0,
+                    help="with --profile-steps: 0 column, 1 tiled kernel")
+    ap.add_argument("--profile-zc", type=int, default=0,
+                    help="with --profile-steps: phi planes per thread/block")
+    ap.add_argument("--profile-gemm", action="store_true",
+                    help="run only the surrogate GEMM shapes (captures)")
     ap.add_argument("--surrogate", action="store_true",
                     help="run the learned warm-start pipeline instead")
     ap.add_argument("--surrogate-train", type=int, default=8192)
     ap.add_argument("--surrogate-held", type=int, default=1024)
     ap.add_argument("--surrogate-epochs", type=int, default=100)
+    ap.add_argument("--configs2", action="store_true",
+                    help="run the larger and other-coordinate variants")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run only a short batch of this many 128x128x16 "
                          "solves (profiler captures)")
@@ -542,6 +643,10 @@ def main():
         return run_surrogate(args)
     if args.profile_batch > 0:
         return run_profile_batch(args)
+    if args.profile_gemm:
+        return run_profile_gemm(args)
+    if args.configs2:
+        return run_configs2(args)
     if args.profile_steps > 0:
         return run_profile_steps(args)
     if args.warmup < 3:
