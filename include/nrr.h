@@ -226,7 +226,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * (NRR_FP64 / NRR_FP32): variant 0 = one thread per (i0, i1) column and zc
  * (1, 2 or 4) phi planes, neighbours read through the caches; variant 1 =
  * tiles of 32 x 4 columns staged plane by plane in shared memory, zc (2, 4,
- * 8 or 16) planes per block.  Curvilinear grids only. */
+ * 8 or 16) planes per block; variant 2 = one (column, plane) per step of a
+ * grid that exactly fills every SM (zc = 1).  Curvilinear grids only. */
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc);
 
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):

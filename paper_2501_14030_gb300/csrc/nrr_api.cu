@@ -887,12 +887,15 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc) {
   TRY(check_grid(g));
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (variant != 0 && variant != 1)
-    return fail(NRR_ERR_INVALID_ARG, "variant must be 0 (column) or 1 (tiled)");
-  if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
-      (variant == 1 && zc != 2 && zc != 4 && zc != 8 && zc != 16))
+  if (variant < 0 || variant > 2)
     return fail(NRR_ERR_INVALID_ARG,
-                "zc must be 1, 2 or 4 (column) or 2, 4, 8 or 16 (tiled)");
+                "variant must be 0 (column), 1 (tiled) or 2 (persistent column)");
+  if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
+      (variant == 1 && zc != 2 && zc != 4 && zc != 8 && zc != 16) ||
+      (variant == 2 && zc != 1))
+    return fail(NRR_ERR_INVALID_ARG,
+                "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled), 1 "
+                "(persistent)");
   g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
@@ -929,8 +932,9 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[7] = {{128, 1, 0}, {128, 2, 0}, {128, 4, 0}, {128, 2, 1},
-                              {128, 4, 1}, {128, 8, 1}, {128, 16, 1}};
+  const LaunchCfg cands[8] = {{128, 1, 0}, {128, 2, 0}, {128, 4, 0}, {128, 2, 1},
+                              {128, 4, 1}, {128, 8, 1}, {128, 16, 1},
+                              {128, 1, 2}};
   for (const LaunchCfg &cand : cands) {
     cfg = cand;
     for (int rep = 0; rep < 2; rep++) {  // first repetition warms up

@@ -46,6 +46,19 @@ __global__ void __launch_bounds__(128)
   stage_curvi_item<R, NG, KIND, ZC>(g, a, e, NG + blockIdx.y * ZC);
 }
 
+// Persistent column kernel: exactly (resident blocks x SMs) blocks stride
+// over single (column, plane) items, so the remainder of the work is spread
+// evenly over all SMs instead of forming a partial last wave.
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(128)
+    stage_curvi_persistent_kernel(Geo g, StageArgs<R> a) {
+  const int ncols = (g.n0 + NG) * g.n1;
+  const int nitems = ncols * g.n2;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+       it += gridDim.x * blockDim.x)
+    stage_curvi_item<R, NG, KIND, 1>(g, a, it % ncols, NG + it / ncols);
+}
+
 // Cartesian: uniform spacing, c = 1, every ghost is an outer ghost evolved by
 // the radiation condition with d_r f = sum_i (x^i/r) D_i f (one-sided inward
 // along directions in which the point lies outside, centred otherwise).
@@ -271,10 +284,42 @@ void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, cudaStream_
   }
 }
 
+// Blocks that fill every SM for one kernel (resident blocks per SM x SMs of
+// the current device), looked up once per kernel instantiation.
+template <typename K>
+int filling_grid(K kernel) {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+    cached = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  return cached;
+}
+
+template <typename R, int NG, int KIND>
+void launch_persistent_kind(const Geo &g, const StageArgs<R> &a, cudaStream_t st) {
+  auto k = stage_curvi_persistent_kernel<R, NG, KIND>;
+  const int items = (g.n0 + NG) * g.n1 * g.n2;
+  const int blocks = min(filling_grid(k), (items + 127) / 128);
+  k<<<blocks, 128, 0, st>>>(g, a);
+}
+
 template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st) {
   const int zc = cfg.zc;
+  if (cfg.variant == 2) {
+    switch (kind) {
+      case STAGE_FIRST: launch_persistent_kind<R, NG, STAGE_FIRST>(g, a, st); break;
+      case STAGE_MID: launch_persistent_kind<R, NG, STAGE_MID>(g, a, st); break;
+      case STAGE_LAST: launch_persistent_kind<R, NG, STAGE_LAST>(g, a, st); break;
+      default: launch_persistent_kind<R, NG, STAGE_RAW>(g, a, st); break;
+    }
+    return;
+  }
   if (cfg.variant == 0) {
     switch (kind) {
       case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, st); break;
