@@ -230,6 +230,16 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * grid that exactly fills every SM (zc = 1).  Curvilinear grids only. */
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc);
 
+/* Programmatic dependent launch of the fused stage kernels, both precisions
+ * (on = 1, the default): each stage kernel is launched so that its blocks
+ * may be scheduled while the preceding kernel on the stream drains; they
+ * read only solve-constant data (column weights, geometry) until that kernel
+ * has completed and its writes are visible, so results are identical either
+ * way.  on = 0 restores plain stream ordering.  Drops the grid's captured
+ * relaxation graphs (rebuilt on the next nrr_relax).
+ * Errors: NRR_ERR_INVALID_ARG for a null grid or on not 0/1. */
+nrr_status nrr_set_pdl(nrr_grid *g, int on);
+
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream (both stage-kernel variants, each over

@@ -904,6 +904,17 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc) {
   return NRR_OK;
 }
 
+nrr_status nrr_set_pdl(nrr_grid *g, int on) {
+  TRY(check_grid(g));
+  if (on != 0 && on != 1) return fail(NRR_ERR_INVALID_ARG, "on must be 0 or 1");
+  g->stage_cfg[0].pdl = on;
+  g->stage_cfg[1].pdl = on;
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  g->graphs.clear();
+  g->graph_kernels.clear();
+  return NRR_OK;
+}
+
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
                         int *best_variant, int *best_zc,
                         double *best_ms_per_launch) {
@@ -935,7 +946,9 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   const LaunchCfg cands[8] = {{128, 1, 0}, {128, 2, 0}, {128, 4, 0}, {128, 2, 1},
                               {128, 4, 1}, {128, 8, 1}, {128, 16, 1},
                               {128, 1, 2}};
-  for (const LaunchCfg &cand : cands) {
+  for (const LaunchCfg &cand0 : cands) {
+    LaunchCfg cand = cand0;
+    cand.pdl = keep.pdl;
     cfg = cand;
     for (int rep = 0; rep < 2; rep++) {  // first repetition warms up
       CUDA_TRY(cudaEventRecord(e0, g->stream));

@@ -51,7 +51,10 @@ struct LaunchCfg {
   int block = 128;  // threads per block (Cartesian and residual kernels)
   int zc = 2;       // curvilinear stages: phi planes per thread (variant 0)
                     // or per block chunk (variant 1)
-  int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel
+  int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel,
+                    // 2 persistent column kernel
+  int pdl = 1;      // stage kernels: programmatic dependent launch (the next
+                    // stage's blocks start while this one drains)
 };
 
 // Cartesian grids use constant coefficients (uniform spacing, c = 1).

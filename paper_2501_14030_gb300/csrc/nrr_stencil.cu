@@ -30,6 +30,7 @@ template <typename R, int NG, int KIND, int TY>
 __global__ void __launch_bounds__(32 * TY)
     stage_tile_kernel(Geo g, StageArgs<R> a, int zc) {
   __shared__ R tile[2][TY + 2 * NG][32 + 2 * NG];
+  pdl_trigger();
   stage_tile_block<R, NG, KIND, TY>(g, a, blockIdx.x, blockIdx.y, blockIdx.z, zc,
                                     tile);
 }
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(32 * TY)
 template <typename R, int NG, int KIND, int ZC>
 __global__ void __launch_bounds__(128)
     stage_curvi_kernel(Geo g, StageArgs<R> a) {
+  pdl_trigger();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (g.n0 + NG) * g.n1) return;
   stage_curvi_item<R, NG, KIND, ZC>(g, a, e, NG + blockIdx.y * ZC);
@@ -52,6 +54,7 @@ __global__ void __launch_bounds__(128)
 template <typename R, int NG, int KIND>
 __global__ void __launch_bounds__(128)
     stage_curvi_persistent_kernel(Geo g, StageArgs<R> a) {
+  pdl_trigger();
   const int ncols = (g.n0 + NG) * g.n1;
   const int nitems = ncols * g.n2;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
@@ -110,8 +113,10 @@ __device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ s
 template <typename R, int NG, int KIND>
 __global__ void __launch_bounds__(128)
     stage_cart_kernel(Geo g, StageArgs<R> a, int zc) {
+  pdl_trigger();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ncol) return;
+  pdl_wait();
   const int i0 = e % g.s0, i1 = e / g.s0;
   const int z0 = blockIdx.y * zc;
   const int z1 = min(z0 + zc, g.s2);
@@ -124,11 +129,11 @@ __global__ void __launch_bounds__(128)
       kv = cart_operator<R, NG>(g, a.su, a.cart, p, u0, ld(a.alpha + p),
                                 ld(a.bc2 + p), a.lin);
       ku = fma(-a.eta, u0, v0);
-      if (a.lin) ku += ld(a.fu + p);
+      if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
     } else {
       ku = cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
       kv = cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
-      if (a.lin) {
+      if (linear_mode<R>(a.lin)) {
         ku += ld(a.fu + p);
         kv += ld(a.bc2 + p);
       }
@@ -263,24 +268,46 @@ __global__ void scale_kernel(double *f, double s, int64_t n) {
 
 constexpr int kTileY = 4;
 
+// Launch with or without the programmatic-serialisation attribute (stage
+// kernels only: each calls pdl_wait() before touching the state).
+template <typename... P, typename... A>
+void launch_stage_kernel(void (*k)(P...), dim3 grid, dim3 block, cudaStream_t st,
+                         int pdl, A... args) {
+  cudaLaunchConfig_t c = {};
+  c.gridDim = grid;
+  c.blockDim = block;
+  c.dynamicSmemBytes = 0;
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  c.attrs = at;
+  c.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&c, k, args...);
+}
+
 template <typename R, int NG, int KIND>
-void launch_tile_kind(const Geo &g, const StageArgs<R> &a, int zc, cudaStream_t st) {
+void launch_tile_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
+                      cudaStream_t st) {
   dim3 grid(tiles_x(g) + 1, tiles_y<kTileY>(g), chunks_z(g, zc));
-  stage_tile_kernel<R, NG, KIND, kTileY><<<grid, 32 * kTileY, 0, st>>>(g, a, zc);
+  launch_stage_kernel(stage_tile_kernel<R, NG, KIND, kTileY>, grid,
+                      dim3(32 * kTileY), st, pdl, g, a, zc);
 }
 
 template <typename R, int NG, int KIND, int ZC>
-void launch_column_zc(const Geo &g, const StageArgs<R> &a, cudaStream_t st) {
+void launch_column_zc(const Geo &g, const StageArgs<R> &a, int pdl, cudaStream_t st) {
   dim3 grid(((g.n0 + NG) * g.n1 + 127) / 128, (g.n2 + ZC - 1) / ZC);
-  stage_curvi_kernel<R, NG, KIND, ZC><<<grid, 128, 0, st>>>(g, a);
+  launch_stage_kernel(stage_curvi_kernel<R, NG, KIND, ZC>, grid, dim3(128), st,
+                      pdl, g, a);
 }
 
 template <typename R, int NG, int KIND>
-void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, cudaStream_t st) {
+void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
+                        cudaStream_t st) {
   switch (zc) {
-    case 1: launch_column_zc<R, NG, KIND, 1>(g, a, st); break;
-    case 4: launch_column_zc<R, NG, KIND, 4>(g, a, st); break;
-    default: launch_column_zc<R, NG, KIND, 2>(g, a, st); break;
+    case 1: launch_column_zc<R, NG, KIND, 1>(g, a, pdl, st); break;
+    case 4: launch_column_zc<R, NG, KIND, 4>(g, a, pdl, st); break;
+    default: launch_column_zc<R, NG, KIND, 2>(g, a, pdl, st); break;
   }
 }
 
@@ -300,40 +327,41 @@ int filling_grid(K kernel) {
 }
 
 template <typename R, int NG, int KIND>
-void launch_persistent_kind(const Geo &g, const StageArgs<R> &a, cudaStream_t st) {
+void launch_persistent_kind(const Geo &g, const StageArgs<R> &a, int pdl,
+                            cudaStream_t st) {
   auto k = stage_curvi_persistent_kernel<R, NG, KIND>;
   const int items = (g.n0 + NG) * g.n1 * g.n2;
   const int blocks = min(filling_grid(k), (items + 127) / 128);
-  k<<<blocks, 128, 0, st>>>(g, a);
+  launch_stage_kernel(k, dim3(blocks), dim3(128), st, pdl, g, a);
 }
 
 template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st) {
-  const int zc = cfg.zc;
+  const int zc = cfg.zc, pdl = cfg.pdl;
   if (cfg.variant == 2) {
     switch (kind) {
-      case STAGE_FIRST: launch_persistent_kind<R, NG, STAGE_FIRST>(g, a, st); break;
-      case STAGE_MID: launch_persistent_kind<R, NG, STAGE_MID>(g, a, st); break;
-      case STAGE_LAST: launch_persistent_kind<R, NG, STAGE_LAST>(g, a, st); break;
-      default: launch_persistent_kind<R, NG, STAGE_RAW>(g, a, st); break;
+      case STAGE_FIRST: launch_persistent_kind<R, NG, STAGE_FIRST>(g, a, pdl, st); break;
+      case STAGE_MID: launch_persistent_kind<R, NG, STAGE_MID>(g, a, pdl, st); break;
+      case STAGE_LAST: launch_persistent_kind<R, NG, STAGE_LAST>(g, a, pdl, st); break;
+      default: launch_persistent_kind<R, NG, STAGE_RAW>(g, a, pdl, st); break;
     }
     return;
   }
   if (cfg.variant == 0) {
     switch (kind) {
-      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, st); break;
-      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, st); break;
-      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, st); break;
-      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, st); break;
+      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
+      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
+      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
+      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
     }
     return;
   }
   switch (kind) {
-    case STAGE_FIRST: launch_tile_kind<R, NG, STAGE_FIRST>(g, a, zc, st); break;
-    case STAGE_MID: launch_tile_kind<R, NG, STAGE_MID>(g, a, zc, st); break;
-    case STAGE_LAST: launch_tile_kind<R, NG, STAGE_LAST>(g, a, zc, st); break;
-    default: launch_tile_kind<R, NG, STAGE_RAW>(g, a, zc, st); break;
+    case STAGE_FIRST: launch_tile_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
+    case STAGE_MID: launch_tile_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
+    case STAGE_LAST: launch_tile_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
+    default: launch_tile_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
   }
 }
 
@@ -342,11 +370,12 @@ void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
                      const LaunchCfg &cfg, cudaStream_t st) {
   if (g.coord == CARTESIAN) {
     dim3 grid((g.ncol + cfg.block - 1) / cfg.block, (g.s2 + cfg.zc - 1) / cfg.zc);
+    dim3 blk(cfg.block);
     switch (kind) {
-      case STAGE_FIRST: stage_cart_kernel<R, NG, STAGE_FIRST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-      case STAGE_MID: stage_cart_kernel<R, NG, STAGE_MID><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-      case STAGE_LAST: stage_cart_kernel<R, NG, STAGE_LAST><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
-      default: stage_cart_kernel<R, NG, STAGE_RAW><<<grid, cfg.block, 0, st>>>(g, a, cfg.zc); break;
+      case STAGE_FIRST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_FIRST>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
+      case STAGE_MID: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_MID>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
+      case STAGE_LAST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_LAST>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
+      default: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_RAW>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
     }
     return;
   }

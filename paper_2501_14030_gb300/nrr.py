@@ -30,6 +30,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
+           "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
            "nrr_batch_autotune", "nrr_gemm_bf16_tn", "nrr_surrogate_create",
@@ -105,6 +106,7 @@ def lib() -> C.CDLL:
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
         "nrr_set_launch": [V, I, I, I],
+        "nrr_set_pdl": [V, I],
         "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int),
                          C.POINTER(C.c_int), D],
         "nrr_batch_create": [I, C.POINTER(GridDesc), C.POINTER(C.c_int),
@@ -340,6 +342,10 @@ class Grid:
     def set_launch(self, zc: int, mode="fp64", variant: int = 0):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         _check(lib().nrr_set_launch(self._h, m, int(variant), int(zc)))
+
+    def set_pdl(self, on: bool):
+        """Programmatic dependent launch of the stage kernels (default on)."""
+        _check(lib().nrr_set_pdl(self._h, int(bool(on))))
 
     def autotune(self, mode="fp64", trial_steps: int = 20):
         """Pick the fastest stage kernel and launch shape; returns
