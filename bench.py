@@ -320,7 +320,7 @@ def run_ours(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "SinhSymTP 128x128x16",
                        "fd_order": 8, "global_batch": world,
-                       "stage_launch": {m: {"variant": ["column", "tiled"][v], "zc": z}
+                       "stage_launch": {m: {"variant": ["column", "tiled", "persistent"][v], "zc": z}
                                         for m, (v, z, _) in tuned.items()},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed before each step (256 MiB write, untimed)"},
@@ -384,7 +384,7 @@ def run_batch(args, nrr, W, torch):
     params = W.batch_parameters(512, 20250124)
     descs = [p["desc"] for p in params]
     b = nrr.Batch(descs, [p["punctures"] for p in params])
-    zc, ms = b.autotune("fp32_dc", 3)
+    zc, ms, var = b.autotune("fp32_dc", 3)
     b.relax(mode="fp32_dc", tol=1e-10, max_iters=100, raise_on_error=False)
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -401,6 +401,7 @@ def run_batch(args, nrr, W, torch):
             "seconds": secs, "solves_per_s": len(descs) / secs,
             "gridpoint_rhs_per_s": rhs / secs,
             "rk4_steps_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())],
+            "stage_variant": ["register-staged", "bulk-copy ring"][var],
             "stage_zc": zc, "fp32_stage_ms_all_solves": ms,
             "graph_launches": 1, "chunks": tot["outer_iters"],
             "grids": "SinhSymTP N0 in {64,96,128}, N1 in {32,64,96,128}, N2 in {8,16}, order 8"}
@@ -536,10 +537,11 @@ def run_profile_batch(args):
     # the autotuner launches the stage kernels outside graphs (kernels inside
     # conditional graph nodes cannot be captured one by one): 3 trial steps
     # x 4 stages x 2 repetitions for each of zc = 1, 2, 4
-    zc, ms = b.autotune("fp32_dc", 3)
+    zc, ms, var = b.autotune("fp32_dc", 3)
     per, tot = b.relax(mode="fp32_dc", tol=1e-10, max_iters=100,
                        raise_on_error=False)
     print(json.dumps({"profile_batch": args.profile_batch, "zc": zc,
+                      "variant": var,
                       "fp32_stage_ms": ms,
                       "steps": tot["iters"], "seconds": tot["seconds"]}))
     b.close()

@@ -298,10 +298,23 @@ nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device);
  * surrogate. */
 nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
 
-/* Autotuner for the batch's stage launch shape (phi planes per thread),
- * timed over all solves; keeps the fastest for later relaxations. */
+/* Stage kernel of a batch for `mode` (NRR_FP64 or NRR_FP32_DC): variant 0
+ * stages each plane of a 32 x 4 column tile through registers into shared
+ * memory; variant 1 streams the planes of a block's chunk through a ring of
+ * three shared-memory slots filled by asynchronous bulk copies (one row per
+ * copy, completing on an mbarrier; only for FD order 8 with every solve's
+ * n0 % 32 == 0 and n1 % 4 == 0).  zc (2, 4, 8 or 16) phi planes per block.
+ * Both variants give bitwise identical results.
+ * Errors: NRR_ERR_INVALID_ARG for other values or an ineligible batch. */
+nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc);
+
+/* Autotuner for the batch's stage kernel (variant and phi planes per block
+ * chunk, as in nrr_batch_set_launch), timed over all solves on the current
+ * state (restored afterwards); keeps the fastest for later relaxations.
+ * Outputs nullable.  NRR_ERR_TIMEOUT if a bulk-copy wait expired. */
 nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
-                              int *best_zc, double *best_ms_per_launch);
+                              int *best_zc, double *best_ms_per_launch,
+                              int *best_variant);
 
 /* BF16 tensor-core GEMM used by the surrogate network (tcgen05 MMA with an
  * FP32 accumulator in tensor memory, TMA-fed 128-byte-swizzled tiles):

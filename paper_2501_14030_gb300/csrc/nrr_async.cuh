@@ -1,0 +1,94 @@
+// nrr_async.cuh -- asynchronous bulk copies (global -> shared memory,
+// completed on an mbarrier) for the stage kernels' plane pipeline.
+//
+// Every wait is bounded: a wait that expires returns false and the caller
+// records an error and drains its copies in flight before the block exits.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace nrr {
+namespace dev {
+
+constexpr long long kAsyncWaitLimit = 1ll << 22;  // try_wait polls
+
+__device__ __forceinline__ uint32_t shared_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init_count(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(shared_addr(bar)),
+               "r"(count)
+               : "memory");
+}
+
+// Makes barrier initialisation visible to the async proxy (bulk copies).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also raises the barrier's expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   shared_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_parity(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(shared_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity) {
+  for (long long i = 0; i < kAsyncWaitLimit; i++)
+    if (mbar_test_parity(bar, parity)) return true;
+  return false;
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// its later async-proxy ones (a buffer read by the threads is refilled).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this block's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src,
+                                              uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(shared_addr(dst)),
+      "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes),
+      "r"(shared_addr(bar))
+      : "memory");
+}
+
+// Tiled tensor copy of one box at coordinates (x, y, z, w) of a 4-D tensor
+// map (in global memory, written before the launch) into shared memory,
+// completing on `bar`.  x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map,
+                                            uint64_t *bar, int x, int y, int z,
+                                            int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(shared_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(shared_addr(bar)), "r"(x),
+      "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+
+}  // namespace dev
+}  // namespace nrr

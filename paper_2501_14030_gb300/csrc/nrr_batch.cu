@@ -11,6 +11,7 @@
 // and the per-solve stop test -- is one CUDA graph whose loop is a
 // conditional WHILE node driven by an on-device control kernel (bounded by a
 // chunk limit and a wall-clock limit read from the global timer).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,6 +72,7 @@ struct SolveDev {
   float *ac2, *fu, *fv;          // linearised source and forcing
   ColumnSet<float> c32;
   double *jac, *rad;
+  dev::TmaFields tf64, tf32;     // tensor maps of the FP64 / FP32 fields
 };
 
 // Control block of one relaxation, in device memory.
@@ -155,23 +157,56 @@ __device__ __forceinline__ StageArgs<float> batch_stage_args<float>(
 
 // --- kernels ----------------------------------------------------------------
 constexpr int kTileY = 4;
+constexpr int kBulkPZ = 2;  // phi planes per ring slot (tensor-copy variant)
+// ring slots per block: the FP64 ring of 3 slots would exceed 48 KB
+template <typename R>
+__host__ __device__ constexpr int bulk_slots() { return sizeof(R) == 4 ? 3 : 2; }
+// i1 rows of the outer shell per shell block (NG columns each)
+template <int NG>
+__host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 
-// Stage kernel over all solves: block b works on solve map[b].x, tile
-// map[b].y of it (tiles counted i0 fastest, then i1, then phi chunks, with
-// one extra i0 tile per row for the outer shell).
-template <typename R, int NG, int KIND>
+// Stage kernel over all solves: block b works on solve map[b].x, item
+// map[b].y of it: first the interior tiles (i0 fastest, then i1, then phi
+// chunks), then the outer-shell blocks (shell_rows() rows of i1 each, then
+// phi chunks).  VAR 0: planes staged
+// through registers (stage_tile_block); VAR 1: planes streamed by tensor
+// copies through a ring of shared-memory slots (stage_bulk_block; order 8,
+// aligned grids), which records an expired copy wait in *err.
+template <typename R, int NG, int KIND, int VAR>
 __global__ void __launch_bounds__(32 * kTileY)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
-                       const int *__restrict__ active, int stage, int mode, int zc) {
-  __shared__ R tile[2][kTileY + 2 * NG][32 + 2 * NG];
+                       const int *__restrict__ active, int stage, int mode, int zc,
+                       int *err) {
   const int2 bm = map[blockIdx.x];
   if (!active[bm.x]) return;
   const SolveDev &sd = sds[bm.x];
   const Geo g = sd.g;
-  const int nx = dev::tiles_x(g) + 1, ny = dev::tiles_y<kTileY>(g);
+  const int nx = dev::tiles_x(g), ny = dev::tiles_y<kTileY>(g);
+  const int nint = nx * ny * dev::chunks_z(g, zc);
   const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
-  dev::stage_tile_block<R, NG, KIND, kTileY>(g, a, bm.y % nx, (bm.y / nx) % ny,
-                                             bm.y / (nx * ny), zc, tile);
+  if (bm.y >= nint) {
+    // outer shell: thread = (shell column, row) of shell_rows<NG>() rows
+    constexpr int rows = shell_rows<NG>();
+    const int nsb = (g.n1 + rows - 1) / rows;
+    const int sidx = bm.y - nint, chunk = sidx / nsb;
+    const int row = threadIdx.x / NG, lane = threadIdx.x - row * NG;
+    const int z0 = NG + chunk * zc;
+    if (row < rows)
+      dev::stage_shell_rows<R, NG, KIND>(g, a, lane, NG + (sidx % nsb) * rows + row,
+                                         z0, min(z0 + zc, NG + g.n2));
+    return;
+  }
+  const int tile_x = bm.y % nx, tile_y = (bm.y / nx) % ny, chunk = bm.y / (nx * ny);
+  if constexpr (VAR == 1) {
+    __shared__ __align__(128) dev::BulkSlot<R, NG, kTileY, kBulkPZ> ring[bulk_slots<R>()];
+    __shared__ __align__(8) uint64_t full[bulk_slots<R>()];
+    dev::stage_bulk_block<R, NG, KIND, kTileY, bulk_slots<R>(), kBulkPZ>(
+        g, a, tile_x, tile_y, chunk, zc, sizeof(R) == 4 ? sd.tf32 : sd.tf64, ring,
+        full, err);
+  } else {
+    __shared__ R tile[2][kTileY + 2 * NG][32 + 2 * NG];
+    dev::stage_tile_block<R, NG, KIND, kTileY>(g, a, tile_x, tile_y, chunk, zc, tile);
+  }
 }
 
 // FP64 residual partial sums over all solves (2 phi planes per item).
@@ -347,10 +382,14 @@ struct nrr_batch {
   int2 *d_map_stage[5] = {};
   int nblk_stage[5] = {};
   int zc[2] = {4, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
+  int variant[2] = {0, 0};  // stage kernel: 0 register-staged, 1 bulk copies
+  int bulk_ok = 0;          // every solve meets the bulk variant's alignment
+  int *d_err = nullptr;     // set by a stage kernel whose copy wait expired
+  CUtensorMap *d_maps = nullptr;  // per solve: u / operand maps, FP32 then FP64
   int64_t total_points = 0, interior_points = 0;
   // relaxation graph and its key
   cudaGraphExec_t exec = nullptr;
-  int g_mode = -1, g_every = 0, g_zc64 = 0, g_zc32 = 0;
+  int g_mode = -1, g_every = 0, g_zc64 = 0, g_zc32 = 0, g_var64 = 0, g_var32 = 0;
   double g_r_int = 0.0;
 };
 
@@ -438,11 +477,13 @@ int zc_index(int zc) {  // planes per chunk 1, 2, 4, 8, 16 -> slots 0..4
 nrr_status stage_map(nrr_batch *b, int zc) {
   if (b->d_map_stage[zc_index(zc)]) return NRR_OK;
   const int ng = b->ng;
-  (void)ng;
   return build_map(
       b, 1,
-      [zc](const Geo &g) {
-        return (int64_t)(dev::tiles_x(g) + 1) * dev::tiles_y<kTileY>(g) *
+      [zc, ng](const Geo &g) {
+        const int rows = ng == 2 ? shell_rows<2>() : ng == 5 ? shell_rows<5>()
+                                                           : shell_rows<4>();
+        return ((int64_t)dev::tiles_x(g) * dev::tiles_y<kTileY>(g) +
+                (g.n1 + rows - 1) / rows) *
                dev::chunks_z(g, zc);
       },
       &b->d_map_stage[zc_index(zc)], &b->nblk_stage[zc_index(zc)], nullptr);
@@ -453,8 +494,15 @@ void launch_bstage_kind(nrr_batch *b, int zc, int stage, int mode,
                         cudaStream_t st) {
   const int2 *map = b->d_map_stage[zc_index(zc)];
   const int nb = b->nblk_stage[zc_index(zc)];
-  batch_stage_kernel<R, NG, KIND><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
-                                                          stage, mode, zc);
+  if constexpr (NG == 4) {
+    if (b->variant[sizeof(R) == 4] == 1) {
+      batch_stage_kernel<R, NG, KIND, 1><<<nb, 32 * kTileY, 0, st>>>(
+          b->d_sd, map, b->d_active, stage, mode, zc, b->d_err);
+      return;
+    }
+  }
+  batch_stage_kernel<R, NG, KIND, 0><<<nb, 32 * kTileY, 0, st>>>(
+      b->d_sd, map, b->d_active, stage, mode, zc, b->d_err);
 }
 
 template <typename R, int NG>
@@ -513,7 +561,8 @@ void launch_chunk(nrr_batch *b, int mode, int every, double r_int,
 
 nrr_status build_relax_graph(nrr_batch *b, int mode, int every, double r_int) {
   if (b->exec && b->g_mode == mode && b->g_every == every &&
-      b->g_r_int == r_int && b->g_zc64 == b->zc[0] && b->g_zc32 == b->zc[1])
+      b->g_r_int == r_int && b->g_zc64 == b->zc[0] && b->g_zc32 == b->zc[1] &&
+      b->g_var64 == b->variant[0] && b->g_var32 == b->variant[1])
     return NRR_OK;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -576,7 +625,37 @@ nrr_status build_relax_graph(nrr_batch *b, int mode, int every, double r_int) {
   b->g_r_int = r_int;
   b->g_zc64 = b->zc[0];
   b->g_zc32 = b->zc[1];
+  b->g_var64 = b->variant[0];
+  b->g_var32 = b->variant[1];
   return NRR_OK;
+}
+
+using TensorMapEncodeFn = CUresult (*)(
+    CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+    CUtensorMapFloatOOBfill);
+
+// 4-D tensor map (i0, i1, i2, field) over the fields of one solve: `base` is
+// its field 0, consecutive fields `stride` elements apart; boxes of
+// box0 x box1 x box2 points of one field.
+bool encode_field_map(CUtensorMap *m, const void *base, const Geo &g,
+                      int nfields, int64_t stride, int esize, int box0, int box1,
+                      int box2) {
+  auto enc = reinterpret_cast<TensorMapEncodeFn>(tensor_map_encoder());
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.s0, (cuuint64_t)g.s1, (cuuint64_t)g.s2,
+                              (cuuint64_t)nfields};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.s0 * esize,
+                                 (cuuint64_t)g.ncol * esize,
+                                 (cuuint64_t)stride * esize};
+  const cuuint32_t box[4] = {(cuuint32_t)box0, (cuuint32_t)box1, (cuuint32_t)box2, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+             4, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 nrr_status bbegin(nrr_batch *b) {
@@ -757,6 +836,39 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
     }
     BTRY(balloc(b, &b->d_sd, (size_t)n));
     BTRY(balloc(b, &b->d_active, (size_t)n));
+    BTRY(balloc(b, &b->d_err, 1));
+    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    // Bulk-copy stage variant: order 8, whole 32-wide tiles in i0 and 4-row
+    // tiles in i1, and rows / field bases on 16-byte boundaries in both
+    // precisions (s0 and every solve's offset multiples of 4 elements).
+    b->bulk_ok = ng == 4;
+    for (int s = 0; s < n; s++) {
+      const Geo &g = b->geos[s];
+      if (g.n0 % 32 || g.n1 % kTileY || g.s0 % 4 || g.npts % 4) b->bulk_ok = 0;
+    }
+    if (b->bulk_ok) {
+      std::vector<CUtensorMap> maps(4 * (size_t)n);
+      BTRY(balloc(b, &b->d_maps, maps.size()));
+      for (int s = 0; s < n && b->bulk_ok; s++) {
+        const Geo &g = b->geos[s];
+        SolveDev &sd = b->host_sd[s];
+        const int tw = 32 + 2 * ng, th = kTileY + 2 * ng;
+        const int pz = kBulkPZ;
+        bool ok = encode_field_map(&maps[4 * s + 0], sd.d, g, 11, total, 4, tw, th, pz) &&
+                  encode_field_map(&maps[4 * s + 1], sd.d, g, 11, total, 4, 32, kTileY, pz) &&
+                  encode_field_map(&maps[4 * s + 2], sd.u, g, n64, total, 8, tw, th, pz) &&
+                  encode_field_map(&maps[4 * s + 3], sd.u, g, n64, total, 8, 32, kTileY, pz);
+        if (!ok) {
+          b->bulk_ok = 0;
+          break;
+        }
+        sd.tf32 = {b->d_maps + 4 * s + 0, b->d_maps + 4 * s + 1, sd.d, total};
+        sd.tf64 = {b->d_maps + 4 * s + 2, b->d_maps + 4 * s + 3, sd.u, total};
+      }
+      if (b->bulk_ok)
+        BCUDA(cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                         cudaMemcpyHostToDevice));
+    }
     BTRY(balloc(b, &b->d_norms, (size_t)n));
     BTRY(balloc(b, &b->d_steps, (size_t)n));
     BTRY(balloc(b, &b->d_ctl, 1));
@@ -843,7 +955,11 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
   ctl.tol = o->tol;
   BCUDA(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, b->stream));
   BTRY(build_relax_graph(b, o->mode, every, o->r_int));
+  BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
   BCUDA(cudaGraphLaunch(b->exec, b->stream));
+  int herr = 0;
+  BCUDA(cudaMemcpyAsync(&herr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                        b->stream));
   std::vector<double> norms(b->n);
   std::vector<long long> steps(b->n);
   BCUDA(cudaMemcpyAsync(norms.data(), b->d_norms, b->n * sizeof(double),
@@ -855,6 +971,8 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
   BCUDA(cudaMemcpyAsync(&ctl, b->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, b->stream));
   BCUDA(cudaStreamSynchronize(b->stream));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (herr)
+    return bfail(NRR_ERR_TIMEOUT, "a stage kernel's shared-memory copy wait expired");
   int n_ok = 0, n_div = 0;
   int64_t max_steps = 0;
   double max_norm = 0.0;
@@ -938,8 +1056,26 @@ nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst) {
   return NRR_OK;
 }
 
+nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc) {
+  if (!b) return bfail(NRR_ERR_INVALID_ARG, "null batch");
+  if (mode != NRR_FP64 && mode != NRR_FP32_DC)
+    return bfail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32_DC");
+  if (variant != 0 && variant != 1)
+    return bfail(NRR_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (variant == 1 && !b->bulk_ok)
+    return bfail(NRR_ERR_INVALID_ARG,
+                 "the bulk-copy variant needs order 8, n0 %% 32 == 0, n1 %% 4 == 0");
+  if (zc != 2 && zc != 4 && zc != 8 && zc != 16)
+    return bfail(NRR_ERR_INVALID_ARG, "zc must be 2, 4, 8 or 16");
+  const int slot = mode == NRR_FP32_DC;
+  b->variant[slot] = variant;
+  b->zc[slot] = zc;
+  return NRR_OK;
+}
+
 nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
-                              int *best_zc, double *best_ms_per_launch) {
+                              int *best_zc, double *best_ms_per_launch,
+                              int *best_variant) {
   if (!b) return bfail(NRR_ERR_INVALID_ARG, "null batch");
   if (mode != NRR_FP64 && mode != NRR_FP32_DC)
     return bfail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32_DC");
@@ -972,10 +1108,13 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
   cudaEvent_t e0, e1;
   BCUDA(cudaEventCreate(&e0));
   BCUDA(cudaEventCreate(&e1));
-  const int keep = b->zc[slot];
-  int best = keep;
+  int best = b->zc[slot], best_var = b->variant[slot];
   double best_ms = 1e30;
-  for (int zc : {2, 4, 8, 16}) {
+  const int cands[7][2] = {{0, 2}, {0, 4}, {0, 8}, {0, 16}, {1, 4}, {1, 8}, {1, 16}};
+  for (const auto &cv : cands) {
+    const int var = cv[0], zc = cv[1];
+    if (var == 1 && !b->bulk_ok) continue;
+    b->variant[slot] = var;
     b->zc[slot] = zc;
     BTRY(stage_map(b, zc));
     for (int rep = 0; rep < 2; rep++) {
@@ -993,12 +1132,18 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
       if (rep == 1 && per < best_ms) {
         best_ms = per;
         best = zc;
+        best_var = var;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->zc[slot] = best;
+  b->variant[slot] = best_var;
+  int herr = 0;
+  BCUDA(cudaMemcpy(&herr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr)
+    return bfail(NRR_ERR_TIMEOUT, "a stage kernel's shared-memory copy wait expired");
   if (mode == NRR_FP64)
     for (int s = 0; s < b->n; s++) {
       size_t by = (size_t)b->geos[s].npts * sizeof(double);
@@ -1008,6 +1153,7 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
   BCUDA(cudaStreamSynchronize(b->stream));
   if (best_zc) *best_zc = best;
   if (best_ms_per_launch) *best_ms_per_launch = best_ms;
+  if (best_variant) *best_variant = best_var;
   return NRR_OK;
 }
 

@@ -236,7 +236,15 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeFn encoder() {
-  static EncodeFn fn = nullptr;
+  return reinterpret_cast<EncodeFn>(tensor_map_encoder());
+}
+
+}  // namespace
+
+// cuTensorMapEncodeTiled from the driver, looked up once; null if the driver
+// does not provide it.
+void *tensor_map_encoder() {
+  static void *fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
     void *p = nullptr;
@@ -244,10 +252,12 @@ EncodeFn encoder() {
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
                                          cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
+      fn = p;
   });
   return fn;
 }
+
+namespace {
 
 // Tensor map of a row-major [rows][cols] BF16 matrix read in tiles of
 // box_rows x 64 with 128-byte swizzle.

@@ -11,6 +11,9 @@ namespace nrr {
 // Sets the calling thread's message returned by nrr_last_error().
 void set_last_error(const char *msg);
 
+// The driver's cuTensorMapEncodeTiled (as a plain pointer), or null.
+void *tensor_map_encoder();
+
 // Stage kinds of the fused RK4 stage kernel (classical RK4: k1..k4 with
 // weights 1/6, 1/3, 1/3, 1/6 and stage offsets 1/2, 1/2, 1):
 //   FIRST: acc = y + b dt k;  out = y + a dt k        (input state: y)

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "nrr_async.cuh"
 #include "nrr_internal.h"
 
 namespace nrr {
@@ -351,7 +352,9 @@ namespace dev {
 // NG-wide halo into shared memory (inner-boundary halo cells read from their
 // images, so the phi + pi planes of reflected cells come in here), each
 // thread keeps the 2NG+1 phi neighbours of its column in a register queue,
-// and the folded column weights are loaded once per thread.  Extra blocks
+// and the folded column weights are loaded once per thread.  The loads of
+// plane i2 + 1 (staged cells and operands, into registers) are issued before
+// plane i2 is computed; one barrier per plane.  Extra blocks
 // (tile_x == number of interior tiles) evolve the outer shell with the
 // radiation condition.
 // ---------------------------------------------------------------------------
@@ -366,6 +369,34 @@ template <int TY>
 __host__ __device__ __forceinline__ int tiles_y(const Geo &g) { return (g.n1 + TY - 1) / TY; }
 __host__ __device__ __forceinline__ int chunks_z(const Geo &g, int zc) { return (g.n2 + zc - 1) / zc; }
 
+// Outer-shell rows of the tiled stage kernels: lane tx < NG of a tile row
+// evolves column (n0 + NG + tx, i1) on planes [z0, z1) with the radiation
+// condition df/dt = -c (d_r f + f/r).
+template <typename R, int NG, int KIND>
+__device__ __forceinline__ void stage_shell_rows(const Geo &g, const StageArgs<R> &a,
+                                                 int tx, int i1, int z0, int z1) {
+  if (tx >= NG || i1 >= g.n1 + NG) return;
+  const int nc = g.ncol;
+  const int i0 = g.n0 + NG + tx;
+  const int col = i0 + g.s0 * i1;
+  const R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
+          rinv = ld(a.col.somm + 2 * nc + col);
+  pdl_wait();
+#pragma unroll 4
+  for (int i2 = z0; i2 < z1; i2++) {
+    const int64_t p = col + (int64_t)nc * i2;
+    R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
+    R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+    R ku = -c * fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), rinv * u0);
+    R kv = -c * fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), rinv * v0);
+    if (linear_mode<R>(a.lin)) {
+      ku += ld(a.fu + p);
+      kv += ld(a.bc2 + p);
+    }
+    stage_epilogue<R, KIND>(a, p, ku, kv);
+  }
+}
+
 template <typename R, int NG, int KIND, int TY>
 __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R> &a,
                                                  int tile_x, int tile_y, int chunk,
@@ -377,30 +408,50 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
   const int z1 = min(z0 + zc, NG + g.n2);
   const int i1 = NG + tile_y * TY + ty;
   if (tile_x == tiles_x(g)) {
-    // outer shell: radiation condition, df/dt = -c (d_r f + f/r)
-    if (tx >= NG || i1 >= g.n1 + NG) return;
-    const int i0 = g.n0 + NG + tx;
-    const int col = i0 + g.s0 * i1;
-    const R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
-            rinv = ld(a.col.somm + 2 * nc + col);
-    pdl_wait();
-    for (int i2 = z0; i2 < z1; i2++) {
-      const int64_t p = col + (int64_t)nc * i2;
-      R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
-      R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
-      R ku = -c * fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), rinv * u0);
-      R kv = -c * fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), rinv * v0);
-      if (linear_mode<R>(a.lin)) {
-        ku += ld(a.fu + p);
-        kv += ld(a.bc2 + p);
-      }
-      stage_epilogue<R, KIND>(a, p, ku, kv);
-    }
+    stage_shell_rows<R, NG, KIND>(g, a, tx, i1, z0, z1);
     return;
   }
   const int i0 = NG + tile_x * 32 + tx;
   const bool active = i0 < g.n0 + NG && i1 < g.n1 + NG;
   const int col = i0 + g.s0 * i1;
+  constexpr int NT = 32 * TY;                   // threads of the block
+  constexpr int NST = (TW * TH + NT - 1) / NT;  // staged cells per thread
+  // The staged cells of this thread (flat index threadIdx.x + k NT of the
+  // TH x TW tile with halo): in-plane offset of the cell's source -- its
+  // image for an inner-boundary halo cell -- and whether that source lies on
+  // the plane phi + pi; -1 for cells past the padded box, which no evolved
+  // point reads.  Computed once; every plane reuses them.
+  int soff[NST];
+  unsigned flip = 0;
+  {
+    const int j0b = tile_x * 32, j1b = tile_y * TY;
+#pragma unroll
+    for (int k = 0; k < NST; k++) {
+      const int cidx = threadIdx.x + k * NT;
+      soff[k] = -1;
+      if (cidx < TW * TH) {
+        const int cy = cidx / TW, cx = cidx - cy * TW;
+        int j0 = j0b + cx, j1 = j1b + cy;
+        if (j0 < g.s0 && j1 < g.s1) {
+          unsigned f = 0;
+          if (j0 < NG) {
+            j0 = 2 * NG - 1 - j0;
+            f = 1;
+            if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
+          }
+          if (j1 < NG) {
+            j1 = 2 * NG - 1 - j1;
+            f ^= 1;
+          } else if (j1 >= g.n1 + NG) {
+            j1 = 2 * g.n1 + 2 * NG - 1 - j1;
+            f ^= 1;
+          }
+          soff[k] = j0 + g.s0 * j1;
+          flip |= f << k;
+        }
+      }
+    }
+  }
   R w[5 * NG + 1];
   R q[2 * NG + 1];
   if (active) {
@@ -413,50 +464,54 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
     for (int k = 0; k < 2 * NG; k++)
       q[k + 1] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
   }
-  const int j0b = NG + tile_x * 32 - NG, j1b = NG + tile_y * TY - NG;
+  // Registers holding the next plane: its staged cells and this thread's
+  // operands.  Plane i2 + 1 is fetched before plane i2 is computed, so its
+  // loads are in flight during the arithmetic.
+  R sreg[NST];
+  R nv = R(0), nal = R(0), nbc = R(0), nyb0 = R(0), nyb1 = R(0), nac0 = R(0),
+    nac1 = R(0), nfu = R(0), nq = R(0);
+#define NRR_TILE_FETCH(PL)                                                       \
+  do {                                                                           \
+    const int pl_ = (PL);                                                        \
+    const R *base_ = a.su + (int64_t)nc * pl_;                                   \
+    const R *bflip_ = a.su + (int64_t)nc * wrap_plane<NG>(g, pl_ + g.n2 / 2);    \
+    _Pragma("unroll") for (int k = 0; k < NST; k++) if (soff[k] >= 0)            \
+        sreg[k] = ld(((flip >> k) & 1u ? bflip_ : base_) + soff[k]);             \
+    if (active) {                                                                \
+      const int64_t p_ = col + (int64_t)nc * pl_;                                \
+      nv = ld(a.sv + p_);                                                        \
+      nal = ld(a.alpha + p_);                                                    \
+      nbc = ld(a.bc2 + p_);                                                      \
+      if (KIND == STAGE_FIRST || KIND == STAGE_MID) {                            \
+        nyb0 = ld(a.bu + p_);                                                    \
+        nyb1 = ld(a.bv + p_);                                                    \
+      }                                                                          \
+      if (KIND == STAGE_MID || KIND == STAGE_LAST) {                             \
+        nac0 = a.au[p_];                                                         \
+        nac1 = a.av[p_];                                                         \
+      }                                                                          \
+      if (linear_mode<R>(a.lin)) nfu = ld(a.fu + p_);                            \
+      nq = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, pl_ + NG));           \
+    }                                                                            \
+  } while (0)
+  NRR_TILE_FETCH(z0);
   int buf = 0;
   for (int i2 = z0; i2 < z1; i2++, buf ^= 1) {
-    // stage plane i2 (tile + halo) into shared memory
-    for (int cidx = threadIdx.x; cidx < TW * TH; cidx += 32 * TY) {
-      const int cy = cidx / TW, cx = cidx - cy * TW;
-      int j0 = j0b + cx, j1 = j1b + cy, j2 = i2;
-      if (j0 >= g.s0 || j1 >= g.s1) continue;
-      if (j0 < NG || j1 < NG || j1 >= g.n1 + NG) {
-        // inner-boundary halo cell: its image, on the plane phi + pi
-        int flip = 0;
-        if (j0 < NG) {
-          j0 = 2 * NG - 1 - j0;
-          flip = 1;
-          if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
-        }
-        if (j1 < NG) {
-          j1 = 2 * NG - 1 - j1;
-          flip ^= 1;
-        } else if (j1 >= g.n1 + NG) {
-          j1 = 2 * g.n1 + 2 * NG - 1 - j1;
-          flip ^= 1;
-        }
-        if (flip) j2 = wrap_plane<NG>(g, j2 + g.n2 / 2);
-      }
-      tile[buf][cy][cx] = ld(a.su + j0 + g.s0 * (j1 + g.s1 * j2));
-    }
+    // Commit plane i2.  The barrier of the previous iteration ordered every
+    // thread's reads of tile[buf] (two planes back) before these writes.
+    R *flat_ = &tile[buf][0][0];
+#pragma unroll
+    for (int k = 0; k < NST; k++)
+      if (soff[k] >= 0) flat_[threadIdx.x + k * NT] = sreg[k];
+    const R v0 = nv, al = nal, bc = nbc, yb0 = nyb0, yb1 = nyb1, ac0 = nac0,
+            ac1 = nac1, fu = nfu;
+#pragma unroll
+    for (int k = 0; k < 2 * NG; k++) q[k] = q[k + 1];
+    q[2 * NG] = nq;
     __syncthreads();
+    if (i2 + 1 < z1) NRR_TILE_FETCH(i2 + 1);
     if (active) {
       const int64_t p = col + (int64_t)nc * i2;
-#pragma unroll
-      for (int k = 0; k < 2 * NG; k++) q[k] = q[k + 1];
-      q[2 * NG] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + NG));
-      const R v0 = ld(a.sv + p), al = ld(a.alpha + p), bc = ld(a.bc2 + p);
-      R yb0 = R(0), yb1 = R(0), ac0 = R(0), ac1 = R(0);
-      if (KIND == STAGE_FIRST || KIND == STAGE_MID) {
-        yb0 = ld(a.bu + p);
-        yb1 = ld(a.bv + p);
-      }
-      if (KIND == STAGE_MID || KIND == STAGE_LAST) {
-        ac0 = a.au[p];
-        ac1 = a.av[p];
-      }
-      const R fu = linear_mode<R>(a.lin) ? ld(a.fu + p) : R(0);
       const R(&t)[TH][TW] = tile[buf];
       const R u0 = t[ty + NG][tx + NG];
       R a0 = w[0] * u0, a1;
@@ -490,6 +545,243 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
       } else if (KIND == STAGE_LAST) {
         a.ou[p] = fma(a.wb, ku, ac0);
         a.ov[p] = fma(a.wb, kv, ac1);
+      } else {
+        a.ou[p] = ku;
+        a.ov[p] = kv;
+      }
+    }
+  }
+#undef NRR_TILE_FETCH
+}
+
+
+// ---------------------------------------------------------------------------
+// TMA-fed tiled stage (same work split as stage_tile_block, order 8): the
+// planes of a block's chunk stream, PZ at a time, through a ring of NS
+// shared-memory slots, each filled by tiled tensor copies -- one
+// (32 + 2 NG) x (TY + 2 NG) x PZ box of u with its halo and one 32 x TY x PZ
+// box per operand array -- that complete on the slot's mbarrier and are
+// issued NS - 1 slots ahead by one thread.  The tensor maps are 4-D (i0, i1,
+// i2, field) over a precision's field arena, one pair per solve.  Each
+// thread evaluates PZ points of its column per slot; it fetches only the
+// inner-boundary image cells itself, one slot ahead, overwriting the box's
+// unmaintained ghost cells.  Requires n0 % 32 == 0, n1 % TY == 0 and the
+// chunk's plane count a multiple of PZ (checked on the host).  In the FIRST
+// stage the base state is the input state (bu == su, bv == sv).
+// ---------------------------------------------------------------------------
+struct TmaFields {
+  const CUtensorMap *map_u;   // box (32 + 2 NG, TY + 2 NG, PZ, 1)
+  const CUtensorMap *map_op;  // box (32, TY, PZ, 1)
+  const void *base;           // field 0 of this solve in the arena
+  int64_t stride;             // elements between consecutive fields
+};
+
+template <typename R, int NG, int TY, int PZ>
+struct BulkSlot {
+  R u[PZ][TY + 2 * NG][32 + 2 * NG];  // PZ planes of u with halo
+  R op[8][PZ][TY][32];                // operand rows, slots below
+};
+enum BulkOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
+
+template <typename R, int NG, int KIND, int TY, int NS, int PZ>
+__device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R> &a,
+                                                 int tile_x, int tile_y, int chunk,
+                                                 int zc, const TmaFields &tf,
+                                                 BulkSlot<R, NG, TY, PZ> *ring,
+                                                 uint64_t *full, int *err) {
+  static_assert((NG * sizeof(R)) % 16 == 0,
+                "operand boxes start at x = NG: 16-byte aligned");
+  constexpr int TW = 32 + 2 * NG, TH = TY + 2 * NG;
+  constexpr int NT = 32 * TY;
+  constexpr int NST = (TW * TH + NT - 1) / NT;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nc = g.ncol;
+  const int z0 = NG + chunk * zc;
+  const int z1 = min(z0 + zc, NG + g.n2);
+  const int i1 = NG + tile_y * TY + ty;
+  if (tile_x == tiles_x(g)) {
+    stage_shell_rows<R, NG, KIND>(g, a, tx, i1, z0, z1);
+    return;
+  }
+  const int nslots = (z1 - z0) / PZ;
+  const int i0 = NG + tile_x * 32 + tx;
+  const int col = i0 + g.s0 * i1;
+  const int j0b = tile_x * 32, j1b = tile_y * TY;
+  const bool use_fu = linear_mode<R>(a.lin);
+  constexpr bool use_b = KIND == STAGE_MID;
+  constexpr bool use_acc = KIND == STAGE_MID || KIND == STAGE_LAST;
+  // Image cells of this thread (tile cells whose source is not the cell
+  // itself): offset of the image in its plane and whether it lies on the
+  // plane phi + pi; -1 for the other cells.
+  int soff[NST];
+  unsigned flip = 0;
+  bool has_img = false;
+#pragma unroll
+  for (int k = 0; k < NST; k++) {
+    const int cidx = threadIdx.x + k * NT;
+    soff[k] = -1;
+    if (cidx < TW * TH) {
+      const int cy = cidx / TW, cx = cidx - cy * TW;
+      int j0 = j0b + cx, j1 = j1b + cy;
+      if (j0 < NG || j1 < NG || j1 >= g.n1 + NG) {
+        unsigned f = 0;
+        if (j0 < NG) {
+          j0 = 2 * NG - 1 - j0;
+          f = 1;
+          if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
+        }
+        if (j1 < NG) {
+          j1 = 2 * NG - 1 - j1;
+          f ^= 1;
+        } else if (j1 >= g.n1 + NG) {
+          j1 = 2 * g.n1 + 2 * NG - 1 - j1;
+          f ^= 1;
+        }
+        soff[k] = j0 + g.s0 * j1;
+        flip |= f << k;
+        has_img = true;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NS; k++) mbar_init_count(&full[k], 1);
+    mbar_init_fence();
+  }
+  R w[5 * NG + 1];
+#pragma unroll
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+  __syncthreads();
+  pdl_wait();
+  // Operands this stage reads (slot mask) and their field indices (the 4th
+  // tensor coordinate); thread 0 issues every copy.
+  const unsigned opmask = (1u << OP_SV) | (1u << OP_AL) | (1u << OP_BC) |
+                          (use_fu ? 1u << OP_FU : 0u) |
+                          (use_b ? (1u << OP_BU) | (1u << OP_BV) : 0u) |
+                          (use_acc ? (1u << OP_AU) | (1u << OP_AV) : 0u);
+  const uint32_t slot_bytes =
+      (uint32_t)(PZ * (TW * TH + __popc(opmask) * TY * 32) * sizeof(R));
+  // Field index of u (fidx[8]) and of each operand: thread 0 only.
+  int fidx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  auto issue = [&](int pl, int sl) {
+    mbar_arrive_expect(&full[sl], slot_bytes);
+    fence_proxy_async_smem();
+    tma_load_4d(&ring[sl].u[0][0][0], tf.map_u, &full[sl], j0b, j1b, pl, fidx[8]);
+#pragma unroll
+    for (int o = 0; o < 8; o++)
+      if ((opmask >> o) & 1u)
+        tma_load_4d(&ring[sl].op[o][0][0][0], tf.map_op, &full[sl], NG + j0b,
+                    NG + j1b, pl, fidx[o]);
+  };
+  if (threadIdx.x == 0) {
+    const R *b0 = static_cast<const R *>(tf.base);
+    const R *optr[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
+#pragma unroll
+    for (int o = 0; o < 8; o++)
+      if ((opmask >> o) & 1u) fidx[o] = (int)((optr[o] - b0) / tf.stride);
+    fidx[8] = (int)((a.su - b0) / tf.stride);
+    for (int k = 0; k < NS - 1 && k < nslots; k++) issue(z0 + PZ * k, k);
+  }
+  // phi queue of this column (planes i2 - NG .. i2 + NG of the slot's first
+  // plane i2) and the image cells of the next slot
+  R q[2 * NG + PZ];
+#pragma unroll
+  for (int k = 0; k < 2 * NG; k++)
+    q[k + PZ] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
+  R nq[PZ];
+#pragma unroll
+  for (int j = 0; j < PZ; j++)
+    nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 + NG + j));
+  R ireg[PZ][NST];
+  auto fetch_images = [&](int pl) {
+    if (!has_img) return;
+#pragma unroll
+    for (int j = 0; j < PZ; j++) {
+      const R *base = a.su + (int64_t)nc * (pl + j);
+      const R *bflip = a.su + (int64_t)nc * wrap_plane<NG>(g, pl + j + g.n2 / 2);
+#pragma unroll
+      for (int k = 0; k < NST; k++)
+        if (soff[k] >= 0) ireg[j][k] = ld(((flip >> k) & 1u ? bflip : base) + soff[k]);
+    }
+  };
+  fetch_images(z0);
+  for (int it = 0; it < nslots; it++) {
+    const int i2 = z0 + PZ * it, sl = it % NS;
+    const bool ok = mbar_wait_parity(&full[sl], (uint32_t)((it / NS) & 1));
+    BulkSlot<R, NG, TY, PZ> &S = ring[sl];
+    if (has_img) {
+#pragma unroll
+      for (int j = 0; j < PZ; j++) {
+        R *flat_u = &S.u[j][0][0];
+#pragma unroll
+        for (int k = 0; k < NST; k++)
+          if (soff[k] >= 0) flat_u[threadIdx.x + k * NT] = ireg[j][k];
+      }
+      // these cells are refilled by tensor copies when the slot comes round
+      fence_proxy_async_smem();
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
+#pragma unroll
+    for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
+    if (__syncthreads_or(!ok)) {
+      // A copy did not complete in time: record it, let the copies still in
+      // flight (slots it .. it + NS - 2) land, bounded, and leave.
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int j = it; j < nslots && j < it + NS - 1; j++)
+          mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0 && it + NS - 1 < nslots)
+      issue(i2 + PZ * (NS - 1), (it + NS - 1) % NS);
+    if (it + 1 < nslots) {
+      fetch_images(i2 + PZ);
+#pragma unroll
+      for (int j = 0; j < PZ; j++)
+        nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
+    }
+#pragma unroll
+    for (int j = 0; j < PZ; j++) {
+      const int64_t p = col + (int64_t)nc * (i2 + j);
+      const R(&t)[TH][TW] = S.u[j];
+      const R u0 = t[ty + NG][tx + NG];
+      const R v0 = S.op[OP_SV][j][ty][tx], al = S.op[OP_AL][j][ty][tx],
+              bc = S.op[OP_BC][j][ty][tx];
+      R a0 = w[0] * u0, a1;
+#pragma unroll
+      for (int k = 1; k <= NG; k++) {
+        a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
+        a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
+      }
+      a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
+      a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
+#pragma unroll
+      for (int k = 2; k <= NG; k++) {
+        a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
+        a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
+      }
+      // q[NG + j] is the centre plane i2 + j
+#pragma unroll
+      for (int k = 1; k <= NG; k++)
+        a0 = fma(w[4 * NG + k], q[NG + j + k] + q[NG + j - k], a0);
+      const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
+      R ku = fma(-a.eta, u0, v0);
+      if (use_fu) ku += S.op[OP_FU][j][ty][tx];
+      if (KIND == STAGE_FIRST) {
+        a.au[p] = fma(a.wb, ku, u0);
+        a.av[p] = fma(a.wb, kv, v0);
+        a.ou[p] = fma(a.wa, ku, u0);
+        a.ov[p] = fma(a.wa, kv, v0);
+      } else if (KIND == STAGE_MID) {
+        a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+        a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+        a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
+        a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
+      } else if (KIND == STAGE_LAST) {
+        a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+        a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
       } else {
         a.ou[p] = ku;
         a.ov[p] = kv;

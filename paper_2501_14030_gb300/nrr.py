@@ -33,7 +33,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
-           "nrr_batch_autotune", "nrr_gemm_bf16_tn", "nrr_surrogate_create",
+           "nrr_batch_autotune", "nrr_batch_set_launch", "nrr_gemm_bf16_tn", "nrr_surrogate_create",
            "nrr_surrogate_destroy", "nrr_surrogate_num_params",
            "nrr_surrogate_fit_scaling", "nrr_surrogate_train",
            "nrr_surrogate_predict", "nrr_surrogate_gradients",
@@ -117,7 +117,9 @@ def lib() -> C.CDLL:
         "nrr_batch_relax": [V, C.POINTER(RelaxOpts), C.POINTER(RelaxResult),
                             C.POINTER(RelaxResult)],
         "nrr_batch_get_u": [V, I, V, I],
-        "nrr_batch_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D],
+        "nrr_batch_autotune": [V, I, C.c_int64, C.POINTER(C.c_int), D,
+                               C.POINTER(C.c_int)],
+        "nrr_batch_set_launch": [V, I, I, I],
         "nrr_gemm_bf16_tn": [V, V, V, I, I, I, V],
         "nrr_surrogate_create": [I, I, I, I, I, C.POINTER(C.c_float), V,
                                  C.POINTER(V)],
@@ -436,12 +438,19 @@ class Batch:
         """Interior u of every solve (equal sizes) into a float32 tensor."""
         _check(lib().nrr_batch_get_interior(self._h, C.c_void_p(out.data_ptr())))
 
-    def autotune(self, mode="fp32_dc", trial_steps: int = 5):
+    def set_launch(self, variant: int, zc: int, mode="fp32_dc"):
+        """Stage kernel of the batch: variant 0 (register-staged planes) or
+        1 (bulk-copy plane ring), zc phi planes per block chunk."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        zc, ms = C.c_int(), C.c_double()
+        _check(lib().nrr_batch_set_launch(self._h, m, int(variant), int(zc)))
+
+    def autotune(self, mode="fp32_dc", trial_steps: int = 5):
+        """Pick the fastest stage kernel; returns (zc, ms/launch, variant)."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        zc, ms, var = C.c_int(), C.c_double(), C.c_int()
         _check(lib().nrr_batch_autotune(self._h, m, int(trial_steps),
-                                        C.byref(zc), C.byref(ms)))
-        return zc.value, ms.value
+                                        C.byref(zc), C.byref(ms), C.byref(var)))
+        return zc.value, ms.value, var.value
 
 
 class Surrogate:

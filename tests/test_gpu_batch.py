@@ -99,3 +99,55 @@ def test_batch_limits_end_the_graph(gpu):
                         raise_on_error=False)
     assert tot["status"] == nrr.ERR_TIMEOUT
     assert per[0]["status"] == nrr.ERR_TIMEOUT and per[0]["iters"] < 6400
+
+
+def aligned_batch(count=4, seed=5, coord="sinhsymtp"):
+    """Order-8 grids that admit the bulk-copy stage variant (n0 % 32 == 0,
+    n1 % 4 == 0), uneven sizes including the axis and theta-edge tiles."""
+    rng = np.random.default_rng(seed)
+    params = W.batch_parameters(count, seed)
+    descs, puncs = [], []
+    for p in params:
+        n = (int(rng.choice([32, 64])), int(rng.choice([8, 12, 20])),
+             int(rng.choice([4, 8])))
+        descs.append(W.grid_desc(coord, n, 8, bscale=p["d"] / 2))
+        puncs.append(p["punctures"])
+    return descs, puncs
+
+
+@pytest.mark.parametrize("coord,mode", [("sinhsymtp", "fp32_dc"),
+                                        ("sinhsymtp", "fp64"),
+                                        ("spherical", "fp32_dc")])
+def test_bulk_copy_variant_bitwise_equals_register_variant(gpu, coord, mode):
+    """Both batch stage kernels evaluate the same arithmetic in the same order
+    on the same operands: after 300 RK4 steps every solve agrees bit for bit,
+    for each plane chunking."""
+    descs, puncs = aligned_batch(coord=coord)
+    results = []
+    for var, zc in [(0, 4), (1, 2), (1, 4), (1, 16)]:
+        b = nrr.Batch(descs, puncs, with_fp64=(mode == "fp64"))
+        b.set_launch(var, zc, mode)
+        per, _ = b.relax(mode=mode, tol=1e-30, max_iters=300, check_every=50,
+                         raise_on_error=False)
+        us = []
+        for i in range(len(descs)):
+            ub = np.zeros(b.shapes[i])
+            b.get_u(i, ub)
+            us.append(ub)
+        results.append(([r["norm"] for r in per], us))
+        b.close()
+    norms0, us0 = results[0]
+    assert all(np.isfinite(norms0)) and max(norms0) > 0
+    for norms, us in results[1:]:
+        assert norms == norms0
+        for a, b_ in zip(us, us0):
+            assert np.array_equal(a, b_)
+
+
+def test_bulk_copy_variant_refused_for_unaligned_grids(gpu):
+    descs, puncs = small_batch(count=2)
+    b = nrr.Batch(descs, puncs)
+    with pytest.raises(nrr.NrrError):
+        b.set_launch(1, 4, "fp32_dc")
+    b.set_launch(0, 4, "fp32_dc")
+    b.close()
