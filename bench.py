@@ -41,6 +41,12 @@ CHECK_EVERY = 50
 SMS, FP64_FMA_PER_CLK = 152, 2
 
 
+# DRAM bytes (read + write) per launch of the FP64 stage kernel at
+# 128x128x16, order 8, from one ncu capture of this kernel (dram__bytes_read
+# + dram__bytes_write, mean of a FIRST and a MID launch).
+STAGE_FP64_DRAM_BYTES = 16.36e6
+
+
 def flops_per_point(ng: int) -> int:
     """Algorithmic FP64 flops per interior point per fused stage launch, as
     the folded operator is evaluated: centre weight (1 mul), 2*ng FMAs in
@@ -243,7 +249,12 @@ def run_ours(args):
     achieved = flops / (ms_launch * 1e-3) / 1e12
     peak = SMS * FP64_FMA_PER_CLK * 2 * 2070e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": STAGE_FP64_DRAM_BYTES,
+                "traffic_note": "dram read+write bytes per launch from one ncu "
+                                "capture (cold L2 per replay; FIRST and MID "
+                                "launches averaged); the 35 MB working set is "
+                                "L2-resident in the timed run",
                 "kernel": "stage_curvi_kernel<double,4,*> (fused RHS + BC + RK4 stage)",
                 "ms_per_launch": ms_launch,
                 "flops_per_launch": flops,

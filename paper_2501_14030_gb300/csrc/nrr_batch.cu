@@ -173,7 +173,7 @@ __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 // copies through a ring of shared-memory slots (stage_bulk_block; order 8,
 // aligned grids), which records an expired copy wait in *err.
 template <typename R, int NG, int KIND, int VAR>
-__global__ void __launch_bounds__(32 * kTileY)
+__global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 5 : 1)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
                        const int *__restrict__ active, int stage, int mode, int zc,
                        int *err) {

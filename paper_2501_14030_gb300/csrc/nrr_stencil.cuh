@@ -704,87 +704,95 @@ __device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R
     }
   };
   fetch_images(z0);
-  for (int it = 0; it < nslots; it++) {
-    const int i2 = z0 + PZ * it, sl = it % NS;
-    const bool ok = mbar_wait_parity(&full[sl], (uint32_t)((it / NS) & 1));
-    BulkSlot<R, NG, TY, PZ> &S = ring[sl];
-    if (has_img) {
+  // The loop runs over rounds of NS slots, unrolled, so that slot indices
+  // and addresses are compile-time constants; `phase` is the parity of the
+  // round's barrier phases.
+  for (int base = 0, phase = 0; base < nslots; base += NS, phase ^= 1) {
+#pragma unroll
+    for (int sl = 0; sl < NS; sl++) {
+      const int it = base + sl;
+      if (it >= nslots) break;
+      const int i2 = z0 + PZ * it;
+      const bool ok = mbar_wait_parity(&full[sl], (uint32_t)phase);
+      BulkSlot<R, NG, TY, PZ> &S = ring[sl];
+      if (has_img) {
+#pragma unroll
+        for (int j = 0; j < PZ; j++) {
+          R *flat_u = &S.u[j][0][0];
+#pragma unroll
+          for (int k = 0; k < NST; k++)
+            if (soff[k] >= 0) flat_u[threadIdx.x + k * NT] = ireg[j][k];
+        }
+        // these cells are refilled by tensor copies when the slot comes round
+        fence_proxy_async_smem();
+      }
+#pragma unroll
+      for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
+#pragma unroll
+      for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
+      if (__syncthreads_or(!ok)) {
+        // A copy did not complete in time: record it, let the copies still in
+        // flight (slots it .. it + NS - 2) land, bounded, and leave.
+        if (threadIdx.x == 0) {
+          atomicExch(err, 1);
+          for (int j = it; j < nslots && j < it + NS - 1; j++)
+            mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
+        }
+        __syncthreads();
+        return;
+      }
+      if (threadIdx.x == 0 && it + NS - 1 < nslots)
+        issue(i2 + PZ * (NS - 1), (sl + NS - 1) % NS);
+      if (it + 1 < nslots) {
+        fetch_images(i2 + PZ);
+#pragma unroll
+        for (int j = 0; j < PZ; j++)
+          nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
+      }
 #pragma unroll
       for (int j = 0; j < PZ; j++) {
-        R *flat_u = &S.u[j][0][0];
+        const int64_t p = col + (int64_t)nc * (i2 + j);
+        const R(&t)[TH][TW] = S.u[j];
+        const R u0 = t[ty + NG][tx + NG];
+        const R v0 = S.op[OP_SV][j][ty][tx], al = S.op[OP_AL][j][ty][tx],
+                bc = S.op[OP_BC][j][ty][tx];
+        R a0 = w[0] * u0, a1;
 #pragma unroll
-        for (int k = 0; k < NST; k++)
-          if (soff[k] >= 0) flat_u[threadIdx.x + k * NT] = ireg[j][k];
-      }
-      // these cells are refilled by tensor copies when the slot comes round
-      fence_proxy_async_smem();
-    }
+        for (int k = 1; k <= NG; k++) {
+          a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
+          a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
+        }
+        a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
+        a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
 #pragma unroll
-    for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
+        for (int k = 2; k <= NG; k++) {
+          a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
+          a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
+        }
+        // q[NG + j] is the centre plane i2 + j
 #pragma unroll
-    for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
-    if (__syncthreads_or(!ok)) {
-      // A copy did not complete in time: record it, let the copies still in
-      // flight (slots it .. it + NS - 2) land, bounded, and leave.
-      if (threadIdx.x == 0) {
-        atomicExch(err, 1);
-        for (int j = it; j < nslots && j < it + NS - 1; j++)
-          mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
-      }
-      __syncthreads();
-      return;
-    }
-    if (threadIdx.x == 0 && it + NS - 1 < nslots)
-      issue(i2 + PZ * (NS - 1), (it + NS - 1) % NS);
-    if (it + 1 < nslots) {
-      fetch_images(i2 + PZ);
-#pragma unroll
-      for (int j = 0; j < PZ; j++)
-        nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
-    }
-#pragma unroll
-    for (int j = 0; j < PZ; j++) {
-      const int64_t p = col + (int64_t)nc * (i2 + j);
-      const R(&t)[TH][TW] = S.u[j];
-      const R u0 = t[ty + NG][tx + NG];
-      const R v0 = S.op[OP_SV][j][ty][tx], al = S.op[OP_AL][j][ty][tx],
-              bc = S.op[OP_BC][j][ty][tx];
-      R a0 = w[0] * u0, a1;
-#pragma unroll
-      for (int k = 1; k <= NG; k++) {
-        a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
-        a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
-      }
-      a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
-      a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
-#pragma unroll
-      for (int k = 2; k <= NG; k++) {
-        a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
-        a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
-      }
-      // q[NG + j] is the centre plane i2 + j
-#pragma unroll
-      for (int k = 1; k <= NG; k++)
-        a0 = fma(w[4 * NG + k], q[NG + j + k] + q[NG + j - k], a0);
-      const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
-      R ku = fma(-a.eta, u0, v0);
-      if (use_fu) ku += S.op[OP_FU][j][ty][tx];
-      if (KIND == STAGE_FIRST) {
-        a.au[p] = fma(a.wb, ku, u0);
-        a.av[p] = fma(a.wb, kv, v0);
-        a.ou[p] = fma(a.wa, ku, u0);
-        a.ov[p] = fma(a.wa, kv, v0);
-      } else if (KIND == STAGE_MID) {
-        a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-        a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
-        a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
-        a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
-      } else if (KIND == STAGE_LAST) {
-        a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-        a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
-      } else {
-        a.ou[p] = ku;
-        a.ov[p] = kv;
+        for (int k = 1; k <= NG; k++)
+          a0 = fma(w[4 * NG + k], q[NG + j + k] + q[NG + j - k], a0);
+        const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
+        R ku = fma(-a.eta, u0, v0);
+        if (use_fu) ku += S.op[OP_FU][j][ty][tx];
+        if (KIND == STAGE_FIRST) {
+          a.au[p] = fma(a.wb, ku, u0);
+          a.av[p] = fma(a.wb, kv, v0);
+          a.ou[p] = fma(a.wa, ku, u0);
+          a.ov[p] = fma(a.wa, kv, v0);
+        } else if (KIND == STAGE_MID) {
+          a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+          a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+          a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
+          a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
+        } else if (KIND == STAGE_LAST) {
+          a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+          a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+        } else {
+          a.ou[p] = ku;
+          a.ov[p] = kv;
+        }
       }
     }
   }
