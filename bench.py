@@ -331,8 +331,10 @@ def run_ours(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "SinhSymTP 128x128x16",
                        "fd_order": 8, "global_batch": world,
-                       "stage_launch": {m: {"variant": ["column", "tiled", "persistent"][v], "zc": z}
-                                        for m, (v, z, _) in tuned.items()},
+                       "stage_launch": {m: dict(zip(("variant", "zc", "block"),
+                                                    (["column", "tiled", "persistent"][v], z, bl)))
+                                        for m, (v, z, bl) in
+                                        ((m, g.get_launch(m)) for m in ("fp64", "fp32"))},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed before each step (256 MiB write, untimed)"},
             "sec_to_residual": {"fp64": t_max_s / args.steps,
@@ -380,7 +382,8 @@ def run_profile_steps(args):
     g.set_punctures(punc)
     dt, eta = g.timestep(0.5)
     if args.profile_zc > 0:
-        g.set_launch(args.profile_zc, args.mode, args.profile_variant)
+        g.set_launch(args.profile_zc, args.mode, args.profile_variant,
+                     args.profile_block)
     g.step(args.profile_steps, dt, eta, mode=args.mode)
     print(json.dumps({"profile_steps": args.profile_steps, "mode": args.mode,
                       "residual": g.residual(100.0)}))
@@ -635,6 +638,8 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--profile-variant", type=int, default=0,
                     help="with --profile-steps: 0 column, 1 tiled kernel")
+    ap.add_argument("--profile-block", type=int, default=0,
+                    help="with --profile-steps: column-kernel block size")
     ap.add_argument("--profile-zc", type=int, default=0,
                     help="with --profile-steps: phi planes per thread/block")
     ap.add_argument("--profile-gemm", action="store_true",

@@ -224,11 +224,19 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
 
 /* Launch shape of the fused stage kernels for the precision of `mode`
  * (NRR_FP64 / NRR_FP32): variant 0 = one thread per (i0, i1) column and zc
- * (1, 2 or 4) phi planes, neighbours read through the caches; variant 1 =
- * tiles of 32 x 4 columns staged plane by plane in shared memory, zc (2, 4,
- * 8 or 16) planes per block; variant 2 = one (column, plane) per step of a
- * grid that exactly fills every SM (zc = 1).  Curvilinear grids only. */
-nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc);
+ * (1, 2 or 4) phi planes, neighbours read through the caches, in blocks of
+ * `block` threads (64, 128 or 256; 0 keeps the current size; also the block
+ * size of the Cartesian stage kernel); variant 1 = tiles of 32 x 4 columns
+ * staged plane by plane in shared memory, zc (2, 4, 8 or 16) planes per
+ * block; variant 2 = one (column, plane) per step of a grid that exactly
+ * fills every SM (zc = 1).  Results do not depend on the shape.
+ * Errors: NRR_ERR_INVALID_ARG for other values. */
+nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block);
+
+/* The current launch shape for `mode` (as set by nrr_set_launch or chosen by
+ * nrr_autotune); outputs nullable. */
+nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
+                          int *block);
 
 /* Programmatic dependent launch of the fused stage kernels, both precisions
  * (on = 1, the default): each stage kernel is launched so that its blocks
@@ -242,8 +250,9 @@ nrr_status nrr_set_pdl(nrr_grid *g, int on);
 
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
- * events on the grid's work stream (both stage-kernel variants, each over
- * its zc values), keeps the fastest for this grid and for
+ * events on the grid's work stream -- variant 0 with (zc, block) in
+ * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
+ * zc in {2, 4, 8, 16}, variant 2 -- keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the
  * punctures set.  *best_zc and *best_ms_per_launch (nullable) report the

@@ -883,8 +883,10 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
   return NRR_OK;
 }
 
-nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc) {
+nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block) {
   TRY(check_grid(g));
+  if (block != 0 && block != 64 && block != 128 && block != 256)
+    return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
   if (variant < 0 || variant > 2)
@@ -898,9 +900,22 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc) {
                 "(persistent)");
   g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
+  if (block) g->stage_cfg[mode == NRR_FP32].block = block;
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
+  return NRR_OK;
+}
+
+nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
+                          int *block) {
+  TRY(check_grid(g));
+  if (mode != NRR_FP64 && mode != NRR_FP32)
+    return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
+  const LaunchCfg &c = g->stage_cfg[mode == NRR_FP32];
+  if (variant) *variant = c.variant;
+  if (zc) *zc = c.zc;
+  if (block) *block = c.block;
   return NRR_OK;
 }
 
@@ -943,9 +958,9 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[8] = {{128, 1, 0}, {128, 2, 0}, {128, 4, 0}, {128, 2, 1},
-                              {128, 4, 1}, {128, 8, 1}, {128, 16, 1},
-                              {128, 1, 2}};
+  const LaunchCfg cands[11] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
+                               {64, 2, 0}, {128, 4, 0}, {128, 2, 1}, {128, 4, 1},
+                               {128, 8, 1}, {128, 16, 1}, {128, 1, 2}};
   for (const LaunchCfg &cand0 : cands) {
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * TY)
 // global memory (L1/L2).  Faster than the tiled kernel on small grids with
 // few phi planes.
 template <typename R, int NG, int KIND, int ZC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     stage_curvi_kernel(Geo g, StageArgs<R> a) {
   pdl_trigger();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,19 +295,20 @@ void launch_tile_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
 }
 
 template <typename R, int NG, int KIND, int ZC>
-void launch_column_zc(const Geo &g, const StageArgs<R> &a, int pdl, cudaStream_t st) {
-  dim3 grid(((g.n0 + NG) * g.n1 + 127) / 128, (g.n2 + ZC - 1) / ZC);
-  launch_stage_kernel(stage_curvi_kernel<R, NG, KIND, ZC>, grid, dim3(128), st,
+void launch_column_zc(const Geo &g, const StageArgs<R> &a, int block, int pdl,
+                      cudaStream_t st) {
+  dim3 grid(((g.n0 + NG) * g.n1 + block - 1) / block, (g.n2 + ZC - 1) / ZC);
+  launch_stage_kernel(stage_curvi_kernel<R, NG, KIND, ZC>, grid, dim3(block), st,
                       pdl, g, a);
 }
 
 template <typename R, int NG, int KIND>
-void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
-                        cudaStream_t st) {
+void launch_column_kind(const Geo &g, const StageArgs<R> &a, int zc, int block,
+                        int pdl, cudaStream_t st) {
   switch (zc) {
-    case 1: launch_column_zc<R, NG, KIND, 1>(g, a, pdl, st); break;
-    case 4: launch_column_zc<R, NG, KIND, 4>(g, a, pdl, st); break;
-    default: launch_column_zc<R, NG, KIND, 2>(g, a, pdl, st); break;
+    case 1: launch_column_zc<R, NG, KIND, 1>(g, a, block, pdl, st); break;
+    case 4: launch_column_zc<R, NG, KIND, 4>(g, a, block, pdl, st); break;
+    default: launch_column_zc<R, NG, KIND, 2>(g, a, block, pdl, st); break;
   }
 }
 
@@ -350,10 +351,10 @@ void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
   }
   if (cfg.variant == 0) {
     switch (kind) {
-      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
-      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
-      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
-      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
+      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, cfg.block, pdl, st); break;
+      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, cfg.block, pdl, st); break;
+      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, cfg.block, pdl, st); break;
+      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, cfg.block, pdl, st); break;
     }
     return;
   }

@@ -30,6 +30,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
+           "nrr_get_launch",
            "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
@@ -105,7 +106,9 @@ def lib() -> C.CDLL:
         "nrr_timestep": [V, C.c_double, D, D],
         "nrr_image_map": [C.POINTER(GridDesc), C.POINTER(C.c_int32)],
         "nrr_profile_stages": [V, I, C.c_double, C.c_double, C.c_int64, D],
-        "nrr_set_launch": [V, I, I, I],
+        "nrr_set_launch": [V, I, I, I, I],
+        "nrr_get_launch": [V, I, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                           C.POINTER(C.c_int)],
         "nrr_set_pdl": [V, I],
         "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int),
                          C.POINTER(C.c_int), D],
@@ -341,9 +344,16 @@ class Grid:
                                         C.byref(ms)))
         return ms.value
 
-    def set_launch(self, zc: int, mode="fp64", variant: int = 0):
+    def set_launch(self, zc: int, mode="fp64", variant: int = 0, block: int = 0):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        _check(lib().nrr_set_launch(self._h, m, int(variant), int(zc)))
+        _check(lib().nrr_set_launch(self._h, m, int(variant), int(zc), int(block)))
+
+    def get_launch(self, mode="fp64"):
+        """(variant, zc, block) of the stage kernels for `mode`."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        v, z, bl = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().nrr_get_launch(self._h, m, C.byref(v), C.byref(z), C.byref(bl)))
+        return v.value, z.value, bl.value
 
     def set_pdl(self, on: bool):
         """Programmatic dependent launch of the stage kernels (default on)."""
