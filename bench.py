@@ -625,6 +625,115 @@ def run_configs2(args):
     return 0
 
 
+def run_streams(args):
+    """Independent patches (the paper's Sec. 5 multi-grid experiment): N = 1..7
+    identical q=4 SinhSymTP 128x128x16 FP64 solves to residual 1e-10, run
+    (a) one after another, (b) concurrently, one grid per host thread and
+    CUDA stream, and (c) as one batch in a single graph launch.  Wall time
+    for all N solves."""
+    import threading
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    desc, punc = W.q4_sinhsymtp_128()
+    grids = []
+    for _ in range(7):
+        g = nrr.Grid(desc)
+        g.set_punctures(punc)
+        grids.append(g)
+    grids[0].autotune("fp64", 20)  # cached for every grid of this shape
+    for g in grids:
+        g.relax(mode="fp64", tol=1e-10, max_iters=100, raise_on_error=False)
+    torch.cuda.synchronize()
+    rows = []
+    for n in range(1, 8):
+        gs = grids[:n]
+        t0 = time.perf_counter()
+        steps = [g.relax(mode="fp64", tol=1e-10)["iters"] for g in gs]
+        seq = time.perf_counter() - t0
+        res = [None] * n
+
+        def work(i):
+            res[i] = gs[i].relax(mode="fp64", tol=1e-10)
+
+        th = [threading.Thread(target=work, args=(i,)) for i in range(n)]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        conc = time.perf_counter() - t0
+        b = nrr.Batch([desc] * n, [punc] * n, with_fp64=True)
+        b.autotune("fp64", 3)
+        b.relax(mode="fp64", tol=1e-10, max_iters=100, raise_on_error=False)
+        t0 = time.perf_counter()
+        per, tot = b.relax(mode="fp64", tol=1e-10)
+        bat = time.perf_counter() - t0
+        b.close()
+        rows.append({"n": n, "rk4_steps": steps[0],
+                     "sequential_s": seq, "streams_s": conc, "batch_graph_s": bat,
+                     "streams_speedup": seq / conc, "batch_speedup": seq / bat,
+                     "all_converged": all(r["status"] == 0 for r in res) and
+                     tot["status"] == 0})
+        print(json.dumps(rows[-1]), flush=True)
+    for g in grids:
+        g.close()
+    print(json.dumps({"independent_patches": rows}), flush=True)
+    return 0
+
+
+def run_order10(args):
+    """The paper's own order (10) on its SinhSymTP workloads, 128x128x16 and
+    512x512x64 (q=4 spinning pair): FP64 relaxation and FP32 inside FP64
+    defect correction to residual 1e-10, plus the fused stage's time per
+    launch for a ladder of grid sizes (kernel weak scaling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    punc = W.spinning_q4_pair()
+    out = {"solves": {}, "stage_us_per_launch": []}
+    for n in [(128, 128, 16), (512, 512, 64)]:
+        desc = W.grid_desc("sinhsymtp", n, 10)
+        g = nrr.Grid(desc)
+        g.set_punctures(punc)
+        for m in ("fp64", "fp32"):
+            g.autotune(m, 10)
+        ent = {"launch": {m: g.get_launch(m) for m in ("fp64", "fp32")}}
+        for mode in ("fp32_dc", "fp64"):
+            g.relax(mode=mode, tol=1e-10, max_iters=100, raise_on_error=False)
+            r = g.relax(mode=mode, tol=1e-10, max_iters=400000, raise_on_error=False)
+            ent[mode] = {"seconds": r["seconds"], "rk4_steps": r["iters"],
+                         "norm": r["norm"], "status": r["status"],
+                         "gridpoint_rhs_per_s": g.interior_points * 4 * r["iters"] / r["seconds"]}
+            print(json.dumps({str(n): {mode: ent[mode]}}), flush=True)
+        ent["speedup_dc_vs_fp64"] = ent["fp64"]["seconds"] / ent["fp32_dc"]["seconds"]
+        out["solves"]["x".join(map(str, n))] = ent
+        g.close()
+        torch.cuda.empty_cache()
+    for n in [(64, 64, 8), (128, 128, 16), (256, 256, 32), (512, 512, 64)]:
+        desc = W.grid_desc("sinhsymtp", n, 10)
+        g = nrr.Grid(desc)
+        g.set_punctures(punc)
+        dt, eta = g.timestep(0.5)
+        row = {"grid": "x".join(map(str, n)), "interior_points": g.interior_points}
+        for m in ("fp64", "fp32"):
+            g.autotune(m, 5)
+            g.profile_stages(10, dt, eta, mode=m)
+            us = g.profile_stages(50, dt, eta, mode=m) * 1e3
+            row[m + "_us"] = us
+            row[m + "_ns_per_point"] = us * 1e3 / g.interior_points
+        out["stage_us_per_launch"].append(row)
+        print(json.dumps(row), flush=True)
+        g.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"order10": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -649,6 +758,10 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=8192)
     ap.add_argument("--surrogate-held", type=int, default=1024)
     ap.add_argument("--surrogate-epochs", type=int, default=100)
+    ap.add_argument("--streams", action="store_true",
+                    help="N = 1..7 independent grids: sequential, streams, batch")
+    ap.add_argument("--order10", action="store_true",
+                    help="order-10 solves at 128x128x16 and 512x512x64")
     ap.add_argument("--configs2", action="store_true",
                     help="run the larger and other-coordinate variants")
     ap.add_argument("--profile-batch", type=int, default=0,
@@ -665,6 +778,10 @@ def main():
         return run_profile_gemm(args)
     if args.configs2:
         return run_configs2(args)
+    if args.streams:
+        return run_streams(args)
+    if args.order10:
+        return run_order10(args)
     if args.profile_steps > 0:
         return run_profile_steps(args)
     if args.warmup < 3:

@@ -235,6 +235,7 @@ StageArgs<R> stage_args(const nrr_grid *g, const FieldSet<R> &f,
   StageArgs<R> a{};
   a.alpha = f.alpha;
   a.bc2 = f.bc2;
+  a.err = g->flag + 2;
   a.col = c;
   a.cart = g->cart;
   a.eta = (R)eta;
@@ -622,6 +623,7 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
     for (int k = 0; k < 2; k++) g->stage_cfg[k] = tuned_or_default(geo, k);
     TRY(dev_alloc(g, &g->partials, 2 * (size_t)nb + 64));
     TRY(dev_alloc(g, &g->flag, 4));
+    CUDA_TRY(cudaMemsetAsync(g->flag, 0, 4 * sizeof(int), g->stream));
     CUDA_TRY(cudaMallocHost(&g->host_pinned, 8 * sizeof(double)));
     // zero all state so unset regions are finite
     for (int c = 0; c < 2; c++) {
@@ -971,6 +973,8 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
         launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, trial_steps);
       else
         launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, trial_steps);
+      // a shape this grid cannot launch is skipped, not chosen
+      if (cudaGetLastError() != cudaSuccess) break;
       CUDA_TRY(cudaEventRecord(e1, g->stream));
       CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -1094,6 +1098,17 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
   }
 
   res.seconds = now_s() - t_start;
+  {
+    // a stage kernel whose bounded wait for its tensor copies expired
+    int stage_err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&stage_err, g->flag + 2, sizeof(int),
+                             cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (stage_err) {
+      CUDA_TRY(cudaMemsetAsync(g->flag + 2, 0, sizeof(int), g->stream));
+      res.status = status = NRR_ERR_TIMEOUT;
+    }
+  }
   if (r) *r = res;
   if (status == NRR_ERR_NOT_CONVERGED)
     return fail(status, "not converged after %lld steps (norm %.3e)",

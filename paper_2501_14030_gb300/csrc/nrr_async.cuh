@@ -76,6 +76,19 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src,
       : "memory");
 }
 
+// Tiled tensor copy of one box at coordinates (x, y, z) of a 3-D tensor map
+// (a kernel parameter or in global memory) into shared memory, completing
+// on `bar`.  x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map,
+                                            uint64_t *bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(shared_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(shared_addr(bar)), "r"(x),
+      "r"(y), "r"(z)
+      : "memory");
+}
+
 // Tiled tensor copy of one box at coordinates (x, y, z, w) of a 4-D tensor
 // map (in global memory, written before the launch) into shared memory,
 // completing on `bar`.  x * element size must be a multiple of 16 bytes.

@@ -55,7 +55,8 @@ struct LaunchCfg {
   int zc = 2;       // curvilinear stages: phi planes per thread (variant 0)
                     // or per block chunk (variant 1)
   int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel,
-                    // 2 persistent column kernel
+                    // 2 persistent column kernel; Cartesian stages: 0
+                    // column kernel, 1 tensor-copy (TMA) tiled kernel
   int pdl = 1;      // stage kernels: programmatic dependent launch (the next
                     // stage's blocks start while this one drains)
 };
@@ -108,6 +109,8 @@ struct StageArgs {
   CartCoef cart;
   R eta, wa, wb;     // damping, a_s dt, b_s dt
   const R *fu;       // forcing of the u equation (lin only)
+  int *err;          // device flag set by a stage kernel whose bounded wait
+                     // for an asynchronous copy expired (nullable)
   int lin;           // 1: increment equation of the defect correction:
                      //    k_u = v - eta u + f_u, k_v = c^2 lap u - alpha u + bc2
                      //    with alpha = c^2 a, bc2 = f_v (forcings also added

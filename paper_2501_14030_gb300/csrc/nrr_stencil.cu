@@ -12,7 +12,12 @@
 // Curvilinear grids: the reference metric, c^2 and the FD weights are folded
 // into per-column weights (the metric is phi-independent), so the operator is
 // 5*ng+1 fused multiply-adds on u plus the source term.
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "nrr_internal.h"
 #include "nrr_stencil.cuh"
@@ -95,23 +100,36 @@ __device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ 
   return -(dr + f0 * rinv);
 }
 
+// Cartesian operator weights in the working precision, converted once per
+// thread (a conversion from FP64 per use would run on the FP64 pipe).
+template <typename R, int NG>
+struct CartW {
+  R c;
+  R k[3][NG];
+  __device__ __forceinline__ explicit CartW(const CartCoef &cc) : c(R(cc.cc)) {
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+      for (int j = 0; j < NG; j++) k[d][j] = R(cc.a[d][j]);
+  }
+};
+
 template <typename R, int NG>
 __device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ su,
-                                           const CartCoef &cc, int64_t p, R u0,
+                                           const CartW<R, NG> &w, int64_t p, R u0,
                                            R al, R bc2, int lin) {
   const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
-  R lap = R(cc.cc) * u0;
+  R lap = w.c * u0;
 #pragma unroll
   for (int d = 0; d < 3; d++)
 #pragma unroll
     for (int k = 1; k <= NG; k++)
-      lap = fma(R(cc.a[d][k - 1]), ld(su + p + k * st[d]) + ld(su + p - k * st[d]),
-                lap);
+      lap = fma(w.k[d][k - 1], ld(su + p + k * st[d]) + ld(su + p - k * st[d]), lap);
   return add_source(lap, u0, al, bc2, lin);
 }
 
 template <typename R, int NG, int KIND>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     stage_cart_kernel(Geo g, StageArgs<R> a, int zc) {
   pdl_trigger();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,12 +139,13 @@ __global__ void __launch_bounds__(128)
   const int z0 = blockIdx.y * zc;
   const int z1 = min(z0 + zc, g.s2);
   const bool in01 = i0 >= NG && i0 < g.n0 + NG && i1 >= NG && i1 < g.n1 + NG;
+  const CartW<R, NG> w(a.cart);
   for (int i2 = z0; i2 < z1; i2++) {
     int64_t p = e + (int64_t)g.ncol * i2;
     R ku, kv;
     if (in01 && i2 >= NG && i2 < g.n2 + NG) {
       R u0 = ld(a.su + p), v0 = ld(a.sv + p);
-      kv = cart_operator<R, NG>(g, a.su, a.cart, p, u0, ld(a.alpha + p),
+      kv = cart_operator<R, NG>(g, a.su, w, p, u0, ld(a.alpha + p),
                                 ld(a.bc2 + p), a.lin);
       ku = fma(-a.eta, u0, v0);
       if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
@@ -139,6 +158,252 @@ __global__ void __launch_bounds__(128)
       }
     }
     stage_epilogue<R, KIND>(a, p, ku, kv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cartesian stage fed by tensor copies (variant 1; order 8, n0 % 32 == 0,
+// n1 % 4 == 0, n2 and the plane chunk even).  Interior blocks: a 32 x 4
+// column tile streams its chunk of planes, two per slot, through a 3-slot
+// shared-memory ring (one 40 x 12 x 2 box of u with its halo, one 32 x 4 x 2
+// box per operand array, completing on the slot's mbarrier; thread 0 issues
+// two slots ahead).  Cartesian ghosts are all outer ghosts, stored and
+// evolved, so the halo box needs no images; the i2 neighbours come from a
+// register queue.  Extra blocks evolve the ghost shell with the radiation
+// condition, one point per thread: first the two i2 slabs, then the ring of
+// ghost columns on the interior planes.
+// ---------------------------------------------------------------------------
+struct CartMaps {
+  CUtensorMap u;       // su, box (40, 12, 2)
+  CUtensorMap op[8];   // operand arrays (BulkOp slots), box (32, 4, 2)
+};
+
+constexpr int kCartTY = 4, kCartPZ = 2;
+template <typename R>
+__host__ __device__ constexpr int cart_slots() { return sizeof(R) == 4 ? 3 : 2; }
+
+__host__ __device__ __forceinline__ int64_t cart_shell_points(const Geo &g) {
+  const int ng = g.ng;
+  return 2 * (int64_t)ng * g.ncol +
+         ((int64_t)g.ncol - (int64_t)g.n0 * g.n1) * g.n2;
+}
+
+// Grid constants of the shell points in the working precision, converted on
+// the host (a conversion from FP64 per point would run on the FP64 pipe).
+template <typename R>
+struct CartShellC {
+  R xmin[3];  // coordinate of padded index 0 + half a cell, per direction
+  R dxx[3];   // spacing
+  R inv2[3];  // 1 / (2 dxx)
+};
+
+// Radiation condition at ghost point (i0, i1, i2) for u and v together:
+// k_f = -(d_r f + f / r) with d_r f = sum_d (x_d / r) D_d f, in the working
+// precision.
+template <typename R, int NG>
+__device__ __forceinline__ void cart_shell_point(const Geo &g, const StageArgs<R> &a,
+                                                 const CartShellC<R> &sc, int i0,
+                                                 int i1, int i2, R &ku, R &kv) {
+  const int ii[3] = {i0, i1, i2};
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
+  const int64_t p = i0 + (int64_t)g.s0 * i1 + (int64_t)g.ncol * i2;
+  R x[3], r2 = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    x[d] = fma(R(ii[d]), sc.dxx[d], sc.xmin[d]);
+    r2 = fma(x[d], x[d], r2);
+  }
+  const R rinv = R(1) / sqrt(r2);
+  const R u0 = ld(a.su + p), v0 = ld(a.sv + p);
+  R dru = R(0), drv = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const R nx = x[d] * rinv, inv2 = sc.inv2[d];
+    R Du, Dv;
+    if (ii[d] >= nn[d] + NG) {
+      Du = (R(3) * u0 - R(4) * ld(a.su + p - st[d]) + ld(a.su + p - 2 * st[d])) * inv2;
+      Dv = (R(3) * v0 - R(4) * ld(a.sv + p - st[d]) + ld(a.sv + p - 2 * st[d])) * inv2;
+    } else if (ii[d] < NG) {
+      Du = -(R(3) * u0 - R(4) * ld(a.su + p + st[d]) + ld(a.su + p + 2 * st[d])) * inv2;
+      Dv = -(R(3) * v0 - R(4) * ld(a.sv + p + st[d]) + ld(a.sv + p + 2 * st[d])) * inv2;
+    } else {
+      Du = (ld(a.su + p + st[d]) - ld(a.su + p - st[d])) * inv2;
+      Dv = (ld(a.sv + p + st[d]) - ld(a.sv + p - st[d])) * inv2;
+    }
+    dru = fma(nx, Du, dru);
+    drv = fma(nx, Dv, drv);
+  }
+  ku = -(dru + u0 * rinv);
+  kv = -(drv + v0 * rinv);
+  if (linear_mode<R>(a.lin)) {
+    ku += ld(a.fu + p);
+    kv += ld(a.bc2 + p);
+  }
+}
+
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
+    stage_cart_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ CartMaps maps,
+                          CartShellC<R> sc, int zc) {
+  constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
+  constexpr int TW = 32 + 2 * NG, TH = TY + 2 * NG;
+  pdl_trigger();
+  const int ntx = g.n0 / 32, nty = g.n1 / TY, nch = (g.n2 + zc - 1) / zc;
+  const int nint = ntx * nty * nch;
+  if ((int)blockIdx.x >= nint) {
+    // ghost shell, one point per thread
+    const int64_t w = (int64_t)(blockIdx.x - nint) * blockDim.x + threadIdx.x;
+    if (w >= cart_shell_points(g)) return;
+    int i0, i1, i2;
+    const int64_t slab = 2 * (int64_t)NG * g.ncol;
+    if (w < slab) {
+      const int pl = (int)(w / g.ncol), rem = (int)(w - (int64_t)pl * g.ncol);
+      i2 = pl < NG ? pl : g.n2 + pl;
+      i1 = rem / g.s0;
+      i0 = rem - i1 * g.s0;
+    } else {
+      const int64_t w2 = w - slab;
+      const int nring = g.ncol - g.n0 * g.n1;
+      const int rc = (int)(w2 % nring);
+      i2 = NG + (int)(w2 / nring);
+      const int band = NG * g.s0;  // the NG ghost rows below and above
+      if (rc < 2 * band) {
+        const int r = rc < band ? rc : rc - band;
+        i1 = r / g.s0 + (rc < band ? 0 : g.n1 + NG);
+        i0 = r - (r / g.s0) * g.s0;
+      } else {
+        const int r = rc - 2 * band;
+        i1 = NG + r / (2 * NG);
+        const int j = r - (r / (2 * NG)) * (2 * NG);
+        i0 = j < NG ? j : g.n0 + j;
+      }
+    }
+    pdl_wait();
+    R ku, kv;
+    cart_shell_point<R, NG>(g, a, sc, i0, i1, i2, ku, kv);
+    stage_epilogue<R, KIND>(a, i0 + (int64_t)g.s0 * i1 + (int64_t)g.ncol * i2, ku, kv);
+    return;
+  }
+  __shared__ __align__(128) BulkSlot<R, NG, TY, PZ> ring[NS];
+  __shared__ __align__(8) uint64_t full[NS];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int tile_x = blockIdx.x % ntx, tile_y = (blockIdx.x / ntx) % nty,
+            chunk = blockIdx.x / (ntx * nty);
+  const int nc = g.ncol;
+  const int z0 = NG + chunk * zc, z1 = min(z0 + zc, NG + g.n2);
+  const int nslots = (z1 - z0) / PZ;
+  const int i0 = NG + tile_x * 32 + tx, i1 = NG + tile_y * TY + ty;
+  const int col = i0 + g.s0 * i1;
+  const int j0b = tile_x * 32, j1b = tile_y * TY;
+  const bool use_fu = linear_mode<R>(a.lin);
+  constexpr bool use_b = KIND == STAGE_MID;
+  constexpr bool use_acc = KIND == STAGE_MID || KIND == STAGE_LAST;
+  const unsigned opmask = (1u << OP_SV) | (1u << OP_AL) | (1u << OP_BC) |
+                          (use_fu ? 1u << OP_FU : 0u) |
+                          (use_b ? (1u << OP_BU) | (1u << OP_BV) : 0u) |
+                          (use_acc ? (1u << OP_AU) | (1u << OP_AV) : 0u);
+  const uint32_t slot_bytes =
+      (uint32_t)(PZ * (TW * TH + __popc(opmask) * TY * 32) * sizeof(R));
+  // operator weights in the working precision
+  const R wc = R(a.cart.cc);
+  R wk[3][NG];
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+#pragma unroll
+    for (int k = 0; k < NG; k++) wk[d][k] = R(a.cart.a[d][k]);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NS; k++) mbar_init_count(&full[k], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  pdl_wait();
+  auto issue = [&](int pl, int sl) {
+    mbar_arrive_expect(&full[sl], slot_bytes);
+    fence_proxy_async_smem();
+    tma_load_3d(&ring[sl].u[0][0][0], &maps.u, &full[sl], j0b, j1b, pl);
+#pragma unroll
+    for (int o = 0; o < 8; o++)
+      if ((opmask >> o) & 1u)
+        tma_load_3d(&ring[sl].op[o][0][0][0], &maps.op[o], &full[sl], NG + j0b,
+                    NG + j1b, pl);
+  };
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NS - 1 && k < nslots; k++) issue(z0 + PZ * k, k);
+  // i2 queue of this column: planes i2 - NG .. i2 + NG of the slot's first
+  // plane (ghost planes are stored: no wrap)
+  R q[2 * NG + PZ];
+#pragma unroll
+  for (int k = 0; k < 2 * NG; k++) q[k + PZ] = ld(a.su + col + (int64_t)nc * (z0 - NG + k));
+  R nq[PZ];
+#pragma unroll
+  for (int j = 0; j < PZ; j++) nq[j] = ld(a.su + col + (int64_t)nc * (z0 + NG + j));
+  for (int base = 0, phase = 0; base < nslots; base += NS, phase ^= 1) {
+#pragma unroll
+    for (int sl = 0; sl < NS; sl++) {
+      const int it = base + sl;
+      if (it >= nslots) break;
+      const int i2 = z0 + PZ * it;
+      const bool ok = mbar_wait_parity(&full[sl], (uint32_t)phase);
+      const BulkSlot<R, NG, TY, PZ> &S = ring[sl];
+#pragma unroll
+      for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
+#pragma unroll
+      for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
+      if (__syncthreads_or(!ok)) {
+        // a copy did not complete in time: record it, let the copies still
+        // in flight (slots it .. it + NS - 2) land, bounded, and leave
+        if (threadIdx.x == 0) {
+          if (a.err) atomicExch(a.err, 1);
+          for (int j = it; j < nslots && j < it + NS - 1; j++)
+            mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
+        }
+        __syncthreads();
+        return;
+      }
+      if (threadIdx.x == 0 && it + NS - 1 < nslots)
+        issue(i2 + PZ * (NS - 1), (sl + NS - 1) % NS);
+      if (it + 1 < nslots) {
+#pragma unroll
+        for (int j = 0; j < PZ; j++)
+          nq[j] = ld(a.su + col + (int64_t)nc * (i2 + PZ + NG + j));
+      }
+#pragma unroll
+      for (int j = 0; j < PZ; j++) {
+        const int64_t p = col + (int64_t)nc * (i2 + j);
+        const R(&t)[TH][TW] = S.u[j];
+        const R u0 = t[ty + NG][tx + NG];
+        const R v0 = S.op[OP_SV][j][ty][tx];
+        R a0 = wc * u0, a1 = R(0);
+#pragma unroll
+        for (int k = 1; k <= NG; k++) {
+          a0 = fma(wk[0][k - 1], t[ty + NG][tx + NG + k] + t[ty + NG][tx + NG - k], a0);
+          a1 = fma(wk[1][k - 1], t[ty + NG + k][tx + NG] + t[ty + NG - k][tx + NG], a1);
+          a0 = fma(wk[2][k - 1], q[NG + j + k] + q[NG + j - k], a0);
+        }
+        const R kv = add_source(a0 + a1, u0, S.op[OP_AL][j][ty][tx],
+                                S.op[OP_BC][j][ty][tx], a.lin);
+        R ku = fma(-a.eta, u0, v0);
+        if (use_fu) ku += S.op[OP_FU][j][ty][tx];
+        if (KIND == STAGE_FIRST) {
+          a.au[p] = fma(a.wb, ku, u0);
+          a.av[p] = fma(a.wb, kv, v0);
+          a.ou[p] = fma(a.wa, ku, u0);
+          a.ov[p] = fma(a.wa, kv, v0);
+        } else if (KIND == STAGE_MID) {
+          a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+          a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+          a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
+          a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
+        } else if (KIND == STAGE_LAST) {
+          a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
+          a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+        } else {
+          a.ou[p] = ku;
+          a.ov[p] = kv;
+        }
+      }
+    }
   }
 }
 
@@ -177,10 +442,11 @@ __global__ void __launch_bounds__(128)
     const int z1 = min(z0 + zc, NG + g.n2);
     double x0 = g.xxmin[0] + (i0 - NG + 0.5) * g.dxx[0];
     double x1 = g.xxmin[1] + (i1 - NG + 0.5) * g.dxx[1];
+    const CartW<R, NG> w(cc);
     for (int i2 = z0; i2 < z1; i2++) {
       int64_t p = i0 + (int64_t)g.s0 * (i1 + (int64_t)g.s1 * i2);
       R u0 = ld(su + p);
-      double H = (double)cart_operator<R, NG>(g, su, cc, p, u0, ld(alpha + p),
+      double H = (double)cart_operator<R, NG>(g, su, w, p, u0, ld(alpha + p),
                                               ld(bc2 + p), lin);
       if (h_out) h_out[p] = H;
       double x2 = g.xxmin[2] + (i2 - NG + 0.5) * g.dxx[2];
@@ -366,10 +632,109 @@ void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
   }
 }
 
+// Tensor maps of whole padded fields (3-D, i0 fastest) for the Cartesian
+// tensor-copy stage, encoded once per (field, box) and reused.
+using TensorMapEncodeFn = CUresult (*)(
+    CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+    CUtensorMapFloatOOBfill);
+struct FieldMapKey {
+  const void *p;
+  int esize, s0, s1, s2, b0, b1;
+  bool operator<(const FieldMapKey &o) const {
+    return std::tie(p, esize, s0, s1, s2, b0, b1) <
+           std::tie(o.p, o.esize, o.s0, o.s1, o.s2, o.b0, o.b1);
+  }
+};
+std::mutex g_fmap_mu;
+std::map<FieldMapKey, CUtensorMap> g_fmaps;
+
+bool field_map(CUtensorMap *out, const void *p, int esize, const Geo &g, int b0,
+               int b1) {
+  std::lock_guard<std::mutex> lock(g_fmap_mu);
+  const FieldMapKey key{p, esize, g.s0, g.s1, g.s2, b0, b1};
+  auto it = g_fmaps.find(key);
+  if (it != g_fmaps.end()) {
+    *out = it->second;
+    return true;
+  }
+  auto enc = reinterpret_cast<TensorMapEncodeFn>(tensor_map_encoder());
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.s0, (cuuint64_t)g.s1, (cuuint64_t)g.s2};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.s0 * esize, (cuuint64_t)g.ncol * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)kCartPZ};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMap m;
+  if (enc(&m, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+          3, const_cast<void *>(p), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  g_fmaps[key] = m;
+  *out = m;
+  return true;
+}
+
+// Whether the Cartesian tensor-copy stage applies to this grid and launch.
+bool cart_tma_ok(const Geo &g, int zc) {
+  return g.ng == 4 && g.n0 % 32 == 0 && g.n1 % kCartTY == 0 && g.n2 % kCartPZ == 0 &&
+         zc % kCartPZ == 0 && g.s0 % 4 == 0;
+}
+
+template <typename R, int NG, int KIND>
+bool launch_cart_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
+                          cudaStream_t st) {
+  CartMaps maps;
+  const int es = (int)sizeof(R);
+  const R *ops[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
+  const bool use_fu = a.lin != 0 && sizeof(R) == 4;
+  const bool use_b = KIND == STAGE_MID, use_acc = KIND == STAGE_MID || KIND == STAGE_LAST;
+  const bool need[8] = {true, true, true, use_fu, use_b, use_b, use_acc, use_acc};
+  if (!field_map(&maps.u, a.su, es, g, 32 + 2 * NG, kCartTY + 2 * NG)) return false;
+  for (int o = 0; o < 8; o++) {
+    if (need[o]) {
+      if (!field_map(&maps.op[o], ops[o], es, g, 32, kCartTY)) return false;
+    } else {
+      maps.op[o] = maps.u;  // unused slot
+    }
+  }
+  CartShellC<R> sc;
+  for (int d = 0; d < 3; d++) {
+    sc.xmin[d] = (R)(g.xxmin[d] + (0.5 - NG) * g.dxx[d]);
+    sc.dxx[d] = (R)g.dxx[d];
+    sc.inv2[d] = (R)(0.5 / g.dxx[d]);
+  }
+  const int nint = (g.n0 / 32) * (g.n1 / kCartTY) * ((g.n2 + zc - 1) / zc);
+  const int nshell = (int)((cart_shell_points(g) + 32 * kCartTY - 1) / (32 * kCartTY));
+  launch_stage_kernel(stage_cart_tma_kernel<R, NG, KIND>, dim3(nint + nshell),
+                      dim3(32 * kCartTY), st, pdl, g, a, maps, sc, zc);
+  return true;
+}
+
+template <typename R, int NG>
+bool launch_cart_tma(const Geo &g, int kind, const StageArgs<R> &a, int zc, int pdl,
+                     cudaStream_t st) {
+  if constexpr (NG != 4) {
+    return false;
+  } else {
+    switch (kind) {
+      case STAGE_FIRST: return launch_cart_tma_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st);
+      case STAGE_MID: return launch_cart_tma_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st);
+      case STAGE_LAST: return launch_cart_tma_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st);
+      default: return launch_cart_tma_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st);
+    }
+  }
+}
+
 template <typename R, int NG>
 void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
                      const LaunchCfg &cfg, cudaStream_t st) {
   if (g.coord == CARTESIAN) {
+    if (cfg.variant == 1 && cart_tma_ok(g, cfg.zc) &&
+        launch_cart_tma<R, NG>(g, kind, a, cfg.zc, cfg.pdl, st))
+      return;
     dim3 grid((g.ncol + cfg.block - 1) / cfg.block, (g.s2 + cfg.zc - 1) / cfg.zc);
     dim3 blk(cfg.block);
     switch (kind) {

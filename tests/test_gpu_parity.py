@@ -28,6 +28,14 @@ CASES = {
     # full-size q=4 grid
     "sinh_128x128x16_o8": W.q4_sinhsymtp_128(),
 }
+# The larger full-size q=4 grids (SinhSymTP 256x256x32, Spherical 128x64x32,
+# Cartesian 256^3, order 8): RHS and residual parity over every point.
+FULL = {
+    "sinh_256x256x32_o8": W.q4_sinhsymtp_256(),
+    "sph_128x64x32_o8": W.q4_spherical_128(),
+    "cart_256x256x256_o8": W.q4_cartesian_256(),
+}
+ALL = {**CASES, **FULL}
 
 
 def _dev(a: np.ndarray) -> torch.Tensor:
@@ -35,7 +43,7 @@ def _dev(a: np.ndarray) -> torch.Tensor:
 
 
 def _setup(name):
-    desc, punc = CASES[name]
+    desc, punc = ALL[name]
     og = oracle_grid(desc)
     alpha, beta = og.source(punc)
     g = nrr.Grid(desc)
@@ -52,7 +60,7 @@ def test_timestep_matches_oracle(gpu, name):
     assert abs(eta - etao) <= 1e-13 * etao
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", list(ALL))
 def test_rhs_parity_fp64(gpu, name):
     desc, punc, og, alpha, beta, g = _setup(name)
     u = W.smooth_random_field(desc, seed=11, amplitude=0.2, noise=0.01)
@@ -83,7 +91,7 @@ def test_source_parity(gpu, name):
     assert rel_err(kv.cpu().numpy(), kv_o, m) <= 1e-12
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", list(ALL))
 def test_residual_and_norm_parity(gpu, name):
     desc, punc, og, alpha, beta, g = _setup(name)
     u = W.smooth_random_field(desc, seed=21, amplitude=0.2, noise=0.01)
@@ -234,3 +242,75 @@ def test_defect_correction_full_size_matches_fp64(gpu):
     assert rdc["status"] == 0 and abs(rdc["iters"] - r64["iters"]) <= 100
     assert og.norm(og.residual(alpha, beta, udc)) < 1.02e-10
     assert rel_err(udc, u64) <= 1e-9
+
+
+# ------------------------------- stage-kernel variants against the oracle
+# Every launch shape must reproduce the oracle; the parity tests above run
+# the default shape.  Cartesian variant 1 is the tensor-copy kernel (order 8,
+# n0 % 32 == 0, n1 % 4 == 0, even n2); curvilinear variants 1 and 2 are the
+# tiled and persistent kernels.
+VARIANT_CASES = {
+    "cart_64x20x24_o8": (W.grid_desc("cartesian", (64, 20, 24), 8, xmax=32.0), Q4),
+    "sinh_64x20x8_o8": (W.grid_desc("sinhsymtp", (64, 20, 8), 8), Q4),
+    "sph_64x20x8_o8": (W.grid_desc("spherical", (64, 20, 8), 8, rmax=64.0), Q4),
+}
+
+
+@pytest.mark.parametrize("name", list(VARIANT_CASES))
+@pytest.mark.parametrize("variant,zc", [(0, 1), (1, 2), (1, 4), (1, 16), (2, 1)])
+def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
+    desc, punc = VARIANT_CASES[name]
+    if desc["coord"] == "cartesian" and variant == 2:
+        pytest.skip("Cartesian grids have variants 0 and 1")
+    og = oracle_grid(desc)
+    alpha, beta = og.source(punc)
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    g.set_launch(zc, "fp64", variant)
+    g.set_launch(zc, "fp32", variant)
+    dt, eta = default_dt_eta(og)
+    u = W.smooth_random_field(desc, seed=41, amplitude=0.2, noise=0.01)
+    v = W.smooth_random_field(desc, seed=42, amplitude=0.1, noise=0.01)
+    ku_o, kv_o = og.rhs(alpha, beta, eta, og.fill_inner_ghosts(u),
+                        og.fill_inner_ghosts(v))
+    for mode, tol in (("fp64", 1e-12), ("fp32", FP32_RHS_TOL)):
+        ku, kv = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+        g.rhs(_dev(u), _dev(v), ku, kv, eta, mode=mode)
+        ku, kv = ku.cpu().numpy(), kv.cpu().numpy()
+        for region, m in region_masks(og).items():
+            assert rel_err(ku, ku_o, m) <= tol, (mode, region, rel_err(ku, ku_o, m))
+            assert rel_err(kv, kv_o, m) <= tol, (mode, region, rel_err(kv, kv_o, m))
+    # 30 RK4 steps from a smooth state (all four stage kinds, both fields)
+    u = og.fill_inner_ghosts(W.smooth_random_field(desc, seed=43, amplitude=0.1))
+    v = og.zeros()
+    g.set_state(_dev(u), _dev(v))
+    g.step(30, dt, eta, mode="fp64")
+    for _ in range(30):
+        og.rk4_step(alpha, beta, eta, dt, u, v)
+    ug, vg = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+    g.get_state(ug, vg)
+    assert rel_err(ug.cpu().numpy(), u) <= 1e-12
+    assert rel_err(vg.cpu().numpy(), v) <= 1e-12
+    g.close()
+
+
+def test_cartesian_tensor_copy_variant_full_size(gpu):
+    """Cartesian 256^3 (order 8) with the tensor-copy stage: FP64 RHS at every
+    point against the oracle."""
+    desc, punc = FULL["cart_256x256x256_o8"]
+    og = oracle_grid(desc)
+    alpha, beta = og.source(punc)
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    g.set_launch(16, "fp64", 1)
+    u = W.smooth_random_field(desc, seed=11, amplitude=0.2, noise=0.01)
+    v = W.smooth_random_field(desc, seed=12, amplitude=0.1, noise=0.01)
+    dt, eta = default_dt_eta(og)
+    ku_o, kv_o = og.rhs(alpha, beta, eta, u, v)
+    ku, kv = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+    g.rhs(_dev(u), _dev(v), ku, kv, eta, mode="fp64")
+    ku, kv = ku.cpu().numpy(), kv.cpu().numpy()
+    for region, m in region_masks(og).items():
+        assert rel_err(ku, ku_o, m) <= 1e-12, (region, rel_err(ku, ku_o, m))
+        assert rel_err(kv, kv_o, m) <= 1e-12, (region, rel_err(kv, kv_o, m))
+    g.close()
