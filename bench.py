@@ -332,7 +332,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "SinhSymTP 128x128x16",
                        "fd_order": 8, "global_batch": world,
                        "stage_launch": {m: dict(zip(("variant", "zc", "block"),
-                                                    (["column", "tiled", "persistent"][v], z, bl)))
+                                                    (["column", "tiled", "persistent", "tensor-copy tiled"][v], z, bl)))
                                         for m, (v, z, bl) in
                                         ((m, g.get_launch(m)) for m in ("fp64", "fp32"))},
                        "parallelism": "replicas" if world > 1 else "single",

@@ -223,13 +223,19 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
                               int64_t steps, double *ms_per_launch);
 
 /* Launch shape of the fused stage kernels for the precision of `mode`
- * (NRR_FP64 / NRR_FP32): variant 0 = one thread per (i0, i1) column and zc
- * (1, 2 or 4) phi planes, neighbours read through the caches, in blocks of
- * `block` threads (64, 128 or 256; 0 keeps the current size; also the block
- * size of the Cartesian stage kernel); variant 1 = tiles of 32 x 4 columns
- * staged plane by plane in shared memory, zc (2, 4, 8 or 16) planes per
- * block; variant 2 = one (column, plane) per step of a grid that exactly
- * fills every SM (zc = 1).  Results do not depend on the shape.
+ * (NRR_FP64 / NRR_FP32).  Curvilinear grids: variant 0 = one thread per
+ * (i0, i1) column and zc (1, 2 or 4) phi planes, neighbours read through the
+ * caches, in blocks of `block` threads (64, 128 or 256; 0 keeps the current
+ * size); variant 1 = tiles of 32 x 4 columns staged plane by plane through
+ * registers into shared memory, zc (2, 4, 8 or 16) planes per block;
+ * variant 2 = one (column, plane) per step of a grid that exactly fills
+ * every SM (zc = 1); variant 3 = 32 x 4 tiles whose planes stream through a
+ * shared-memory ring filled by tensor (TMA) copies, zc (2, 4, 8 or 16)
+ * planes per block, for FD order 8 with n0 % 32 == 0 and n1 % 4 == 0 (other
+ * grids run variant 1 instead).  Cartesian grids: variant 1 = the tensor-copy
+ * kernel under the same conditions, any other variant the column kernel
+ * (zc planes per thread, `block` threads).  Results do not depend on the
+ * shape beyond rounding order.
  * Errors: NRR_ERR_INVALID_ARG for other values. */
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block);
 
@@ -252,7 +258,8 @@ nrr_status nrr_set_pdl(nrr_grid *g, int on);
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in
  * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
- * zc in {2, 4, 8, 16}, variant 2 -- keeps the fastest for this grid and for
+ * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16} -- skips
+ * shapes the grid cannot launch, keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the
  * punctures set.  *best_zc and *best_ms_per_launch (nullable) report the

@@ -891,15 +891,16 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block)
     return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (variant < 0 || variant > 2)
+  if (variant < 0 || variant > 3)
     return fail(NRR_ERR_INVALID_ARG,
-                "variant must be 0 (column), 1 (tiled) or 2 (persistent column)");
+                "variant must be 0 (column), 1 (tiled), 2 (persistent column) or "
+                "3 (tensor-copy tiled)");
   if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
-      (variant == 1 && zc != 2 && zc != 4 && zc != 8 && zc != 16) ||
+      ((variant == 1 || variant == 3) && zc != 2 && zc != 4 && zc != 8 && zc != 16) ||
       (variant == 2 && zc != 1))
     return fail(NRR_ERR_INVALID_ARG,
-                "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled), 1 "
-                "(persistent)");
+                "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled, tensor-copy), "
+                "1 (persistent)");
   g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
   if (block) g->stage_cfg[mode == NRR_FP32].block = block;
@@ -960,9 +961,10 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[11] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
+  const LaunchCfg cands[14] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
                                {64, 2, 0}, {128, 4, 0}, {128, 2, 1}, {128, 4, 1},
-                               {128, 8, 1}, {128, 16, 1}, {128, 1, 2}};
+                               {128, 8, 1}, {128, 16, 1}, {128, 1, 2}, {128, 4, 3},
+                               {128, 8, 3}, {128, 16, 3}};
   for (const LaunchCfg &cand0 : cands) {
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;

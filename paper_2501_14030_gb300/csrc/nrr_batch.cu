@@ -72,7 +72,7 @@ struct SolveDev {
   float *ac2, *fu, *fv;          // linearised source and forcing
   ColumnSet<float> c32;
   double *jac, *rad;
-  dev::TmaFields tf64, tf32;     // tensor maps of the FP64 / FP32 fields
+  dev::ArenaSrc tf64, tf32;      // tensor maps of the FP64 / FP32 fields
 };
 
 // Control block of one relaxation, in device memory.

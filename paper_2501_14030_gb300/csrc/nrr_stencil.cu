@@ -173,10 +173,7 @@ __global__ void __launch_bounds__(256)
 // condition, one point per thread: first the two i2 slabs, then the ring of
 // ghost columns on the interior planes.
 // ---------------------------------------------------------------------------
-struct CartMaps {
-  CUtensorMap u;       // su, box (40, 12, 2)
-  CUtensorMap op[8];   // operand arrays (BulkOp slots), box (32, 4, 2)
-};
+using CartMaps = FieldSrc;  // su box (40, 12, 2), operand boxes (32, 4, 2)
 
 constexpr int kCartTY = 4, kCartPZ = 2;
 template <typename R>
@@ -407,6 +404,38 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
   }
 }
 
+// Curvilinear stage fed by tensor copies (variant 3; order 8, n0 % 32 == 0,
+// n1 % 4 == 0): interior blocks run stage_bulk_block on a 32 x 4 column tile
+// and a chunk of phi planes with one 3-D tensor map per array (kernel
+// parameter); the blocks after them evolve the outer shell, 32 rows of i1
+// and the NG shell columns each.
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
+    stage_curvi_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ FieldSrc maps,
+                           int zc) {
+  constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
+  pdl_trigger();
+  const int ntx = g.n0 / 32, nty = g.n1 / TY, nch = chunks_z(g, zc);
+  const int nint = ntx * nty * nch;
+  if ((int)blockIdx.x >= nint) {
+    constexpr int rows = 32 * TY / NG;
+    const int nsb = (g.n1 + rows - 1) / rows;
+    const int sidx = blockIdx.x - nint, chunk = sidx / nsb;
+    const int row = threadIdx.x / NG, lane = threadIdx.x - row * NG;
+    const int z0 = NG + chunk * zc;
+    if (row < rows)
+      stage_shell_rows<R, NG, KIND>(g, a, lane, NG + (sidx % nsb) * rows + row, z0,
+                                    min(z0 + zc, NG + g.n2));
+    return;
+  }
+  __shared__ __align__(128) BulkSlot<R, NG, TY, PZ> ring[NS];
+  __shared__ __align__(8) uint64_t full[NS];
+  stage_bulk_block<R, NG, KIND, TY, NS, PZ>(g, a, blockIdx.x % ntx,
+                                            (blockIdx.x / ntx) % nty,
+                                            blockIdx.x / (ntx * nty), zc, maps, ring,
+                                            full, a.err);
+}
+
 // Residual H at interior points and the block partials of H^2 J, J over
 // r < r_int (the volume-weighted L2 norm of Alg. 1's residual).
 template <typename R, int NG>
@@ -602,36 +631,6 @@ void launch_persistent_kind(const Geo &g, const StageArgs<R> &a, int pdl,
   launch_stage_kernel(k, dim3(blocks), dim3(128), st, pdl, g, a);
 }
 
-template <typename R, int NG>
-void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
-                  const LaunchCfg &cfg, cudaStream_t st) {
-  const int zc = cfg.zc, pdl = cfg.pdl;
-  if (cfg.variant == 2) {
-    switch (kind) {
-      case STAGE_FIRST: launch_persistent_kind<R, NG, STAGE_FIRST>(g, a, pdl, st); break;
-      case STAGE_MID: launch_persistent_kind<R, NG, STAGE_MID>(g, a, pdl, st); break;
-      case STAGE_LAST: launch_persistent_kind<R, NG, STAGE_LAST>(g, a, pdl, st); break;
-      default: launch_persistent_kind<R, NG, STAGE_RAW>(g, a, pdl, st); break;
-    }
-    return;
-  }
-  if (cfg.variant == 0) {
-    switch (kind) {
-      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, cfg.block, pdl, st); break;
-      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, cfg.block, pdl, st); break;
-      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, cfg.block, pdl, st); break;
-      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, cfg.block, pdl, st); break;
-    }
-    return;
-  }
-  switch (kind) {
-    case STAGE_FIRST: launch_tile_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
-    case STAGE_MID: launch_tile_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
-    case STAGE_LAST: launch_tile_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
-    default: launch_tile_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
-  }
-}
-
 // Tensor maps of whole padded fields (3-D, i0 fastest) for the Cartesian
 // tensor-copy stage, encoded once per (field, box) and reused.
 using TensorMapEncodeFn = CUresult (*)(
@@ -683,23 +682,54 @@ bool cart_tma_ok(const Geo &g, int zc) {
          zc % kCartPZ == 0 && g.s0 % 4 == 0;
 }
 
+// Whether the curvilinear tensor-copy stage applies to this grid and launch.
+bool curvi_tma_ok(const Geo &g, int zc) {
+  return g.ng == 4 && g.n0 % 32 == 0 && g.n1 % kCartTY == 0 &&
+         g.n2 % kCartPZ == 0 && zc % kCartPZ == 0 && g.s0 % 4 == 0;
+}
+
+// Maps of the arrays a stage kind reads: su with halo boxes, operands with
+// tile boxes; false if the driver cannot encode them.
 template <typename R, int NG, int KIND>
-bool launch_cart_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
-                          cudaStream_t st) {
-  CartMaps maps;
+bool stage_field_maps(FieldSrc *m, const Geo &g, const StageArgs<R> &a, int b0u,
+                      int b1u) {
   const int es = (int)sizeof(R);
   const R *ops[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
   const bool use_fu = a.lin != 0 && sizeof(R) == 4;
   const bool use_b = KIND == STAGE_MID, use_acc = KIND == STAGE_MID || KIND == STAGE_LAST;
   const bool need[8] = {true, true, true, use_fu, use_b, use_b, use_acc, use_acc};
-  if (!field_map(&maps.u, a.su, es, g, 32 + 2 * NG, kCartTY + 2 * NG)) return false;
+  if (!field_map(&m->u, a.su, es, g, b0u, b1u)) return false;
   for (int o = 0; o < 8; o++) {
     if (need[o]) {
-      if (!field_map(&maps.op[o], ops[o], es, g, 32, kCartTY)) return false;
+      if (!field_map(&m->op[o], ops[o], es, g, 32, kCartTY)) return false;
     } else {
-      maps.op[o] = maps.u;  // unused slot
+      m->op[o] = m->u;  // unused slot
     }
   }
+  return true;
+}
+
+template <typename R, int NG, int KIND>
+bool launch_curvi_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
+                           cudaStream_t st) {
+  FieldSrc maps;
+  if (!stage_field_maps<R, NG, KIND>(&maps, g, a, 32 + 2 * NG, kCartTY + 2 * NG))
+    return false;
+  constexpr int rows = 32 * kCartTY / NG;
+  const int nch = chunks_z(g, zc);
+  const int nint = (g.n0 / 32) * (g.n1 / kCartTY) * nch;
+  const int nshell = ((g.n1 + rows - 1) / rows) * nch;
+  launch_stage_kernel(stage_curvi_tma_kernel<R, NG, KIND>, dim3(nint + nshell),
+                      dim3(32 * kCartTY), st, pdl, g, a, maps, zc);
+  return true;
+}
+
+template <typename R, int NG, int KIND>
+bool launch_cart_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
+                          cudaStream_t st) {
+  CartMaps maps;
+  if (!stage_field_maps<R, NG, KIND>(&maps, g, a, 32 + 2 * NG, kCartTY + 2 * NG))
+    return false;
   CartShellC<R> sc;
   for (int d = 0; d < 3; d++) {
     sc.xmin[d] = (R)(g.xxmin[d] + (0.5 - NG) * g.dxx[d]);
@@ -725,6 +755,55 @@ bool launch_cart_tma(const Geo &g, int kind, const StageArgs<R> &a, int zc, int 
       case STAGE_LAST: return launch_cart_tma_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st);
       default: return launch_cart_tma_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st);
     }
+  }
+}
+
+template <typename R, int NG>
+void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
+                  const LaunchCfg &cfg, cudaStream_t st) {
+  const int zc = cfg.zc, pdl = cfg.pdl;
+  if (cfg.variant == 3) {
+    if constexpr (NG == 4) {
+      if (curvi_tma_ok(g, zc)) {
+        bool ok = false;
+        switch (kind) {
+          case STAGE_FIRST: ok = launch_curvi_tma_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
+          case STAGE_MID: ok = launch_curvi_tma_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
+          case STAGE_LAST: ok = launch_curvi_tma_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
+          default: ok = launch_curvi_tma_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
+        }
+        if (ok) return;
+      }
+    }
+    // not applicable here: the register-staged tiled kernel does the same work
+    LaunchCfg tiled = cfg;
+    tiled.variant = 1;
+    launch_curvi<R, NG>(g, kind, a, tiled, st);
+    return;
+  }
+  if (cfg.variant == 2) {
+    switch (kind) {
+      case STAGE_FIRST: launch_persistent_kind<R, NG, STAGE_FIRST>(g, a, pdl, st); break;
+      case STAGE_MID: launch_persistent_kind<R, NG, STAGE_MID>(g, a, pdl, st); break;
+      case STAGE_LAST: launch_persistent_kind<R, NG, STAGE_LAST>(g, a, pdl, st); break;
+      default: launch_persistent_kind<R, NG, STAGE_RAW>(g, a, pdl, st); break;
+    }
+    return;
+  }
+  if (cfg.variant == 0) {
+    switch (kind) {
+      case STAGE_FIRST: launch_column_kind<R, NG, STAGE_FIRST>(g, a, zc, cfg.block, pdl, st); break;
+      case STAGE_MID: launch_column_kind<R, NG, STAGE_MID>(g, a, zc, cfg.block, pdl, st); break;
+      case STAGE_LAST: launch_column_kind<R, NG, STAGE_LAST>(g, a, zc, cfg.block, pdl, st); break;
+      default: launch_column_kind<R, NG, STAGE_RAW>(g, a, zc, cfg.block, pdl, st); break;
+    }
+    return;
+  }
+  switch (kind) {
+    case STAGE_FIRST: launch_tile_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
+    case STAGE_MID: launch_tile_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
+    case STAGE_LAST: launch_tile_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
+    default: launch_tile_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
   }
 }
 

@@ -561,19 +561,49 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
 // shared-memory slots, each filled by tiled tensor copies -- one
 // (32 + 2 NG) x (TY + 2 NG) x PZ box of u with its halo and one 32 x TY x PZ
 // box per operand array -- that complete on the slot's mbarrier and are
-// issued NS - 1 slots ahead by one thread.  The tensor maps are 4-D (i0, i1,
-// i2, field) over a precision's field arena, one pair per solve.  Each
+// issued NS - 1 slots ahead by one thread (maps: ArenaSrc or FieldSrc).  Each
 // thread evaluates PZ points of its column per slot; it fetches only the
 // inner-boundary image cells itself, one slot ahead, overwriting the box's
 // unmaintained ghost cells.  Requires n0 % 32 == 0, n1 % TY == 0 and the
 // chunk's plane count a multiple of PZ (checked on the host).  In the FIRST
 // stage the base state is the input state (bu == su, bv == sv).
 // ---------------------------------------------------------------------------
-struct TmaFields {
+// Where the tensor copies come from.  ArenaSrc: one pair of 4-D maps
+// (i0, i1, i2, field) per solve over a precision's field arena, the field
+// index being the 4th coordinate (batches).  FieldSrc: one 3-D map per array
+// (single grids); it must stay a __grid_constant__ kernel parameter, since a
+// tensor copy names its map by address.
+struct ArenaSrc {
   const CUtensorMap *map_u;   // box (32 + 2 NG, TY + 2 NG, PZ, 1)
   const CUtensorMap *map_op;  // box (32, TY, PZ, 1)
   const void *base;           // field 0 of this solve in the arena
   int64_t stride;             // elements between consecutive fields
+  template <typename R>
+  __device__ __forceinline__ int field(const R *p) const {
+    return (int)((p - static_cast<const R *>(base)) / stride);
+  }
+  __device__ __forceinline__ void load_u(void *dst, uint64_t *bar, int x, int y,
+                                         int z, int f) const {
+    tma_load_4d(dst, map_u, bar, x, y, z, f);
+  }
+  __device__ __forceinline__ void load_op(int, void *dst, uint64_t *bar, int x,
+                                          int y, int z, int f) const {
+    tma_load_4d(dst, map_op, bar, x, y, z, f);
+  }
+};
+struct FieldSrc {
+  CUtensorMap u;      // su, box (32 + 2 NG, TY + 2 NG, PZ)
+  CUtensorMap op[8];  // operand arrays by BulkOp slot, box (32, TY, PZ)
+  template <typename R>
+  __device__ __forceinline__ int field(const R *) const { return 0; }
+  __device__ __forceinline__ void load_u(void *dst, uint64_t *bar, int x, int y,
+                                         int z, int) const {
+    tma_load_3d(dst, &u, bar, x, y, z);
+  }
+  __device__ __forceinline__ void load_op(int o, void *dst, uint64_t *bar, int x,
+                                          int y, int z, int) const {
+    tma_load_3d(dst, &op[o], bar, x, y, z);
+  }
 };
 
 template <typename R, int NG, int TY, int PZ>
@@ -583,10 +613,10 @@ struct BulkSlot {
 };
 enum BulkOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
 
-template <typename R, int NG, int KIND, int TY, int NS, int PZ>
+template <typename R, int NG, int KIND, int TY, int NS, int PZ, typename Src>
 __device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R> &a,
                                                  int tile_x, int tile_y, int chunk,
-                                                 int zc, const TmaFields &tf,
+                                                 int zc, const Src &src,
                                                  BulkSlot<R, NG, TY, PZ> *ring,
                                                  uint64_t *full, int *err) {
   static_assert((NG * sizeof(R)) % 16 == 0,
@@ -660,25 +690,25 @@ __device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R
                           (use_acc ? (1u << OP_AU) | (1u << OP_AV) : 0u);
   const uint32_t slot_bytes =
       (uint32_t)(PZ * (TW * TH + __popc(opmask) * TY * 32) * sizeof(R));
-  // Field index of u (fidx[8]) and of each operand: thread 0 only.
+  // Source coordinate (field index for an arena) of u (fidx[8]) and of
+  // each operand: thread 0 only.
   int fidx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   auto issue = [&](int pl, int sl) {
     mbar_arrive_expect(&full[sl], slot_bytes);
     fence_proxy_async_smem();
-    tma_load_4d(&ring[sl].u[0][0][0], tf.map_u, &full[sl], j0b, j1b, pl, fidx[8]);
+    src.load_u(&ring[sl].u[0][0][0], &full[sl], j0b, j1b, pl, fidx[8]);
 #pragma unroll
     for (int o = 0; o < 8; o++)
       if ((opmask >> o) & 1u)
-        tma_load_4d(&ring[sl].op[o][0][0][0], tf.map_op, &full[sl], NG + j0b,
-                    NG + j1b, pl, fidx[o]);
+        src.load_op(o, &ring[sl].op[o][0][0][0], &full[sl], NG + j0b, NG + j1b,
+                    pl, fidx[o]);
   };
   if (threadIdx.x == 0) {
-    const R *b0 = static_cast<const R *>(tf.base);
     const R *optr[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
 #pragma unroll
     for (int o = 0; o < 8; o++)
-      if ((opmask >> o) & 1u) fidx[o] = (int)((optr[o] - b0) / tf.stride);
-    fidx[8] = (int)((a.su - b0) / tf.stride);
+      if ((opmask >> o) & 1u) fidx[o] = src.field(optr[o]);
+    fidx[8] = src.field(a.su);
     for (int k = 0; k < NS - 1 && k < nslots; k++) issue(z0 + PZ * k, k);
   }
   // phi queue of this column (planes i2 - NG .. i2 + NG of the slot's first
