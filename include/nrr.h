@@ -314,20 +314,25 @@ nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device);
  * surrogate. */
 nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
 
-/* Stage kernel of a batch for `mode` (NRR_FP64 or NRR_FP32_DC): variant 0
- * stages each plane of a 32 x 4 column tile through registers into shared
- * memory; variant 1 streams the planes of a block's chunk through a ring of
- * three shared-memory slots filled by asynchronous bulk copies (one row per
- * copy, completing on an mbarrier; only for FD order 8 with every solve's
- * n0 % 32 == 0 and n1 % 4 == 0).  zc (2, 4, 8 or 16) phi planes per block.
- * Both variants give bitwise identical results.
+/* Stage kernel of a batch for `mode` (NRR_FP64, or NRR_FP32_DC for its FP32
+ * stages; the FP64 defect evaluations of NRR_FP32_DC use the NRR_FP64
+ * setting).  Variant 0 stages each plane of a 32 x 4 column tile through
+ * registers into shared memory; variant 1 streams the planes of a block's
+ * chunk through a ring of shared-memory slots filled by tensor (TMA) copies
+ * from per-solve 4-D tensor maps, completing on mbarriers (only for FD order
+ * 8 with every solve's n0 % 32 == 0 and n1 % 4 == 0); both take zc (2, 4, 8
+ * or 16) phi planes per block and give bitwise identical results.  Variant
+ * 2 = one thread per column of evolved points and zc (1, 2 or 4) planes.
+ * Defaults: variant 2, zc 1 for FP64; variant 0, zc 4 for FP32.
  * Errors: NRR_ERR_INVALID_ARG for other values or an ineligible batch. */
 nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc);
 
 /* Autotuner for the batch's stage kernel (variant and phi planes per block
  * chunk, as in nrr_batch_set_launch), timed over all solves on the current
  * state (restored afterwards); keeps the fastest for later relaxations.
- * Outputs nullable.  NRR_ERR_TIMEOUT if a bulk-copy wait expired. */
+ * Candidates: variant 0 with zc 2, 4, 8, 16; variant 1 with zc 4, 8, 16 (when
+ * eligible); variant 2 with zc 1, 2.  Outputs nullable.  NRR_ERR_TIMEOUT if a
+ * tensor-copy wait expired. */
 nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
                               int *best_zc, double *best_ms_per_launch,
                               int *best_variant);

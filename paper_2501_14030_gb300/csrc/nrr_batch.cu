@@ -171,7 +171,8 @@ __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 // phi chunks).  VAR 0: planes staged
 // through registers (stage_tile_block); VAR 1: planes streamed by tensor
 // copies through a ring of shared-memory slots (stage_bulk_block; order 8,
-// aligned grids), which records an expired copy wait in *err.
+// aligned grids), which records an expired copy wait in *err; VAR 2: one
+// thread per column of evolved points and zc planes (stage_curvi_item).
 template <typename R, int NG, int KIND, int VAR>
 __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 5 : 1)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
@@ -181,9 +182,23 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 5 : 
   if (!active[bm.x]) return;
   const SolveDev &sd = sds[bm.x];
   const Geo g = sd.g;
+  const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
+  if constexpr (VAR == 2) {
+    // column kernel: thread = one (i0, i1) column of evolved points (shell
+    // columns last) and zc phi planes
+    const int ncols = (g.n0 + NG) * g.n1, ncb = (ncols + 32 * kTileY - 1) / (32 * kTileY);
+    const int e = (bm.y % ncb) * 32 * kTileY + threadIdx.x;
+    if (e >= ncols) return;
+    const int z0 = NG + (bm.y / ncb) * zc;
+    switch (zc) {
+      case 1: dev::stage_curvi_item<R, NG, KIND, 1>(g, a, e, z0); break;
+      case 2: dev::stage_curvi_item<R, NG, KIND, 2>(g, a, e, z0); break;
+      default: dev::stage_curvi_item<R, NG, KIND, 4>(g, a, e, z0); break;
+    }
+    return;
+  }
   const int nx = dev::tiles_x(g), ny = dev::tiles_y<kTileY>(g);
   const int nint = nx * ny * dev::chunks_z(g, zc);
-  const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
   if (bm.y >= nint) {
     // outer shell: thread = (shell column, row) of shell_rows<NG>() rows
     constexpr int rows = shell_rows<NG>();
@@ -381,8 +396,11 @@ struct nrr_batch {
   int nblk_res = 0, nblk_pts = 0;
   int2 *d_map_stage[5] = {};
   int nblk_stage[5] = {};
-  int zc[2] = {4, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
-  int variant[2] = {0, 0};  // stage kernel: 0 register-staged, 1 bulk copies
+  int2 *d_map_col[3] = {};  // column variant, zc = 1, 2, 4
+  int nblk_col[3] = {};
+  int zc[2] = {1, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
+  // stage kernel: 0 register-staged tiles, 1 tensor-copy tiles, 2 columns
+  int variant[2] = {2, 0};
   int bulk_ok = 0;          // every solve meets the bulk variant's alignment
   int *d_err = nullptr;     // set by a stage kernel whose copy wait expired
   CUtensorMap *d_maps = nullptr;  // per solve: u / operand maps, FP32 then FP64
@@ -489,9 +507,33 @@ nrr_status stage_map(nrr_batch *b, int zc) {
       &b->d_map_stage[zc_index(zc)], &b->nblk_stage[zc_index(zc)], nullptr);
 }
 
+int col_index(int zc) { return zc <= 1 ? 0 : zc == 2 ? 1 : 2; }
+
+nrr_status col_map(nrr_batch *b, int zc) {
+  if (b->d_map_col[col_index(zc)]) return NRR_OK;
+  const int ng = b->ng;
+  return build_map(
+      b, 1,
+      [zc, ng](const Geo &g) {
+        const int64_t ncols = (int64_t)(g.n0 + ng) * g.n1;
+        return ((ncols + 32 * kTileY - 1) / (32 * kTileY)) * ((g.n2 + zc - 1) / zc);
+      },
+      &b->d_map_col[col_index(zc)], &b->nblk_col[col_index(zc)], nullptr);
+}
+
+// The launch map of the stage kernel for (variant, zc).
+nrr_status stage_map_for(nrr_batch *b, int variant, int zc) {
+  return variant == 2 ? col_map(b, zc) : stage_map(b, zc);
+}
+
 template <typename R, int NG, int KIND>
 void launch_bstage_kind(nrr_batch *b, int zc, int stage, int mode,
                         cudaStream_t st) {
+  if (b->variant[sizeof(R) == 4] == 2) {
+    batch_stage_kernel<R, NG, KIND, 2><<<b->nblk_col[col_index(zc)], 32 * kTileY, 0, st>>>(
+        b->d_sd, b->d_map_col[col_index(zc)], b->d_active, stage, mode, zc, b->d_err);
+    return;
+  }
   const int2 *map = b->d_map_stage[zc_index(zc)];
   const int nb = b->nblk_stage[zc_index(zc)];
   if constexpr (NG == 4) {
@@ -568,8 +610,8 @@ nrr_status build_relax_graph(nrr_batch *b, int mode, int every, double r_int) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  BTRY(stage_map(b, b->zc[0]));
-  BTRY(stage_map(b, b->zc[1]));
+  BTRY(stage_map_for(b, b->variant[0], b->zc[0]));
+  BTRY(stage_map_for(b, b->variant[1], b->zc[1]));
   cudaGraph_t graph;
   BCUDA(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
@@ -1060,13 +1102,15 @@ nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc) {
   if (!b) return bfail(NRR_ERR_INVALID_ARG, "null batch");
   if (mode != NRR_FP64 && mode != NRR_FP32_DC)
     return bfail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32_DC");
-  if (variant != 0 && variant != 1)
-    return bfail(NRR_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (variant < 0 || variant > 2)
+    return bfail(NRR_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   if (variant == 1 && !b->bulk_ok)
     return bfail(NRR_ERR_INVALID_ARG,
                  "the bulk-copy variant needs order 8, n0 %% 32 == 0, n1 %% 4 == 0");
-  if (zc != 2 && zc != 4 && zc != 8 && zc != 16)
-    return bfail(NRR_ERR_INVALID_ARG, "zc must be 2, 4, 8 or 16");
+  if ((variant == 2 && zc != 1 && zc != 2 && zc != 4) ||
+      (variant != 2 && zc != 2 && zc != 4 && zc != 8 && zc != 16))
+    return bfail(NRR_ERR_INVALID_ARG,
+                 "zc must be 1, 2 or 4 (columns) or 2, 4, 8 or 16 (tiles)");
   const int slot = mode == NRR_FP32_DC;
   b->variant[slot] = variant;
   b->zc[slot] = zc;
@@ -1110,13 +1154,14 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
   BCUDA(cudaEventCreate(&e1));
   int best = b->zc[slot], best_var = b->variant[slot];
   double best_ms = 1e30;
-  const int cands[7][2] = {{0, 2}, {0, 4}, {0, 8}, {0, 16}, {1, 4}, {1, 8}, {1, 16}};
+  const int cands[9][2] = {{0, 2}, {0, 4}, {0, 8}, {0, 16}, {1, 4},
+                           {1, 8}, {1, 16}, {2, 1}, {2, 2}};
   for (const auto &cv : cands) {
     const int var = cv[0], zc = cv[1];
     if (var == 1 && !b->bulk_ok) continue;
     b->variant[slot] = var;
     b->zc[slot] = zc;
-    BTRY(stage_map(b, zc));
+    BTRY(stage_map_for(b, var, zc));
     for (int rep = 0; rep < 2; rep++) {
       BCUDA(cudaEventRecord(e0, b->stream));
       for (int64_t t = 0; t < trial_steps; t++)

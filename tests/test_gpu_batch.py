@@ -119,12 +119,13 @@ def aligned_batch(count=4, seed=5, coord="sinhsymtp"):
                                         ("sinhsymtp", "fp64"),
                                         ("spherical", "fp32_dc")])
 def test_bulk_copy_variant_bitwise_equals_register_variant(gpu, coord, mode):
-    """Both batch stage kernels evaluate the same arithmetic in the same order
-    on the same operands: after 300 RK4 steps every solve agrees bit for bit,
-    for each plane chunking."""
+    """The batch stage kernels (register-staged tiles, tensor-copy tiles,
+    columns) evaluate the same arithmetic in the same order on the same
+    operands: after 300 RK4 steps every solve agrees bit for bit, for each
+    plane chunking."""
     descs, puncs = aligned_batch(coord=coord)
     results = []
-    for var, zc in [(0, 4), (1, 2), (1, 4), (1, 16)]:
+    for var, zc in [(0, 4), (1, 2), (1, 4), (1, 16), (2, 1), (2, 2)]:
         b = nrr.Batch(descs, puncs, with_fp64=(mode == "fp64"))
         b.set_launch(var, zc, mode)
         per, _ = b.relax(mode=mode, tol=1e-30, max_iters=300, check_every=50,
