@@ -275,11 +275,21 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
                       const ColumnSet<R> &c, double dt, double eta,
                       int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
+  const LaunchCfg &cfg = g->stage_cfg[sizeof(R) == 4];
+  if (cfg.variant == 4 && g->geo.coord != CARTESIAN) {
+    // all steps in one cooperative launch (grid barriers between stages)
+    StageArgs<R> sa[4];
+    for (int k = 0; k < 4; k++) sa[k] = stage_args<R>(g, f, c, k, dt, eta);
+    g_launches += 1;
+    launch_stage_steps<R>(g->geo, sa, (int)steps,
+                          reinterpret_cast<unsigned *>(g->flag + 3), cfg, g->stream);
+    return;
+  }
   g_launches += 4 * steps;
   for (int64_t s = 0; s < steps; s++)
     for (int k = 0; k < 4; k++)
-      launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta),
-                      g->stage_cfg[sizeof(R) == 4], g->stream);
+      launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta), cfg,
+                      g->stream);
 }
 
 // Residual + norm of the current state in precision R into scalars[1..3].
@@ -891,16 +901,16 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block)
     return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (variant < 0 || variant > 3)
+  if (variant < 0 || variant > 4)
     return fail(NRR_ERR_INVALID_ARG,
-                "variant must be 0 (column), 1 (tiled), 2 (persistent column) or "
-                "3 (tensor-copy tiled)");
+                "variant must be 0 (column), 1 (tiled), 2 (persistent column), "
+                "3 (tensor-copy tiled) or 4 (multi-stage)");
   if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
       ((variant == 1 || variant == 3) && zc != 2 && zc != 4 && zc != 8 && zc != 16) ||
-      (variant == 2 && zc != 1))
+      ((variant == 2 || variant == 4) && zc != 1))
     return fail(NRR_ERR_INVALID_ARG,
                 "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled, tensor-copy), "
-                "1 (persistent)");
+                "1 (persistent, multi-stage)");
   g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
   if (block) g->stage_cfg[mode == NRR_FP32].block = block;
@@ -961,10 +971,10 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[14] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
+  const LaunchCfg cands[15] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
                                {64, 2, 0}, {128, 4, 0}, {128, 2, 1}, {128, 4, 1},
                                {128, 8, 1}, {128, 16, 1}, {128, 1, 2}, {128, 4, 3},
-                               {128, 8, 3}, {128, 16, 3}};
+                               {128, 8, 3}, {128, 16, 3}, {128, 1, 4}};
   for (const LaunchCfg &cand0 : cands) {
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;

@@ -55,8 +55,9 @@ struct LaunchCfg {
   int zc = 2;       // curvilinear stages: phi planes per thread (variant 0)
                     // or per block chunk (variant 1)
   int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel,
-                    // 2 persistent column kernel; Cartesian stages: 0
-                    // column kernel, 1 tensor-copy (TMA) tiled kernel
+                    // 2 persistent column kernel, 3 tensor-copy tiled
+                    // kernel, 4 multi-stage cooperative kernel; Cartesian
+                    // stages: 0 column kernel, 1 tensor-copy tiled kernel
   int pdl = 1;      // stage kernels: programmatic dependent launch (the next
                     // stage's blocks start while this one drains)
 };
@@ -120,6 +121,14 @@ struct StageArgs {
 template <typename R>
 void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st);
+
+// `steps` RK4 steps (stage arguments FIRST, MID, MID, LAST) in one
+// cooperative launch of the multi-stage curvilinear kernel; `count` is a
+// device word for its grid barriers (reset by this call).
+template <typename R>
+cudaError_t launch_stage_steps(const Geo &g, const StageArgs<R> (&sa)[4], int steps,
+                               unsigned *count, const LaunchCfg &cfg,
+                               cudaStream_t st);
 
 // Residual H (c^-2 times the scaled operator) at interior points and the
 // per-block partial sums of H^2 J and J over r < r_int.  h_out nullable.

@@ -436,6 +436,105 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
                                             full, a.err);
 }
 
+// ---------------------------------------------------------------------------
+// Multi-stage curvilinear kernel (variant 4): one cooperative launch runs
+// `steps` RK4 steps -- every stage over all (column, plane) items of the
+// evolved points, grid-strided -- with a grid barrier after each stage, so
+// that small grids do not pay a launch and ramp per stage.  State written by
+// an earlier stage is read through L2 (coherent loads); every barrier wait
+// is bounded and records an expiry in the error flag.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct StageArgs4 {
+  StageArgs<R> s[4];  // FIRST, MID, MID, LAST
+};
+
+constexpr long long kBarrierPolls = 1ll << 22;
+
+// Arrive at barrier `target` (cumulative arrivals expected) and wait for
+// every block; thread 0 of each block arrives after the block's writes.
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned target,
+                                             int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    // once any barrier has expired no later one waits, so a launch spends
+    // at most one bounded wait before it drains
+    const bool expired = err && *(volatile int *)err != 0;
+    for (long long i = 0; !expired; i++) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (i > kBarrierPolls) {
+        if (err) atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int NG>
+__global__ void __launch_bounds__(128)
+    stage_curvi_multi_kernel(Geo g, StageArgs4<R> sa, int steps, unsigned *count) {
+  pdl_trigger();
+  const int ncols = (g.n0 + NG) * g.n1;
+  const int nitems = ncols * g.n2;
+  const int nthr = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned target = 0;
+  for (int s = 0; s < steps; s++) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      for (int it = tid; it < nitems; it += nthr) {
+        const int e = it % ncols, z = NG + it / ncols;
+        if (k == 0)
+          stage_curvi_item<R, NG, STAGE_FIRST, 1, true>(g, sa.s[0], e, z);
+        else if (k == 3)
+          stage_curvi_item<R, NG, STAGE_LAST, 1, true>(g, sa.s[3], e, z);
+        else
+          stage_curvi_item<R, NG, STAGE_MID, 1, true>(g, sa.s[k], e, z);
+      }
+      target += gridDim.x;
+      grid_barrier(count, target, sa.s[0].err);
+    }
+  }
+}
+
+template <typename R, int NG>
+cudaError_t launch_multi_ng(const Geo &g, const StageArgs4<R> &sa, int steps,
+                            unsigned *count, int pdl, cudaStream_t st) {
+  auto k = stage_curvi_multi_kernel<R, NG>;
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0);
+  }
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // as many items per thread as the resident grid needs, spread evenly
+  const int64_t items = (int64_t)(g.n0 + NG) * g.n1 * g.n2;
+  const int64_t ipt = (items + 128ll * per_sm * sms - 1) / (128ll * per_sm * sms);
+  const int blocks = (int)((items + 128 * ipt - 1) / (128 * ipt));
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3(blocks);
+  c.blockDim = dim3(128);
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;  // all blocks resident at once
+  at[0].val.cooperative = 1;
+  c.attrs = at;
+  c.numAttrs = 1;
+  (void)pdl;
+  return cudaLaunchKernelEx(&c, k, g, sa, steps, count);
+}
+
+
 // Residual H at interior points and the block partials of H^2 J, J over
 // r < r_int (the volume-weighted L2 norm of Alg. 1's residual).
 template <typename R, int NG>
@@ -762,6 +861,14 @@ template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st) {
   const int zc = cfg.zc, pdl = cfg.pdl;
+  if (cfg.variant == 4) {
+    // single stage launches of the multi-stage shape: the column kernel
+    LaunchCfg col = cfg;
+    col.variant = 0;
+    col.zc = 1;
+    launch_curvi<R, NG>(g, kind, a, col, st);
+    return;
+  }
   if (cfg.variant == 3) {
     if constexpr (NG == 4) {
       if (curvi_tma_ok(g, zc)) {
@@ -855,6 +962,28 @@ void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
     default: break;
   }
 }
+template <typename R>
+cudaError_t launch_stage_steps(const Geo &g, const StageArgs<R> (&sa)[4], int steps,
+                               unsigned *count, const LaunchCfg &cfg,
+                               cudaStream_t st) {
+  StageArgs4<R> s4;
+  for (int k = 0; k < 4; k++) s4.s[k] = sa[k];
+  switch (g.ng) {
+    case 2: return launch_multi_ng<R, 2>(g, s4, steps, count, cfg.pdl, st);
+    case 4: return launch_multi_ng<R, 4>(g, s4, steps, count, cfg.pdl, st);
+    case 5: return launch_multi_ng<R, 5>(g, s4, steps, count, cfg.pdl, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_stage_steps<double>(const Geo &,
+                                                const StageArgs<double> (&)[4], int,
+                                                unsigned *, const LaunchCfg &,
+                                                cudaStream_t);
+template cudaError_t launch_stage_steps<float>(const Geo &,
+                                               const StageArgs<float> (&)[4], int,
+                                               unsigned *, const LaunchCfg &,
+                                               cudaStream_t);
+
 template void launch_stage<double>(const Geo &, int, const StageArgs<double> &,
                                    const LaunchCfg &, cudaStream_t);
 template void launch_stage<float>(const Geo &, int, const StageArgs<float> &,

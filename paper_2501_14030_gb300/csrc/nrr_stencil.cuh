@@ -17,6 +17,17 @@ __device__ __forceinline__ R ld(const R *p) {
   return __ldg(p);
 }
 
+// Loads of state written earlier in the same launch (the multi-stage kernel
+// below, after a grid barrier) go through L2 (ld.global.cg); everything
+// else through the read-only path.
+template <bool COH, typename R>
+__device__ __forceinline__ R lds(const R *p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
 // Programmatic dependent launch: a stage kernel launched with the
 // programmatic-serialisation attribute may start while the preceding kernel
 // on its stream drains.  Before pdl_wait() it reads only data that no kernel
@@ -78,7 +89,7 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
 // pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  Two
 // independent accumulation chains per point (xx0 + phi, xx1) and ZC points
 // interleaved give the FP64 pipe independent work.
-template <typename R, int NG, int ZC>
+template <typename R, int NG, int ZC, bool COH = false>
 __device__ __forceinline__ void curvi_operator(
     const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
     int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
@@ -100,8 +111,8 @@ __device__ __forceinline__ void curvi_operator(
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
       const int64_t p = col + nc * wp[NG + j];
-      R up = ld(su + p + k);
-      R um = refl ? ld(su + rcol + nc * wh[j]) : ld(su + p - k);
+      R up = lds<COH>(su + p + k);
+      R um = refl ? lds<COH>(su + rcol + nc * wh[j]) : lds<COH>(su + p - k);
       a0[j] = fma(w[k], up, a0[j]);
       a0[j] = fma(w[NG + k], um, a0[j]);
     }
@@ -115,8 +126,8 @@ __device__ __forceinline__ void curvi_operator(
     const int cm = i0 + s0 * (rm ? 2 * NG - 1 - im : im);
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
-      R up = ld(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
-      R um = ld(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
+      R up = lds<COH>(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
+      R um = lds<COH>(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
       a1[j] = k == 1 ? w[2 * NG + k] * up : fma(w[2 * NG + k], up, a1[j]);
       a1[j] = fma(w[3 * NG + k], um, a1[j]);
     }
@@ -126,8 +137,8 @@ __device__ __forceinline__ void curvi_operator(
   for (int k = 1; k <= NG; k++) {
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
-      R sp = ld(su + col + nc * wp[NG + j + k]);
-      R sm = ld(su + col + nc * wp[NG + j - k]);
+      R sp = lds<COH>(su + col + nc * wp[NG + j + k]);
+      R sm = lds<COH>(su + col + nc * wp[NG + j - k]);
       a0[j] = fma(w[4 * NG + k], sp + sm, a0[j]);
     }
   }
@@ -161,17 +172,17 @@ __device__ __forceinline__ void plane_tables(const Geo &g, int z0, int (&wp)[ZC 
   for (int j = 0; j < ZC; j++) wh[j] = wrap_plane<NG>(g, min(z0 + j, last) + g.n2 / 2);
 }
 
-template <typename R, int KIND>
+template <typename R, int KIND, bool COH = false>
 __device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
                                                R ku, R kv) {
   if (KIND == STAGE_FIRST) {
-    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    R yu = lds<COH>(a.bu + p), yv = lds<COH>(a.bv + p);
     a.au[p] = fma(a.wb, ku, yu);
     a.av[p] = fma(a.wb, kv, yv);
     a.ou[p] = fma(a.wa, ku, yu);
     a.ov[p] = fma(a.wa, kv, yv);
   } else if (KIND == STAGE_MID) {
-    R yu = ld(a.bu + p), yv = ld(a.bv + p);
+    R yu = lds<COH>(a.bu + p), yv = lds<COH>(a.bv + p);
     a.au[p] = fma(a.wb, ku, a.au[p]);
     a.av[p] = fma(a.wb, kv, a.av[p]);
     a.ou[p] = fma(a.wa, ku, yu);
@@ -190,7 +201,7 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
 // interior ones (i0 fastest); the NG n1 columns after them form the outer
 // shell i0 >= n0+ng.  Numbering the shell last keeps the short radiation
 // path out of the interior warps (except the one warp at the seam).
-template <typename R, int NG, int KIND, int ZC>
+template <typename R, int NG, int KIND, int ZC, bool COH = false>
 __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R> &a,
                                                  int e, int z0) {
   const int nint = g.n0 * g.n1;
@@ -210,8 +221,10 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
     for (int j = 0; j < ZC; j++) {
       if (z0 + j >= zend) break;
       int64_t p = col + (int64_t)nc * (z0 + j);
-      R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
-      R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+      R u0 = lds<COH>(a.su + p), u1 = lds<COH>(a.su + p - 1),
+        u2 = lds<COH>(a.su + p - 2);
+      R v0 = lds<COH>(a.sv + p), v1 = lds<COH>(a.sv + p - 1),
+        v2 = lds<COH>(a.sv + p - 2);
       R du = fma(R(3), u0, fma(R(-4), u1, u2));
       R dv = fma(R(3), v0, fma(R(-4), v1, v2));
       R ku = -c * fma(kdb, du, rinv * u0);
@@ -220,7 +233,7 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
         ku += ld(a.fu + p);
         kv += ld(a.bc2 + p);
       }
-      stage_epilogue<R, KIND>(a, p, ku, kv);
+      stage_epilogue<R, KIND, COH>(a, p, ku, kv);
     }
     return;
   }
@@ -234,8 +247,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
     int64_t p = col + (int64_t)nc * wp[NG + j];
-    u0[j] = ld(a.su + p);
-    v0[j] = ld(a.sv + p);
+    u0[j] = lds<COH>(a.su + p);
+    v0[j] = lds<COH>(a.sv + p);
     al[j] = ld(a.alpha + p);
     bc[j] = ld(a.bc2 + p);
   }
@@ -246,8 +259,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
   for (int j = 0; j < ZC; j++) {
     int64_t p = col + (int64_t)nc * wp[NG + j];
     if (KIND == STAGE_FIRST || KIND == STAGE_MID) {
-      yb[0][j] = ld(a.bu + p);
-      yb[1][j] = ld(a.bv + p);
+      yb[0][j] = lds<COH>(a.bu + p);
+      yb[1][j] = lds<COH>(a.bv + p);
     }
     if (KIND == STAGE_MID || KIND == STAGE_LAST) {
       ac[0][j] = a.au[p];
@@ -255,8 +268,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
     }
     fu[j] = linear_mode<R>(a.lin) ? ld(a.fu + p) : R(0);
   }
-  curvi_operator<R, NG, ZC>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv,
-                            a.lin);
+  curvi_operator<R, NG, ZC, COH>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv,
+                                 a.lin);
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
     if (z0 + j >= zend) break;

@@ -248,7 +248,9 @@ def test_defect_correction_full_size_matches_fp64(gpu):
 # Every launch shape must reproduce the oracle; the parity tests above run
 # the default shape.  Cartesian variant 1 is the tensor-copy kernel (order 8,
 # n0 % 32 == 0, n1 % 4 == 0, even n2); curvilinear variants 1 and 2 are the
-# tiled and persistent kernels and variant 3 the tensor-copy tiled kernel.
+# tiled and persistent kernels, variant 3 the tensor-copy tiled kernel and
+# variant 4 the multi-stage cooperative kernel (RK4 steps only; single RHS
+# evaluations use the column kernel).
 VARIANT_CASES = {
     "cart_64x20x24_o8": (W.grid_desc("cartesian", (64, 20, 24), 8, xmax=32.0), Q4),
     "sinh_64x20x8_o8": (W.grid_desc("sinhsymtp", (64, 20, 8), 8), Q4),
@@ -258,10 +260,10 @@ VARIANT_CASES = {
 
 @pytest.mark.parametrize("name", list(VARIANT_CASES))
 @pytest.mark.parametrize("variant,zc", [(0, 1), (1, 2), (1, 4), (1, 16), (2, 1),
-                                        (3, 2), (3, 4), (3, 16)])
+                                        (3, 2), (3, 4), (3, 16), (4, 1)])
 def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
     desc, punc = VARIANT_CASES[name]
-    if desc["coord"] == "cartesian" and variant == 2:
+    if desc["coord"] == "cartesian" and variant in (2, 4):
         pytest.skip("Cartesian grids have variants 0 and 1")
     og = oracle_grid(desc)
     alpha, beta = og.source(punc)
