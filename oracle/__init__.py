@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "nrr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-SINHSYMTP, SPHERICAL, CARTESIAN = 0, 1, 2
+SINHSYMTP, SPHERICAL, CARTESIAN, SINHSPHERICAL = 0, 1, 2, 3
 INTERIOR, OUTER, INNER = 0, 1, 2
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 

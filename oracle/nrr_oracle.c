@@ -138,6 +138,30 @@ static void geom_spherical(double x0, double x1, double x2, point_geom *o) {
   o->drdxx0 = 1.0;
 }
 
+/* SinhSpherical: spherical coordinates with r = AMAX sinh(xx0/w)/sinh(1/w)
+ * (xx0 in [0,1]).  h = (r', r, r sin th); with J = r' r^2 sin th,
+ *   J/h0^2 = r^2 sin th / r'  =>  g0 = 2/(r r') - r''/r'^3,
+ *   J/h1^2 = r' sin th        =>  g1 = cot th / r^2.                        */
+static void geom_sinhspherical(const or_desc *d, double x0, double x1,
+                               double x2, point_geom *o) {
+  double w = d->sinhwaa;
+  double r = d->amax * sinh(x0 / w) / sinh(1.0 / w);
+  double rp = d->amax * cosh(x0 / w) / (w * sinh(1.0 / w));
+  double rpp = r / (w * w);
+  double st = sin(x1), ct = cos(x1);
+  o->x = r * st * cos(x2);
+  o->y = r * st * sin(x2);
+  o->z = r * ct;
+  o->r = fabs(r);
+  o->h[0] = rp;
+  o->h[1] = r;
+  o->h[2] = r * st;
+  o->gl[0] = 2.0 / (r * rp) - rpp / (rp * rp * rp);
+  o->gl[1] = ct / (r * r * st);
+  o->gl[2] = 0.0;
+  o->drdxx0 = rp;
+}
+
 static void geom_cartesian(double x0, double x1, double x2, point_geom *o) {
   o->x = x0;
   o->y = x1;
@@ -156,6 +180,8 @@ static void geom_at(const or_desc *d, double x0, double x1, double x2,
     geom_sinhsymtp(d, x0, x1, x2, o);
   else if (d->coord == OR_SPHERICAL)
     geom_spherical(x0, x1, x2, o);
+  else if (d->coord == OR_SINHSPHERICAL)
+    geom_sinhspherical(d, x0, x1, x2, o);
   else
     geom_cartesian(x0, x1, x2, o);
 }
@@ -175,6 +201,10 @@ static void cart_to_xx(const or_desc *d, double x, double y, double z,
     double A = sqrt(A2), Z = sqrt(A2 + b * b);
     xx[0] = w * asinh(A * sinh(1.0 / w) / d->amax);
     xx[1] = atan2(rho * Z, z * A);
+  } else if (d->coord == OR_SINHSPHERICAL) {
+    double w = d->sinhwaa;
+    xx[0] = w * asinh(sqrt(rho2 + z * z) * sinh(1.0 / w) / d->amax);
+    xx[1] = atan2(rho, z);
   } else {
     xx[0] = sqrt(rho2 + z * z);
     xx[1] = atan2(rho, z);
@@ -190,7 +220,8 @@ static void grid_dims(const or_desc *d, double xxmin[3], double xxmax[3]) {
     return;
   }
   xxmin[0] = 0.0;
-  xxmax[0] = d->coord == OR_SINHSYMTP ? 1.0 : d->rmax;
+  xxmax[0] = (d->coord == OR_SINHSYMTP || d->coord == OR_SINHSPHERICAL) ? 1.0
+                                                                       : d->rmax;
   xxmin[1] = 0.0;
   xxmax[1] = OR_PI;
   xxmin[2] = -OR_PI;
@@ -228,6 +259,8 @@ or_grid *or_grid_new(const or_desc *d, char *err, int errlen) {
   g->d = *d;
   if (d->order < 2 || d->order > 12 || (d->order & 1))
     FAIL("unsupported FD order %d", d->order);
+  if (d->coord < OR_SINHSYMTP || d->coord > OR_SINHSPHERICAL)
+    FAIL("unknown coordinate system %d", d->coord);
   g->ng = d->order / 2;
   for (int i = 0; i < 3; i++) {
     if (d->n[i] < 1) FAIL("n[%d] must be positive", i);

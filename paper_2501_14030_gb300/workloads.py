@@ -5,7 +5,8 @@ seeded random grid functions -- and none of the solver's arithmetic.  Both the
 CUDA path and the CPU oracle receive their inputs from here.
 
 Grid descriptors are plain dicts: ``coord`` ("sinhsymtp" | "spherical" |
-"cartesian"), ``n`` (interior points per direction), ``order`` (centred FD
+"cartesian" | "sinhspherical"), ``n`` (interior points per direction),
+``order`` (centred FD
 order) and the coordinate parameters ``amax``, ``bscale``, ``sinhwaa``,
 ``rmax``, ``xmax``.
 
@@ -16,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-COORDS = {"sinhsymtp": 0, "spherical": 1, "cartesian": 2}
+COORDS = {"sinhsymtp": 0, "spherical": 1, "cartesian": 2, "sinhspherical": 3}
 
 
 def grid_desc(coord: str, n, order: int, *, amax: float = 1.0e4,
@@ -69,6 +70,11 @@ def q4_sinhsymtp_256():
 
 def q4_spherical_128():
     return grid_desc("spherical", (128, 64, 32), 8, rmax=64.0), spinning_q4_pair()
+
+
+def q4_sinhspherical_128():
+    """SinhSpherical 128x64x16 (AMAX 1e4, SINHWAA 0.07), order 8."""
+    return grid_desc("sinhspherical", (128, 64, 16), 8), spinning_q4_pair()
 
 
 def q4_cartesian_256():

@@ -61,6 +61,7 @@ def _gauss(x, y, z, x0=(0.7, -0.4, 1.3), s=2.0):
     ("sinhsymtp", dict(amax=40.0, bscale=2.0, sinhwaa=0.4)),
     ("spherical", dict(rmax=12.0)),
     ("cartesian", dict(xmax=8.0)),
+    ("sinhspherical", dict(amax=40.0, sinhwaa=0.4)),
 ])
 @pytest.mark.parametrize("order", [4, 8])
 def test_laplacian_converges_at_fd_order(oracle_mod, coord, kw, order):
@@ -93,6 +94,10 @@ def _d_dxx(f, axis, h):
     W.grid_desc("sinhsymtp", (96, 64, 64), 4, amax=40.0, bscale=2.0,
                 sinhwaa=0.4),
     W.grid_desc("spherical", (96, 64, 64), 4, rmax=20.0),
+    W.grid_desc("sinhspherical", (96, 64, 64), 4, amax=40.0, sinhwaa=0.4),
+    # the strong stretch of SINHWAA 0.07 needs finer xx0 sampling for the
+    # fourth-order numerical derivative to resolve J / h0^2
+    W.grid_desc("sinhspherical", (192, 64, 64), 4),
 ])
 def test_scale_factors_match_coordinate_map(oracle_mod, desc):
     """h_i = |d(x,y,z)/d xx_i| and g_i = (1/J) d_i (J / h_i^2), by
@@ -115,6 +120,25 @@ def test_scale_factors_match_coordinate_map(oracle_mod, desc):
         scale = np.abs(gl[i])[sl] + 1.0 / np.abs(h[i] ** 2 * g.dxx[i])[sl]
         err = np.abs(gnum - gl[i])[sl] / scale
         assert err.max() < 2e-4, (i, err.max())
+
+
+def test_sinhspherical_reduces_to_spherical(oracle_mod):
+    """As SINHWAA grows, sinh(xx0/w)/sinh(1/w) -> xx0: SinhSpherical with
+    amax = R tends to Spherical with rmax = R, at the rate 1/w^2.  Its xx0 is
+    r / R, so h0 and g0 carry the factors R and 1/R of that change of
+    variable; r, h1, h2 and g1 agree directly."""
+    R = 30.0
+    sph = oracle_grid(W.grid_desc("spherical", (12, 10, 4), 4, rmax=R))
+    scale = {"r": 1.0, "h0": 1.0 / R, "h1": 1.0, "h2": 1.0, "g0": R, "g1": 1.0}
+    diffs = []
+    for w in (50.0, 100.0):
+        sh = oracle_grid(W.grid_desc("sinhspherical", (12, 10, 4), 4,
+                                     amax=R, sinhwaa=w))
+        m = sh.field("kind") == 0
+        d = max(np.abs(sh.field(f) * k - sph.field(f))[m].max() /
+                np.abs(sph.field(f))[m].max() for f, k in scale.items())
+        diffs.append(d)
+    assert diffs[1] < 1e-4 and 3.5 < diffs[0] / diffs[1] < 4.5, diffs
 
 
 def test_sinhsymtp_geometry_closed_forms(oracle_mod):
@@ -200,6 +224,7 @@ def test_source_alpha_beta_definition(oracle_mod):
     W.grid_desc("sinhsymtp", (32, 16, 2), 4),
     W.grid_desc("sinhsymtp", (20, 12, 8), 8),
     W.grid_desc("spherical", (20, 12, 8), 10, rmax=30.0),
+    W.grid_desc("sinhspherical", (20, 12, 8), 8),
 ])
 def test_inner_ghost_images_round_trip(oracle_mod, desc):
     O = oracle_mod
@@ -351,6 +376,7 @@ def test_momentum_flip_gives_identical_u(oracle_mod):
     W.grid_desc("sinhsymtp", (8, 4, 2), 4),
     W.grid_desc("sinhsymtp", (8, 8, 2), 8, amax=20.0, sinhwaa=0.3),
     W.grid_desc("cartesian", (8, 8, 8), 4, xmax=16.0),
+    W.grid_desc("sinhspherical", (8, 4, 2), 4, amax=20.0, sinhwaa=0.3),
 ])
 def test_relaxation_agrees_with_dense_newton(oracle_mod, desc):
     """The relaxation's steady state is the solution of the discrete
