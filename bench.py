@@ -564,7 +564,8 @@ def run_profile_batch(args):
 
 def run_configs2(args):
     """The q=4 spinning pair on SinhSymTP 256x256x32, Spherical 128x64x32 and
-    Cartesian 256^3 (order 8): FP32 relaxation inside the FP64
+    Cartesian 256^3 (order 8), and on the added SinhSpherical 128x64x16 grid:
+    FP32 relaxation inside the FP64
     defect-correction loop against the plain FP64 relaxation, with the
     difference of the two solutions and the oracle's residual of the
     defect-corrected one (r < 100)."""
@@ -579,7 +580,8 @@ def run_configs2(args):
     out = {}
     for name, mk in [("sinhsymtp_256x256x32", W.q4_sinhsymtp_256),
                      ("spherical_128x64x32", W.q4_spherical_128),
-                     ("cartesian_256^3", W.q4_cartesian_256)]:
+                     ("cartesian_256^3", W.q4_cartesian_256),
+                     ("sinhspherical_128x64x16", W.q4_sinhspherical_128)]:
         desc, punc = mk()
         g = nrr.Grid(desc)
         g.set_punctures(punc)

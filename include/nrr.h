@@ -54,7 +54,7 @@ typedef enum {
                              /* punctures are set)                          */
 } nrr_status;
 
-enum { NRR_SINHSYMTP = 0, NRR_SPHERICAL = 1, NRR_CARTESIAN = 2 };
+enum { NRR_SINHSYMTP = 0, NRR_SPHERICAL = 1, NRR_CARTESIAN = 2, NRR_SINHSPHERICAL = 3 };
 enum { NRR_FP64 = 0, NRR_FP32 = 1, NRR_FP32_DC = 2 };
 enum { NRR_INIT_ZERO = 0, NRR_INIT_CURRENT = 1, NRR_INIT_HOST = 2,
        NRR_INIT_DEVICE = 3 };
@@ -68,6 +68,9 @@ enum { NRR_INIT_ZERO = 0, NRR_INIT_CURRENT = 1, NRR_INIT_HOST = 2,
  *             z = sqrt(A^2 + bscale^2) cos(th), w = sinhwaa.
  *             NRR_SPHERICAL: xx0 = r in [0,rmax].
  *             NRR_CARTESIAN: [-xmax, xmax]^3.
+ *             NRR_SINHSPHERICAL: xx0 in [0,1], r = amax sinh(xx0/w)/sinh(1/w),
+ *             theta and phi as above (a sinh-stretched spherical grid, one of
+ *             the further families of Sec. 6).
  *   n[3]      interior points per direction (n[2] even for curvilinear grids).
  *   fd_order  4, 8 or 10.                                                    */
 typedef struct {
@@ -425,6 +428,7 @@ int64_t nrr_kernel_launches(void);
  * race on it and must be serialised by the caller.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before capturing any stream.
+ * Coordinates: SinhSymTP, Spherical and Cartesian (not SinhSpherical).
  * Errors: NRR_ERR_INVALID_ARG (bad descriptor, punctures or size),
  * NRR_ERR_CUDA (lookup or launch failure). */
 nrr_status nrr_residual_noalloc(const nrr_grid_desc *d, int npunct,

@@ -158,7 +158,7 @@ size_t footprint_bytes(const Geo &geo) {
 
 nrr_status validate_desc(const nrr_grid_desc *d) {
   if (!d) return fail(NRR_ERR_INVALID_ARG, "null grid descriptor");
-  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_CARTESIAN)
+  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_SINHSPHERICAL)
     return fail(NRR_ERR_INVALID_ARG, "unknown coordinate system %d", d->coord);
   if (d->fd_order != 4 && d->fd_order != 8 && d->fd_order != 10)
     return fail(NRR_ERR_INVALID_ARG, "fd_order must be 4, 8 or 10 (got %d)",
@@ -184,6 +184,8 @@ nrr_status validate_desc(const nrr_grid_desc *d) {
     return fail(NRR_ERR_INVALID_ARG, "SinhSymTP needs amax > 0, sinhwaa > 0");
   if (d->coord == NRR_SPHERICAL && !(d->rmax > 0))
     return fail(NRR_ERR_INVALID_ARG, "Spherical needs rmax > 0");
+  if (d->coord == NRR_SINHSPHERICAL && !(d->amax > 0 && d->sinhwaa > 0))
+    return fail(NRR_ERR_INVALID_ARG, "SinhSpherical needs amax > 0, sinhwaa > 0");
   if (d->coord == NRR_CARTESIAN && !(d->xmax > 0))
     return fail(NRR_ERR_INVALID_ARG, "Cartesian needs xmax > 0");
   return NRR_OK;
@@ -209,7 +211,8 @@ Geo make_geo(const nrr_grid_desc *d) {
     }
   } else {
     xmin[0] = 0.0;
-    xmax[0] = d->coord == NRR_SINHSYMTP ? 1.0 : d->rmax;
+    xmax[0] = (d->coord == NRR_SINHSYMTP || d->coord == NRR_SINHSPHERICAL) ? 1.0
+                                                                         : d->rmax;
     xmin[1] = 0.0;
     xmax[1] = M_PI;
     xmin[2] = -M_PI;

@@ -453,7 +453,8 @@ Geo batch_geo(const nrr_grid_desc &d) {
   g.ncol = g.s0 * g.s1;
   g.npts = (int64_t)g.ncol * g.s2;
   g.xxmin[0] = 0.0;
-  g.dxx[0] = (d.coord == NRR_SINHSYMTP ? 1.0 : d.rmax) / g.n0;
+  g.dxx[0] = ((d.coord == NRR_SINHSYMTP || d.coord == NRR_SINHSPHERICAL) ? 1.0 : d.rmax) /
+             g.n0;
   g.xxmin[1] = 0.0;
   g.dxx[1] = M_PI / g.n1;
   g.xxmin[2] = -M_PI;
@@ -723,8 +724,10 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
   size_t bytes = 0;
   for (int s = 0; s < n; s++) {
     const nrr_grid_desc &d = descs[s];
-    if (d.coord != NRR_SINHSYMTP && d.coord != NRR_SPHERICAL)
-      return bfail(NRR_ERR_INVALID_ARG, "solve %d: batches take SinhSymTP or Spherical grids", s);
+    if (d.coord != NRR_SINHSYMTP && d.coord != NRR_SPHERICAL &&
+        d.coord != NRR_SINHSPHERICAL)
+      return bfail(NRR_ERR_INVALID_ARG,
+                   "solve %d: batches take SinhSymTP, Spherical or SinhSpherical grids", s);
     if (d.fd_order != order || (order != 4 && order != 8 && order != 10))
       return bfail(NRR_ERR_INVALID_ARG, "solve %d: one FD order (4, 8 or 10) per batch", s);
     int ng = order / 2;
@@ -735,6 +738,8 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
       return bfail(NRR_ERR_INVALID_ARG, "solve %d: bad SinhSymTP parameters", s);
     if (d.coord == NRR_SPHERICAL && !(d.rmax > 0))
       return bfail(NRR_ERR_INVALID_ARG, "solve %d: bad rmax", s);
+    if (d.coord == NRR_SINHSPHERICAL && !(d.amax > 0 && d.sinhwaa > 0))
+      return bfail(NRR_ERR_INVALID_ARG, "solve %d: bad SinhSpherical parameters", s);
     if (npunct[s] < 1 || npunct[s] > 8 || !punct[s])
       return bfail(NRR_ERR_INVALID_ARG, "solve %d: need 1..8 punctures", s);
     for (int a = 0; a < npunct[s]; a++)

@@ -16,7 +16,13 @@
 
 namespace nrr {
 
-enum Coord { SINHSYMTP = 0, SPHERICAL = 1, CARTESIAN = 2 };
+enum Coord { SINHSYMTP = 0, SPHERICAL = 1, CARTESIAN = 2, SINHSPHERICAL = 3 };
+
+// Spherical-like maps (radius odd in xx0): the xx0 < 0 image also reflects
+// theta.
+NRR_HD bool spherical_like(int coord) {
+  return coord == SPHERICAL || coord == SINHSPHERICAL;
+}
 
 // Everything a kernel needs to know about one grid, passed by value.
 struct Geo {
@@ -47,7 +53,7 @@ NRR_HD int wrap_phi(const Geo &g, int i2) {
 // an exact grid point):
 //   SinhSymTP: (xx0,th,ph) with xx0<0 -> (-xx0, th, ph+pi)   [A odd, Z even]
 //              th<0 -> (-th, ph+pi); th>pi -> (2pi-th, ph+pi)
-//   Spherical: r<0 -> (-r, pi-th, ph+pi); theta rules as above
+//   Spherical, SinhSpherical: r<0 -> (-r, pi-th, ph+pi); theta rules as above
 //   phi periodic.
 // Evolved points (interior and the outer shell) map to themselves.
 NRR_HD void image_of(const Geo &g, int &i0, int &i1, int &i2) {
@@ -55,7 +61,7 @@ NRR_HD void image_of(const Geo &g, int &i0, int &i1, int &i2) {
   if (i0 < g.ng) {
     i0 = 2 * g.ng - 1 - i0;
     flip ^= 1;
-    if (g.coord == SPHERICAL) i1 = g.n1 + 2 * g.ng - 1 - i1;
+    if (spherical_like(g.coord)) i1 = g.n1 + 2 * g.ng - 1 - i1;
   }
   if (i1 < g.ng) {
     i1 = 2 * g.ng - 1 - i1;

@@ -1,7 +1,8 @@
 // nrr_setup.cu -- device set-up of one grid (arXiv 2501.14030, Alg. 1 set-up:
 // coordinate arrays, reference-metric precompute, constant source terms).
 //
-// Curvilinear grids (SinhSymTP, Spherical) have a reference metric that does
+// Curvilinear grids (SinhSymTP, Spherical, SinhSpherical) have a reference
+// metric that does
 // not depend on phi, so everything except the source lives in per-column
 // arrays indexed col = i0 + s0*i1.
 #include <cuda_runtime.h>
@@ -25,6 +26,8 @@ struct ColGeom {
 //   h0 = A' V / Z, h1 = V, h2 = A sin th,
 //   g0 = (Z^2 + A^2 - A Z^2 A''/A'^2) / (A' A V^2),  g1 = cot th / V^2.
 // Spherical: h = (1, r, r sin th), g0 = 2/r, g1 = cot th / r^2.
+// SinhSpherical, r = amax sinh(xx0/w)/sinh(1/w): h = (r', r, r sin th),
+//   g0 = 2/(r r') - r''/r'^3, g1 = cot th / r^2.
 __device__ ColGeom column_geom(const Geo &g, double xx0, double th) {
   ColGeom o;
   double st, ct;
@@ -48,6 +51,19 @@ __device__ ColGeom column_geom(const Geo &g, double xx0, double th) {
     o.gl[1] = ct / (st * V2);
     o.r = sqrt(A * A + b * b * ct * ct);
     o.drdxx0 = A * Ap / o.r;
+  } else if (g.coord == SINHSPHERICAL) {
+    double w = g.sinhwaa;
+    double sh1 = sinh(1.0 / w);
+    double r = g.amax * sinh(xx0 / w) / sh1;
+    double rp = g.amax * cosh(xx0 / w) / (w * sh1);
+    double rpp = r / (w * w);
+    o.h[0] = rp;
+    o.h[1] = r;
+    o.h[2] = r * st;
+    o.gl[0] = 2.0 / (r * rp) - rpp / (rp * rp * rp);
+    o.gl[1] = ct / (r * r * st);
+    o.r = fabs(r);
+    o.drdxx0 = rp;
   } else {
     double r = xx0;
     o.h[0] = 1.0;
@@ -171,9 +187,12 @@ __device__ void cart_position(const Geo &g, int i0, int i1, int i2,
     x[1] = A * st * sp;
     x[2] = Z * ct;
   } else {
-    x[0] = xx0 * st * cp;
-    x[1] = xx0 * st * sp;
-    x[2] = xx0 * ct;
+    const double r = g.coord == SINHSPHERICAL
+                         ? g.amax * sinh(xx0 / g.sinhwaa) / sinh(1.0 / g.sinhwaa)
+                         : xx0;
+    x[0] = r * st * cp;
+    x[1] = r * st * sp;
+    x[2] = r * ct;
   }
 }
 

@@ -107,7 +107,7 @@ __device__ __forceinline__ void curvi_operator(
     const int im = i0 - k;
     const bool refl = im < NG;
     const int rcol = (2 * NG - 1 - im) +
-                     s0 * (g.coord == SPHERICAL ? g.n1 + 2 * NG - 1 - i1 : i1);
+                     s0 * (spherical_like(g.coord) ? g.n1 + 2 * NG - 1 - i1 : i1);
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
       const int64_t p = col + nc * wp[NG + j];
@@ -450,7 +450,7 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
           if (j0 < NG) {
             j0 = 2 * NG - 1 - j0;
             f = 1;
-            if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
+            if (spherical_like(g.coord)) j1 = g.n1 + 2 * NG - 1 - j1;
           }
           if (j1 < NG) {
             j1 = 2 * NG - 1 - j1;
@@ -671,7 +671,7 @@ __device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R
         if (j0 < NG) {
           j0 = 2 * NG - 1 - j0;
           f = 1;
-          if (g.coord == SPHERICAL) j1 = g.n1 + 2 * NG - 1 - j1;
+          if (spherical_like(g.coord)) j1 = g.n1 + 2 * NG - 1 - j1;
         }
         if (j1 < NG) {
           j1 = 2 * NG - 1 - j1;

@@ -37,7 +37,8 @@ Geo desc_geo(const nrr_grid_desc &d) {
   g.ncol = g.s0 * g.s1;
   g.npts = (int64_t)g.ncol * g.s2;
   g.xxmin[0] = 0.0;
-  g.dxx[0] = (d.coord == NRR_SINHSYMTP ? 1.0 : d.rmax) / g.n0;
+  g.dxx[0] = ((d.coord == NRR_SINHSYMTP || d.coord == NRR_SINHSPHERICAL) ? 1.0 : d.rmax) /
+             g.n0;
   g.xxmin[1] = 0.0;
   g.dxx[1] = M_PI / g.n1;
   g.xxmin[2] = -M_PI;

@@ -25,6 +25,9 @@ CASES = {
     "sph_40x22x8_o8": (W.grid_desc("spherical", (40, 22, 8), 8, rmax=64.0), Q4),
     "cart_26x20x22_o4": (W.grid_desc("cartesian", (26, 20, 22), 4, xmax=32.0), Q4),
     "cart_20x18x24_o8": (W.grid_desc("cartesian", (20, 18, 24), 8, xmax=32.0), Q4),
+    "sinhsph_40x22x8_o8": (W.grid_desc("sinhspherical", (40, 22, 8), 8), Q4),
+    "sinhsph_36x20x6_o4": (W.grid_desc("sinhspherical", (36, 20, 6), 4,
+                                       amax=200.0, sinhwaa=0.2), Q4),
     # full-size q=4 grid
     "sinh_128x128x16_o8": W.q4_sinhsymtp_128(),
 }
@@ -32,6 +35,7 @@ CASES = {
 # Cartesian 256^3, order 8): RHS and residual parity over every point.
 FULL = {
     "sinh_256x256x32_o8": W.q4_sinhsymtp_256(),
+    "sinhsph_128x64x16_o8": W.q4_sinhspherical_128(),
     "sph_128x64x32_o8": W.q4_spherical_128(),
     "cart_256x256x256_o8": W.q4_cartesian_256(),
 }
@@ -108,6 +112,7 @@ def test_residual_and_norm_parity(gpu, name):
 
 @pytest.mark.parametrize("name,steps", [("sinh_32x16x2_o4", 200),
                                         ("sinh_44x26x6_o8", 60),
+                                        ("sinhsph_40x22x8_o8", 60),
                                         ("sinh_36x20x10_o10", 40),
                                         ("sph_40x22x8_o8", 60),
                                         ("cart_26x20x22_o4", 60),
@@ -129,7 +134,7 @@ def test_trajectory_parity_fp64(gpu, name, steps):
 
 
 @pytest.mark.parametrize("name", ["sinh_32x16x2_o4", "sph_40x22x8_o8",
-                                  "cart_26x20x22_o4"])
+                                  "cart_26x20x22_o4", "sinhsph_36x20x6_o4"])
 def test_relax_converged_parity(gpu, name):
     """Full solves to 1e-10: same step count, u within 1e-10."""
     desc, punc, og, alpha, beta, g = _setup(name)
@@ -255,6 +260,7 @@ VARIANT_CASES = {
     "cart_64x20x24_o8": (W.grid_desc("cartesian", (64, 20, 24), 8, xmax=32.0), Q4),
     "sinh_64x20x8_o8": (W.grid_desc("sinhsymtp", (64, 20, 8), 8), Q4),
     "sph_64x20x8_o8": (W.grid_desc("spherical", (64, 20, 8), 8, rmax=64.0), Q4),
+    "sinhsph_64x20x8_o8": (W.grid_desc("sinhspherical", (64, 20, 8), 8), Q4),
 }
 
 
