@@ -231,13 +231,10 @@ def run_ours(args):
     launches = nrr.kernel_launches() - launches0
     clk = clocks.stop()
 
-    # whole job: every rank solved the same number of RHS evaluations
-    my = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(my, op=dist.ReduceOp.MAX)
-    t_max_s = my.item() / 1e3
-    rhs_evals = n_int * 4 * iters
-    value = world * rhs_evals / t_max_s
+    # whole job: the slowest rank's time, the RHS evaluations of all ranks
+    from paper_2501_14030_gb300.replicas import job_rate
+    t_max_s, _, value = job_rate(total_ms / 1e3, float(n_int * 4 * iters), dist,
+                                 device="cuda")
 
     # ---- dominant kernel: the fused RK4 stage, timed on its own stream
     dt, eta = g.timestep(0.5)
@@ -304,7 +301,8 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
         e2e_iters += r["iters"]
-    e2e_value = world * n_int * 4 * e2e_iters / (e2e_ms / 1e3)
+    e2e_value = job_rate(e2e_ms / 1e3, float(n_int * 4 * e2e_iters), dist,
+                         device="cuda")[2]
     h2d = 2 * (10 * 8)  # two nrr_puncture structs
     d2h = int(np.prod(g.shape)) * 8
 
