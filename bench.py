@@ -367,15 +367,18 @@ def run_ours(args):
 
 
 def run_profile_steps(args):
-    """A short fixed workload for profiler captures: set-up, then
-    `--profile-steps` RK4 steps (4 fused stage launches each) and one
-    residual, in the precision given by --mode.  Prints nothing timed."""
+    """A short fixed workload for profiler captures: set-up of the q=4 grid
+    named by --profile-grid, then `--profile-steps` RK4 steps (4 fused stage
+    launches each) and one residual, in the precision given by --mode.
+    Prints nothing timed."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_14030_gb300 import nrr, workloads as W
     torch.cuda.set_device(0)
-    desc, punc = W.q4_sinhsymtp_128()
+    grids = {"sinhsymtp128": W.q4_sinhsymtp_128, "sinhsymtp256": W.q4_sinhsymtp_256,
+             "cartesian256": W.q4_cartesian_256}
+    desc, punc = grids[args.profile_grid]()
     g = nrr.Grid(desc)
     g.set_punctures(punc)
     dt, eta = g.timestep(0.5)
@@ -413,7 +416,7 @@ def run_batch(args, nrr, W, torch):
             "seconds": secs, "solves_per_s": len(descs) / secs,
             "gridpoint_rhs_per_s": rhs / secs,
             "rk4_steps_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())],
-            "stage_variant": ["register-staged", "bulk-copy ring"][var],
+            "stage_variant": ["register-staged tiles", "tensor-copy ring", "columns"][var],
             "stage_zc": zc, "fp32_stage_ms_all_solves": ms,
             "graph_launches": 1, "chunks": tot["outer_iters"],
             "grids": "SinhSymTP N0 in {64,96,128}, N1 in {32,64,96,128}, N2 in {8,16}, order 8"}
@@ -747,6 +750,9 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--profile-variant", type=int, default=0,
                     help="with --profile-steps: 0 column, 1 tiled kernel")
+    ap.add_argument("--profile-grid", default="sinhsymtp128",
+                    choices=["sinhsymtp128", "sinhsymtp256", "cartesian256"],
+                    help="with --profile-steps: the q=4 grid to step")
     ap.add_argument("--profile-block", type=int, default=0,
                     help="with --profile-steps: column-kernel block size")
     ap.add_argument("--profile-zc", type=int, default=0,
