@@ -1,5 +1,5 @@
-// nrr_async.cuh -- asynchronous bulk copies (global -> shared memory,
-// completed on an mbarrier) for the stage kernels' plane pipeline.
+// nrr_async.cuh -- mbarriers and tensor (TMA) copies (global -> shared
+// memory, completing on an mbarrier) for the stage kernels' plane pipeline.
 //
 // Every wait is bounded: a wait that expires returns false and the caller
 // records an error and drains its copies in flight before the block exits.
@@ -25,7 +25,7 @@ __device__ __forceinline__ void mbar_init_count(uint64_t *bar, uint32_t count) {
                : "memory");
 }
 
-// Makes barrier initialisation visible to the async proxy (bulk copies).
+// Makes barrier initialisation visible to the async proxy (tensor copies).
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -62,18 +62,6 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
 // its later async-proxy ones (a buffer read by the threads is refilled).
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-// from global to this block's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src,
-                                              uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1], %2, [%3];" ::"r"(shared_addr(dst)),
-      "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes),
-      "r"(shared_addr(bar))
-      : "memory");
 }
 
 // Tiled tensor copy of one box at coordinates (x, y, z) of a 3-D tensor map

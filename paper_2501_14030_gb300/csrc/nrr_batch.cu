@@ -157,10 +157,10 @@ __device__ __forceinline__ StageArgs<float> batch_stage_args<float>(
 
 // --- kernels ----------------------------------------------------------------
 constexpr int kTileY = 4;
-constexpr int kBulkPZ = 2;  // phi planes per ring slot (tensor-copy variant)
+constexpr int kTmaPZ = 2;  // phi planes per ring slot (tensor-copy variant)
 // ring slots per block: the FP64 ring of 3 slots would exceed 48 KB
 template <typename R>
-__host__ __device__ constexpr int bulk_slots() { return sizeof(R) == 4 ? 3 : 2; }
+__host__ __device__ constexpr int tma_slots() { return sizeof(R) == 4 ? 3 : 2; }
 // i1 rows of the outer shell per shell block (NG columns each)
 template <int NG>
 __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
@@ -170,7 +170,7 @@ __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 // chunks), then the outer-shell blocks (shell_rows() rows of i1 each, then
 // phi chunks).  VAR 0: planes staged
 // through registers (stage_tile_block); VAR 1: planes streamed by tensor
-// copies through a ring of shared-memory slots (stage_bulk_block; order 8,
+// copies through a ring of shared-memory slots (stage_tma_block; order 8,
 // aligned grids), which records an expired copy wait in *err; VAR 2: one
 // thread per column of evolved points and zc planes (stage_curvi_item).
 template <typename R, int NG, int KIND, int VAR>
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 5 : 
   }
   const int tile_x = bm.y % nx, tile_y = (bm.y / nx) % ny, chunk = bm.y / (nx * ny);
   if constexpr (VAR == 1) {
-    __shared__ __align__(128) dev::BulkSlot<R, NG, kTileY, kBulkPZ> ring[bulk_slots<R>()];
-    __shared__ __align__(8) uint64_t full[bulk_slots<R>()];
-    dev::stage_bulk_block<R, NG, KIND, kTileY, bulk_slots<R>(), kBulkPZ>(
+    __shared__ __align__(128) dev::TmaSlot<R, NG, kTileY, kTmaPZ> ring[tma_slots<R>()];
+    __shared__ __align__(8) uint64_t full[tma_slots<R>()];
+    dev::stage_tma_block<R, NG, KIND, kTileY, tma_slots<R>(), kTmaPZ>(
         g, a, tile_x, tile_y, chunk, zc, sizeof(R) == 4 ? sd.tf32 : sd.tf64, ring,
         full, err);
   } else {
@@ -401,7 +401,7 @@ struct nrr_batch {
   int zc[2] = {1, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
   // stage kernel: 0 register-staged tiles, 1 tensor-copy tiles, 2 columns
   int variant[2] = {2, 0};
-  int bulk_ok = 0;          // every solve meets the bulk variant's alignment
+  int tma_ok = 0;           // every solve meets the tensor-copy variant's shape
   int *d_err = nullptr;     // set by a stage kernel whose copy wait expired
   CUtensorMap *d_maps = nullptr;  // per solve: u / operand maps, FP32 then FP64
   int64_t total_points = 0, interior_points = 0;
@@ -885,34 +885,34 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
     BTRY(balloc(b, &b->d_active, (size_t)n));
     BTRY(balloc(b, &b->d_err, 1));
     BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
-    // Bulk-copy stage variant: order 8, whole 32-wide tiles in i0 and 4-row
+    // Tensor-copy stage variant: order 8, whole 32-wide tiles in i0 and 4-row
     // tiles in i1, and rows / field bases on 16-byte boundaries in both
     // precisions (s0 and every solve's offset multiples of 4 elements).
-    b->bulk_ok = ng == 4;
+    b->tma_ok = ng == 4;
     for (int s = 0; s < n; s++) {
       const Geo &g = b->geos[s];
-      if (g.n0 % 32 || g.n1 % kTileY || g.s0 % 4 || g.npts % 4) b->bulk_ok = 0;
+      if (g.n0 % 32 || g.n1 % kTileY || g.s0 % 4 || g.npts % 4) b->tma_ok = 0;
     }
-    if (b->bulk_ok) {
+    if (b->tma_ok) {
       std::vector<CUtensorMap> maps(4 * (size_t)n);
       BTRY(balloc(b, &b->d_maps, maps.size()));
-      for (int s = 0; s < n && b->bulk_ok; s++) {
+      for (int s = 0; s < n && b->tma_ok; s++) {
         const Geo &g = b->geos[s];
         SolveDev &sd = b->host_sd[s];
         const int tw = 32 + 2 * ng, th = kTileY + 2 * ng;
-        const int pz = kBulkPZ;
+        const int pz = kTmaPZ;
         bool ok = encode_field_map(&maps[4 * s + 0], sd.d, g, 11, total, 4, tw, th, pz) &&
                   encode_field_map(&maps[4 * s + 1], sd.d, g, 11, total, 4, 32, kTileY, pz) &&
                   encode_field_map(&maps[4 * s + 2], sd.u, g, n64, total, 8, tw, th, pz) &&
                   encode_field_map(&maps[4 * s + 3], sd.u, g, n64, total, 8, 32, kTileY, pz);
         if (!ok) {
-          b->bulk_ok = 0;
+          b->tma_ok = 0;
           break;
         }
         sd.tf32 = {b->d_maps + 4 * s + 0, b->d_maps + 4 * s + 1, sd.d, total};
         sd.tf64 = {b->d_maps + 4 * s + 2, b->d_maps + 4 * s + 3, sd.u, total};
       }
-      if (b->bulk_ok)
+      if (b->tma_ok)
         BCUDA(cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                          cudaMemcpyHostToDevice));
     }
@@ -1109,9 +1109,9 @@ nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc) {
     return bfail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32_DC");
   if (variant < 0 || variant > 2)
     return bfail(NRR_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
-  if (variant == 1 && !b->bulk_ok)
+  if (variant == 1 && !b->tma_ok)
     return bfail(NRR_ERR_INVALID_ARG,
-                 "the bulk-copy variant needs order 8, n0 %% 32 == 0, n1 %% 4 == 0");
+                 "the tensor-copy variant needs order 8, n0 %% 32 == 0, n1 %% 4 == 0");
   if ((variant == 2 && zc != 1 && zc != 2 && zc != 4) ||
       (variant != 2 && zc != 2 && zc != 4 && zc != 8 && zc != 16))
     return bfail(NRR_ERR_INVALID_ARG,
@@ -1163,7 +1163,7 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
                            {1, 8}, {1, 16}, {2, 1}, {2, 2}};
   for (const auto &cv : cands) {
     const int var = cv[0], zc = cv[1];
-    if (var == 1 && !b->bulk_ok) continue;
+    if (var == 1 && !b->tma_ok) continue;
     b->variant[slot] = var;
     b->zc[slot] = zc;
     BTRY(stage_map_for(b, var, zc));

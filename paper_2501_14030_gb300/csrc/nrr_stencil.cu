@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
     stage_epilogue<R, KIND>(a, i0 + (int64_t)g.s0 * i1 + (int64_t)g.ncol * i2, ku, kv);
     return;
   }
-  __shared__ __align__(128) BulkSlot<R, NG, TY, PZ> ring[NS];
+  __shared__ __align__(128) TmaSlot<R, NG, TY, PZ> ring[NS];
   __shared__ __align__(8) uint64_t full[NS];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int tile_x = blockIdx.x % ntx, tile_y = (blockIdx.x / ntx) % nty,
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
       if (it >= nslots) break;
       const int i2 = z0 + PZ * it;
       const bool ok = mbar_wait_parity(&full[sl], (uint32_t)phase);
-      const BulkSlot<R, NG, TY, PZ> &S = ring[sl];
+      const TmaSlot<R, NG, TY, PZ> &S = ring[sl];
 #pragma unroll
       for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
 #pragma unroll
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
 }
 
 // Curvilinear stage fed by tensor copies (variant 3; order 8, n0 % 32 == 0,
-// n1 % 4 == 0): interior blocks run stage_bulk_block on a 32 x 4 column tile
+// n1 % 4 == 0): interior blocks run stage_tma_block on a 32 x 4 column tile
 // and a chunk of phi planes with one 3-D tensor map per array (kernel
 // parameter); the blocks after them evolve the outer shell, 32 rows of i1
 // and the NG shell columns each.
@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
                                     min(z0 + zc, NG + g.n2));
     return;
   }
-  __shared__ __align__(128) BulkSlot<R, NG, TY, PZ> ring[NS];
+  __shared__ __align__(128) TmaSlot<R, NG, TY, PZ> ring[NS];
   __shared__ __align__(8) uint64_t full[NS];
-  stage_bulk_block<R, NG, KIND, TY, NS, PZ>(g, a, blockIdx.x % ntx,
+  stage_tma_block<R, NG, KIND, TY, NS, PZ>(g, a, blockIdx.x % ntx,
                                             (blockIdx.x / ntx) % nty,
                                             blockIdx.x / (ntx * nty), zc, maps, ring,
                                             full, a.err);

@@ -606,7 +606,7 @@ struct ArenaSrc {
 };
 struct FieldSrc {
   CUtensorMap u;      // su, box (32 + 2 NG, TY + 2 NG, PZ)
-  CUtensorMap op[8];  // operand arrays by BulkOp slot, box (32, TY, PZ)
+  CUtensorMap op[8];  // operand arrays by TmaOp slot, box (32, TY, PZ)
   template <typename R>
   __device__ __forceinline__ int field(const R *) const { return 0; }
   __device__ __forceinline__ void load_u(void *dst, uint64_t *bar, int x, int y,
@@ -620,17 +620,17 @@ struct FieldSrc {
 };
 
 template <typename R, int NG, int TY, int PZ>
-struct BulkSlot {
+struct TmaSlot {
   R u[PZ][TY + 2 * NG][32 + 2 * NG];  // PZ planes of u with halo
   R op[8][PZ][TY][32];                // operand rows, slots below
 };
-enum BulkOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
+enum TmaOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
 
 template <typename R, int NG, int KIND, int TY, int NS, int PZ, typename Src>
-__device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R> &a,
+__device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R> &a,
                                                  int tile_x, int tile_y, int chunk,
                                                  int zc, const Src &src,
-                                                 BulkSlot<R, NG, TY, PZ> *ring,
+                                                 TmaSlot<R, NG, TY, PZ> *ring,
                                                  uint64_t *full, int *err) {
   static_assert((NG * sizeof(R)) % 16 == 0,
                 "operand boxes start at x = NG: 16-byte aligned");
@@ -757,7 +757,7 @@ __device__ __forceinline__ void stage_bulk_block(const Geo &g, const StageArgs<R
       if (it >= nslots) break;
       const int i2 = z0 + PZ * it;
       const bool ok = mbar_wait_parity(&full[sl], (uint32_t)phase);
-      BulkSlot<R, NG, TY, PZ> &S = ring[sl];
+      TmaSlot<R, NG, TY, PZ> &S = ring[sl];
       if (has_img) {
 #pragma unroll
         for (int j = 0; j < PZ; j++) {

@@ -102,7 +102,7 @@ def test_batch_limits_end_the_graph(gpu):
 
 
 def aligned_batch(count=4, seed=5, coord="sinhsymtp"):
-    """Order-8 grids that admit the bulk-copy stage variant (n0 % 32 == 0,
+    """Order-8 grids that admit the tensor-copy stage variant (n0 % 32 == 0,
     n1 % 4 == 0), uneven sizes including the axis and theta-edge tiles."""
     rng = np.random.default_rng(seed)
     params = W.batch_parameters(count, seed)
@@ -118,7 +118,7 @@ def aligned_batch(count=4, seed=5, coord="sinhsymtp"):
 @pytest.mark.parametrize("coord,mode", [("sinhsymtp", "fp32_dc"),
                                         ("sinhsymtp", "fp64"),
                                         ("spherical", "fp32_dc")])
-def test_bulk_copy_variant_bitwise_equals_register_variant(gpu, coord, mode):
+def test_batch_stage_variants_bitwise_equal(gpu, coord, mode):
     """The batch stage kernels (register-staged tiles, tensor-copy tiles,
     columns) evaluate the same arithmetic in the same order on the same
     operands: after 300 RK4 steps every solve agrees bit for bit, for each
@@ -145,7 +145,7 @@ def test_bulk_copy_variant_bitwise_equals_register_variant(gpu, coord, mode):
             assert np.array_equal(a, b_)
 
 
-def test_bulk_copy_variant_refused_for_unaligned_grids(gpu):
+def test_tensor_copy_variant_refused_for_unaligned_grids(gpu):
     descs, puncs = small_batch(count=2)
     b = nrr.Batch(descs, puncs)
     with pytest.raises(nrr.NrrError):
