@@ -406,6 +406,18 @@ nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
  * (graph replays count every kernel node). */
 int64_t nrr_kernel_launches(void);
 
+/* Diagnostic (the paper has no counterpart): runs one bounded wait of the
+ * kind the stage kernels use on something that never happens -- which = 0:
+ * an mbarrier phase that nothing completes (the tensor-copy pipeline's
+ * wait); which = 1: a grid barrier that expects one block more than the grid
+ * has (the multi-stage kernel's barrier) -- and reports in *expired (host)
+ * whether the wait gave up and recorded its error, as it must.  The kernel
+ * returns normally, so the context stays usable.  Takes up to a few seconds
+ * (the poll limits of those waits).  Work on `stream` (NULL = legacy
+ * default); blocks until done.  Allocates 8 bytes of device memory.
+ * Errors: NRR_ERR_INVALID_ARG, NRR_ERR_OOM, NRR_ERR_CUDA. */
+nrr_status nrr_selftest_wait_expiry(int which, void *stream, int *expired);
+
 /* Residual norm without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc,
  * for instance an application whose memory manager already owns the whole

@@ -13,7 +13,10 @@
 namespace nrr {
 namespace dev {
 
-constexpr long long kAsyncWaitLimit = 1ll << 22;  // try_wait polls
+// try_wait polls before a wait gives up: about a second on sm_103a (a poll
+// suspends ~4 us when the phase is incomplete); a healthy copy completes in
+// microseconds.
+constexpr long long kAsyncWaitLimit = 1ll << 18;
 
 __device__ __forceinline__ uint32_t shared_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -89,6 +92,33 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map,
       "l"(reinterpret_cast<uint64_t>(map)), "r"(shared_addr(bar)), "r"(x),
       "r"(y), "r"(z), "r"(w)
       : "memory");
+}
+
+constexpr long long kBarrierPolls = 1ll << 22;
+
+// Arrive at barrier `target` (cumulative arrivals expected) and wait for
+// every block; thread 0 of each block arrives after the block's writes.
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned target,
+                                             int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    // once any barrier has expired no later one waits, so a launch spends
+    // at most one bounded wait before it drains
+    const bool expired = err && *(volatile int *)err != 0;
+    for (long long i = 0; !expired; i++) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (i > kBarrierPolls) {
+        if (err) atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace dev

@@ -27,7 +27,7 @@ namespace nrr {
 namespace {
 
 constexpr int BM = 128, BK = 64, STAGES = 4;
-constexpr long long kWaitLimit = 1ll << 22;  // try_wait polls before giving up
+constexpr long long kWaitLimit = 1ll << 18;  // try_wait polls (about a second)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);

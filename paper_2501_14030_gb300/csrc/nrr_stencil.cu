@@ -449,33 +449,6 @@ struct StageArgs4 {
   StageArgs<R> s[4];  // FIRST, MID, MID, LAST
 };
 
-constexpr long long kBarrierPolls = 1ll << 22;
-
-// Arrive at barrier `target` (cumulative arrivals expected) and wait for
-// every block; thread 0 of each block arrives after the block's writes.
-__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned target,
-                                             int *err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
-    // once any barrier has expired no later one waits, so a launch spends
-    // at most one bounded wait before it drains
-    const bool expired = err && *(volatile int *)err != 0;
-    for (long long i = 0; !expired; i++) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
-      if (v >= target) break;
-      if (i > kBarrierPolls) {
-        if (err) atomicExch(err, 1);
-        break;
-      }
-      __nanosleep(64);
-    }
-  }
-  __syncthreads();
-}
-
 template <typename R, int NG>
 __global__ void __launch_bounds__(128)
     stage_curvi_multi_kernel(Geo g, StageArgs4<R> sa, int steps, unsigned *count) {

@@ -30,7 +30,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
-           "nrr_get_launch",
+           "nrr_get_launch", "nrr_selftest_wait_expiry",
            "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
         "nrr_get_launch": [V, I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                            C.POINTER(C.c_int)],
         "nrr_set_pdl": [V, I],
+        "nrr_selftest_wait_expiry": [I, V, C.POINTER(C.c_int)],
         "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int),
                          C.POINTER(C.c_int), D],
         "nrr_batch_create": [I, C.POINTER(GridDesc), C.POINTER(C.c_int),
@@ -526,3 +527,14 @@ class Surrogate:
         _check(lib().nrr_surrogate_get_params(
             self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
         return p
+
+
+def selftest_wait_expiry(which: int) -> bool:
+    """Run one bounded wait on something that never happens (0: an mbarrier
+    phase, 1: a grid barrier); True if it expired and recorded its error."""
+    import torch
+    out = C.c_int()
+    _check(lib().nrr_selftest_wait_expiry(int(which),
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          C.byref(out)))
+    return bool(out.value)

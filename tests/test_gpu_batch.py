@@ -152,3 +152,20 @@ def test_tensor_copy_variant_refused_for_unaligned_grids(gpu):
         b.set_launch(1, 4, "fp32_dc")
     b.set_launch(0, 4, "fp32_dc")
     b.close()
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_expires_and_context_survives(gpu, which):
+    """A tensor-copy wait (0) and a grid barrier (1) on events that never
+    happen give up, record their error and return; the next solve on the
+    same context still converges."""
+    import time
+    t0 = time.perf_counter()
+    assert nrr.selftest_wait_expiry(which)
+    assert time.perf_counter() - t0 < 60.0
+    desc, punc = W.small_equal_mass()
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    r = g.relax(mode="fp64", tol=1e-10)
+    assert r["status"] == 0 and r["norm"] < 1e-10
+    g.close()
