@@ -518,7 +518,11 @@ def run_profile_gemm(args):
     from paper_2501_14030_gb300 import nrr
     torch.cuda.set_device(0)
     g = torch.Generator(device="cuda").manual_seed(0)
-    for (M, N, K) in [(256, 16384, 512), (16384, 512, 256), (8192, 16384, 512)]:
+    # network shapes at batch 256 (forward of the 512 -> 16384 layer, its
+    # input gradient with K = 16384, its weight gradient, a hidden layer) and
+    # a large M for the tensor-core rate
+    for (M, N, K) in [(256, 16384, 512), (256, 512, 16384), (16384, 512, 256),
+                      (256, 512, 512), (8192, 16384, 512)]:
         A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
         D = torch.empty((M, N), dtype=torch.float32, device="cuda")

@@ -26,7 +26,11 @@ namespace nrr {
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
+// Pipeline depth: three 128 x 64 + BN x 64 stages leave room for two CTAs
+// per SM (one CTA's epilogue overlaps another's main loop), and the freed
+// stages hold the accumulator tile for the coalesced store.
+constexpr int STAGES = 3;
 constexpr long long kWaitLimit = 1ll << 18;  // try_wait polls (about a second)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -95,11 +99,13 @@ __device__ __forceinline__ uint32_t mma_idesc() {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap map_a,
                         const __grid_constant__ CUtensorMap map_b, float *D,
                         int M, int N, int K, int ldd, int *err) {
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  static_assert((size_t)BM * (BN + 4) * 4 <= (size_t)STAGES * (A_BYTES + B_BYTES),
+                "the epilogue's row staging must fit in the pipeline buffers");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -185,12 +191,17 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // Epilogue: accumulator rows 32*warp + lane, BN columns.
+  // Epilogue: accumulator rows 32*warp + lane, BN columns.  Each warp moves
+  // its 32 rows from tensor memory into the (now idle) pipeline buffers, one
+  // row per thread, then stores them row by row with the whole warp, so that
+  // every global store is a contiguous run of the output row.  Row stride
+  // BN + 4 floats keeps both shared-memory passes free of bank conflicts.
   const bool ready = mbar_wait(done, 0, err, 3);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: decide per warp, not per thread
   if (__all_sync(0xffffffffu, ready && *((volatile int *)err) == 0)) {
-    const int row = m0 + 32 * warp + lane;
+    constexpr int LDS = BN + 4;
+    float *stage = reinterpret_cast<float *>(smem) + (size_t)32 * warp * LDS;
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
     for (int c = 0; c < BN; c += 16) {
@@ -204,14 +215,21 @@ __global__ void __launch_bounds__(128, 1)
             "=r"(r[15])
           : "r"(taddr + (uint32_t)c));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        float4 *dst = reinterpret_cast<float4 *>(D + (int64_t)row * ldd + n0 + c);
+      float4 *srow = reinterpret_cast<float4 *>(stage + lane * LDS + c);
 #pragma unroll
-        for (int q = 0; q < 4; q++)
-          dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                               __uint_as_float(r[4 * q + 2]),
-                               __uint_as_float(r[4 * q + 3]));
-      }
+      for (int q = 0; q < 4; q++)
+        srow[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                              __uint_as_float(r[4 * q + 2]),
+                              __uint_as_float(r[4 * q + 3]));
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32; rr++) {
+      const int row = m0 + 32 * warp + rr;
+      if (row >= M) break;
+      const float4 *src = reinterpret_cast<const float4 *>(stage + rr * LDS);
+      float4 *dst = reinterpret_cast<float4 *>(D + (int64_t)row * ldd + n0);
+#pragma unroll
+      for (int c4 = lane; c4 < BN / 4; c4 += 32) dst[c4] = src[c4];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
