@@ -257,6 +257,20 @@ nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
  * Errors: NRR_ERR_INVALID_ARG for a null grid or on not 0/1. */
 nrr_status nrr_set_pdl(nrr_grid *g, int on);
 
+/* The autotuner's cache as a file (JSON): every launch shape chosen in this
+ * process by nrr_autotune (or loaded), keyed by coordinates, interior sizes,
+ * FD order and precision.  nrr_autotune_save writes it to `path`;
+ * nrr_autotune_load adds the entries of such a file to the cache, so that
+ * grids created afterwards with a matching key start with that shape without
+ * tuning (grids that exist already keep theirs); nrr_autotune_clear empties
+ * the cache.  Host only; no GPU work.
+ * Errors: NRR_ERR_INVALID_ARG (null path; an unreadable, malformed or
+ * invalid file, in which case nothing is added), NRR_ERR_STATE (the file
+ * cannot be written). */
+nrr_status nrr_autotune_save(const char *path);
+nrr_status nrr_autotune_load(const char *path);
+nrr_status nrr_autotune_clear(void);
+
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in

@@ -133,6 +133,56 @@ LaunchCfg tuned_or_default(const Geo &g, int prec) {
   return it != g_tuned.end() ? it->second : LaunchCfg{};
 }
 
+// Whether a launch shape is one nrr_set_launch accepts.
+bool valid_shape(const LaunchCfg &c) {
+  const bool zc_ok =
+      c.variant == 0   ? (c.zc == 1 || c.zc == 2 || c.zc == 4)
+      : (c.variant == 1 || c.variant == 3)
+          ? (c.zc == 2 || c.zc == 4 || c.zc == 8 || c.zc == 16)
+          : (c.variant == 2 || c.variant == 4) && c.zc == 1;
+  return c.variant >= 0 && c.variant <= 4 && zc_ok &&
+         (c.block == 64 || c.block == 128 || c.block == 256) &&
+         (c.pdl == 0 || c.pdl == 1);
+}
+
+// Integer value of "key": in [b, e) of a JSON object; false if absent.
+bool json_int(const char *b, const char *e, const char *key, int *out) {
+  char pat[64];
+  snprintf(pat, sizeof pat, "\"%s\"", key);
+  const size_t n = strlen(pat);
+  for (const char *p = b; p + n <= e; p++) {
+    if (strncmp(p, pat, n) != 0) continue;
+    p += n;
+    while (p < e && (*p == ' ' || *p == ':' || *p == '\t' || *p == '\n' || *p == '[')) p++;
+    char *end = nullptr;
+    long v = strtol(p, &end, 10);
+    if (end == p || end > e) return false;
+    *out = (int)v;
+    return true;
+  }
+  return false;
+}
+
+// The three integers of "n": [a, b, c].
+bool json_int3(const char *b, const char *e, const char *key, int out[3]) {
+  char pat[64];
+  snprintf(pat, sizeof pat, "\"%s\"", key);
+  const char *p = strstr(b, pat);
+  if (!p || p >= e) return false;
+  p = strchr(p, '[');
+  if (!p || p >= e) return false;
+  p++;
+  for (int i = 0; i < 3; i++) {
+    char *end = nullptr;
+    long v = strtol(p, &end, 10);
+    if (end == p || end > e) return false;
+    out[i] = (int)v;
+    p = end;
+    while (p < e && (*p == ',' || *p == ' ')) p++;
+  }
+  return true;
+}
+
 template <typename T>
 nrr_status dev_alloc(nrr_grid *g, T **p, size_t count) {
   void *ptr = nullptr;
@@ -943,6 +993,81 @@ nrr_status nrr_set_pdl(nrr_grid *g, int on) {
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
+  return NRR_OK;
+}
+
+nrr_status nrr_autotune_save(const char *path) {
+  if (!path) return fail(NRR_ERR_INVALID_ARG, "null path");
+  std::map<TuneKey, LaunchCfg> copy;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    copy = g_tuned;
+  }
+  FILE *f = fopen(path, "w");
+  if (!f) return fail(NRR_ERR_STATE, "cannot write %s", path);
+  fprintf(f, "{\"nrr_autotune\": 1, \"entries\": [");
+  bool first = true;
+  for (const auto &kv : copy) {
+    const TuneKey &k = kv.first;
+    const LaunchCfg &c = kv.second;
+    fprintf(f,
+            "%s\n  {\"coord\": %d, \"n\": [%d, %d, %d], \"ng\": %d, "
+            "\"fp32\": %d, \"variant\": %d, \"zc\": %d, \"block\": %d, "
+            "\"pdl\": %d}",
+            first ? "" : ",", k.coord, k.n0, k.n1, k.n2, k.ng, k.prec, c.variant,
+            c.zc, c.block, c.pdl);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  const bool ok = fclose(f) == 0;
+  return ok ? NRR_OK : fail(NRR_ERR_STATE, "cannot write %s", path);
+}
+
+nrr_status nrr_autotune_load(const char *path) {
+  if (!path) return fail(NRR_ERR_INVALID_ARG, "null path");
+  FILE *f = fopen(path, "r");
+  if (!f) return fail(NRR_ERR_INVALID_ARG, "cannot read %s", path);
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+  fclose(f);
+  if (text.find("\"nrr_autotune\"") == std::string::npos)
+    return fail(NRR_ERR_INVALID_ARG, "%s is not an autotuner file", path);
+  // entries are the objects after the "entries" key
+  size_t pos = text.find("\"entries\"");
+  if (pos == std::string::npos) return fail(NRR_ERR_INVALID_ARG, "no entries in %s", path);
+  std::map<TuneKey, LaunchCfg> add;
+  while ((pos = text.find('{', pos + 1)) != std::string::npos) {
+    const size_t end = text.find('}', pos);
+    if (end == std::string::npos) return fail(NRR_ERR_INVALID_ARG, "unterminated entry");
+    const char *b = text.c_str() + pos, *e = text.c_str() + end;
+    TuneKey k{};
+    LaunchCfg c{};
+    int n[3];
+    if (!json_int(b, e, "coord", &k.coord) || !json_int3(b, e, "n", n) ||
+        !json_int(b, e, "ng", &k.ng) || !json_int(b, e, "fp32", &k.prec) ||
+        !json_int(b, e, "variant", &c.variant) || !json_int(b, e, "zc", &c.zc) ||
+        !json_int(b, e, "block", &c.block) || !json_int(b, e, "pdl", &c.pdl))
+      return fail(NRR_ERR_INVALID_ARG, "incomplete entry at byte %zu of %s", pos, path);
+    k.n0 = n[0];
+    k.n1 = n[1];
+    k.n2 = n[2];
+    if (k.coord < NRR_SINHSYMTP || k.coord > NRR_SINHSPHERICAL || k.ng < 1 ||
+        k.ng > 6 || (k.prec != 0 && k.prec != 1) || k.n0 < 1 || k.n1 < 1 ||
+        k.n2 < 1 || !valid_shape(c))
+      return fail(NRR_ERR_INVALID_ARG, "invalid entry at byte %zu of %s", pos, path);
+    add[k] = c;
+    pos = end;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto &kv : add) g_tuned[kv.first] = kv.second;
+  return NRR_OK;
+}
+
+nrr_status nrr_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned.clear();
   return NRR_OK;
 }
 

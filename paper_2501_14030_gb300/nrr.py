@@ -30,7 +30,8 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_get_state", "nrr_set_state", "nrr_rhs", "nrr_step",
            "nrr_timestep", "nrr_image_map", "nrr_profile_stages",
            "nrr_kernel_launches", "nrr_residual_noalloc", "nrr_set_launch",
-           "nrr_get_launch", "nrr_selftest_wait_expiry",
+           "nrr_get_launch", "nrr_selftest_wait_expiry", "nrr_autotune_save",
+           "nrr_autotune_load", "nrr_autotune_clear",
            "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
@@ -111,6 +112,9 @@ def lib() -> C.CDLL:
                            C.POINTER(C.c_int)],
         "nrr_set_pdl": [V, I],
         "nrr_selftest_wait_expiry": [I, V, C.POINTER(C.c_int)],
+        "nrr_autotune_save": [C.c_char_p],
+        "nrr_autotune_load": [C.c_char_p],
+        "nrr_autotune_clear": [],
         "nrr_autotune": [V, I, C.c_int64, C.POINTER(C.c_int),
                          C.POINTER(C.c_int), D],
         "nrr_batch_create": [I, C.POINTER(GridDesc), C.POINTER(C.c_int),
@@ -538,3 +542,17 @@ def selftest_wait_expiry(which: int) -> bool:
                                           C.c_void_p(torch.cuda.current_stream().cuda_stream),
                                           C.byref(out)))
     return bool(out.value)
+
+
+def autotune_save(path: str) -> None:
+    """Write the autotuner's cache (launch shapes by grid key) to a JSON file."""
+    _check(lib().nrr_autotune_save(str(path).encode()))
+
+
+def autotune_load(path: str) -> None:
+    """Add a saved autotuner cache; later grids with matching keys use it."""
+    _check(lib().nrr_autotune_load(str(path).encode()))
+
+
+def autotune_clear() -> None:
+    _check(lib().nrr_autotune_clear())

@@ -323,3 +323,22 @@ def test_cartesian_tensor_copy_variant_full_size(gpu):
         assert rel_err(ku, ku_o, m) <= 1e-12, (region, rel_err(ku, ku_o, m))
         assert rel_err(kv, kv_o, m) <= 1e-12, (region, rel_err(kv, kv_o, m))
     g.close()
+
+
+def test_loaded_autotune_entry_sets_new_grids_shape(gpu, tmp_path):
+    """A grid created after loading a cache entry for its key starts with
+    that shape; grids of other keys keep the default."""
+    import json
+    nrr.autotune_clear()
+    (tmp_path / "t.json").write_text(json.dumps({"nrr_autotune": 1, "entries": [
+        {"coord": 0, "n": [32, 16, 2], "ng": 2, "fp32": 0, "variant": 1, "zc": 2,
+         "block": 128, "pdl": 1}]}))
+    nrr.autotune_load(str(tmp_path / "t.json"))
+    desc, punc = W.small_equal_mass()
+    g = nrr.Grid(desc)
+    assert g.get_launch("fp64") == (1, 2, 128)
+    g.close()
+    g2 = nrr.Grid(W.grid_desc("sinhsymtp", (36, 16, 2), 4))
+    assert g2.get_launch("fp64")[0] == 0
+    g2.close()
+    nrr.autotune_clear()
