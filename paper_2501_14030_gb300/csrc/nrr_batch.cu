@@ -158,9 +158,10 @@ __device__ __forceinline__ StageArgs<float> batch_stage_args<float>(
 // --- kernels ----------------------------------------------------------------
 constexpr int kTileY = 4;
 constexpr int kTmaPZ = 2;  // phi planes per ring slot (tensor-copy variant)
-// ring slots per block: the FP64 ring of 3 slots would exceed 48 KB
+// ring slots per block: two (one slot pair in flight while one is computed);
+// a deeper ring takes shared memory that L1 needs (measured slower)
 template <typename R>
-__host__ __device__ constexpr int tma_slots() { return sizeof(R) == 4 ? 3 : 2; }
+__host__ __device__ constexpr int tma_slots() { return 2; }
 // i1 rows of the outer shell per shell block (NG columns each)
 template <int NG>
 __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
@@ -174,7 +175,7 @@ __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 // aligned grids), which records an expired copy wait in *err; VAR 2: one
 // thread per column of evolved points and zc planes (stage_curvi_item).
 template <typename R, int NG, int KIND, int VAR>
-__global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 1)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
                        const int *__restrict__ active, int stage, int mode, int zc,
                        int *err) {

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // Cartesian stage fed by tensor copies (variant 1; order 8, n0 % 32 == 0,
 // n1 % 4 == 0, n2 and the plane chunk even).  Interior blocks: a 32 x 4
-// column tile streams its chunk of planes, two per slot, through a 3-slot
+// column tile streams its chunk of planes, two per slot, through a 2-slot
 // shared-memory ring (one 40 x 12 x 2 box of u with its halo, one 32 x 4 x 2
 // box per operand array, completing on the slot's mbarrier; thread 0 issues
 // two slots ahead).  Cartesian ghosts are all outer ghosts, stored and
@@ -177,7 +177,7 @@ using CartMaps = FieldSrc;  // su box (40, 12, 2), operand boxes (32, 4, 2)
 
 constexpr int kCartTY = 4, kCartPZ = 2;
 template <typename R>
-__host__ __device__ constexpr int cart_slots() { return sizeof(R) == 4 ? 3 : 2; }
+__host__ __device__ constexpr int cart_slots() { return 2; }
 
 __host__ __device__ __forceinline__ int64_t cart_shell_points(const Geo &g) {
   const int ng = g.ng;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void cart_shell_point(const Geo &g, const StageArgs<R
 }
 
 template <typename R, int NG, int KIND>
-__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
     stage_cart_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ CartMaps maps,
                           CartShellC<R> sc, int zc) {
   constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
 // parameter); the blocks after them evolve the outer shell, 32 rows of i1
 // and the NG shell columns each.
 template <typename R, int NG, int KIND>
-__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
     stage_curvi_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ FieldSrc maps,
                            int zc) {
   constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
