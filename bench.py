@@ -311,6 +311,10 @@ def run_ours(args):
                   max_iters=iters // max(1, args.steps), raise_on_error=False)
 
     batch = None if args.no_batch else run_batch(args, nrr, W, torch)
+    # warm start from the learned surrogate, compact: 2048 training solves,
+    # 800 training steps, 128 held-out solves cold vs warm (the full
+    # 8192 / 1024 pipeline is `--surrogate`)
+    warm = None if args.no_surrogate else surrogate_pipeline(nrr, W, torch, 2048, 128, 100)
 
     line = None
     if rank == 0:
@@ -350,6 +354,7 @@ def run_ours(args):
                 "fp32_stage_us_per_launch": ms32 * 1e3,
                 "fp32_stage_GBps_algorithmic": bytes32 / (ms32 * 1e-3) / 1e9},
             "batch_512": batch,
+            "surrogate_warm_start": warm,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -422,16 +427,11 @@ def run_batch(args, nrr, W, torch):
             "grids": "SinhSymTP N0 in {64,96,128}, N1 in {32,64,96,128}, N2 in {8,16}, order 8"}
 
 
-def run_surrogate(args):
-    """Surrogate pipeline: 8192 solver-generated coarse solutions (64x32x8),
-    device training of the 12 -> 512x4 -> 16384 network, then 1024 held-out
-    solves at 128x128x16 started cold and from the network's prediction."""
+def surrogate_pipeline(nrr, W, torch, n_train: int, n_held: int, epochs: int):
+    """Solver-generated coarse solutions (64x32x8), device training of the
+    12 -> 512x4 -> 16384 network, then `n_held` held-out solves at 128x128x16
+    started cold and from the network's prediction; returns a summary dict."""
     import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2501_14030_gb300 import nrr, workloads as W
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -444,7 +444,6 @@ def run_surrogate(args):
         return out, e0.elapsed_time(e1) / 1e3
 
     coarse_n, fine_n = (64, 32, 8), (128, 128, 16)
-    n_train, n_held = args.surrogate_train, args.surrogate_held
     train = W.batch_parameters(n_train, seed=1)
     cdesc = [W.grid_desc("sinhsymtp", coarse_n, 8, bscale=p["d"] / 2) for p in train]
     b = nrr.Batch(cdesc, [p["punctures"] for p in train])
@@ -458,7 +457,7 @@ def run_surrogate(args):
     dims = W.mlp_dims(n_out=n_out)
     net = nrr.Surrogate(dims, W.mlp_init_params(dims, seed=3), batch=256)
     net.fit_scaling(Y)
-    steps = args.surrogate_epochs * (n_train // 256)
+    steps = epochs * (n_train // 256)
     order = torch.from_numpy(W.minibatch_order(n_train, 256, steps, seed=4)).cuda()
     losses, t_train = timed(lambda: net.train(X, Y, order, steps, lr=1e-3))
     flops_step = 6 * 256 * sum(a * b_ for a, b_ in zip(dims[:-1], dims[1:]))
@@ -489,7 +488,7 @@ def run_surrogate(args):
     warm.close()
     it_c = np.array([r["iters"] for r in per_c])
     it_w = np.array([r["iters"] for r in per_w])
-    line = {"surrogate": {
+    return {
         "train_solves": n_train, "train_grid": "SinhSymTP 64x32x8, order 8",
         "train_data_seconds": t_gen,
         "train_converged": int(sum(r["status"] == 0 for r in per)),
@@ -503,8 +502,20 @@ def run_surrogate(args):
                  "status": tot_w["status"], "mean_rk4_steps": float(it_w.mean()),
                  "max_rk4_steps": int(it_w.max())},
         "step_reduction": float(1.0 - it_w.mean() / it_c.mean()),
-        "time_reduction": float(1.0 - (t_warm + t_pred) / t_cold)}}
-    print(json.dumps(line), flush=True)
+        "time_reduction": float(1.0 - (t_warm + t_pred) / t_cold)}
+
+
+def run_surrogate(args):
+    """The full surrogate pipeline: 8192 training solves (default), 1024
+    held-out solves."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    out = surrogate_pipeline(nrr, W, torch, args.surrogate_train,
+                             args.surrogate_held, args.surrogate_epochs)
+    print(json.dumps({"surrogate": out}), flush=True)
     return 0
 
 
@@ -777,6 +788,8 @@ def main():
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="run only a short batch of this many 128x128x16 "
                          "solves (profiler captures)")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the compact surrogate warm-start section")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-solve batch in the default run")
     args = ap.parse_args()
