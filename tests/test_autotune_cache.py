@@ -8,6 +8,14 @@ import pytest
 
 from paper_2501_14030_gb300 import nrr
 
+
+@pytest.fixture(autouse=True, scope="module")
+def _built_library():
+    from paper_2501_14030_gb300 import build
+    build.build()
+    nrr.lib()
+
+
 ENTRIES = [
     {"coord": 0, "n": [128, 128, 16], "ng": 4, "fp32": 0, "variant": 0, "zc": 1,
      "block": 64, "pdl": 1},
