@@ -169,3 +169,29 @@ def test_bounded_wait_expires_and_context_survives(gpu, which):
     r = g.relax(mode="fp64", tol=1e-10)
     assert r["status"] == 0 and r["norm"] < 1e-10
     g.close()
+
+
+def test_full_sweep_sampled_solves_checked_by_oracle(gpu):
+    """The 512-solve parameter sweep at full size, in the launch shape the
+    bench times (autotuned, defect correction, one graph launch): every solve
+    converges, and the oracle's residual of eight sampled solves (the largest
+    and smallest grids among them) is below the threshold too."""
+    params = W.batch_parameters(512, 20250124)
+    descs = [p["desc"] for p in params]
+    b = nrr.Batch(descs, [p["punctures"] for p in params])
+    b.autotune("fp32_dc", 3)
+    per, tot = b.relax(mode="fp32_dc", tol=1e-10)
+    assert tot["status"] == 0
+    assert all(r["status"] == 0 and r["norm"] < 1e-10 for r in per)
+    size = [int(np.prod(d["n"])) for d in descs]
+    order = np.argsort(size)
+    rng = np.random.default_rng(9)
+    pick = sorted({int(order[0]), int(order[-1]),
+                   *map(int, rng.choice(512, size=6, replace=False))})
+    for i in pick:
+        ub = np.zeros(b.shapes[i])
+        b.get_u(i, ub)
+        og = oracle_grid(descs[i])
+        alpha, beta = og.source(params[i]["punctures"])
+        assert og.norm(og.residual(alpha, beta, ub)) < 1.02e-10, (i, descs[i]["n"])
+    b.close()
