@@ -371,12 +371,6 @@ namespace dev {
 // (tile_x == number of interior tiles) evolve the outer shell with the
 // radiation condition.
 // ---------------------------------------------------------------------------
-template <int TY, int NG>
-struct TileDims {
-  static constexpr int W = 32 + 2 * NG;  // staged width (i0)
-  static constexpr int H = TY + 2 * NG;  // staged height (i1)
-};
-
 __host__ __device__ __forceinline__ int tiles_x(const Geo &g) { return (g.n0 + 31) / 32; }
 template <int TY>
 __host__ __device__ __forceinline__ int tiles_y(const Geo &g) { return (g.n1 + TY - 1) / TY; }
