@@ -235,7 +235,13 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * every SM (zc = 1); variant 3 = 32 x 4 tiles whose planes stream through a
  * shared-memory ring filled by tensor (TMA) copies, zc (2, 4, 8 or 16)
  * planes per block, for FD order 8 with n0 % 32 == 0 and n1 % 4 == 0 (other
- * grids run variant 1 instead).  Cartesian grids: variant 1 = the tensor-copy
+ * grids run variant 1 instead); variant 4 = the RK4 steps between two norm
+ * checks in one cooperative launch of a column kernel with grid barriers
+ * between stages (zc = 1); variant 5 = the same multi-stage launch over
+ * variant 3's tensor-copy tiles, zc (2, 4, 8 or 16) planes per tile, under
+ * variant 3's conditions (other grids run variant 4 instead).  Single stage
+ * launches of variants 4 and 5 run variants 0 and 3.  Cartesian grids:
+ * variant 1 = the tensor-copy
  * kernel under the same conditions, any other variant the column kernel
  * (zc planes per thread, `block` threads).  Results do not depend on the
  * shape beyond rounding order.
@@ -275,7 +281,8 @@ nrr_status nrr_autotune_clear(void);
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in
  * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
- * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16} -- skips
+ * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16}, variant 4,
+ * variant 5 with zc in {4, 8, 16} -- skips
  * shapes the grid cannot launch, keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the

@@ -137,10 +137,10 @@ LaunchCfg tuned_or_default(const Geo &g, int prec) {
 bool valid_shape(const LaunchCfg &c) {
   const bool zc_ok =
       c.variant == 0   ? (c.zc == 1 || c.zc == 2 || c.zc == 4)
-      : (c.variant == 1 || c.variant == 3)
+      : (c.variant == 1 || c.variant == 3 || c.variant == 5)
           ? (c.zc == 2 || c.zc == 4 || c.zc == 8 || c.zc == 16)
           : (c.variant == 2 || c.variant == 4) && c.zc == 1;
-  return c.variant >= 0 && c.variant <= 4 && zc_ok &&
+  return c.variant >= 0 && c.variant <= 5 && zc_ok &&
          (c.block == 64 || c.block == 128 || c.block == 256) &&
          (c.pdl == 0 || c.pdl == 1);
 }
@@ -329,7 +329,7 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
                       int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
   const LaunchCfg &cfg = g->stage_cfg[sizeof(R) == 4];
-  if (cfg.variant == 4 && g->geo.coord != CARTESIAN) {
+  if ((cfg.variant == 4 || cfg.variant == 5) && g->geo.coord != CARTESIAN) {
     // all steps in one cooperative launch (grid barriers between stages)
     StageArgs<R> sa[4];
     for (int k = 0; k < 4; k++) sa[k] = stage_args<R>(g, f, c, k, dt, eta);
@@ -954,12 +954,14 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block)
     return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (variant < 0 || variant > 4)
+  if (variant < 0 || variant > 5)
     return fail(NRR_ERR_INVALID_ARG,
                 "variant must be 0 (column), 1 (tiled), 2 (persistent column), "
-                "3 (tensor-copy tiled) or 4 (multi-stage)");
+                "3 (tensor-copy tiled), 4 (multi-stage) or 5 (multi-stage "
+                "tensor-copy)");
   if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
-      ((variant == 1 || variant == 3) && zc != 2 && zc != 4 && zc != 8 && zc != 16) ||
+      ((variant == 1 || variant == 3 || variant == 5) && zc != 2 && zc != 4 &&
+       zc != 8 && zc != 16) ||
       ((variant == 2 || variant == 4) && zc != 1))
     return fail(NRR_ERR_INVALID_ARG,
                 "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled, tensor-copy), "
@@ -1099,10 +1101,11 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[15] = {{128, 1, 0}, {64, 1, 0}, {256, 1, 0}, {128, 2, 0},
-                               {64, 2, 0}, {128, 4, 0}, {128, 2, 1}, {128, 4, 1},
-                               {128, 8, 1}, {128, 16, 1}, {128, 1, 2}, {128, 4, 3},
-                               {128, 8, 3}, {128, 16, 3}, {128, 1, 4}};
+  const LaunchCfg cands[18] = {{128, 1, 0},  {64, 1, 0},  {256, 1, 0}, {128, 2, 0},
+                               {64, 2, 0},   {128, 4, 0}, {128, 2, 1}, {128, 4, 1},
+                               {128, 8, 1},  {128, 16, 1}, {128, 1, 2}, {128, 4, 3},
+                               {128, 8, 3},  {128, 16, 3}, {128, 1, 4}, {128, 4, 5},
+                               {128, 8, 5},  {128, 16, 5}};
   for (const LaunchCfg &cand0 : cands) {
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;

@@ -61,6 +61,19 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
   return false;
 }
 
+// Ends an mbarrier object's life so that its word can be initialised again
+// (a block that runs several tiles in one launch).
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(shared_addr(bar)) : "memory");
+}
+
+// Orders this thread's generic-proxy accesses of all state spaces against
+// its async-proxy ones: global stores of one stage before the tensor copies
+// that later read them in the same launch.
+__device__ __forceinline__ void fence_proxy_async_all() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+
 // Orders this thread's earlier generic-proxy shared-memory accesses before
 // its later async-proxy ones (a buffer read by the threads is refilled).
 __device__ __forceinline__ void fence_proxy_async_smem() {

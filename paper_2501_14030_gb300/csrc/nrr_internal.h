@@ -56,7 +56,8 @@ struct LaunchCfg {
                     // or per block chunk (variant 1)
   int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel,
                     // 2 persistent column kernel, 3 tensor-copy tiled
-                    // kernel, 4 multi-stage cooperative kernel; Cartesian
+                    // kernel, 4 multi-stage cooperative kernel, 5 its
+                    // tensor-copy tiled form; Cartesian
                     // stages: 0 column kernel, 1 tensor-copy tiled kernel
   int pdl = 1;      // stage kernels: programmatic dependent launch (the next
                     // stage's blocks start while this one drains)
@@ -123,8 +124,10 @@ void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st);
 
 // `steps` RK4 steps (stage arguments FIRST, MID, MID, LAST) in one
-// cooperative launch of the multi-stage curvilinear kernel; `count` is a
-// device word for its grid barriers (reset by this call).
+// cooperative launch of a multi-stage curvilinear kernel (variant 5: the
+// tensor-copy tiled form where the grid allows it, else variant 4's
+// column form); `count` is a device word for its grid barriers (reset by
+// this call).
 template <typename R>
 cudaError_t launch_stage_steps(const Geo &g, const StageArgs<R> (&sa)[4], int steps,
                                unsigned *count, const LaunchCfg &cfg,

@@ -515,6 +515,77 @@ cudaError_t launch_multi_ng(const Geo &g, const StageArgs4<R> &sa, int steps,
   return cudaLaunchKernelEx(&c, k, g, sa, steps, count);
 }
 
+// Multi-stage tensor-copy kernel (variant 5; the grids of variant 3): the
+// cooperative multi-stage launch of variant 4 over variant 3's work items --
+// interior tiles staged through tensor copies, then shell blocks -- so that
+// a block's stencil reads come from shared memory instead of a cache that
+// each grid barrier leaves cold.  Tensor copies read global memory through
+// the async proxy: every thread fences its stores of a stage before the
+// barrier and the issuing thread fences again after it.  State read by
+// plain loads (phi queue, image cells, shell) goes through L2.
+struct FieldSrc4 {
+  FieldSrc s[4];  // FIRST, MID, MID, LAST
+};
+
+template <typename R, int NG, int KIND>
+__device__ __forceinline__ void multi_tma_stage(const Geo &g, const StageArgs<R> &a,
+                                                const FieldSrc &maps, int zc,
+                                                TmaSlot<R, NG, kCartTY, kCartPZ> *ring,
+                                                uint64_t *full, bool &inited) {
+  constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
+  constexpr int rows = 32 * TY / NG;
+  const int ntx = g.n0 / 32, nty = g.n1 / TY, nch = chunks_z(g, zc);
+  const int nint = ntx * nty * nch;
+  const int nsb = (g.n1 + rows - 1) / rows;
+  const int nitems = nint + nsb * nch;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // after an expired wait the remaining items are skipped (uniformly)
+    if (__syncthreads_or(threadIdx.x == 0 && *(volatile int *)a.err != 0)) return;
+    if (it < nint) {
+      if (inited && threadIdx.x == 0)
+        for (int k = 0; k < NS; k++) mbar_inval(&full[k]);
+      inited = true;
+      stage_tma_block<R, NG, KIND, TY, NS, PZ, FieldSrc, true>(
+          g, a, it % ntx, (it / ntx) % nty, it / (ntx * nty), zc, maps, ring, full,
+          a.err);
+    } else {
+      const int sidx = it - nint, chunk = sidx / nsb;
+      const int row = threadIdx.x / NG, lane = threadIdx.x - row * NG;
+      const int z0 = NG + chunk * zc;
+      if (row < rows)
+        stage_shell_rows<R, NG, KIND, true>(g, a, lane, NG + (sidx % nsb) * rows + row,
+                                            z0, min(z0 + zc, NG + g.n2));
+    }
+  }
+}
+
+template <typename R, int NG>
+__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 4 : 1)
+    stage_curvi_multi_tma_kernel(Geo g, StageArgs4<R> sa,
+                                 const __grid_constant__ FieldSrc4 maps, int zc,
+                                 int steps, unsigned *count) {
+  __shared__ __align__(128) TmaSlot<R, NG, kCartTY, kCartPZ> ring[cart_slots<R>()];
+  __shared__ __align__(8) uint64_t full[cart_slots<R>()];
+  pdl_trigger();
+  bool inited = false;
+  unsigned target = 0;
+  for (int s = 0; s < steps; s++) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (k == 0)
+        multi_tma_stage<R, NG, STAGE_FIRST>(g, sa.s[0], maps.s[0], zc, ring, full, inited);
+      else if (k == 3)
+        multi_tma_stage<R, NG, STAGE_LAST>(g, sa.s[3], maps.s[3], zc, ring, full, inited);
+      else
+        multi_tma_stage<R, NG, STAGE_MID>(g, sa.s[k], maps.s[k], zc, ring, full, inited);
+      fence_proxy_async_all();
+      target += gridDim.x;
+      grid_barrier(count, target, sa.s[0].err);
+      if (threadIdx.x == 0) fence_proxy_async_all();
+    }
+  }
+}
+
 
 // Residual H at interior points and the block partials of H^2 J, J over
 // r < r_int (the volume-weighted L2 norm of Alg. 1's residual).
@@ -838,6 +909,51 @@ bool launch_cart_tma(const Geo &g, int kind, const StageArgs<R> &a, int zc, int 
   }
 }
 
+// One cooperative launch of the multi-stage tensor-copy kernel; false if
+// the maps cannot be encoded (the caller falls back to variant 4's shape).
+template <typename R, int NG>
+bool launch_multi_tma(const Geo &g, const StageArgs4<R> &sa, int zc, int steps,
+                      unsigned *count, cudaStream_t st, cudaError_t *err) {
+  constexpr int b0 = 32 + 2 * NG, b1 = kCartTY + 2 * NG;
+  FieldSrc4 maps;
+  if (!stage_field_maps<R, NG, STAGE_FIRST>(&maps.s[0], g, sa.s[0], b0, b1) ||
+      !stage_field_maps<R, NG, STAGE_MID>(&maps.s[1], g, sa.s[1], b0, b1) ||
+      !stage_field_maps<R, NG, STAGE_MID>(&maps.s[2], g, sa.s[2], b0, b1) ||
+      !stage_field_maps<R, NG, STAGE_LAST>(&maps.s[3], g, sa.s[3], b0, b1))
+    return false;
+  auto k = stage_curvi_multi_tma_kernel<R, NG>;
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * kCartTY, 0);
+  }
+  if (per_sm < 1) {
+    *err = cudaErrorInvalidConfiguration;
+    return true;
+  }
+  constexpr int rows = 32 * kCartTY / NG;
+  const int nch = chunks_z(g, zc);
+  const int items = (g.n0 / 32) * (g.n1 / kCartTY) * nch + ((g.n1 + rows - 1) / rows) * nch;
+  // as many items per block as the resident grid needs, spread evenly
+  const int ipb = (items + per_sm * sms - 1) / (per_sm * sms);
+  const int blocks = (items + ipb - 1) / ipb;
+  *err = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+  if (*err != cudaSuccess) return true;
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3(blocks);
+  c.blockDim = dim3(32 * kCartTY);
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  c.attrs = at;
+  c.numAttrs = 1;
+  *err = cudaLaunchKernelEx(&c, k, g, sa, maps, zc, steps, count);
+  return true;
+}
+
 template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st) {
@@ -848,6 +964,13 @@ void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
     col.variant = 0;
     col.zc = 1;
     launch_curvi<R, NG>(g, kind, a, col, st);
+    return;
+  }
+  if (cfg.variant == 5) {
+    // single stage launches of the multi-stage tensor-copy shape: variant 3
+    LaunchCfg tc = cfg;
+    tc.variant = 3;
+    launch_curvi<R, NG>(g, kind, a, tc, st);
     return;
   }
   if (cfg.variant == 3) {
@@ -949,6 +1072,10 @@ cudaError_t launch_stage_steps(const Geo &g, const StageArgs<R> (&sa)[4], int st
                                cudaStream_t st) {
   StageArgs4<R> s4;
   for (int k = 0; k < 4; k++) s4.s[k] = sa[k];
+  if (cfg.variant == 5 && g.ng == 4 && curvi_tma_ok(g, cfg.zc)) {
+    cudaError_t e = cudaSuccess;
+    if (launch_multi_tma<R, 4>(g, s4, cfg.zc, steps, count, st, &e)) return e;
+  }
   switch (g.ng) {
     case 2: return launch_multi_ng<R, 2>(g, s4, steps, count, cfg.pdl, st);
     case 4: return launch_multi_ng<R, 4>(g, s4, steps, count, cfg.pdl, st);

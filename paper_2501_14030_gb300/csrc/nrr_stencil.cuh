@@ -379,7 +379,7 @@ __host__ __device__ __forceinline__ int chunks_z(const Geo &g, int zc) { return 
 // Outer-shell rows of the tiled stage kernels: lane tx < NG of a tile row
 // evolves column (n0 + NG + tx, i1) on planes [z0, z1) with the radiation
 // condition df/dt = -c (d_r f + f/r).
-template <typename R, int NG, int KIND>
+template <typename R, int NG, int KIND, bool COH = false>
 __device__ __forceinline__ void stage_shell_rows(const Geo &g, const StageArgs<R> &a,
                                                  int tx, int i1, int z0, int z1) {
   if (tx >= NG || i1 >= g.n1 + NG) return;
@@ -392,15 +392,15 @@ __device__ __forceinline__ void stage_shell_rows(const Geo &g, const StageArgs<R
 #pragma unroll 4
   for (int i2 = z0; i2 < z1; i2++) {
     const int64_t p = col + (int64_t)nc * i2;
-    R u0 = ld(a.su + p), u1 = ld(a.su + p - 1), u2 = ld(a.su + p - 2);
-    R v0 = ld(a.sv + p), v1 = ld(a.sv + p - 1), v2 = ld(a.sv + p - 2);
+    R u0 = lds<COH>(a.su + p), u1 = lds<COH>(a.su + p - 1), u2 = lds<COH>(a.su + p - 2);
+    R v0 = lds<COH>(a.sv + p), v1 = lds<COH>(a.sv + p - 1), v2 = lds<COH>(a.sv + p - 2);
     R ku = -c * fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), rinv * u0);
     R kv = -c * fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), rinv * v0);
     if (linear_mode<R>(a.lin)) {
       ku += ld(a.fu + p);
       kv += ld(a.bc2 + p);
     }
-    stage_epilogue<R, KIND>(a, p, ku, kv);
+    stage_epilogue<R, KIND, COH>(a, p, ku, kv);
   }
 }
 
@@ -620,7 +620,8 @@ struct TmaSlot {
 };
 enum TmaOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
 
-template <typename R, int NG, int KIND, int TY, int NS, int PZ, typename Src>
+template <typename R, int NG, int KIND, int TY, int NS, int PZ, typename Src,
+          bool COH = false>
 __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R> &a,
                                                  int tile_x, int tile_y, int chunk,
                                                  int zc, const Src &src,
@@ -637,7 +638,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
   const int z1 = min(z0 + zc, NG + g.n2);
   const int i1 = NG + tile_y * TY + ty;
   if (tile_x == tiles_x(g)) {
-    stage_shell_rows<R, NG, KIND>(g, a, tx, i1, z0, z1);
+    stage_shell_rows<R, NG, KIND, COH>(g, a, tx, i1, z0, z1);
     return;
   }
   const int nslots = (z1 - z0) / PZ;
@@ -723,11 +724,11 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
   R q[2 * NG + PZ];
 #pragma unroll
   for (int k = 0; k < 2 * NG; k++)
-    q[k + PZ] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
+    q[k + PZ] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
   R nq[PZ];
 #pragma unroll
   for (int j = 0; j < PZ; j++)
-    nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 + NG + j));
+    nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 + NG + j));
   R ireg[PZ][NST];
   auto fetch_images = [&](int pl) {
     if (!has_img) return;
@@ -737,7 +738,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
       const R *bflip = a.su + (int64_t)nc * wrap_plane<NG>(g, pl + j + g.n2 / 2);
 #pragma unroll
       for (int k = 0; k < NST; k++)
-        if (soff[k] >= 0) ireg[j][k] = ld(((flip >> k) & 1u ? bflip : base) + soff[k]);
+        if (soff[k] >= 0) ireg[j][k] = lds<COH>(((flip >> k) & 1u ? bflip : base) + soff[k]);
     }
   };
   fetch_images(z0);
@@ -784,7 +785,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
         fetch_images(i2 + PZ);
 #pragma unroll
         for (int j = 0; j < PZ; j++)
-          nq[j] = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
+          nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
       }
 #pragma unroll
       for (int j = 0; j < PZ; j++) {

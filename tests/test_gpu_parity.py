@@ -249,13 +249,31 @@ def test_defect_correction_full_size_matches_fp64(gpu):
     assert rel_err(udc, u64) <= 1e-9
 
 
+def test_multi_stage_tensor_copy_full_size_solves(gpu):
+    """128x128x16 with the multi-stage tensor-copy launch in both precisions:
+    the FP64 and the defect-correction solves reach the tolerance, confirmed
+    by the oracle's residual, in the FP64 solve's number of steps."""
+    desc, punc, og, alpha, beta, g = _setup("sinh_128x128x16_o8")
+    g.set_launch(2, "fp64", 5)
+    g.set_launch(4, "fp32", 5)
+    u = np.zeros(og.shape)
+    r64 = g.relax(mode="fp64", tol=1e-10, check_every=50)
+    g.get_state(u)
+    assert r64["status"] == 0 and og.norm(og.residual(alpha, beta, u)) < 1.02e-10
+    rdc = g.relax(mode="fp32_dc", tol=1e-10, check_every=50)
+    g.get_state(u)
+    assert rdc["status"] == 0 and abs(rdc["iters"] - r64["iters"]) <= 100
+    assert og.norm(og.residual(alpha, beta, u)) < 1.02e-10
+
+
 # ------------------------------- stage-kernel variants against the oracle
 # Every launch shape must reproduce the oracle; the parity tests above run
 # the default shape.  Cartesian variant 1 is the tensor-copy kernel (order 8,
 # n0 % 32 == 0, n1 % 4 == 0, even n2); curvilinear variants 1 and 2 are the
 # tiled and persistent kernels, variant 3 the tensor-copy tiled kernel and
-# variant 4 the multi-stage cooperative kernel (RK4 steps only; single RHS
-# evaluations use the column kernel).
+# variant 4 the multi-stage cooperative kernel and variant 5 its
+# tensor-copy tiled form (RK4 steps only; single RHS evaluations use the
+# column and the tensor-copy kernels).
 VARIANT_CASES = {
     "cart_64x20x24_o8": (W.grid_desc("cartesian", (64, 20, 24), 8, xmax=32.0), Q4),
     "sinh_64x20x8_o8": (W.grid_desc("sinhsymtp", (64, 20, 8), 8), Q4),
@@ -266,10 +284,11 @@ VARIANT_CASES = {
 
 @pytest.mark.parametrize("name", list(VARIANT_CASES))
 @pytest.mark.parametrize("variant,zc", [(0, 1), (1, 2), (1, 4), (1, 16), (2, 1),
-                                        (3, 2), (3, 4), (3, 16), (4, 1)])
+                                        (3, 2), (3, 4), (3, 16), (4, 1), (5, 2),
+                                        (5, 16)])
 def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
     desc, punc = VARIANT_CASES[name]
-    if desc["coord"] == "cartesian" and variant in (2, 4):
+    if desc["coord"] == "cartesian" and variant in (2, 4, 5):
         pytest.skip("Cartesian grids have variants 0 and 1")
     og = oracle_grid(desc)
     alpha, beta = og.source(punc)
@@ -301,6 +320,37 @@ def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
     assert rel_err(ug.cpu().numpy(), u) <= 1e-12
     assert rel_err(vg.cpu().numpy(), v) <= 1e-12
     g.close()
+
+
+@pytest.mark.parametrize("n,zc", [((64, 20, 8), 2), ((128, 64, 16), 2),
+                                  ((128, 64, 16), 16)])
+def test_multi_stage_tensor_copy_equals_single_stage_launches(gpu, n, zc):
+    """Variant 5 runs the tensor-copy tile code of variant 3 inside one
+    cooperative launch per chunk of steps: the same arithmetic per point, so
+    trajectories agree bit for bit in both precisions (the 128 x 64 x 16
+    grid at zc = 2 has more tiles than resident blocks, so blocks run
+    several tiles per stage)."""
+    desc = W.grid_desc("sinhsymtp", n, 8)
+    og = oracle_grid(desc)
+    dt, eta = default_dt_eta(og)
+    u0 = og.fill_inner_ghosts(W.smooth_random_field(desc, seed=44, amplitude=0.1))
+    v0 = W.smooth_random_field(desc, seed=45, amplitude=0.05)
+    out = {}
+    for variant in (3, 5):
+        g = nrr.Grid(desc)
+        g.set_punctures(Q4)
+        for mode in ("fp64", "fp32"):
+            g.set_launch(zc, mode, variant)
+            g.set_state(_dev(u0), _dev(v0))
+            g.step(23, dt, eta, mode=mode)
+            ug, vg = torch.empty_like(_dev(u0)), torch.empty_like(_dev(u0))
+            g.get_state(ug, vg)
+            out[variant, mode] = (ug.cpu(), vg.cpu())
+        g.close()
+    for mode in ("fp64", "fp32"):
+        assert torch.equal(out[3, mode][0], out[5, mode][0]), mode
+        assert torch.equal(out[3, mode][1], out[5, mode][1]), mode
+    assert torch.isfinite(out[5, "fp32"][0]).all()
 
 
 def test_cartesian_tensor_copy_variant_full_size(gpu):
