@@ -86,9 +86,12 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
 
 // c^2 [lap(u) + source] at ZC interior points of one column (i0, i1) of a
 // curvilinear grid, planes pl[0..ZC).  wp[] holds the wrapped phi planes
-// pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  Two
-// independent accumulation chains per point (xx0 + phi, xx1) and ZC points
-// interleaved give the FP64 pipe independent work.
+// pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  One
+// accumulation chain per point -- centre, xx0, xx1, phi, then the source --
+// in the order every curvilinear stage kernel uses: on the FP64 pipe (a
+// warp instruction every 64 cycles per SM sub-partition) latency is hidden
+// by the other warps, and a second chain would cost its own multiply and
+// the add that joins the two.
 template <typename R, int NG, int ZC, bool COH = false>
 __device__ __forceinline__ void curvi_operator(
     const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
@@ -97,7 +100,7 @@ __device__ __forceinline__ void curvi_operator(
     int lin) {
   const int64_t nc = g.ncol;
   const int s0 = g.s0;
-  R a0[ZC], a1[ZC];
+  R a0[ZC];
 #pragma unroll
   for (int j = 0; j < ZC; j++) a0[j] = w[0] * u0[j];
   // xx0: the + side stays inside the padded box; the - side may cross
@@ -128,8 +131,8 @@ __device__ __forceinline__ void curvi_operator(
     for (int j = 0; j < ZC; j++) {
       R up = lds<COH>(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
       R um = lds<COH>(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
-      a1[j] = k == 1 ? w[2 * NG + k] * up : fma(w[2 * NG + k], up, a1[j]);
-      a1[j] = fma(w[3 * NG + k], um, a1[j]);
+      a0[j] = fma(w[2 * NG + k], up, a0[j]);
+      a0[j] = fma(w[3 * NG + k], um, a0[j]);
     }
   }
   // phi: periodic.
@@ -144,7 +147,7 @@ __device__ __forceinline__ void curvi_operator(
   }
 #pragma unroll
   for (int j = 0; j < ZC; j++)
-    out[j] = add_source(a0[j] + a1[j], u0[j], al[j], bc[j], lin);
+    out[j] = add_source(a0[j], u0[j], al[j], bc[j], lin);
 }
 
 // phi index into [NG, NG+n2) by adding or subtracting periods (offsets are a
@@ -521,22 +524,20 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
       const int64_t p = col + (int64_t)nc * i2;
       const R(&t)[TH][TW] = tile[buf];
       const R u0 = t[ty + NG][tx + NG];
-      R a0 = w[0] * u0, a1;
+      R a0 = w[0] * u0;
 #pragma unroll
       for (int k = 1; k <= NG; k++) {
         a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
         a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
       }
-      a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
-      a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
 #pragma unroll
-      for (int k = 2; k <= NG; k++) {
-        a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
-        a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
+      for (int k = 1; k <= NG; k++) {
+        a0 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a0);
+        a0 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a0);
       }
 #pragma unroll
       for (int k = 1; k <= NG; k++) a0 = fma(w[4 * NG + k], q[NG + k] + q[NG - k], a0);
-      const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
+      const R kv = add_source(a0, u0, al, bc, a.lin);
       R ku = fma(-a.eta, u0, v0);
       if (linear_mode<R>(a.lin)) ku += fu;
       if (KIND == STAGE_FIRST) {
@@ -794,24 +795,22 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
         const R u0 = t[ty + NG][tx + NG];
         const R v0 = S.op[OP_SV][j][ty][tx], al = S.op[OP_AL][j][ty][tx],
                 bc = S.op[OP_BC][j][ty][tx];
-        R a0 = w[0] * u0, a1;
+        R a0 = w[0] * u0;
 #pragma unroll
         for (int k = 1; k <= NG; k++) {
           a0 = fma(w[k], t[ty + NG][tx + NG + k], a0);
           a0 = fma(w[NG + k], t[ty + NG][tx + NG - k], a0);
         }
-        a1 = w[2 * NG + 1] * t[ty + NG + 1][tx + NG];
-        a1 = fma(w[3 * NG + 1], t[ty + NG - 1][tx + NG], a1);
 #pragma unroll
-        for (int k = 2; k <= NG; k++) {
-          a1 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a1);
-          a1 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a1);
+        for (int k = 1; k <= NG; k++) {
+          a0 = fma(w[2 * NG + k], t[ty + NG + k][tx + NG], a0);
+          a0 = fma(w[3 * NG + k], t[ty + NG - k][tx + NG], a0);
         }
         // q[NG + j] is the centre plane i2 + j
 #pragma unroll
         for (int k = 1; k <= NG; k++)
           a0 = fma(w[4 * NG + k], q[NG + j + k] + q[NG + j - k], a0);
-        const R kv = add_source(a0 + a1, u0, al, bc, a.lin);
+        const R kv = add_source(a0, u0, al, bc, a.lin);
         R ku = fma(-a.eta, u0, v0);
         if (use_fu) ku += S.op[OP_FU][j][ty][tx];
         if (KIND == STAGE_FIRST) {
