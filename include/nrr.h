@@ -204,7 +204,9 @@ nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
 
 /* Takes `steps` RK4 steps (paper Alg. 1 inner loop) from the current state
  * in precision `mode` with time step dt and damping eta, without norm checks.
- * For trajectory comparisons and benchmarks. */
+ * For trajectory comparisons and benchmarks.  NRR_ERR_TIMEOUT if a stage
+ * kernel's bounded wait (tensor copies, grid barrier) expired; nrr_rhs and
+ * nrr_profile_stages report it the same way. */
 nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
                     int64_t steps);
 

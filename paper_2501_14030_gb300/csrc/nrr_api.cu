@@ -357,6 +357,20 @@ void launch_norm(const nrr_grid *g, const FieldSet<R> &f, const ColumnSet<R> &c,
   launch_norm_finalize(g->partials, nb, g->scalars + 1, g->stream);
 }
 
+// After the stream has drained: NRR_ERR_TIMEOUT (and the flag cleared) if a
+// stage kernel's bounded wait -- for its tensor copies or at a grid barrier --
+// expired since the flag was last cleared.
+nrr_status take_stage_error(nrr_grid *g) {
+  int stage_err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&stage_err, g->flag + 2, sizeof(int),
+                           cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (!stage_err) return NRR_OK;
+  CUDA_TRY(cudaMemsetAsync(g->flag + 2, 0, sizeof(int), g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return fail(NRR_ERR_TIMEOUT, "a stage kernel's bounded wait expired");
+}
+
 nrr_status sync_read_norm(nrr_grid *g, double *out) {
   CUDA_TRY(cudaMemcpyAsync(g->host_pinned, g->scalars + 1, sizeof(double),
                            cudaMemcpyDeviceToHost, g->stream));
@@ -895,8 +909,7 @@ nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
   launch_fill_ghosts<double>(g->geo, ku, g->stream);
   launch_fill_ghosts<double>(g->geo, kv, g->stream);
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  return NRR_OK;
+  return take_stage_error(g);
 }
 
 nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
@@ -916,8 +929,7 @@ nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
   }
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaStreamSynchronize(g->stream));
-  return NRR_OK;
+  return take_stage_error(g);
 }
 
 nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
@@ -945,7 +957,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms_per_launch = (double)ms / (4.0 * (double)steps);
-  return NRR_OK;
+  CUDA_TRY(cudaGetLastError());
+  return take_stage_error(g);
 }
 
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block) {
@@ -1122,6 +1135,8 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
       CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      // a shape whose bounded waits expired is skipped (and the flag cleared)
+      if (take_stage_error(g) != NRR_OK) break;
       double per = ms / (4.0 * (double)trial_steps);
       if (rep == 1 && per < best_ms) {
         best_ms = per;
