@@ -178,6 +178,55 @@ def test_brill_lindquist_is_exactly_zero(gpu):
     assert not u.any()
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp32_dc"])
+def test_relax_outcomes_other_than_convergence(gpu, mode):
+    """nrr_relax stops with a status instead of running on: exactly
+    max_iters steps -> NOT_CONVERGED; CFL 2, beyond RK4's stability for this
+    operator (the oracle's relaxation blows up there too) -> DIVERGED; a
+    1 ms wall-clock limit on a solve of ~0.1 s -> TIMEOUT; and with
+    raise_on_error the binding raises."""
+    desc, punc, og, alpha, beta, g = _setup("sinh_44x26x6_o8")
+    r = g.relax(mode=mode, tol=1e-10, max_iters=100, check_every=50,
+                raise_on_error=False)
+    assert r["status"] == nrr.ERR_NOT_CONVERGED and r["iters"] == 100, r
+    r = g.relax(mode=mode, tol=1e-10, cfl=2.0, max_iters=20000, check_every=50,
+                raise_on_error=False)
+    assert r["status"] == nrr.ERR_DIVERGED, r
+    u, v = og.zeros(), og.zeros()
+    dt, eta = default_dt_eta(og)
+    _, _, st = og.relax(alpha, beta, u, v, eta=eta, dt=2.0 * og.dsmin, tol=1e-10,
+                        max_iters=20000, check_every=50)
+    assert st == 2  # the oracle's diverged status
+    with pytest.raises(nrr.NrrError):
+        g.relax(mode=mode, tol=1e-10, max_iters=100, check_every=50)
+    g.close()
+    desc, punc, og, alpha, beta, g = _setup("sinh_128x128x16_o8")
+    r = g.relax(mode=mode, tol=1e-10, timeout_ms=1, check_every=50,
+                raise_on_error=False)
+    assert r["status"] == nrr.ERR_TIMEOUT and r["iters"] < 6400, r
+    g.close()
+
+
+def test_relax_initial_data_modes(gpu):
+    """Warm starts: a converged u handed back from host memory, from device
+    memory, or left in place (INIT_CURRENT) meets the tolerance at the first
+    norm check; INIT_ZERO starts over."""
+    desc, punc, og, alpha, beta, g = _setup("sinh_44x26x6_o8")
+    r0 = g.relax(mode="fp64", tol=1e-10, check_every=50)
+    u = np.zeros(og.shape)
+    g.get_state(u)
+    for u0 in (u, _dev(u)):
+        g.relax(mode="fp64", tol=1e-10, max_iters=100, check_every=50,
+                raise_on_error=False)  # move the state away first
+        r = g.relax(mode="fp64", tol=1e-10, u0=u0, check_every=50)
+        assert r["status"] == 0 and r["iters"] <= 50, r
+    r = g.relax(mode="fp64", tol=1e-10, initial=nrr.INIT_CURRENT, check_every=50)
+    assert r["status"] == 0 and r["iters"] <= 50, r
+    r = g.relax(mode="fp64", tol=1e-10, initial=nrr.INIT_ZERO, check_every=50)
+    assert r["iters"] == r0["iters"]
+    g.close()
+
+
 # ------------------------------------------------ FP32 and defect correction
 FP32_RHS_TOL = 2e-5  # see test docstring
 
