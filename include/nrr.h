@@ -237,7 +237,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * every SM (zc = 1); variant 3 = 32 x 4 tiles whose planes stream through a
  * shared-memory ring filled by tensor (TMA) copies, zc (2, 4, 8 or 16)
  * planes per block, for FD order 8 with n0 % 32 == 0 and n1 % 4 == 0 (other
- * grids run variant 1 instead); variant 4 = the RK4 steps between two norm
+ * grids run variant 1 instead; in FP32, block 256 selects 32 x 8 tiles
+ * where n1 % 8 == 0); variant 4 = the RK4 steps between two norm
  * checks in one cooperative launch of a column kernel with grid barriers
  * between stages (zc = 1); variant 5 = the same multi-stage launch over
  * variant 3's tensor-copy tiles, zc (2, 4, 8 or 16) planes per tile, under
@@ -283,7 +284,8 @@ nrr_status nrr_autotune_clear(void);
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in
  * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
- * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16}, variant 4,
+ * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16} and block
+ * 128 or 256, variant 4,
  * variant 5 with zc in {4, 8, 16} -- skips
  * shapes the grid cannot launch, keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in

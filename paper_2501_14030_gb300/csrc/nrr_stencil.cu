@@ -413,15 +413,16 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
 }
 
 // Curvilinear stage fed by tensor copies (variant 3; order 8, n0 % 32 == 0,
-// n1 % 4 == 0): interior blocks run stage_tma_block on a 32 x 4 column tile
-// and a chunk of phi planes with one 3-D tensor map per array (kernel
-// parameter); the blocks after them evolve the outer shell, 32 rows of i1
-// and the NG shell columns each.
-template <typename R, int NG, int KIND>
-__global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
+// n1 % TY == 0): interior blocks run stage_tma_block on a 32 x TY column
+// tile (TY = 4 or 8) and a chunk of phi planes with one 3-D tensor map per
+// array (kernel parameter); the blocks after them evolve the outer shell,
+// 32 TY / NG rows of i1 and the NG shell columns each.  Both tile heights
+// keep 80 registers and 768 threads per SM in FP32.
+template <typename R, int NG, int KIND, int TY>
+__global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 24 / TY : 1)
     stage_curvi_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ FieldSrc maps,
                            int zc) {
-  constexpr int TY = kCartTY, PZ = kCartPZ, NS = cart_slots<R>();
+  constexpr int PZ = kCartPZ, NS = cart_slots<R>();
   pdl_trigger();
   const int ntx = g.n0 / 32, nty = g.n1 / TY, nch = chunks_z(g, zc);
   const int nint = ntx * nty * nch;
@@ -833,9 +834,10 @@ bool cart_tma_ok(const Geo &g, int zc) {
          zc % kCartPZ == 0 && g.s0 % 4 == 0;
 }
 
-// Whether the curvilinear tensor-copy stage applies to this grid and launch.
-bool curvi_tma_ok(const Geo &g, int zc) {
-  return g.ng == 4 && g.n0 % 32 == 0 && g.n1 % kCartTY == 0 &&
+// Whether the curvilinear tensor-copy stage with tiles of ty rows applies
+// to this grid and launch.
+bool curvi_tma_ok(const Geo &g, int zc, int ty = kCartTY) {
+  return g.ng == 4 && g.n0 % 32 == 0 && g.n1 % ty == 0 &&
          g.n2 % kCartPZ == 0 && zc % kCartPZ == 0 && g.s0 % 4 == 0;
 }
 
@@ -843,7 +845,7 @@ bool curvi_tma_ok(const Geo &g, int zc) {
 // tile boxes; false if the driver cannot encode them.
 template <typename R, int NG, int KIND>
 bool stage_field_maps(FieldSrc *m, const Geo &g, const StageArgs<R> &a, int b0u,
-                      int b1u) {
+                      int b1u, int ty = kCartTY) {
   const int es = (int)sizeof(R);
   const R *ops[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
   const bool use_fu = a.lin != 0 && sizeof(R) == 4;
@@ -852,7 +854,7 @@ bool stage_field_maps(FieldSrc *m, const Geo &g, const StageArgs<R> &a, int b0u,
   if (!field_map(&m->u, a.su, es, g, b0u, b1u)) return false;
   for (int o = 0; o < 8; o++) {
     if (need[o]) {
-      if (!field_map(&m->op[o], ops[o], es, g, 32, kCartTY)) return false;
+      if (!field_map(&m->op[o], ops[o], es, g, 32, ty)) return false;
     } else {
       m->op[o] = m->u;  // unused slot
     }
@@ -860,18 +862,18 @@ bool stage_field_maps(FieldSrc *m, const Geo &g, const StageArgs<R> &a, int b0u,
   return true;
 }
 
-template <typename R, int NG, int KIND>
+template <typename R, int NG, int KIND, int TY>
 bool launch_curvi_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
                            cudaStream_t st) {
   FieldSrc maps;
-  if (!stage_field_maps<R, NG, KIND>(&maps, g, a, 32 + 2 * NG, kCartTY + 2 * NG))
+  if (!stage_field_maps<R, NG, KIND>(&maps, g, a, 32 + 2 * NG, TY + 2 * NG, TY))
     return false;
-  constexpr int rows = 32 * kCartTY / NG;
+  constexpr int rows = 32 * TY / NG;
   const int nch = chunks_z(g, zc);
-  const int nint = (g.n0 / 32) * (g.n1 / kCartTY) * nch;
+  const int nint = (g.n0 / 32) * (g.n1 / TY) * nch;
   const int nshell = ((g.n1 + rows - 1) / rows) * nch;
-  launch_stage_kernel(stage_curvi_tma_kernel<R, NG, KIND>, dim3(nint + nshell),
-                      dim3(32 * kCartTY), st, pdl, g, a, maps, zc);
+  launch_stage_kernel(stage_curvi_tma_kernel<R, NG, KIND, TY>, dim3(nint + nshell),
+                      dim3(32 * TY), st, pdl, g, a, maps, zc);
   return true;
 }
 
@@ -975,13 +977,27 @@ void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
   }
   if (cfg.variant == 3) {
     if constexpr (NG == 4) {
+      // FP32: 256-thread blocks select tiles of 8 rows of i1, others 4 (an
+      // FP64 ring of 8-row tiles would exceed 48 KB of static shared memory)
+      if constexpr (sizeof(R) == 4) {
+        if (cfg.block == 256 && curvi_tma_ok(g, zc, 8)) {
+          bool ok = false;
+          switch (kind) {
+            case STAGE_FIRST: ok = launch_curvi_tma_kind<R, NG, STAGE_FIRST, 8>(g, a, zc, pdl, st); break;
+            case STAGE_MID: ok = launch_curvi_tma_kind<R, NG, STAGE_MID, 8>(g, a, zc, pdl, st); break;
+            case STAGE_LAST: ok = launch_curvi_tma_kind<R, NG, STAGE_LAST, 8>(g, a, zc, pdl, st); break;
+            default: ok = launch_curvi_tma_kind<R, NG, STAGE_RAW, 8>(g, a, zc, pdl, st); break;
+          }
+          if (ok) return;
+        }
+      }
       if (curvi_tma_ok(g, zc)) {
         bool ok = false;
         switch (kind) {
-          case STAGE_FIRST: ok = launch_curvi_tma_kind<R, NG, STAGE_FIRST>(g, a, zc, pdl, st); break;
-          case STAGE_MID: ok = launch_curvi_tma_kind<R, NG, STAGE_MID>(g, a, zc, pdl, st); break;
-          case STAGE_LAST: ok = launch_curvi_tma_kind<R, NG, STAGE_LAST>(g, a, zc, pdl, st); break;
-          default: ok = launch_curvi_tma_kind<R, NG, STAGE_RAW>(g, a, zc, pdl, st); break;
+          case STAGE_FIRST: ok = launch_curvi_tma_kind<R, NG, STAGE_FIRST, 4>(g, a, zc, pdl, st); break;
+          case STAGE_MID: ok = launch_curvi_tma_kind<R, NG, STAGE_MID, 4>(g, a, zc, pdl, st); break;
+          case STAGE_LAST: ok = launch_curvi_tma_kind<R, NG, STAGE_LAST, 4>(g, a, zc, pdl, st); break;
+          default: ok = launch_curvi_tma_kind<R, NG, STAGE_RAW, 4>(g, a, zc, pdl, st); break;
         }
         if (ok) return;
       }

@@ -371,6 +371,46 @@ def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
     g.close()
 
 
+@pytest.mark.parametrize("coord,n,zc", [("sinhsymtp", (64, 24, 8), 4),
+                                         ("spherical", (64, 32, 8), 2),
+                                         ("sinhspherical", (64, 40, 8), 16)])
+def test_tensor_copy_tiles_of_8_rows(gpu, coord, n, zc):
+    """FP32 tensor-copy stage with 32 x 8 tiles (256-thread blocks): the RHS
+    against the oracle, and trajectories bit for bit equal to the 32 x 4
+    tiles (the same arithmetic per point; only the tiling differs)."""
+    extra = {"rmax": 64.0} if coord == "spherical" else {}
+    desc = W.grid_desc(coord, n, 8, **extra)
+    og = oracle_grid(desc)
+    alpha, beta = og.source(Q4)
+    dt, eta = default_dt_eta(og)
+    u = W.smooth_random_field(desc, seed=51, amplitude=0.2, noise=0.01)
+    v = W.smooth_random_field(desc, seed=52, amplitude=0.1, noise=0.01)
+    ku_o, kv_o = og.rhs(alpha, beta, eta, og.fill_inner_ghosts(u),
+                        og.fill_inner_ghosts(v))
+    out = {}
+    for block in (128, 256):
+        g = nrr.Grid(desc)
+        g.set_punctures(Q4)
+        g.set_launch(zc, "fp32", 3, block)
+        assert g.get_launch("fp32") == (3, zc, block)
+        ku, kv = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+        g.rhs(_dev(u), _dev(v), ku, kv, eta, mode="fp32")
+        ku, kv = ku.cpu().numpy(), kv.cpu().numpy()
+        for region, m in region_masks(og).items():
+            assert rel_err(ku, ku_o, m) <= FP32_RHS_TOL, (block, region)
+            assert rel_err(kv, kv_o, m) <= FP32_RHS_TOL, (block, region)
+        g.set_state(_dev(og.fill_inner_ghosts(u)), _dev(v))
+        g.step(17, dt, eta, mode="fp32")
+        ug, vg = torch.empty_like(_dev(u)), torch.empty_like(_dev(u))
+        g.get_state(ug, vg)
+        out[block] = (ug.cpu(), vg.cpu(), ku, kv)
+        g.close()
+    for k in range(4):
+        a, b = out[128][k], out[256][k]
+        assert (torch.equal(a, b) if isinstance(a, torch.Tensor)
+                else np.array_equal(a, b)), k
+
+
 @pytest.mark.parametrize("n,zc", [((64, 20, 8), 2), ((128, 64, 16), 2),
                                   ((128, 64, 16), 16)])
 def test_multi_stage_tensor_copy_equals_single_stage_launches(gpu, n, zc):
