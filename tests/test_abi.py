@@ -85,3 +85,15 @@ def test_host_image_map_matches_oracle_cartesian_matching(lib, oracle_mod,
                                                           desc):
     og = oracle_grid(desc)
     assert np.array_equal(nrr.image_map(desc), og.field("image"))
+
+
+def test_bench_names_every_documented_stage_variant():
+    """bench.py reports the autotuner's launch shape by name: every
+    curvilinear stage variant that nrr_set_launch documents has one."""
+    text = open(os.path.join(ROOT, "include", "nrr.h")).read()
+    doc = text[text.index("Launch shape of the fused stage kernels"):
+               text.index("nrr_status nrr_set_launch(")]
+    documented = {int(v) for v in re.findall(r"variant (\d)", doc)}
+    import bench
+    assert documented == set(range(6))
+    assert documented <= set(bench.STAGE_VARIANTS)
