@@ -158,7 +158,10 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
                            nrr_grid **out);
 nrr_status nrr_destroy_grid(nrr_grid *g);
 
-/* Padded dims s[3], ghost width, and interior point count of a grid. */
+/* Padded dims s[3] (interior plus NG ghost zones on each side, paper Sec. 4
+ * memory layout), ghost width NG = fd_order/2, and interior point count of
+ * a grid; outputs are caller-owned host memory.
+ * Errors: NRR_ERR_INVALID_ARG for a null grid. */
 nrr_status nrr_grid_dims(const nrr_grid *g, int s[3], int *ng,
                          int64_t *interior_points);
 
@@ -172,8 +175,13 @@ nrr_status nrr_set_punctures(nrr_grid *g, int n, const nrr_puncture *p);
 
 /* Relaxes to tol (paper Alg. 1 relaxation loop).  Returns NRR_OK when the
  * norm fell below tol, else NRR_ERR_NOT_CONVERGED / NRR_ERR_DIVERGED /
- * NRR_ERR_TIMEOUT; *r (optional) is filled in every case.  The converged
- * state stays on the grid (nrr_get_u). */
+ * NRR_ERR_TIMEOUT (also when a stage kernel's bounded wait expired);
+ * *r (optional, caller-owned) is filled in every case.  The final state
+ * stays on the grid (nrr_get_state).
+ * Errors: NRR_ERR_INVALID_ARG (null grid or options, tol <= 0, cfl <= 0,
+ * r_int <= 0, check_every < 1, a negative max_iters, inner_steps or
+ * max_outer, an unknown mode or initial, a null u0 for
+ * NRR_INIT_HOST/DEVICE), NRR_ERR_STATE (punctures not set), NRR_ERR_CUDA. */
 nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
                      nrr_relax_result *r);
 
@@ -181,16 +189,23 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
  * and its L2 norm over r < r_int: sqrt(sum H^2 J / sum J) over interior
  * points, J = h0 h1 h2 the reference-metric volume factor.
  * h_out (nullable): padded array of s0*s1*s2 doubles, zero off the interior;
- * device pointer when h_on_device, else host. */
+ * device pointer when h_on_device, else host; caller-owned.  norm_out
+ * (host) nullable.  Errors: NRR_ERR_INVALID_ARG (null grid), NRR_ERR_STATE
+ * (punctures not set), NRR_ERR_CUDA. */
 nrr_status nrr_residual(nrr_grid *g, double r_int, double *norm_out,
                         double *h_out, int h_on_device);
 
-/* Copies the current u (and v) out, padded layout with inner ghosts filled,
- * FP64 whatever the solve mode. */
+/* Copies the current state u (and v) of the relaxation system (paper Sec. 2)
+ * out, padded layout with inner ghosts filled, FP64 whatever the solve mode;
+ * u and v nullable (NULL: not copied); caller-owned arrays of s0*s1*s2
+ * doubles, device pointers when on_device.
+ * Errors: NRR_ERR_INVALID_ARG (null grid), NRR_ERR_CUDA. */
 nrr_status nrr_get_state(nrr_grid *g, double *u, double *v, int on_device);
 
-/* Replaces the state (u, v) from padded FP64 arrays (inner ghosts ignored).
- * v may be NULL (v = 0).  Used for checkpoint/resume and warm starts. */
+/* Replaces the state (u, v) of the relaxation system (paper Sec. 2) from
+ * padded FP64 arrays (inner ghosts ignored), copied; v may be NULL (v = 0);
+ * device pointers when on_device.  Used for checkpoint/resume and warm
+ * starts.  Errors: NRR_ERR_INVALID_ARG (null grid or u), NRR_ERR_CUDA. */
 nrr_status nrr_set_state(nrr_grid *g, const double *u, const double *v,
                          int on_device);
 
@@ -198,32 +213,43 @@ nrr_status nrr_set_state(nrr_grid *g, const double *u, const double *v,
  * conditions (paper Sec. 2 system; Alg. 1 RHS then BC) on the given state,
  * in the precision of `mode` (NRR_FP64 / NRR_FP32), with damping eta.
  * u, v in: padded FP64; ku, kv out: padded FP64, values at evolved points
- * and inner ghosts (copied from their images).  All device pointers. */
+ * and inner ghosts (copied from their images).  All device pointers,
+ * caller-owned.  Errors: NRR_ERR_INVALID_ARG (null pointer, unknown mode),
+ * NRR_ERR_STATE (punctures not set), NRR_ERR_TIMEOUT (a bounded wait
+ * expired), NRR_ERR_CUDA. */
 nrr_status nrr_rhs(nrr_grid *g, int mode, double eta, const double *u,
                    const double *v, double *ku, double *kv);
 
 /* Takes `steps` RK4 steps (paper Alg. 1 inner loop) from the current state
  * in precision `mode` with time step dt and damping eta, without norm checks.
- * For trajectory comparisons and benchmarks.  NRR_ERR_TIMEOUT if a stage
- * kernel's bounded wait (tensor copies, grid barrier) expired; nrr_rhs and
- * nrr_profile_stages report it the same way. */
+ * For trajectory comparisons and benchmarks.
+ * Errors: NRR_ERR_INVALID_ARG (steps < 0, dt <= 0, unknown mode),
+ * NRR_ERR_STATE (punctures not set), NRR_ERR_TIMEOUT if a stage kernel's
+ * bounded wait (tensor copies, grid barrier) expired, NRR_ERR_CUDA. */
 nrr_status nrr_step(nrr_grid *g, int mode, double dt, double eta,
                     int64_t steps);
 
-/* The time step the solver uses for a given CFL factor, and the default
- * damping: dt = cfl * min ds over the interior, eta = 2 pi cfl / (n0 dt). */
+/* The time step the solver uses for a given CFL factor (paper Sec. 2: the
+ * wave speed follows the local spacing so that one dt satisfies the CFL
+ * condition everywhere), and the default damping: dt = cfl * min ds over
+ * the interior, eta = 2 pi cfl / (n0 dt).  Host outputs, nullable.
+ * Errors: NRR_ERR_INVALID_ARG (null grid, cfl <= 0). */
 nrr_status nrr_timestep(const nrr_grid *g, double cfl, double *dt,
                         double *eta_default);
 
-/* Host-side image map of the inner boundary: out[p] = flat index of the
- * evolved point whose value ghost p copies, or p itself for evolved points.
- * out: host array of s0*s1*s2 int32.  Pure host computation, no device. */
+/* Host-side image map of the inner boundary (paper Sec. 2 inner boundary
+ * conditions; Alg. 1 BC): out[p] = flat index of the evolved point whose
+ * value ghost p copies, or p itself for evolved points.
+ * out: caller-owned host array of s0*s1*s2 int32.  Pure host computation,
+ * no device.  Errors: NRR_ERR_INVALID_ARG (bad descriptor, null out). */
 nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
 
 /* Measurement hook: takes `steps` RK4 steps exactly as nrr_step does, with
  * CUDA events recorded on the grid's work stream around them, and returns
  * the average device time of one fused stage launch in *ms_per_launch
- * (4 launches per step).  The state advances. */
+ * (4 launches per step).  The state advances.
+ * Errors: as nrr_step, and NRR_ERR_INVALID_ARG for steps < 1 or a null
+ * output. */
 nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
                               int64_t steps, double *ms_per_launch);
 
@@ -252,7 +278,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block);
 
 /* The current launch shape for `mode` (as set by nrr_set_launch or chosen by
- * nrr_autotune); outputs nullable. */
+ * nrr_autotune); host outputs, nullable.
+ * Errors: NRR_ERR_INVALID_ARG (null grid, unknown mode). */
 nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
                           int *block);
 
@@ -300,18 +327,23 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
  * there on several streams; here one graph launch for all of them) ------- */
 typedef struct nrr_batch nrr_batch;
 
-/* Creates a batch of n solves of uneven sizes: descs[i] (SinhSymTP or
- * Spherical, one fd_order for the whole batch), npunct[i] punctures at
+/* Creates a batch of n solves of uneven sizes: descs[i] (SinhSymTP,
+ * Spherical or SinhSpherical, one fd_order for the whole batch), npunct[i] punctures at
  * punct[i] (host arrays, copied).  Computes the footprint first
  * (NRR_ERR_OOM before any allocation), then allocates one arena per field
  * and runs the set-up of every solve on the device.  flags bit 0: also
  * allocate FP64 stage buffers so that NRR_FP64 batch relaxations are
  * possible (NRR_FP32_DC needs no extra storage).  stream: as for
- * nrr_create_grid. */
+ * nrr_create_grid.  The paper runs independent patches on separate streams
+ * (Sec. 4 scalability, Sec. 5); here one batch object and one graph.
+ * Errors: NRR_ERR_INVALID_ARG (n < 1, a bad descriptor, mixed orders or
+ * a Cartesian grid, bad punctures), NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
                             const int *npunct, const nrr_puncture *const *punct,
                             int flags, void *stream, nrr_batch **out);
 nrr_status nrr_batch_destroy(nrr_batch *b);
+/* Padded and interior points summed over the solves (host outputs,
+ * nullable).  Errors: NRR_ERR_INVALID_ARG for a null batch. */
 nrr_status nrr_batch_info(const nrr_batch *b, int64_t *total_points,
                           int64_t *interior_points);
 
@@ -324,22 +356,32 @@ nrr_status nrr_batch_info(const nrr_batch *b, int64_t *total_points,
  * or timeout_ms has passed (measured on the device).  per_solve (nullable,
  * n entries) receives each solve's steps, norm and status; total (nullable)
  * the largest step count, the number of chunks and the largest norm.
- * Returns NRR_OK when every solve converged. */
+ * Returns NRR_OK when every solve converged (paper Alg. 1 per solve),
+ * else NRR_ERR_NOT_CONVERGED / NRR_ERR_DIVERGED / NRR_ERR_TIMEOUT (also
+ * when a stage kernel's bounded wait expired).
+ * Errors: NRR_ERR_INVALID_ARG (null batch or options, a mode or initial
+ * other than those above, NRR_FP64 without flags bit 0), NRR_ERR_CUDA. */
 nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
                            nrr_relax_result *per_solve,
                            nrr_relax_result *total);
 
-/* Copies u of solve i out (padded FP64 layout, inner ghosts filled). */
+/* Copies u of solve i out (padded FP64 layout, inner ghosts filled) to a
+ * caller-owned array, device pointer when on_device.
+ * Errors: NRR_ERR_INVALID_ARG (null argument, i out of range),
+ * NRR_ERR_CUDA. */
 nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device);
 
 /* Sets u of solve i (padded FP64 layout; inner ghosts ignored) for a warm
  * start: a following nrr_batch_relax with initial = NRR_INIT_DEVICE starts
- * from the u of every solve with v = eta u. */
+ * from the u of every solve with v = eta u.  u: caller-owned, copied.
+ * Errors: NRR_ERR_INVALID_ARG (null argument, i out of range),
+ * NRR_ERR_CUDA. */
 nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device);
 
 /* Interior u of every solve as FP32, dst (device) [n][n0*n1*n2] with i0
  * fastest; all solves must have the same size.  Training targets of the
- * surrogate. */
+ * surrogate.  Errors: NRR_ERR_INVALID_ARG (null argument, solves of
+ * different sizes), NRR_ERR_CUDA. */
 nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
 
 /* Stage kernel of a batch for `mode` (NRR_FP64, or NRR_FP32_DC for its FP32
@@ -370,7 +412,9 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
  * D[m][n] = sum_k A[m][k] B[n][k] for row-major BF16 A (M x K) and B
  * (N x K) -- both K-major -- and row-major FP32 D (M x N).  All device
  * pointers, 16-byte aligned; M % 128 == 0, N % 64 == 0, K % 64 == 0.
- * Synchronous on `stream`; NRR_ERR_TIMEOUT if a pipeline wait expired. */
+ * Synchronous on `stream`; NRR_ERR_TIMEOUT if a pipeline wait expired.
+ * Errors: NRR_ERR_INVALID_ARG (null or misaligned pointer, a size that is
+ * not a multiple of the tile), NRR_ERR_CUDA. */
 nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
                             int N, int K, void *stream);
 
@@ -383,7 +427,11 @@ typedef struct nrr_surrogate nrr_surrogate;
  * packed layout -- for each layer l, W_l as [out][in] row-major then b_l
  * [out] -- of nrr_surrogate_num_params() floats (the caller draws them).
  * Limits: n_in <= 64, hidden and n_out multiples of 128, batch a multiple
- * of 128.  Output scaling starts as the identity (mean 0, std 1). */
+ * of 128.  Output scaling starts as the identity (mean 0, std 1).  The
+ * paper has no surrogate; this serves the warm start of nrr_relax
+ * (NRR_INIT_HOST/DEVICE) and nrr_batch_relax.  init_params is copied.
+ * Errors: NRR_ERR_INVALID_ARG (sizes outside the limits, null pointers),
+ * NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_create(int n_in, int hidden, int depth, int n_out,
                                 int batch, const float *init_params,
                                 void *stream, nrr_surrogate **out);
@@ -391,7 +439,8 @@ nrr_status nrr_surrogate_destroy(nrr_surrogate *s);
 int64_t nrr_surrogate_num_params(const nrr_surrogate *s);
 
 /* Sets the output scaling to the per-output mean and standard deviation of
- * Y (device, [n][n_out] FP32); the network learns (Y - mean)/std. */
+ * Y (device, [n][n_out] FP32); the network learns (Y - mean)/std.
+ * Errors: NRR_ERR_INVALID_ARG (null argument, n < 1), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
                                      int64_t n);
 
@@ -400,22 +449,30 @@ nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
  * order[t*batch .. (t+1)*batch) (device int32; the caller draws the
  * shuffles).  X: device [n][n_in], Y: device [n][n_out].  loss_out
  * (nullable, host, steps floats) receives each step's mean squared error of
- * the scaled outputs. */
+ * the scaled outputs.
+ * Errors: NRR_ERR_INVALID_ARG (null argument, n < batch, lr <= 0),
+ * NRR_ERR_TIMEOUT (a GEMM pipeline wait expired), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
                                int64_t n, const int32_t *order, int64_t steps,
                                double lr, double weight_decay, float *loss_out);
 
-/* out (device [n][n_out]) = network(X) mapped back through the scaling. */
+/* out (device [n][n_out]) = network(X) mapped back through the scaling;
+ * X device [n][n_in]; any n >= 1 (processed in chunks of `batch` rows).
+ * Errors: NRR_ERR_INVALID_ARG (null argument, n < 1), NRR_ERR_TIMEOUT,
+ * NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_predict(nrr_surrogate *s, const float *X, int64_t n,
                                  float *out);
 
 /* Loss and parameter gradients of one minibatch (the first `batch` rows of
  * X, Y; device) without updating: grads is a host array in the logical
- * packed layout.  For gradient checks. */
+ * packed layout.  For gradient checks.  Errors: NRR_ERR_INVALID_ARG (null
+ * argument), NRR_ERR_TIMEOUT, NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_gradients(nrr_surrogate *s, const float *X,
                                    const float *Y, float *grads, double *loss);
 
-/* Current parameters in the logical packed layout (host). */
+/* Current parameters in the logical packed layout (caller-owned host array
+ * of nrr_surrogate_num_params() floats).
+ * Errors: NRR_ERR_INVALID_ARG (null argument), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_get_params(nrr_surrogate *s, float *params);
 
 /* Warm-start prolongation: u on the fine grid (device, padded FP64, every
@@ -423,7 +480,10 @@ nrr_status nrr_surrogate_get_params(nrr_surrogate *s, float *params);
  * coarse interior values uc (device, [n2][n1][n0] FP32) of a grid of the
  * same curvilinear family and parameters; coarse neighbours across the inner
  * boundary come from their images, beyond the outer boundary the last
- * interior plane is used.  Synchronous on `stream`. */
+ * interior plane is used.  Synchronous on `stream`.
+ * Errors: NRR_ERR_INVALID_ARG (null argument, grids of different families
+ * or parameters, a bad descriptor, a fine grid above 2^31 points),
+ * NRR_ERR_CUDA. */
 nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
                        const nrr_grid_desc *fine, double *uf, void *stream);
 
