@@ -244,7 +244,8 @@ nrr_status nrr_timestep(const nrr_grid *g, double cfl, double *dt,
  * no device.  Errors: NRR_ERR_INVALID_ARG (bad descriptor, null out). */
 nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
 
-/* Measurement hook: takes `steps` RK4 steps exactly as nrr_step does, with
+/* Measurement hook (the per-kernel timings of paper Sec. 5, taken with CUDA
+ * events here): takes `steps` RK4 steps exactly as nrr_step does, with
  * CUDA events recorded on the grid's work stream around them, and returns
  * the average device time of one fused stage launch in *ms_per_launch
  * (4 launches per step).  The state advances.
@@ -253,37 +254,37 @@ nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out);
 nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
                               int64_t steps, double *ms_per_launch);
 
-/* Launch shape of the fused stage kernels for the precision of `mode`
- * (NRR_FP64 / NRR_FP32).  Curvilinear grids: variant 0 = one thread per
- * (i0, i1) column and zc (1, 2 or 4) phi planes, neighbours read through the
- * caches, in blocks of `block` threads (64, 128 or 256; 0 keeps the current
- * size); variant 1 = tiles of 32 x 4 columns staged plane by plane through
- * registers into shared memory, zc (2, 4, 8 or 16) planes per block;
- * variant 2 = one (column, plane) per step of a grid that exactly fills
- * every SM (zc = 1); variant 3 = 32 x 4 tiles whose planes stream through a
- * shared-memory ring filled by tensor (TMA) copies, zc (2, 4, 8 or 16)
- * planes per block, for FD order 8 with n0 % 32 == 0 and n1 % 4 == 0 (other
- * grids run variant 1 instead; in FP32, block 256 selects 32 x 8 tiles
- * where n1 % 8 == 0); variant 4 = the RK4 steps between two norm
- * checks in one cooperative launch of a column kernel with grid barriers
- * between stages (zc = 1); variant 5 = the same multi-stage launch over
- * variant 3's tensor-copy tiles, zc (2, 4, 8 or 16) planes per tile, under
- * variant 3's conditions (other grids run variant 4 instead).  Single stage
- * launches of variants 4 and 5 run variants 0 and 3.  Cartesian grids:
- * variant 1 = the tensor-copy
- * kernel under the same conditions, any other variant the column kernel
- * (zc planes per thread, `block` threads).  Results do not depend on the
- * shape beyond rounding order.
+/* Launch shape of the fused stage kernels for the precision of `mode` (NRR_FP64
+ * / NRR_FP32); the paper fixes one thread block shape (Sec. 4, parallelization
+ * strategy), this library offers several. Curvilinear grids: variant 0 = one
+ * thread per (i0, i1) column and zc (1, 2 or 4) phi planes, neighbours read
+ * through the caches, in blocks of `block` threads (64, 128 or 256; 0 keeps the
+ * current size); variant 1 = tiles of 32 x 4 columns staged plane by plane
+ * through registers into shared memory, zc (2, 4, 8 or 16) planes per block;
+ * variant 2 = one (column, plane) per step of a grid that exactly fills every
+ * SM (zc = 1); variant 3 = 32 x 4 tiles whose planes stream through a shared-
+ * memory ring filled by tensor (TMA) copies, zc (2, 4, 8 or 16) planes per
+ * block, for FD order 8 with n0 % 32 == 0 and n1 % 4 == 0 (other grids run
+ * variant 1 instead; in FP32, block 256 selects 32 x 8 tiles where n1 % 8 ==
+ * 0); variant 4 = the RK4 steps between two norm checks in one cooperative
+ * launch of a column kernel with grid barriers between stages (zc = 1); variant
+ * 5 = the same multi-stage launch over variant 3's tensor-copy tiles, zc (2, 4,
+ * 8 or 16) planes per tile, under variant 3's conditions (other grids run
+ * variant 4 instead). Single stage launches of variants 4 and 5 run variants 0
+ * and 3. Cartesian grids: variant 1 = the tensor-copy kernel under the same
+ * conditions, any other variant the column kernel (zc planes per thread,
+ * `block` threads). Results do not depend on the shape beyond rounding order.
  * Errors: NRR_ERR_INVALID_ARG for other values. */
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block);
 
 /* The current launch shape for `mode` (as set by nrr_set_launch or chosen by
- * nrr_autotune); host outputs, nullable.
+ * nrr_autotune; no paper counterpart); host outputs, nullable.
  * Errors: NRR_ERR_INVALID_ARG (null grid, unknown mode). */
 nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
                           int *block);
 
-/* Programmatic dependent launch of the fused stage kernels, both precisions
+/* Programmatic dependent launch (no paper counterpart; the paper launches
+ * its kernels in sequence, Sec. 4) of the fused stage kernels, both precisions
  * (on = 1, the default): each stage kernel is launched so that its blocks
  * may be scheduled while the preceding kernel on the stream drains; they
  * read only solve-constant data (column weights, geometry) until that kernel
@@ -293,16 +294,15 @@ nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
  * Errors: NRR_ERR_INVALID_ARG for a null grid or on not 0/1. */
 nrr_status nrr_set_pdl(nrr_grid *g, int on);
 
-/* The autotuner's cache as a file (JSON): every launch shape chosen in this
- * process by nrr_autotune (or loaded), keyed by coordinates, interior sizes,
- * FD order and precision.  nrr_autotune_save writes it to `path`;
- * nrr_autotune_load adds the entries of such a file to the cache, so that
- * grids created afterwards with a matching key start with that shape without
- * tuning (grids that exist already keep theirs); nrr_autotune_clear empties
- * the cache.  Host only; no GPU work.
- * Errors: NRR_ERR_INVALID_ARG (null path; an unreadable, malformed or
- * invalid file, in which case nothing is added), NRR_ERR_STATE (the file
- * cannot be written). */
+/* The autotuner's cache as a file (JSON; no paper counterpart): every launch
+ * shape chosen in this process by nrr_autotune (or loaded), keyed by
+ * coordinates, interior sizes, FD order and precision. nrr_autotune_save writes
+ * it to `path`; nrr_autotune_load adds the entries of such a file to the cache,
+ * so that grids created afterwards with a matching key start with that shape
+ * without tuning (grids that exist already keep theirs); nrr_autotune_clear
+ * empties the cache. Host only; no GPU work. Errors: NRR_ERR_INVALID_ARG (null
+ * path; an unreadable, malformed or invalid file, in which case nothing is
+ * added), NRR_ERR_STATE (the file cannot be written). */
 nrr_status nrr_autotune_save(const char *path);
 nrr_status nrr_autotune_load(const char *path);
 nrr_status nrr_autotune_clear(void);
@@ -318,7 +318,9 @@ nrr_status nrr_autotune_clear(void);
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the
  * punctures set.  *best_zc and *best_ms_per_launch (nullable) report the
- * choice and its average time per stage launch. */
+ * choice and its average time per stage launch.
+ * Errors: NRR_ERR_INVALID_ARG (null grid, unknown mode, trial_steps < 1),
+ * NRR_ERR_STATE (punctures not set), NRR_ERR_CUDA. */
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
                         int *best_variant, int *best_zc,
                         double *best_ms_per_launch);
@@ -327,23 +329,23 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
  * there on several streams; here one graph launch for all of them) ------- */
 typedef struct nrr_batch nrr_batch;
 
-/* Creates a batch of n solves of uneven sizes: descs[i] (SinhSymTP,
- * Spherical or SinhSpherical, one fd_order for the whole batch), npunct[i] punctures at
- * punct[i] (host arrays, copied).  Computes the footprint first
- * (NRR_ERR_OOM before any allocation), then allocates one arena per field
- * and runs the set-up of every solve on the device.  flags bit 0: also
- * allocate FP64 stage buffers so that NRR_FP64 batch relaxations are
- * possible (NRR_FP32_DC needs no extra storage).  stream: as for
- * nrr_create_grid.  The paper runs independent patches on separate streams
- * (Sec. 4 scalability, Sec. 5); here one batch object and one graph.
- * Errors: NRR_ERR_INVALID_ARG (n < 1, a bad descriptor, mixed orders or
- * a Cartesian grid, bad punctures), NRR_ERR_OOM, NRR_ERR_CUDA. */
+/* Creates a batch of n solves of uneven sizes: descs[i] (SinhSymTP, Spherical
+ * or SinhSpherical, one fd_order for the whole batch), npunct[i] punctures at
+ * punct[i] (host arrays, copied). Computes the footprint first (NRR_ERR_OOM
+ * before any allocation), then allocates one arena per field and runs the set-
+ * up of every solve on the device. flags bit 0: also allocate FP64 stage
+ * buffers so that NRR_FP64 batch relaxations are possible (NRR_FP32_DC needs no
+ * extra storage). stream: as for nrr_create_grid. The paper runs independent
+ * patches on separate streams (Sec. 4 scalability, Sec. 5); here one batch
+ * object and one graph. Errors: NRR_ERR_INVALID_ARG (n < 1, a bad descriptor,
+ * mixed orders or a Cartesian grid, bad punctures), NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
                             const int *npunct, const nrr_puncture *const *punct,
                             int flags, void *stream, nrr_batch **out);
 nrr_status nrr_batch_destroy(nrr_batch *b);
-/* Padded and interior points summed over the solves (host outputs,
- * nullable).  Errors: NRR_ERR_INVALID_ARG for a null batch. */
+/* Padded and interior points summed over the solves (host outputs, nullable;
+ * the storage of paper Sec. 4 per solve). Errors: NRR_ERR_INVALID_ARG for a
+ * null batch. */
 nrr_status nrr_batch_info(const nrr_batch *b, int64_t *total_points,
                           int64_t *interior_points);
 
@@ -365,26 +367,30 @@ nrr_status nrr_batch_relax(nrr_batch *b, const nrr_relax_opts *o,
                            nrr_relax_result *per_solve,
                            nrr_relax_result *total);
 
-/* Copies u of solve i out (padded FP64 layout, inner ghosts filled) to a
+/* Copies u of solve i (the relaxed field of paper Sec. 2) out (padded FP64
+ * layout, inner ghosts filled) to a
  * caller-owned array, device pointer when on_device.
  * Errors: NRR_ERR_INVALID_ARG (null argument, i out of range),
  * NRR_ERR_CUDA. */
 nrr_status nrr_batch_get_u(nrr_batch *b, int i, double *dst, int on_device);
 
-/* Sets u of solve i (padded FP64 layout; inner ghosts ignored) for a warm
+/* Sets u of solve i (the field of paper Sec. 2; padded FP64 layout; inner
+ * ghosts ignored) for a warm
  * start: a following nrr_batch_relax with initial = NRR_INIT_DEVICE starts
  * from the u of every solve with v = eta u.  u: caller-owned, copied.
  * Errors: NRR_ERR_INVALID_ARG (null argument, i out of range),
  * NRR_ERR_CUDA. */
 nrr_status nrr_batch_set_u(nrr_batch *b, int i, const double *u, int on_device);
 
-/* Interior u of every solve as FP32, dst (device) [n][n0*n1*n2] with i0
+/* Interior u (paper Sec. 2) of every solve as FP32, dst (device)
+ * [n][n0*n1*n2] with i0
  * fastest; all solves must have the same size.  Training targets of the
  * surrogate.  Errors: NRR_ERR_INVALID_ARG (null argument, solves of
  * different sizes), NRR_ERR_CUDA. */
 nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
 
-/* Stage kernel of a batch for `mode` (NRR_FP64, or NRR_FP32_DC for its FP32
+/* Stage kernel (paper Alg. 1 RHS, BC and RK substep, fused) of a batch for
+ * `mode` (NRR_FP64, or NRR_FP32_DC for its FP32
  * stages; the FP64 defect evaluations of NRR_FP32_DC use the NRR_FP64
  * setting).  Variant 0 stages each plane of a 32 x 4 column tile through
  * registers into shared memory; variant 1 streams the planes of a block's
@@ -397,7 +403,8 @@ nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
  * Errors: NRR_ERR_INVALID_ARG for other values or an ineligible batch. */
 nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc);
 
-/* Autotuner for the batch's stage kernel (variant and phi planes per block
+/* Autotuner (no paper counterpart; the paper fixes the block, Sec. 4) for
+ * the batch's stage kernel (variant and phi planes per block
  * chunk, as in nrr_batch_set_launch), timed over all solves on the current
  * state (restored afterwards); keeps the fastest for later relaxations.
  * Candidates: variant 0 with zc 2, 4, 8, 16; variant 1 with zc 4, 8, 16 (when
@@ -407,7 +414,8 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
                               int *best_zc, double *best_ms_per_launch,
                               int *best_variant);
 
-/* BF16 tensor-core GEMM used by the surrogate network (tcgen05 MMA with an
+/* BF16 tensor-core GEMM used by the surrogate network (no paper
+ * counterpart: the paper has no learned component) (tcgen05 MMA with an
  * FP32 accumulator in tensor memory, TMA-fed 128-byte-swizzled tiles):
  * D[m][n] = sum_k A[m][k] B[n][k] for row-major BF16 A (M x K) and B
  * (N x K) -- both K-major -- and row-major FP32 D (M x N).  All device
@@ -438,13 +446,15 @@ nrr_status nrr_surrogate_create(int n_in, int hidden, int depth, int n_out,
 nrr_status nrr_surrogate_destroy(nrr_surrogate *s);
 int64_t nrr_surrogate_num_params(const nrr_surrogate *s);
 
-/* Sets the output scaling to the per-output mean and standard deviation of
+/* Surrogate (no paper counterpart).  Sets the output scaling to the
+ * per-output mean and standard deviation of
  * Y (device, [n][n_out] FP32); the network learns (Y - mean)/std.
  * Errors: NRR_ERR_INVALID_ARG (null argument, n < 1), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
                                      int64_t n);
 
-/* `steps` AdamW steps (beta 0.9/0.999, eps 1e-8, decoupled weight decay on
+/* Surrogate training (no paper counterpart): `steps` AdamW steps (beta
+ * 0.9/0.999, eps 1e-8, decoupled weight decay on
  * weights) on minibatches of `batch` rows: step t uses the sample indices
  * order[t*batch .. (t+1)*batch) (device int32; the caller draws the
  * shuffles).  X: device [n][n_in], Y: device [n][n_out].  loss_out
@@ -456,26 +466,30 @@ nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
                                int64_t n, const int32_t *order, int64_t steps,
                                double lr, double weight_decay, float *loss_out);
 
-/* out (device [n][n_out]) = network(X) mapped back through the scaling;
+/* Surrogate inference (no paper counterpart): out (device [n][n_out]) =
+ * network(X) mapped back through the scaling;
  * X device [n][n_in]; any n >= 1 (processed in chunks of `batch` rows).
  * Errors: NRR_ERR_INVALID_ARG (null argument, n < 1), NRR_ERR_TIMEOUT,
  * NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_predict(nrr_surrogate *s, const float *X, int64_t n,
                                  float *out);
 
-/* Loss and parameter gradients of one minibatch (the first `batch` rows of
+/* Surrogate (no paper counterpart): loss and parameter gradients of one
+ * minibatch (the first `batch` rows of
  * X, Y; device) without updating: grads is a host array in the logical
  * packed layout.  For gradient checks.  Errors: NRR_ERR_INVALID_ARG (null
  * argument), NRR_ERR_TIMEOUT, NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_gradients(nrr_surrogate *s, const float *X,
                                    const float *Y, float *grads, double *loss);
 
-/* Current parameters in the logical packed layout (caller-owned host array
+/* Surrogate (no paper counterpart): current parameters in the logical
+ * packed layout (caller-owned host array
  * of nrr_surrogate_num_params() floats).
  * Errors: NRR_ERR_INVALID_ARG (null argument), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_get_params(nrr_surrogate *s, float *params);
 
-/* Warm-start prolongation: u on the fine grid (device, padded FP64, every
+/* Warm-start prolongation (no paper counterpart; it feeds the initial data
+ * of paper Alg. 1's relaxation): u on the fine grid (device, padded FP64, every
  * point written) interpolated trilinearly in the coordinates xx from the
  * coarse interior values uc (device, [n2][n1][n0] FP32) of a grid of the
  * same curvilinear family and parameters; coarse neighbours across the inner
@@ -488,7 +502,8 @@ nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
                        const nrr_grid_desc *fine, double *uf, void *stream);
 
 /* Cumulative number of kernels this library has launched in this process
- * (graph replays count every kernel node). */
+ * (graph replays count every kernel node); a measurement counter with no
+ * paper counterpart.  Cannot fail. */
 int64_t nrr_kernel_launches(void);
 
 /* Diagnostic (the paper has no counterpart): runs one bounded wait of the
