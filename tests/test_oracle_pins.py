@@ -11,6 +11,7 @@ solve of the discrete steady state.
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -22,18 +23,30 @@ pytestmark = pytest.mark.usefixtures("oracle_mod")
 
 
 # ------------------------------------------------------------ FD weights
+def _golden_fd_weights():
+    """Full stencils (offsets -m..m) from tests/golden/fd_weights_centred.txt
+    (Fornberg's table)."""
+    from fractions import Fraction
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "fd_weights_centred.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            order, d, k, w = line.split()
+            rows.setdefault((int(order), int(d)), {})[int(k)] = float(Fraction(w))
+    out = {}
+    for (order, d), wk in rows.items():
+        m = order // 2
+        sign = -1.0 if d == 1 else 1.0
+        out[order, d] = [sign * wk[-k] if k < 0 else wk.get(k, 0.0)
+                         for k in range(-m, m + 1)]
+    return out
+
+
 def test_fd_weights_textbook_values(oracle_mod):
-    O = oracle_mod
-    exp = {
-        (2, 1): [-0.5, 0.0, 0.5],
-        (2, 2): [1.0, -2.0, 1.0],
-        (4, 1): [1 / 12, -2 / 3, 0.0, 2 / 3, -1 / 12],
-        (4, 2): [-1 / 12, 4 / 3, -5 / 2, 4 / 3, -1 / 12],
-        (8, 2): [-1 / 560, 8 / 315, -1 / 5, 8 / 5, -205 / 72, 8 / 5, -1 / 5,
-                 8 / 315, -1 / 560],
-    }
+    exp = _golden_fd_weights()
+    assert len(exp) == 10
     for (order, d), w in exp.items():
-        np.testing.assert_allclose(O.fd_weights(order, d), w, rtol=0,
+        np.testing.assert_allclose(oracle_mod.fd_weights(order, d), w, rtol=0,
                                    atol=1e-14)
 
 
