@@ -311,9 +311,8 @@ nrr_status nrr_autotune_clear(void);
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in
  * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
- * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {4, 8, 16} and block
- * 128 or 256, variant 4,
- * variant 5 with zc in {4, 8, 16} -- skips
+ * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {2, 4, 8, 16} and
+ * block 128 or 256, variant 4, variant 5 with zc in {4, 8, 16} -- skips
  * shapes the grid cannot launch, keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
  * this process, and restores the state it started from.  Needs the

@@ -1114,12 +1114,12 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[21] = {{128, 1, 0},  {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
+  const LaunchCfg cands[23] = {{128, 1, 0},  {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
                                {64, 2, 0},   {128, 4, 0},  {128, 2, 1},  {128, 4, 1},
-                               {128, 8, 1},  {128, 16, 1}, {128, 1, 2},  {128, 4, 3},
-                               {128, 8, 3},  {128, 16, 3}, {256, 4, 3},  {256, 8, 3},
-                               {256, 16, 3}, {128, 1, 4},  {128, 4, 5},  {128, 8, 5},
-                               {128, 16, 5}};
+                               {128, 8, 1},  {128, 16, 1}, {128, 1, 2},  {128, 2, 3},
+                               {128, 4, 3},  {128, 8, 3},  {128, 16, 3}, {256, 2, 3},
+                               {256, 4, 3},  {256, 8, 3},  {256, 16, 3}, {128, 1, 4},
+                               {128, 4, 5},  {128, 8, 5},  {128, 16, 5}};
   for (const LaunchCfg &cand0 : cands) {
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;
