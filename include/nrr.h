@@ -258,7 +258,7 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * / NRR_FP32); the paper fixes one thread block shape (Sec. 4, parallelization
  * strategy), this library offers several. Curvilinear grids: variant 0 = one
  * thread per (i0, i1) column and zc (1, 2 or 4) phi planes, neighbours read
- * through the caches, in blocks of `block` threads (64, 128 or 256; 0 keeps the
+ * through the caches, in blocks of `block` threads (32, 64, 128 or 256; 0 keeps the
  * current size); variant 1 = tiles of 32 x 4 columns staged plane by plane
  * through registers into shared memory, zc (2, 4, 8 or 16) planes per block;
  * variant 2 = one (column, plane) per step of a grid that exactly fills every
@@ -310,7 +310,7 @@ nrr_status nrr_autotune_clear(void);
 /* Autotuner (project-written; the paper fixes its block shape, Sec. 4):
  * times `trial_steps` RK4 steps for each candidate launch shape with CUDA
  * events on the grid's work stream -- variant 0 with (zc, block) in
- * {(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
+ * {(1, 32), (1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (4, 128)}, variant 1 with
  * zc in {2, 4, 8, 16}, variant 2, variant 3 with zc in {2, 4, 8, 16} and
  * block 128 or 256, variant 4, variant 5 with zc in {4, 8, 16} -- skips
  * shapes the grid cannot launch, keeps the fastest for this grid and for

@@ -141,7 +141,7 @@ bool valid_shape(const LaunchCfg &c) {
           ? (c.zc == 2 || c.zc == 4 || c.zc == 8 || c.zc == 16)
           : (c.variant == 2 || c.variant == 4) && c.zc == 1;
   return c.variant >= 0 && c.variant <= 5 && zc_ok &&
-         (c.block == 64 || c.block == 128 || c.block == 256) &&
+         (c.block == 32 || c.block == 64 || c.block == 128 || c.block == 256) &&
          (c.pdl == 0 || c.pdl == 1);
 }
 
@@ -963,8 +963,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
 
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block) {
   TRY(check_grid(g));
-  if (block != 0 && block != 64 && block != 128 && block != 256)
-    return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 64, 128 or 256");
+  if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
+    return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 32, 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
   if (variant < 0 || variant > 5)
@@ -1114,7 +1114,7 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[23] = {{128, 1, 0},  {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
+  const LaunchCfg cands[24] = {{128, 1, 0},  {32, 1, 0},   {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
                                {64, 2, 0},   {128, 4, 0},  {128, 2, 1},  {128, 4, 1},
                                {128, 8, 1},  {128, 16, 1}, {128, 1, 2},  {128, 2, 3},
                                {128, 4, 3},  {128, 8, 3},  {128, 16, 3}, {256, 2, 3},
