@@ -371,6 +371,33 @@ def test_stage_variants_rhs_and_trajectory(gpu, name, variant, zc):
     g.close()
 
 
+def test_column_kernel_block_sizes_agree(gpu):
+    """The column kernel's block size only regroups threads: 32-, 64-,
+    128- and 256-thread blocks give bit-identical trajectories in both
+    precisions on a grid with ragged tiles."""
+    desc = W.grid_desc("sinhsymtp", (44, 26, 6), 8)
+    og = oracle_grid(desc)
+    dt, eta = default_dt_eta(og)
+    u0 = og.fill_inner_ghosts(W.smooth_random_field(desc, seed=61, amplitude=0.1))
+    v0 = W.smooth_random_field(desc, seed=62, amplitude=0.05)
+    out = {}
+    for block in (32, 64, 128, 256):
+        g = nrr.Grid(desc)
+        g.set_punctures(Q4)
+        for mode in ("fp64", "fp32"):
+            g.set_launch(1, mode, 0, block)
+            g.set_state(_dev(u0), _dev(v0))
+            g.step(11, dt, eta, mode=mode)
+            ug, vg = torch.empty_like(_dev(u0)), torch.empty_like(_dev(u0))
+            g.get_state(ug, vg)
+            out[block, mode] = (ug.cpu(), vg.cpu())
+        g.close()
+    for block in (32, 64, 256):
+        for mode in ("fp64", "fp32"):
+            assert torch.equal(out[block, mode][0], out[128, mode][0]), (block, mode)
+            assert torch.equal(out[block, mode][1], out[128, mode][1]), (block, mode)
+
+
 @pytest.mark.parametrize("coord,n,zc", [("sinhsymtp", (64, 24, 8), 4),
                                          ("spherical", (64, 32, 8), 2),
                                          ("sinhspherical", (64, 40, 8), 16)])
