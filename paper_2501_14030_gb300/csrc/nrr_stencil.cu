@@ -14,12 +14,13 @@
 // 5*ng+1 fused multiply-adds on u plus the source term.
 //
 // Stage-kernel variants (chosen per grid by the autotuner): the column kernel
-// (neighbours through the caches), register-staged tiles, a persistent
-// grid-strided column kernel, tiles fed by tensor (TMA) copies through an
-// mbarrier ring, and a multi-stage cooperative kernel that runs whole chunks
-// of RK4 steps with grid barriers; Cartesian grids have a column kernel and a
-// tensor-copy kernel with separate ghost-shell blocks.  Each stage kernel
-// may be launched with programmatic dependent launch.
+// (neighbours through the caches, 32-256 threads per block), register-staged
+// tiles, a persistent grid-strided column kernel, 32 x 4 or (FP32) 32 x 8
+// tiles fed by tensor (TMA) copies through an mbarrier ring, and multi-stage
+// cooperative kernels (column items or tensor-copy tiles) that run whole
+// chunks of RK4 steps with grid barriers; Cartesian grids have a column
+// kernel and a tensor-copy kernel with separate ghost-shell blocks.  Each
+// stage kernel may be launched with programmatic dependent launch.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
