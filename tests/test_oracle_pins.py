@@ -278,6 +278,30 @@ def test_rk4_update_on_linear_ode(oracle_mod):
     assert np.abs(v[sl] - v0).max() < 1e-10
 
 
+# ------------------------------------------------ wave speed and time step
+def test_wave_speed_makes_the_local_courant_number_uniform(oracle_mod):
+    """Sec. 2: the wave speed is proportional to the local grid spacing, so
+    with dt = CFL x (smallest spacing) every interior point runs at the same
+    Courant number c dt / ds = CFL.  The spacing is the smallest of
+    h_i dxx_i with the textbook spherical scale factors (1, r, r sin theta);
+    c is 1 where it is smallest and above 1 elsewhere."""
+    O = oracle_mod
+    g = oracle_grid(W.grid_desc("spherical", (40, 22, 8), 8, rmax=64.0))
+    inner = g.field("kind") == O.INTERIOR
+    r, th = g.field("xx0"), g.field("xx1")
+    d0, d1, d2 = g.dxx
+    ds = np.minimum(np.minimum(d0 * np.ones_like(r), d1 * np.abs(r)),
+                    d2 * np.abs(r * np.sin(th)))
+    np.testing.assert_allclose(g.field("dsmin")[inner], ds[inner], rtol=1e-13)
+    assert g.dsmin == pytest.approx(ds[inner].min(), rel=1e-13)
+    # the smallest cell: first radial point next to the axis, h2 dphi
+    assert g.dsmin == pytest.approx((d0 / 2) * np.sin(d1 / 2) * d2, rel=1e-12)
+    c = g.field("c")[inner]
+    assert c.min() == pytest.approx(1.0, rel=1e-14) and (c >= 1.0 - 1e-14).all()
+    cfl = 0.5
+    np.testing.assert_allclose(c * (cfl * g.dsmin) / ds[inner], cfl, rtol=1e-13)
+
+
 # ------------------------------------------------ radiation condition
 def test_radiation_condition_on_exact_profiles(oracle_mod):
     """Outer ghosts: for f = const the backward difference vanishes and
