@@ -328,6 +328,10 @@ VARIANT_CASES = {
     "sinh_64x20x8_o8": (W.grid_desc("sinhsymtp", (64, 20, 8), 8), Q4),
     "sph_64x20x8_o8": (W.grid_desc("spherical", (64, 20, 8), 8, rmax=64.0), Q4),
     "sinhsph_64x20x8_o8": (W.grid_desc("sinhspherical", (64, 20, 8), 8), Q4),
+    # fewer phi planes than the stencil radius: the phi stencil and the
+    # phi + pi images wrap around the whole circle more than once
+    "sinh_32x8x2_o8": (W.grid_desc("sinhsymtp", (32, 8, 2), 8), Q4),
+    "sph_64x12x4_o8": (W.grid_desc("spherical", (64, 12, 4), 8, rmax=64.0), Q4),
 }
 
 
