@@ -462,3 +462,33 @@ def test_linear_rhs_matches_relaxation_rhs_structure(oracle_mod):
     kd, kw = g.linear_rhs(z, beta, 0.3, z, z)
     assert np.array_equal(ku, kd)
     np.testing.assert_allclose(kw, kv, rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------ recorded reference
+def test_oracle_matches_its_recorded_reference(oracle_mod):
+    """Regression record (not an independent pin): the oracle's relaxation
+    of the small equal-mass workload as tests/golden/make_oracle_reference.py
+    wrote it.  A change of the oracle's arithmetic must regenerate the file
+    and name, in its commit, the passage that justifies it."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location(
+        "make_oracle_reference", os.path.join(here, "make_oracle_reference.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    rec = {}
+    samples = {}
+    for line in open(os.path.join(here, "oracle_small_equal_mass.txt")):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "u":
+            samples[tuple(int(x) for x in f[1:4])] = float(f[4])
+        else:
+            rec[f[0]] = float(f[1])
+    iters, norm, status, got = mod.compute()
+    assert status == 0 and iters == int(rec["steps"])
+    assert norm == pytest.approx(rec["norm"], rel=1e-9)
+    assert set(got) == set(samples)
+    for k, val in samples.items():
+        assert got[k] == pytest.approx(val, rel=1e-11, abs=1e-20), k
