@@ -327,6 +327,52 @@ def test_radiation_condition_on_exact_profiles(oracle_mod):
     np.testing.assert_allclose(drb[inner], dnum, rtol=1e-4)
 
 
+def test_cartesian_radiation_condition_on_polynomials(oracle_mod):
+    """Cartesian outer ghosts (every ghost of a Cartesian grid):
+    d_r f = sum_i (x^i/r) D_i f with D_i one-sided inward (second order)
+    along the directions in which the point lies outside, centred otherwise.
+    Both second-order differences are exact on polynomials of degree <= 2,
+    so for f = const, f = x^i and f = x^2 the condition is exact:
+    k = -c f/r, -c (x^i/r + x^i/r), -c (2 x^2/r + x^2/r).  On f = x^3 the
+    two stencils differ by known amounts -- one-sided 3x^2 - 2h^2, centred
+    3x^2 + h^2 (Taylor expansion) -- which pins which one is used where,
+    including edge and corner ghosts that lie outside in y or z only."""
+    O = oracle_mod
+    g = oracle_grid(W.grid_desc("cartesian", (10, 8, 6), 4, xmax=4.0))
+    alpha, beta = g.zeros(), g.zeros()
+    outer = g.field("kind") == O.OUTER
+    assert outer.sum() == g.npts - 10 * 8 * 6
+    c, r = g.field("c"), g.field("r")
+    pos = [g.field("x"), g.field("y"), g.field("z")]
+    ku, _ = g.rhs(alpha, beta, 0.0, np.full(g.shape, 0.75), g.zeros())
+    np.testing.assert_allclose(ku[outer], (-c * 0.75 / r)[outer], rtol=1e-13)
+    for i in range(3):
+        f = pos[i].copy()
+        ku, kv = g.rhs(alpha, beta, 0.0, f, f.copy())
+        expect = -c * 2.0 * f / r
+        np.testing.assert_allclose(ku[outer], expect[outer], rtol=1e-12,
+                                   atol=1e-14)
+        np.testing.assert_allclose(kv[outer], expect[outer], rtol=1e-12,
+                                   atol=1e-14)
+        f = pos[i] ** 2
+        ku, _ = g.rhs(alpha, beta, 0.0, f, g.zeros())
+        np.testing.assert_allclose(ku[outer], (-c * 3.0 * f / r)[outer],
+                                   rtol=1e-12, atol=1e-13)
+    # f = x^3: which stencil along x depends on whether the point lies
+    # outside the interior range in x (one-sided) or not (centred)
+    x, h = pos[0], g.dxx[0]
+    i0 = np.broadcast_to(np.arange(g.s[0])[None, None, :], g.shape)
+    out_x = (i0 < g.ng) | (i0 >= g.ng + g.n[0])
+    Dx = np.where(out_x, 3 * x ** 2 - 2 * h ** 2, 3 * x ** 2 + h ** 2)
+    ku, _ = g.rhs(alpha, beta, 0.0, x ** 3, g.zeros())
+    expect = -c * (x / r * Dx + x ** 3 / r)
+    np.testing.assert_allclose(ku[outer], expect[outer], rtol=1e-11,
+                               atol=1e-12)
+    # some outer ghosts lie outside only in y or z: their x difference is the
+    # centred one
+    assert (outer & ~out_x).sum() > 0
+
+
 # ------------------------------------------------------------ norm
 def test_norm_of_unit_residual_is_one(oracle_mod):
     g = oracle_grid(W.grid_desc("sinhsymtp", (32, 16, 4), 4))
@@ -334,6 +380,36 @@ def test_norm_of_unit_residual_is_one(oracle_mod):
     H = np.zeros(g.shape)
     H[g.field("r") >= 100.0] = 7.0
     assert g.norm(H) == 0.0
+
+
+def test_norm_weights_cells_by_their_volume(oracle_mod):
+    """The norm is a volume average: sqrt(sum H^2 J / sum J) over r < r_int
+    with J = h0 h1 h2, the reference-metric volume factor.  On a Spherical
+    grid (J = r^2 sin(theta)) with H = 1 inside r < R1 and 0 elsewhere it is
+    the square root of the volume fraction (R1/R)^3 up to the midpoint rule.
+    With unit radial cells and R1 = K1, R = K on cell faces the midpoint sum
+    of r^2 over the first K cells is K^3/3 - K/12 exactly, and the theta and
+    phi sums cancel in the ratio, so the norm squared is
+    (K1^3 - K1/4) / (K^3 - K/4).  An unweighted mean would give K1/K; a
+    1/J weight something larger still."""
+    K1, K = 10, 40
+    g = oracle_grid(W.grid_desc("spherical", (64, 16, 4), 4, rmax=64.0))
+    assert g.dxx[0] == 1.0
+    r = g.field("r")
+    H = np.where(r < K1, 1.0, 0.0)
+    nrm = g.norm(H, r_int=float(K))
+    exact = math.sqrt((K1 ** 3 - K1 / 4) / (K ** 3 - K / 4))
+    assert nrm == pytest.approx(exact, rel=1e-13)
+    assert nrm == pytest.approx((K1 / K) ** 1.5, rel=2e-3)
+    assert abs(nrm - math.sqrt(K1 / K)) > 0.3
+    # the same volume fraction on a SinhSymTP grid (J from its own scale
+    # factors), where the cell faces do not fall on r = R1: within the
+    # resolution of the shell r = R1
+    gs = oracle_grid(W.grid_desc("sinhsymtp", (128, 64, 4), 4, amax=64.0,
+                                 bscale=1.0, sinhwaa=0.4))
+    rs = gs.field("r")
+    nrm = gs.norm(np.where(rs < 8.0, 1.0, 0.0), r_int=24.0)
+    assert nrm == pytest.approx((8.0 / 24.0) ** 1.5, rel=0.03)
 
 
 # ------------------------------------------------- special solutions
