@@ -538,10 +538,15 @@ nrr_status nrr_selftest_wait_expiry(int which, void *stream, int *expired);
  * overlap on the GPU (on different streams, or from several host threads)
  * race on it and must be serialised by the caller.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before capturing any stream.
+ * device current; make that first call before capturing any stream.  The
+ * address is remembered with the device's context and looked up again when
+ * another context is current (after cudaDeviceReset, for instance).
+ * The caller's buffers cannot be checked here: u and h_out must hold
+ * s0*s1*s2 doubles and norm_out at least one.
  * Coordinates: SinhSymTP, Spherical and Cartesian (not SinhSpherical).
- * Errors: NRR_ERR_INVALID_ARG (bad descriptor, punctures or size),
- * NRR_ERR_CUDA (lookup or launch failure). */
+ * Errors: NRR_ERR_INVALID_ARG (null pointer, a descriptor the grid calls
+ * reject -- see nrr_create_grid --, SinhSpherical, punctures, r_int <= 0,
+ * n0*n1 beyond the scratch), NRR_ERR_CUDA (lookup or launch failure). */
 nrr_status nrr_residual_noalloc(const nrr_grid_desc *d, int npunct,
                                 const nrr_puncture *p, const double *u,
                                 double r_int, double *norm_out, double *h_out,

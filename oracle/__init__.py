@@ -20,6 +20,7 @@ are stated in ``nrr_oracle.c`` beside the code that implements them.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -30,7 +31,7 @@ _SRC = os.path.join(_HERE, "nrr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-SINHSYMTP, SPHERICAL, CARTESIAN, SINHSPHERICAL = 0, 1, 2, 3
+SINHSYMTP, SPHERICAL, CARTESIAN, SINHSPHERICAL, SINHCYLINDRICAL = 0, 1, 2, 3, 4
 INTERIOR, OUTER, INNER = 0, 1, 2
 CONVERGED, NOT_CONVERGED, DIVERGED = 0, 1, 2
 
@@ -59,7 +60,8 @@ class _Desc(C.Structure):
     _fields_ = [("coord", C.c_int), ("n", C.c_int * 3), ("order", C.c_int),
                 ("amax", C.c_double), ("bscale", C.c_double),
                 ("sinhwaa", C.c_double), ("rmax", C.c_double),
-                ("xmax", C.c_double)]
+                ("xmax", C.c_double), ("zmax", C.c_double),
+                ("sinhwz", C.c_double)]
 
 
 class Puncture(C.Structure):
@@ -155,9 +157,10 @@ class Grid:
 
     def __init__(self, coord: int, n, order: int, amax: float = 1.0e4,
                  bscale: float = 5.0, sinhwaa: float = 0.07,
-                 rmax: float = 64.0, xmax: float = 32.0):
+                 rmax: float = 64.0, xmax: float = 32.0, zmax: float = 1.0e4,
+                 sinhwz: float = 0.07):
         d = _Desc(coord, (C.c_int * 3)(*[int(v) for v in n]), int(order),
-                  amax, bscale, sinhwaa, rmax, xmax)
+                  amax, bscale, sinhwaa, rmax, xmax, zmax, sinhwz)
         err = C.create_string_buffer(256)
         h = lib().or_grid_new(C.byref(d), err, 256)
         if not h:
@@ -265,3 +268,27 @@ class Grid:
         if it < 0:
             raise RuntimeError("oracle newton failed (%d)" % it)
         return it, step.value
+
+
+_COORD_NAMES = {"sinhsymtp": SINHSYMTP, "spherical": SPHERICAL,
+                "cartesian": CARTESIAN, "sinhspherical": SINHSPHERICAL,
+                "sinhcylindrical": SINHCYLINDRICAL}
+
+
+def grid_from_desc(desc: dict) -> Grid:
+    """Oracle grid for a descriptor dict: coord name, n, order and the map
+    parameters amax, bscale, sinhwaa, rmax, xmax (and zmax, sinhwz)."""
+    return Grid(_COORD_NAMES[desc["coord"]], desc["n"], desc["order"],
+                amax=desc["amax"], bscale=desc["bscale"],
+                sinhwaa=desc["sinhwaa"], rmax=desc["rmax"], xmax=desc["xmax"],
+                zmax=desc.get("zmax", 1.0e4), sinhwz=desc.get("sinhwz", 0.07))
+
+
+def default_dt_eta(og: Grid, cfl: float = 0.5) -> tuple[float, float]:
+    """Time step and damping of the relaxation: dt = cfl * (smallest local
+    spacing), so that one step satisfies the CFL limit at every point once
+    the wave speed follows the local spacing (Sec. 2); eta dt =
+    2 pi cfl / n0, the damping reading (critical damping of the longest
+    mode along xx0)."""
+    dt = cfl * og.dsmin
+    return dt, 2.0 * math.pi * cfl / (og.n[0] * dt)

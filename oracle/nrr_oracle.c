@@ -162,6 +162,36 @@ static void geom_sinhspherical(const or_desc *d, double x0, double x1,
   o->drdxx0 = rp;
 }
 
+/* SinhCylindrical, stored as (rho, z, ph) so that the periodic direction is
+ * the third: rho = AMAX sinh(xx0/w)/sinh(1/w) (xx0 in [0,1]),
+ * z = ZMAX sinh(xx1/wz)/sinh(1/wz) (xx1 in [-1,1]), ph = xx2;
+ * x = rho cos ph, y = rho sin ph.  h = (rho', z', rho); with
+ * J = rho' z' rho,
+ *   J/h0^2 = z' rho / rho'  =>  g0 = 1/(rho rho') - rho''/rho'^3,
+ *   J/h1^2 = rho' rho / z'  =>  g1 = -z''/z'^3,
+ *   J/h2^2 independent of ph => g2 = 0.                                    */
+static void geom_sinhcylindrical(const or_desc *d, double x0, double x1,
+                                 double x2, point_geom *o) {
+  double w = d->sinhwaa, wz = d->sinhwz;
+  double rho = d->amax * sinh(x0 / w) / sinh(1.0 / w);
+  double rhop = d->amax * cosh(x0 / w) / (w * sinh(1.0 / w));
+  double rhopp = rho / (w * w);
+  double z = d->zmax * sinh(x1 / wz) / sinh(1.0 / wz);
+  double zp = d->zmax * cosh(x1 / wz) / (wz * sinh(1.0 / wz));
+  double zpp = z / (wz * wz);
+  o->x = rho * cos(x2);
+  o->y = rho * sin(x2);
+  o->z = z;
+  o->r = sqrt(rho * rho + z * z);
+  o->h[0] = rhop;
+  o->h[1] = zp;
+  o->h[2] = rho;
+  o->gl[0] = 1.0 / (rho * rhop) - rhopp / (rhop * rhop * rhop);
+  o->gl[1] = -zpp / (zp * zp * zp);
+  o->gl[2] = 0.0;
+  o->drdxx0 = rhop;  /* d rho / d xx0; the radiation condition uses both */
+}
+
 static void geom_cartesian(double x0, double x1, double x2, point_geom *o) {
   o->x = x0;
   o->y = x1;
@@ -182,6 +212,8 @@ static void geom_at(const or_desc *d, double x0, double x1, double x2,
     geom_spherical(x0, x1, x2, o);
   else if (d->coord == OR_SINHSPHERICAL)
     geom_sinhspherical(d, x0, x1, x2, o);
+  else if (d->coord == OR_SINHCYLINDRICAL)
+    geom_sinhcylindrical(d, x0, x1, x2, o);
   else
     geom_cartesian(x0, x1, x2, o);
 }
@@ -205,6 +237,9 @@ static void cart_to_xx(const or_desc *d, double x, double y, double z,
     double w = d->sinhwaa;
     xx[0] = w * asinh(sqrt(rho2 + z * z) * sinh(1.0 / w) / d->amax);
     xx[1] = atan2(rho, z);
+  } else if (d->coord == OR_SINHCYLINDRICAL) {
+    xx[0] = d->sinhwaa * asinh(rho * sinh(1.0 / d->sinhwaa) / d->amax);
+    xx[1] = d->sinhwz * asinh(z * sinh(1.0 / d->sinhwz) / d->zmax);
   } else {
     xx[0] = sqrt(rho2 + z * z);
     xx[1] = atan2(rho, z);
@@ -220,10 +255,14 @@ static void grid_dims(const or_desc *d, double xxmin[3], double xxmax[3]) {
     return;
   }
   xxmin[0] = 0.0;
-  xxmax[0] = (d->coord == OR_SINHSYMTP || d->coord == OR_SINHSPHERICAL) ? 1.0
-                                                                       : d->rmax;
+  xxmax[0] = (d->coord == OR_SINHSYMTP || d->coord == OR_SINHSPHERICAL ||
+              d->coord == OR_SINHCYLINDRICAL) ? 1.0 : d->rmax;
   xxmin[1] = 0.0;
   xxmax[1] = OR_PI;
+  if (d->coord == OR_SINHCYLINDRICAL) {
+    xxmin[1] = -1.0;
+    xxmax[1] = 1.0;
+  }
   xxmin[2] = -OR_PI;
   xxmax[2] = OR_PI;
 }
@@ -259,8 +298,11 @@ or_grid *or_grid_new(const or_desc *d, char *err, int errlen) {
   g->d = *d;
   if (d->order < 2 || d->order > 12 || (d->order & 1))
     FAIL("unsupported FD order %d", d->order);
-  if (d->coord < OR_SINHSYMTP || d->coord > OR_SINHSPHERICAL)
+  if (d->coord < OR_SINHSYMTP || d->coord > OR_SINHCYLINDRICAL)
     FAIL("unknown coordinate system %d", d->coord);
+  if (d->coord == OR_SINHCYLINDRICAL &&
+      !(d->amax > 0 && d->sinhwaa > 0 && d->zmax > 0 && d->sinhwz > 0))
+    FAIL("SinhCylindrical needs amax, sinhwaa, zmax, sinhwz > 0");
   g->ng = d->order / 2;
   for (int i = 0; i < 3; i++) {
     if (d->n[i] < 1) FAIL("n[%d] must be positive", i);
@@ -323,6 +365,11 @@ or_grid *or_grid_new(const or_desc *d, char *err, int errlen) {
           g->kind[p] = OR_INTERIOR;
         else if (d->coord == OR_CARTESIAN)
           g->kind[p] = OR_OUTER;
+        else if (d->coord == OR_SINHCYLINDRICAL)
+          /* rho < 0 and ph outside [-pi, pi) are images; every other
+           * ghost lies beyond the cylinder's side or its ends */
+          g->kind[p] = (i0 >= g->ng && in_interior(g, i2, 2)) ? OR_OUTER
+                                                               : OR_INNER;
         else if (i0 >= g->ng + d->n[0] && in_interior(g, i1, 1) &&
                  in_interior(g, i2, 2))
           g->kind[p] = OR_OUTER;
@@ -357,8 +404,11 @@ or_grid *or_grid_new(const or_desc *d, char *err, int errlen) {
       if (k == 2) k_int = ((k_int % d->n[2]) + d->n[2]) % d->n[2];
       ii[k] = k_int + g->ng;
     }
-    if (ii[0] < g->ng || ii[0] >= g->s[0] || !in_interior(g, ii[1], 1) ||
-        !in_interior(g, ii[2], 2))
+    /* (a SinhCylindrical image may lie beyond the ends in z: i1 spans the
+     * padded range there) */
+    int i1_ok = d->coord == OR_SINHCYLINDRICAL ? (ii[1] >= 0 && ii[1] < g->s[1])
+                                               : in_interior(g, ii[1], 1);
+    if (ii[0] < g->ng || ii[0] >= g->s[0] || !i1_ok || !in_interior(g, ii[2], 2))
       FAIL("ghost %ld: image index out of range", p);
     long q = pidx(g, ii[0], ii[1], ii[2]);
     double scale = 1.0 + g->r[p];
@@ -505,6 +555,29 @@ void or_fill_inner_ghosts(const or_grid *g, double *f) {
 static double radiation_df(const or_grid *g, const double *f, int i0, int i1,
                            int i2) {
   long p = pidx(g, i0, i1, i2);
+  if (g->d.coord == OR_SINHCYLINDRICAL) {
+    /* d_r f = (rho/r) d_rho f + (z/r) d_z f with d_rho = (1/rho') d_xx0 and
+     * d_z = (1/z') d_xx1; each difference one-sided inward where the point
+     * lies beyond that direction's outer boundary, centred otherwise (an
+     * xx0 neighbour at rho < 0 is an inner ghost, filled from its image). */
+    int ii[2] = {i0, i1};
+    long stride[2] = {1, g->s[0]};
+    double scale[2] = {g->x[p] * cos(g->xx[2][p]) + g->y[p] * sin(g->xx[2][p]),
+                       g->z[p]};  /* rho and z */
+    double dr = 0.0;
+    for (int dir = 0; dir < 2; dir++) {
+      long st = stride[dir];
+      double D;
+      if (ii[dir] >= g->ng + g->d.n[dir])
+        D = (3.0 * f[p] - 4.0 * f[p - st] + f[p - 2 * st]) / (2.0 * g->dxx[dir]);
+      else if (ii[dir] < g->ng)
+        D = -(3.0 * f[p] - 4.0 * f[p + st] + f[p + 2 * st]) / (2.0 * g->dxx[dir]);
+      else
+        D = (f[p + st] - f[p - st]) / (2.0 * g->dxx[dir]);
+      dr += scale[dir] / g->r[p] * D / g->h[dir][p];
+    }
+    return dr + f[p] / g->r[p];
+  }
   if (g->d.coord != OR_CARTESIAN) {
     double db = (3.0 * f[p] - 4.0 * f[p - 1] + f[p - 2]) / (2.0 * g->dxx[0]);
     return db / g->drdxx0[p] + f[p] / g->r[p];
@@ -771,12 +844,14 @@ int or_newton(const or_grid *g, const double *alpha, const double *beta,
             long supp[7];
             int ns = 0;
             supp[ns++] = p;
-            if (g->d.coord != OR_CARTESIAN) {
+            if (g->d.coord != OR_CARTESIAN &&
+                g->d.coord != OR_SINHCYLINDRICAL) {
               supp[ns++] = p - 1;
               supp[ns++] = p - 2;
             } else {
               int ii[3] = {i0, i1, i2};
-              for (int dir = 0; dir < 3; dir++) {
+              int ndir = g->d.coord == OR_CARTESIAN ? 3 : 2;
+              for (int dir = 0; dir < ndir; dir++) {
                 long st = stride[dir];
                 if (ii[dir] >= g->ng + g->d.n[dir]) {
                   supp[ns++] = p - st;

@@ -19,20 +19,24 @@
 extern "C" {
 #endif
 
-enum { OR_SINHSYMTP = 0, OR_SPHERICAL = 1, OR_CARTESIAN = 2, OR_SINHSPHERICAL = 3 };
+enum { OR_SINHSYMTP = 0, OR_SPHERICAL = 1, OR_CARTESIAN = 2, OR_SINHSPHERICAL = 3,
+       OR_SINHCYLINDRICAL = 4 };
 enum { OR_INTERIOR = 0, OR_OUTER = 1, OR_INNER = 2 };
 enum { OR_CONVERGED = 0, OR_NOT_CONVERGED = 1, OR_DIVERGED = 2 };
 
 typedef struct {
   int coord;       /* OR_SINHSYMTP / OR_SPHERICAL / OR_CARTESIAN /
-                      OR_SINHSPHERICAL                                 */
+                      OR_SINHSPHERICAL / OR_SINHCYLINDRICAL            */
   int n[3];        /* interior points per direction                      */
   int order;       /* centred finite-difference order: 2,4,6,8,10,12     */
-  double amax;     /* SinhSymTP outer extent                              */
+  double amax;     /* SinhSymTP / SinhSpherical outer extent; SinhCylindrical
+                      outer cylindrical radius                            */
   double bscale;   /* SinhSymTP focal half-distance                       */
-  double sinhwaa;  /* SinhSymTP sinh width                                */
+  double sinhwaa;  /* sinh width of xx0                                   */
   double rmax;     /* Spherical outer radius                              */
   double xmax;     /* Cartesian half-width                                */
+  double zmax;     /* SinhCylindrical half-height                         */
+  double sinhwz;   /* SinhCylindrical sinh width of xx1 (the z direction) */
 } or_desc;
 
 typedef struct {

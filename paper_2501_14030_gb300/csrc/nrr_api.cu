@@ -206,7 +206,9 @@ size_t footprint_bytes(const Geo &geo) {
   return b;
 }
 
-nrr_status validate_desc(const nrr_grid_desc *d) {
+}  // namespace
+
+nrr_status nrr::check_grid_desc(const nrr_grid_desc *d) {
   if (!d) return fail(NRR_ERR_INVALID_ARG, "null grid descriptor");
   if (d->coord < NRR_SINHSYMTP || d->coord > NRR_SINHSPHERICAL)
     return fail(NRR_ERR_INVALID_ARG, "unknown coordinate system %d", d->coord);
@@ -217,6 +219,12 @@ nrr_status validate_desc(const nrr_grid_desc *d) {
   for (int i = 0; i < 3; i++)
     if (d->n[i] < 1 || d->n[i] > (1 << 16))
       return fail(NRR_ERR_INVALID_ARG, "n[%d] = %d out of range", i, d->n[i]);
+  // Per-column arrays are indexed with 32-bit integers: the padded plane
+  // s0*s1 (computed in 64 bits here) must fit.
+  const int64_t plane = (int64_t)(d->n[0] + 2 * ng) * (int64_t)(d->n[1] + 2 * ng);
+  if (plane > (int64_t)INT32_MAX)
+    return fail(NRR_ERR_INVALID_ARG, "padded plane s0*s1 = %lld exceeds 2^31 - 1",
+                (long long)plane);
   if (d->coord != NRR_CARTESIAN) {
     if (d->n[2] & 1)
       return fail(NRR_ERR_INVALID_ARG, "n2 must be even on curvilinear grids");
@@ -241,7 +249,7 @@ nrr_status validate_desc(const nrr_grid_desc *d) {
   return NRR_OK;
 }
 
-Geo make_geo(const nrr_grid_desc *d) {
+Geo nrr::grid_geo(const nrr_grid_desc *d) {
   Geo g{};
   g.coord = d->coord;
   g.n0 = d->n[0];
@@ -278,6 +286,8 @@ Geo make_geo(const nrr_grid_desc *d) {
   g.sinhwaa = d->sinhwaa;
   return g;
 }
+
+namespace {
 
 template <typename R>
 StageArgs<R> stage_args(const nrr_grid *g, const FieldSet<R> &f,
@@ -621,9 +631,12 @@ nrr_status nrr_default_opts(nrr_relax_opts *o) {
 }
 
 nrr_status nrr_image_map(const nrr_grid_desc *d, int32_t *out) {
-  TRY(validate_desc(d));
+  TRY(check_grid_desc(d));
   if (!out) return fail(NRR_ERR_INVALID_ARG, "null output");
-  Geo g = make_geo(d);
+  Geo g = grid_geo(d);
+  if (g.npts > (int64_t)INT32_MAX)
+    return fail(NRR_ERR_INVALID_ARG, "grid of %lld points: indices exceed int32",
+                (long long)g.npts);
   for (int i2 = 0; i2 < g.s2; i2++)
     for (int i1 = 0; i1 < g.s1; i1++)
       for (int i0 = 0; i0 < g.s0; i0++) {
@@ -639,8 +652,8 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
                            nrr_grid **out) {
   if (!out) return fail(NRR_ERR_INVALID_ARG, "null output handle");
   *out = nullptr;
-  TRY(validate_desc(d));
-  Geo geo = make_geo(d);
+  TRY(check_grid_desc(d));
+  Geo geo = grid_geo(d);
   if (geo.npts > (int64_t)1 << 31)
     return fail(NRR_ERR_INVALID_ARG, "grid of %lld points exceeds 2^31",
                 (long long)geo.npts);

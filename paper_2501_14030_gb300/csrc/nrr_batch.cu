@@ -441,30 +441,6 @@ nrr_status balloc(nrr_batch *b, T **p, size_t count) {
   return NRR_OK;
 }
 
-Geo batch_geo(const nrr_grid_desc &d) {
-  Geo g{};
-  g.coord = d.coord;
-  g.n0 = d.n[0];
-  g.n1 = d.n[1];
-  g.n2 = d.n[2];
-  g.ng = d.fd_order / 2;
-  g.s0 = g.n0 + 2 * g.ng;
-  g.s1 = g.n1 + 2 * g.ng;
-  g.s2 = g.n2 + 2 * g.ng;
-  g.ncol = g.s0 * g.s1;
-  g.npts = (int64_t)g.ncol * g.s2;
-  g.xxmin[0] = 0.0;
-  g.dxx[0] = ((d.coord == NRR_SINHSYMTP || d.coord == NRR_SINHSPHERICAL) ? 1.0 : d.rmax) /
-             g.n0;
-  g.xxmin[1] = 0.0;
-  g.dxx[1] = M_PI / g.n1;
-  g.xxmin[2] = -M_PI;
-  g.dxx[2] = 2.0 * M_PI / g.n2;
-  g.amax = d.amax;
-  g.bscale = d.bscale;
-  g.sinhwaa = d.sinhwaa;
-  return g;
-}
 
 // Block map over `per_solve(s)` items of every solve, `bs` items per block;
 // ranges[s] = (first block of s, its block count).
@@ -725,6 +701,10 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
   size_t bytes = 0;
   for (int s = 0; s < n; s++) {
     const nrr_grid_desc &d = descs[s];
+    {
+      nrr_status st = check_grid_desc(&d);
+      if (st != NRR_OK) return st;
+    }
     if (d.coord != NRR_SINHSYMTP && d.coord != NRR_SPHERICAL &&
         d.coord != NRR_SINHSPHERICAL)
       return bfail(NRR_ERR_INVALID_ARG,
@@ -746,7 +726,7 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
     for (int a = 0; a < npunct[s]; a++)
       if (!(punct[s][a].m > 0.0))
         return bfail(NRR_ERR_INVALID_ARG, "solve %d: puncture mass must be positive", s);
-    Geo g = batch_geo(d);
+    Geo g = grid_geo(&d);
     total += g.npts;
     nint += (int64_t)g.n0 * g.n1 * g.n2;
     size_t per = (flags & 1) ? (12 * 8 + 11 * 4) : (6 * 8 + 11 * 4);
@@ -778,7 +758,7 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
     // arenas
     int64_t ctot = 0;
     for (int s = 0; s < n; s++) {
-      b->geos.push_back(batch_geo(descs[s]));
+      b->geos.push_back(grid_geo(&descs[s]));
       ctot += b->geos[s].ncol;
     }
     const int n64 = b->with_fp64 ? 12 : 6;

@@ -3,7 +3,7 @@
 // K-major BF16 in global memory.
 //
 // One CTA computes a 128 x BN tile.  Warp 0 (one lane) streams 128x64 and
-// BNx64 operand tiles into a 4-stage shared-memory ring with TMA
+// BNx64 operand tiles into a STAGES-deep (3) shared-memory ring with TMA
 // (128-byte swizzle); warp 1 (one lane) issues tcgen05.mma (M=128, N=BN,
 // K=16 per instruction) into an FP32 accumulator in tensor memory and
 // releases each stage with tcgen05.commit; then all four warps read the

@@ -4,12 +4,22 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/nrr.h"
 #include "nrr_common.cuh"
 
 namespace nrr {
 
 // Sets the calling thread's message returned by nrr_last_error().
 void set_last_error(const char *msg);
+
+// The one check of a grid descriptor that every entry point taking one
+// uses: known coordinates, FD order 4/8/10, sizes (curvilinear: even n2,
+// n0 and n1 >= fd_order/2; Cartesian: n >= 2; each n <= 65536 and the
+// padded plane s0*s1 below 2^31, computed in 64 bits) and positive map
+// parameters.  NRR_OK, or NRR_ERR_INVALID_ARG with nrr_last_error() set.
+nrr_status check_grid_desc(const nrr_grid_desc *d);
+// Padded sizes, coordinate ranges and spacings of a checked descriptor.
+Geo grid_geo(const nrr_grid_desc *d);
 
 // The driver's cuTensorMapEncodeTiled (as a plain pointer), or null.
 void *tensor_map_encoder();

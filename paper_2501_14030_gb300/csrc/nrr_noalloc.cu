@@ -11,6 +11,7 @@
 // recomputed per point, and the only scratch -- the per-block partial sums of
 // the norm -- lives in the file-scope array below, which every GPU that loads
 // the library holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -40,18 +41,45 @@ nrr_status fail(nrr_status s, const char *fmt, ...) {
 
 // Device address of the scratch array, looked up once per device with that
 // device current.  The host-side symbol is only a stand-in and must never be
-// passed to a kernel.
+// passed to a kernel.  The address belongs to the device's context: it is
+// remembered together with that context, and looked up again when the
+// current context differs (after cudaDeviceReset, for instance, the runtime
+// creates a new primary context and reloads the module).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
 
 cudaError_t scratch_for_device(int dev, double **out) {
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  // No context current yet on this thread (ctx null), a context other than
+  // the remembered one, or no lookup so far: look the address up.  The
+  // lookup itself makes the device's primary context current.
+  if (!g_scratch_ptr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    if (!get || get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
     g_scratch_ptr[dev] = static_cast<double *>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -236,63 +264,31 @@ extern "C" nrr_status nrr_residual_noalloc(const nrr_grid_desc *d, int npunct,
   using namespace nrr;
   if (!d || !p || !u || !norm_out)
     return fail(NRR_ERR_INVALID_ARG, "null argument");
-  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_CARTESIAN)
-    return fail(NRR_ERR_INVALID_ARG, "unknown coordinate system %d", d->coord);
-  if (d->fd_order != 4 && d->fd_order != 8 && d->fd_order != 10)
-    return fail(NRR_ERR_INVALID_ARG, "fd_order must be 4, 8 or 10");
-  int ng = d->fd_order / 2;
-  for (int i = 0; i < 3; i++)
-    if (d->n[i] < 2 || d->n[i] > (1 << 16))
-      return fail(NRR_ERR_INVALID_ARG, "n[%d] = %d out of range", i, d->n[i]);
-  if (d->coord != NRR_CARTESIAN && ((d->n[2] & 1) || d->n[1] < ng || d->n[0] < ng))
-    return fail(NRR_ERR_INVALID_ARG, "curvilinear grid needs even n2 and n0,n1 >= ng");
+  {
+    nrr_status s = check_grid_desc(d);  // the check every entry point shares
+    if (s != NRR_OK) return s;
+  }
+  if (d->coord == NRR_SINHSPHERICAL)
+    return fail(NRR_ERR_INVALID_ARG,
+                "the allocation-free residual takes SinhSymTP, Spherical or Cartesian grids");
   if (npunct < 1 || npunct > 8)
     return fail(NRR_ERR_INVALID_ARG, "need 1..8 punctures (got %d)", npunct);
   if (!(r_int > 0.0)) return fail(NRR_ERR_INVALID_ARG, "r_int must be positive");
-
-  Geo g{};
-  g.coord = d->coord;
-  g.n0 = d->n[0];
-  g.n1 = d->n[1];
-  g.n2 = d->n[2];
-  g.ng = ng;
-  g.s0 = g.n0 + 2 * ng;
-  g.s1 = g.n1 + 2 * ng;
-  g.s2 = g.n2 + 2 * ng;
-  g.ncol = g.s0 * g.s1;
-  g.npts = (int64_t)g.ncol * g.s2;
+  const int ng = d->fd_order / 2;
+  const Geo g = grid_geo(d);
   if (g.npts > ((int64_t)1 << 31))
     return fail(NRR_ERR_INVALID_ARG, "grid exceeds 2^31 points");
-  double lo[3], hi[3];
-  if (d->coord == NRR_CARTESIAN) {
-    for (int i = 0; i < 3; i++) {
-      lo[i] = -d->xmax;
-      hi[i] = d->xmax;
-    }
-  } else {
-    lo[0] = 0.0;
-    hi[0] = d->coord == NRR_SINHSYMTP ? 1.0 : d->rmax;
-    lo[1] = 0.0;
-    hi[1] = M_PI;
-    lo[2] = -M_PI;
-    hi[2] = M_PI;
-  }
-  const int nn[3] = {g.n0, g.n1, g.n2};
-  for (int i = 0; i < 3; i++) {
-    g.xxmin[i] = lo[i];
-    g.dxx[i] = (hi[i] - lo[i]) / nn[i];
-  }
-  g.amax = d->amax;
-  g.bscale = d->bscale;
-  g.sinhwaa = d->sinhwaa;
 
   // Launch shape: 128 columns per block in x; phi planes per thread chosen
   // so that the block count fits the static scratch.
-  const int bx = (g.n0 * g.n1 + 127) / 128;
-  if (bx > kMaxBlocks)
+  // (64-bit products: n0 and n1 may each be up to 65536.)
+  const int64_t ncols = (int64_t)g.n0 * g.n1;
+  const int64_t bx64 = (ncols + 127) / 128;
+  if (bx64 > kMaxBlocks)
     return fail(NRR_ERR_INVALID_ARG,
-                "n0*n1 = %d needs %d partial sums; the static scratch holds %d",
-                g.n0 * g.n1, bx, kMaxBlocks);
+                "n0*n1 = %lld needs %lld partial sums; the static scratch holds %d",
+                (long long)ncols, (long long)bx64, kMaxBlocks);
+  const int bx = (int)bx64;  // 1 <= bx <= kMaxBlocks
   int by_max = kMaxBlocks / bx;
   int zc = (g.n2 + by_max - 1) / by_max;
   if (zc < 1) zc = 1;

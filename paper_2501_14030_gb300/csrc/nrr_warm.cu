@@ -24,30 +24,6 @@ nrr_status wfail(nrr_status s, const char *fmt, ...) {
   return s;
 }
 
-Geo desc_geo(const nrr_grid_desc &d) {
-  Geo g{};
-  g.coord = d.coord;
-  g.n0 = d.n[0];
-  g.n1 = d.n[1];
-  g.n2 = d.n[2];
-  g.ng = d.fd_order / 2;
-  g.s0 = g.n0 + 2 * g.ng;
-  g.s1 = g.n1 + 2 * g.ng;
-  g.s2 = g.n2 + 2 * g.ng;
-  g.ncol = g.s0 * g.s1;
-  g.npts = (int64_t)g.ncol * g.s2;
-  g.xxmin[0] = 0.0;
-  g.dxx[0] = ((d.coord == NRR_SINHSYMTP || d.coord == NRR_SINHSPHERICAL) ? 1.0 : d.rmax) /
-             g.n0;
-  g.xxmin[1] = 0.0;
-  g.dxx[1] = M_PI / g.n1;
-  g.xxmin[2] = -M_PI;
-  g.dxx[2] = 2.0 * M_PI / g.n2;
-  g.amax = d.amax;
-  g.bscale = d.bscale;
-  g.sinhwaa = d.sinhwaa;
-  return g;
-}
 
 // Coarse value at padded coarse indices (j0, j1, j2): inner ghosts through
 // their images, points beyond the outer boundary clamped to the last
@@ -104,14 +80,14 @@ extern "C" nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
     return wfail(NRR_ERR_INVALID_ARG, "SinhSymTP parameters differ");
   if (coarse->coord == NRR_SPHERICAL && coarse->rmax != fine->rmax)
     return wfail(NRR_ERR_INVALID_ARG, "rmax differs");
+  if (coarse->coord == NRR_SINHSPHERICAL &&
+      (coarse->amax != fine->amax || coarse->sinhwaa != fine->sinhwaa))
+    return wfail(NRR_ERR_INVALID_ARG, "SinhSpherical parameters differ");
   for (const nrr_grid_desc *d : {coarse, fine}) {
-    const int ng = d->fd_order / 2;
-    if ((d->fd_order != 4 && d->fd_order != 8 && d->fd_order != 10) || d->n[0] < ng ||
-        d->n[1] < ng || d->n[2] < 2 || (d->n[2] & 1) || d->n[0] > 65536 ||
-        d->n[1] > 65536 || d->n[2] > 65536)
-      return wfail(NRR_ERR_INVALID_ARG, "bad grid descriptor");
+    nrr_status s = check_grid_desc(d);
+    if (s != NRR_OK) return s;
   }
-  const Geo c = desc_geo(*coarse), f = desc_geo(*fine);
+  const Geo c = grid_geo(coarse), f = grid_geo(fine);
   if (f.npts > ((int64_t)1 << 31)) return wfail(NRR_ERR_INVALID_ARG, "fine grid too large");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   prolong_kernel<<<(unsigned)((f.npts + 255) / 256), 256, 0, st>>>(c, uc, f, uf);

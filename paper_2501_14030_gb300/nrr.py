@@ -194,11 +194,46 @@ def image_map(desc: dict) -> np.ndarray:
     return out
 
 
+def _require_f64(name: str, t, numel: int, exact: bool) -> None:
+    """Raises ValueError unless t is a contiguous float64 tensor with `numel`
+    elements (at least `numel` if not exact).  The C side receives bare
+    pointers and cannot check any of this."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64 (got %s)" % (name, t.dtype))
+    if (t.numel() != numel) if exact else (t.numel() < numel):
+        raise ValueError("%s has %d elements, needs %s%d" % (
+            name, t.numel(), "" if exact else "at least ", numel))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def _require_current_device(name: str, t) -> None:
+    import torch
+    if t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor (got %s)" % (name, t.device))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (
+            name, t.device.index, torch.cuda.current_device()))
+
+
 def residual_noalloc(desc: dict, punctures, u, norm_out, h_out=None,
                      r_int: float = 100.0, stream=None) -> None:
     """Residual norm of a device u without device allocation (queued on
     `stream`, default the current torch stream); writes norm_out[0] and,
-    if given, H into h_out.  All tensors on the current device."""
+    if given, H into h_out.  u and h_out: float64, contiguous, exactly
+    s0*s1*s2 elements (padded layout); norm_out: float64, >= 1 element; all
+    on the current CUDA device.  Checked here, before the call."""
+    npts = int(np.prod(workloads.padded_shape(desc)))
+    tensors = [("u", u, npts, True), ("norm_out", norm_out, 1, False)]
+    if h_out is not None:
+        tensors.append(("h_out", h_out, npts, True))
+    for name, t, n, exact in tensors:
+        _require_f64(name, t, n, exact)
+    for name, t, _, _ in tensors:
+        _require_current_device(name, t)
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()

@@ -5,10 +5,11 @@ seeded random grid functions -- and none of the solver's arithmetic.  Both the
 CUDA path and the CPU oracle receive their inputs from here.
 
 Grid descriptors are plain dicts: ``coord`` ("sinhsymtp" | "spherical" |
-"cartesian" | "sinhspherical"), ``n`` (interior points per direction),
-``order`` (centred FD
-order) and the coordinate parameters ``amax``, ``bscale``, ``sinhwaa``,
-``rmax``, ``xmax``.
+"cartesian" | "sinhspherical" | "sinhcylindrical"), ``n`` (interior points
+per direction), ``order`` (centred FD order) and the coordinate parameters
+``amax``, ``bscale``, ``sinhwaa``, ``rmax``, ``xmax``, ``zmax``, ``sinhwz``
+(SinhCylindrical: rho = amax sinh(xx0/sinhwaa)/sinh(1/sinhwaa), z = zmax
+sinh(xx1/sinhwz)/sinh(1/sinhwz), stored as (rho, z, phi)).
 
 Puncture dicts: ``m`` (bare mass), ``x`` (position), ``P`` (momentum), ``S``
 (spin angular momentum; a dimensionless spin chi maps to S = chi m^2).
@@ -17,16 +18,18 @@ from __future__ import annotations
 
 import numpy as np
 
-COORDS = {"sinhsymtp": 0, "spherical": 1, "cartesian": 2, "sinhspherical": 3}
+COORDS = {"sinhsymtp": 0, "spherical": 1, "cartesian": 2, "sinhspherical": 3,
+          "sinhcylindrical": 4}
 
 
 def grid_desc(coord: str, n, order: int, *, amax: float = 1.0e4,
               bscale: float = 5.0, sinhwaa: float = 0.07, rmax: float = 64.0,
-              xmax: float = 32.0) -> dict:
+              xmax: float = 32.0, zmax: float = 1.0e4,
+              sinhwz: float = 0.07) -> dict:
     return {"coord": coord, "n": tuple(int(v) for v in n), "order": int(order),
             "amax": float(amax), "bscale": float(bscale),
             "sinhwaa": float(sinhwaa), "rmax": float(rmax),
-            "xmax": float(xmax)}
+            "xmax": float(xmax), "zmax": float(zmax), "sinhwz": float(sinhwz)}
 
 
 def _punc(m, x, P, chi=(0.0, 0.0, 0.0)):

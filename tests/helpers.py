@@ -1,8 +1,6 @@
 """Shared test helpers: oracle grids from workload descriptors, comparisons."""
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from paper_2501_14030_gb300 import workloads as W
@@ -10,16 +8,13 @@ from paper_2501_14030_gb300 import workloads as W
 
 def oracle_grid(desc: dict):
     import oracle as O
-    return O.Grid(W.COORDS[desc["coord"]], desc["n"], desc["order"],
-                  amax=desc["amax"], bscale=desc["bscale"],
-                  sinhwaa=desc["sinhwaa"], rmax=desc["rmax"],
-                  xmax=desc["xmax"])
+    return O.grid_from_desc(desc)
 
 
 def default_dt_eta(og, cfl: float = 0.5):
     """dt = cfl min ds; eta dt = 2 pi cfl / n0 (the damping reading)."""
-    dt = cfl * og.dsmin
-    return dt, 2.0 * math.pi * cfl / (og.n[0] * dt)
+    import oracle as O
+    return O.default_dt_eta(og, cfl)
 
 
 def region_masks(og):

@@ -98,3 +98,65 @@ def test_bench_names_every_documented_stage_variant():
     import bench
     assert documented == set(range(6))
     assert documented <= set(bench.STAGE_VARIANTS)
+
+
+@pytest.mark.parametrize("coord", ["cartesian", "sinhsymtp"])
+def test_descriptor_sizes_are_checked_in_64_bits(lib, coord):
+    """n0 = n1 = 65536 are each within range, but the padded plane s0*s1
+    overflows 32-bit integers.  The descriptor check shared by every entry
+    point computes it in 64 bits and rejects the grid on the host, before any
+    pointer is used or any device work is queued (the pointers below are
+    never dereferenced; this test runs without a GPU)."""
+    d = nrr.make_desc(W.grid_desc(coord, (65536, 65536, 2), 4))
+    out = (C.c_int32 * 1)()
+    assert lib.nrr_image_map(C.byref(d), out) == nrr.ERR_INVALID_ARG
+    assert b"s0*s1" in lib.nrr_last_error()
+    punc = nrr.make_punctures(W.spinning_q4_pair())
+    st = lib.nrr_residual_noalloc(C.byref(d), 2, punc, C.c_void_p(256), 100.0,
+                                  C.c_void_p(256), None, None)
+    assert st == nrr.ERR_INVALID_ARG
+    assert b"s0*s1" in lib.nrr_last_error()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(coord="sinhsymtp", sinhwaa=0.0),
+    dict(coord="sinhsymtp", amax=0.0),
+    dict(coord="spherical", rmax=0.0),
+    dict(coord="cartesian", xmax=0.0),
+    dict(coord="sinhspherical"),
+])
+def test_noalloc_residual_rejects_bad_descriptors_on_host(lib, bad):
+    """The allocation-free residual applies the same descriptor check as
+    nrr_create_grid (map parameters included) and takes no SinhSpherical
+    grid; all of it on the host, before any device call."""
+    kw = {k: v for k, v in bad.items() if k != "coord"}
+    d = nrr.make_desc(W.grid_desc(bad["coord"], (16, 8, 4), 4, **kw))
+    punc = nrr.make_punctures(W.spinning_q4_pair())
+    st = lib.nrr_residual_noalloc(C.byref(d), 2, punc, C.c_void_p(256), 100.0,
+                                  C.c_void_p(256), None, None)
+    assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()
+
+
+def test_noalloc_binding_checks_tensors_before_the_call(lib):
+    """The C side gets bare pointers and cannot see the buffers' sizes, so
+    the binding refuses a u or h_out that is not a contiguous float64 CUDA
+    tensor of exactly s0*s1*s2 elements, and a norm_out that is not float64,
+    before anything is passed to the library."""
+    import torch
+    desc = W.grid_desc("sinhsymtp", (16, 8, 4), 4)
+    shape = W.padded_shape(desc)
+    good = torch.zeros(shape, dtype=torch.float64)
+    norm = torch.zeros(1, dtype=torch.float64)
+    cases = [
+        (torch.zeros(shape, dtype=torch.float32), norm, None, "float64"),
+        (torch.zeros(good.numel() - 1, dtype=torch.float64), norm, None, "elements"),
+        (torch.zeros(shape[::-1], dtype=torch.float64).transpose(0, 2), norm,
+         None, "contiguous"),
+        (good, norm, None, "CUDA"),
+        (good, torch.zeros(1, dtype=torch.float32), None, "float64"),
+        (good, torch.zeros(0, dtype=torch.float64), None, "elements"),
+        (good, norm, torch.zeros(7, dtype=torch.float64), "elements"),
+    ]
+    for u, n, h, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            nrr.residual_noalloc(desc, W.spinning_q4_pair(), u, n, h)

@@ -75,6 +75,7 @@ def _gauss(x, y, z, x0=(0.7, -0.4, 1.3), s=2.0):
     ("spherical", dict(rmax=12.0)),
     ("cartesian", dict(xmax=8.0)),
     ("sinhspherical", dict(amax=40.0, sinhwaa=0.4)),
+    ("sinhcylindrical", dict(amax=20.0, sinhwaa=0.4, zmax=20.0, sinhwz=0.4)),
 ])
 @pytest.mark.parametrize("order", [4, 8])
 def test_laplacian_converges_at_fd_order(oracle_mod, coord, kw, order):
@@ -111,6 +112,8 @@ def _d_dxx(f, axis, h):
     # the strong stretch of SINHWAA 0.07 needs finer xx0 sampling for the
     # fourth-order numerical derivative to resolve J / h0^2
     W.grid_desc("sinhspherical", (192, 64, 64), 4),
+    W.grid_desc("sinhcylindrical", (96, 64, 64), 4, amax=20.0, sinhwaa=0.4,
+                zmax=20.0, sinhwz=0.4),
 ])
 def test_scale_factors_match_coordinate_map(oracle_mod, desc):
     """h_i = |d(x,y,z)/d xx_i| and g_i = (1/J) d_i (J / h_i^2), by
@@ -150,6 +153,28 @@ def test_sinhspherical_reduces_to_spherical(oracle_mod):
         m = sh.field("kind") == 0
         d = max(np.abs(sh.field(f) * k - sph.field(f))[m].max() /
                 np.abs(sph.field(f))[m].max() for f, k in scale.items())
+        diffs.append(d)
+    assert diffs[1] < 1e-4 and 3.5 < diffs[0] / diffs[1] < 4.5, diffs
+
+
+def test_sinhcylindrical_reduces_to_cylindrical(oracle_mod):
+    """As both sinh widths grow, rho -> R xx0 and z -> Z xx1: the scale
+    factors tend to the textbook cylindrical ones (R, Z, rho) and the
+    Laplacian's first-derivative terms to (1/(rho R), 0), the cylindrical
+    d_rho (1/rho) term in the coordinates xx0 = rho/R, at the rate 1/w^2."""
+    R, Z = 30.0, 20.0
+    diffs = []
+    for w in (50.0, 100.0):
+        g = oracle_grid(W.grid_desc("sinhcylindrical", (12, 10, 4), 4, amax=R,
+                                    sinhwaa=w, zmax=Z, sinhwz=w))
+        m = g.field("kind") == 0
+        rho, z = R * g.field("xx0"), Z * g.field("xx1")
+        expect = {"h0": np.full(g.shape, R), "h1": np.full(g.shape, Z),
+                  "h2": rho, "g0": 1.0 / (rho * R),
+                  "r": np.hypot(rho, z)}
+        d = max(np.abs(g.field(f) - e)[m].max() / np.abs(e)[m].max()
+                for f, e in expect.items())
+        d = max(d, np.abs(g.field("g1"))[m].max() * Z * Z)
         diffs.append(d)
     assert diffs[1] < 1e-4 and 3.5 < diffs[0] / diffs[1] < 4.5, diffs
 
@@ -238,6 +263,8 @@ def test_source_alpha_beta_definition(oracle_mod):
     W.grid_desc("sinhsymtp", (20, 12, 8), 8),
     W.grid_desc("spherical", (20, 12, 8), 10, rmax=30.0),
     W.grid_desc("sinhspherical", (20, 12, 8), 8),
+    W.grid_desc("sinhcylindrical", (20, 12, 8), 8, amax=50.0, sinhwaa=0.3,
+                zmax=40.0, sinhwz=0.3),
 ])
 def test_inner_ghost_images_round_trip(oracle_mod, desc):
     O = oracle_mod
@@ -373,6 +400,54 @@ def test_cartesian_radiation_condition_on_polynomials(oracle_mod):
     assert (outer & ~out_x).sum() > 0
 
 
+def test_sinhcylindrical_radiation_condition(oracle_mod):
+    """SinhCylindrical outer ghosts lie beyond the side (rho > amax) or the
+    ends (|z| > zmax): d_r f = (rho/r) (1/rho') D_xx0 f + (z/r) (1/z') D_xx1 f,
+    each difference one-sided inward where the point lies beyond that
+    direction's boundary and centred otherwise.  Exact on profiles linear in
+    xx0 or xx1; f = xx1^3 separates the one-sided (3x^2 - 2h^2) from the
+    centred (3x^2 + h^2) difference; the classification puts rho < 0 and the
+    periodic phi ghosts among the images and everything else beyond the
+    boundary among the evolved outer points."""
+    O = oracle_mod
+    g = oracle_grid(W.grid_desc("sinhcylindrical", (12, 10, 4), 4, amax=20.0,
+                                sinhwaa=0.3, zmax=15.0, sinhwz=0.3))
+    kind = g.field("kind")
+    i0 = np.broadcast_to(np.arange(g.s[0])[None, None, :], g.shape)
+    i1 = np.broadcast_to(np.arange(g.s[1])[None, :, None], g.shape)
+    i2 = np.broadcast_to(np.arange(g.s[2])[:, None, None], g.shape)
+    ng = g.ng
+    in1 = (i1 >= ng) & (i1 < ng + g.n[1])
+    in2 = (i2 >= ng) & (i2 < ng + g.n[2])
+    assert (kind[(i0 < ng) | ~in2] == O.INNER).all()
+    outer = kind == O.OUTER
+    np.testing.assert_array_equal(
+        outer, (i0 >= ng) & in2 & ((i0 >= ng + g.n[0]) | ~in1))
+    alpha, beta = g.zeros(), g.zeros()
+    c, r, z = g.field("c"), g.field("r"), g.field("z")
+    rho = np.hypot(g.field("x"), g.field("y"))
+    h0, h1 = g.field("h0"), g.field("h1")
+    xx0, xx1 = g.field("xx0"), g.field("xx1")
+    ku, _ = g.rhs(alpha, beta, 0.0, np.full(g.shape, 0.5), g.zeros())
+    np.testing.assert_allclose(ku[outer], (-c * 0.5 / r)[outer], rtol=1e-13)
+    # f = xx1: exact in both stencils along xx1; constant along xx0
+    ku, _ = g.rhs(alpha, beta, 0.0, xx1.copy(), g.zeros())
+    expect = -c * (z / r / h1 + xx1 / r)
+    np.testing.assert_allclose(ku[outer], expect[outer], rtol=1e-12, atol=1e-14)
+    # f = xx0 where the xx0 stencil stays at rho > 0 (i0 > ng)
+    ku, _ = g.rhs(alpha, beta, 0.0, xx0.copy(), g.zeros())
+    expect = -c * (rho / r / h0 + xx0 / r)
+    m = outer & (i0 > ng)
+    np.testing.assert_allclose(ku[m], expect[m], rtol=1e-12, atol=1e-14)
+    # f = xx1^3: one-sided beyond the ends, centred on the side face
+    h = g.dxx[1]
+    D1 = np.where(in1, 3 * xx1 ** 2 + h ** 2, 3 * xx1 ** 2 - 2 * h ** 2)
+    ku, _ = g.rhs(alpha, beta, 0.0, xx1 ** 3, g.zeros())
+    expect = -c * (z / r / h1 * D1 + xx1 ** 3 / r)
+    np.testing.assert_allclose(ku[outer], expect[outer], rtol=1e-11, atol=1e-13)
+    assert (outer & in1).sum() > 0 and (outer & ~in1).sum() > 0
+
+
 # ------------------------------------------------------------ norm
 def test_norm_of_unit_residual_is_one(oracle_mod):
     g = oracle_grid(W.grid_desc("sinhsymtp", (32, 16, 4), 4))
@@ -490,6 +565,8 @@ def test_momentum_flip_gives_identical_u(oracle_mod):
     W.grid_desc("sinhsymtp", (8, 8, 2), 8, amax=20.0, sinhwaa=0.3),
     W.grid_desc("cartesian", (8, 8, 8), 4, xmax=16.0),
     W.grid_desc("sinhspherical", (8, 4, 2), 4, amax=20.0, sinhwaa=0.3),
+    W.grid_desc("sinhcylindrical", (6, 8, 2), 4, amax=20.0, sinhwaa=0.3,
+                zmax=20.0, sinhwz=0.3),
 ])
 def test_relaxation_agrees_with_dense_newton(oracle_mod, desc):
     """The relaxation's steady state is the solution of the discrete
