@@ -113,6 +113,27 @@ def lib():
                                        D, D]
         _lib.or_newton.argtypes = [C.c_void_p, D, D, D, C.c_int, C.c_double,
                                    D]
+        _lib.or_grid_set_speed_reference.argtypes = [C.c_void_p, C.c_double]
+        L = C.POINTER(C.c_long)
+        _lib.or_link_new.restype = C.c_void_p
+        _lib.or_link_new.argtypes = [C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_double, C.c_int, C.c_char_p, C.c_int]
+        _lib.or_link_free.argtypes = [C.c_void_p]
+        _lib.or_link_count.restype = C.c_long
+        _lib.or_link_count.argtypes = [C.c_void_p]
+        _lib.or_link_get.argtypes = [C.c_void_p, L, L, D]
+        _lib.or_link_apply.argtypes = [C.c_void_p, D, D]
+        _lib.or_link_conflict.argtypes = [C.c_void_p, C.c_void_p]
+        _lib.or_patch_rk4_step.argtypes = [C.c_void_p, D, D, C.c_void_p, D, D,
+                                           C.c_void_p, C.c_void_p, C.c_double,
+                                           C.c_double, D, D, D, D]
+        _lib.or_patch_norm.restype = C.c_double
+        _lib.or_patch_norm.argtypes = [C.c_void_p, D, C.c_void_p, C.c_void_p,
+                                       D, C.c_void_p, C.c_double]
+        _lib.or_patch_relax.argtypes = [C.c_void_p, D, D, C.c_void_p, D, D,
+                                        C.c_void_p, C.c_void_p,
+                                        C.POINTER(_RelaxParams), D, D, D, D,
+                                        C.POINTER(_RelaxResult)]
     return _lib
 
 
@@ -198,6 +219,11 @@ class Grid:
 
     def zeros(self) -> np.ndarray:
         return np.zeros(self.shape)
+
+    def set_speed_reference(self, ds_ref: float) -> None:
+        """c = local spacing / ds_ref (a patch of a multi-patch system)."""
+        lib().or_grid_set_speed_reference(self._h, float(ds_ref))
+        self.dsmin = float(ds_ref)
 
     def source(self, punctures):
         alpha, beta = self.zeros(), self.zeros()
@@ -292,3 +318,74 @@ def default_dt_eta(og: Grid, cfl: float = 0.5) -> tuple[float, float]:
     mode along xx0)."""
     dt = cfl * og.dsmin
     return dt, 2.0 * math.pi * cfl / (og.n[0] * dt)
+
+
+class Link:
+    """Receivers of patch `recv` interpolated from patch `donor` (q-point
+    Lagrange interpolation per direction in the donor's coordinates).
+    kind 0: every ghost of a Cartesian patch; kind 1: interior points with
+    max(|x|, |y|, |z|) < hole."""
+
+    def __init__(self, recv: Grid, donor: Grid, kind: int, hole: float = 0.0,
+                 q: int = 4):
+        err = C.create_string_buffer(256)
+        h = lib().or_link_new(recv._h, donor._h, int(kind), float(hole), int(q),
+                              err, 256)
+        if not h:
+            raise ValueError("oracle link: " + err.value.decode())
+        self._h, self.q = h, q
+        self.recv_grid, self.donor_grid = recv, donor
+        self.n = lib().or_link_count(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_link_free(h)
+            self._h = None
+
+    def arrays(self):
+        """(receiver flat indices, donor flat indices [n, q^3], weights)."""
+        m = self.q ** 3
+        recv = np.zeros(self.n, dtype=np.int64)
+        donor = np.zeros((self.n, m), dtype=np.int64)
+        w = np.zeros((self.n, m))
+        lib().or_link_get(self._h, recv.ctypes.data_as(C.POINTER(C.c_long)),
+                          donor.ctypes.data_as(C.POINTER(C.c_long)), _dp(w))
+        return recv, donor, w
+
+    def apply(self, f_donor: np.ndarray, f_recv: np.ndarray) -> None:
+        lib().or_link_apply(self._h, _dp(np.ascontiguousarray(f_donor)),
+                            _dp(f_recv))
+
+    def conflicts_with(self, other: "Link") -> bool:
+        return bool(lib().or_link_conflict(self._h, other._h))
+
+
+def patch_rk4_step(a: Grid, src_a, b: Grid, src_b, la: Link, lb: Link, eta,
+                   dt, ua, va, ub, vb) -> None:
+    """One RK4 step of the two-patch system in place (src_* = (alpha, beta))."""
+    lib().or_patch_rk4_step(a._h, _dp(src_a[0]), _dp(src_a[1]), b._h,
+                            _dp(src_b[0]), _dp(src_b[1]), la._h, lb._h,
+                            float(eta), float(dt), _dp(ua), _dp(va), _dp(ub),
+                            _dp(vb))
+
+
+def patch_norm(a: Grid, Ha, la: Link, b: Grid, Hb, lb: Link,
+               r_int: float = 100.0) -> float:
+    return lib().or_patch_norm(a._h, _dp(np.ascontiguousarray(Ha)), la._h,
+                               b._h, _dp(np.ascontiguousarray(Hb)), lb._h,
+                               float(r_int))
+
+
+def patch_relax(a: Grid, src_a, b: Grid, src_b, la: Link, lb: Link, ua, va,
+                ub, vb, *, eta, dt, tol=1e-10, r_int=100.0, max_iters=100000,
+                check_every=1):
+    """Relax the two-patch system in place; returns (iters, norm, status)."""
+    prm = _RelaxParams(float(eta), float(dt), float(tol), float(r_int),
+                       int(max_iters), int(check_every))
+    res = _RelaxResult()
+    lib().or_patch_relax(a._h, _dp(src_a[0]), _dp(src_a[1]), b._h,
+                         _dp(src_b[0]), _dp(src_b[1]), la._h, lb._h,
+                         C.byref(prm), _dp(ua), _dp(va), _dp(ub), _dp(vb),
+                         C.byref(res))
+    return res.iters, res.norm, res.status

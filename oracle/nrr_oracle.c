@@ -901,3 +901,254 @@ int or_newton(const or_grid *g, const double *alpha, const double *beta,
   free(F);
   return it;
 }
+
+void or_grid_set_speed_reference(or_grid *g, double ds_ref) {
+  g->dsmin_global = ds_ref;
+  for (long p = 0; p < g->npts; p++) g->c[p] = g->dsmin[p] / ds_ref;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two overlapping patches (Sec. 5: several patches of one solve; Sec. 6:   */
+/* multipatch grids with interpolation between patches).                    */
+/* ------------------------------------------------------------------------ */
+struct or_link {
+  long n;       /* receivers                                              */
+  int q;        /* interpolation points per direction                     */
+  long *recv;   /* receiver flat index in the receiving patch             */
+  long *donor;  /* [n][q^3] donor flat indices (images of inner ghosts)   */
+  double *w;    /* [n][q^3] products of the three Lagrange weights        */
+};
+
+void or_link_free(or_link *l) {
+  if (!l) return;
+  free(l->recv);
+  free(l->donor);
+  free(l->w);
+  free(l);
+}
+
+long or_link_count(const or_link *l) { return l->n; }
+
+void or_link_get(const or_link *l, long *recv, long *donor, double *w) {
+  long m = (long)l->q * l->q * l->q;
+  memcpy(recv, l->recv, sizeof(long) * (size_t)l->n);
+  memcpy(donor, l->donor, sizeof(long) * (size_t)(l->n * m));
+  memcpy(w, l->w, sizeof(double) * (size_t)(l->n * m));
+}
+
+/* Lagrange weights of the q nodes base, base+1, ... at position f (all in
+ * units of the grid index): w_j = prod_{m != j} (f - t_m) / (t_j - t_m). */
+static void lagrange_weights(int q, int base, double f, double *w) {
+  for (int j = 0; j < q; j++) {
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m < q; m++) {
+      if (m == j) continue;
+      num *= f - (double)(base + m);
+      den *= (double)(j - m);
+    }
+    w[j] = num / den;
+  }
+}
+
+or_link *or_link_new(const or_grid *rg, const or_grid *dg, int kind,
+                     double hole, int q, char *err, int errlen) {
+#define LFAIL(...)                                       \
+  do {                                                   \
+    if (err) snprintf(err, (size_t)errlen, __VA_ARGS__); \
+    or_link_free(l);                                     \
+    return NULL;                                         \
+  } while (0)
+  or_link *l = (or_link *)calloc(1, sizeof(or_link));
+  if (!l) return NULL;
+  if (q < 2 || q > 6 || (q & 1)) LFAIL("q must be 2, 4 or 6");
+  if (q / 2 > dg->ng) LFAIL("q/2 exceeds the donor's ghost width");
+  if (kind == 0 && rg->d.coord != OR_CARTESIAN)
+    LFAIL("ghost receivers need a Cartesian receiving patch");
+  if (kind != 0 && kind != 1) LFAIL("unknown receiver kind");
+  long m = (long)q * q * q;
+  long n = 0;
+  for (long p = 0; p < rg->npts; p++) {
+    int take = kind == 0 ? rg->kind[p] == OR_OUTER
+                         : rg->kind[p] == OR_INTERIOR &&
+                               fmax(fabs(rg->x[p]), fmax(fabs(rg->y[p]), fabs(rg->z[p]))) < hole;
+    n += take;
+  }
+  l->n = n;
+  l->q = q;
+  l->recv = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+  l->donor = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n * m : 1));
+  l->w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n * m : 1));
+  if (!l->recv || !l->donor || !l->w) LFAIL("out of memory");
+  long r = 0;
+  for (long p = 0; p < rg->npts; p++) {
+    int take = kind == 0 ? rg->kind[p] == OR_OUTER
+                         : rg->kind[p] == OR_INTERIOR &&
+                               fmax(fabs(rg->x[p]), fmax(fabs(rg->y[p]), fabs(rg->z[p]))) < hole;
+    if (!take) continue;
+    /* the receiver's position in the donor's coordinates, as a fractional
+     * padded index (cell centre i at i) */
+    double xx[3];
+    if (dg->d.coord == OR_CARTESIAN) {
+      xx[0] = rg->x[p];
+      xx[1] = rg->y[p];
+      xx[2] = rg->z[p];
+    } else {
+      cart_to_xx(&dg->d, rg->x[p], rg->y[p], rg->z[p], xx);
+    }
+    int base[3];
+    double wd[3][6];
+    for (int d = 0; d < 3; d++) {
+      double f = (xx[d] - dg->xxmin[d]) / dg->dxx[d] - 0.5 + dg->ng;
+      base[d] = (int)floor(f) - (q / 2 - 1);
+      if (base[d] < 0 || base[d] + q - 1 >= dg->s[d])
+        LFAIL("receiver %ld: donor stencil leaves the donor (direction %d)", p, d);
+      lagrange_weights(q, base[d], f, wd[d]);
+    }
+    long k = 0;
+    for (int c = 0; c < q; c++)
+      for (int b = 0; b < q; b++)
+        for (int a = 0; a < q; a++, k++) {
+          long dp = pidx(dg, base[0] + a, base[1] + b, base[2] + c);
+          if (dg->kind[dp] == OR_INNER) dp = dg->image[dp];
+          l->donor[r * m + k] = dp;
+          l->w[r * m + k] = wd[0][a] * wd[1][b] * wd[2][c];
+        }
+    l->recv[r++] = p;
+  }
+  return l;
+#undef LFAIL
+}
+
+void or_link_apply(const or_link *l, const double *f_donor, double *f_recv) {
+  long m = (long)l->q * l->q * l->q;
+  for (long r = 0; r < l->n; r++) {
+    double s = 0.0;
+    for (long k = 0; k < m; k++) s += l->w[r * m + k] * f_donor[l->donor[r * m + k]];
+    f_recv[l->recv[r]] = s;
+  }
+}
+
+int or_link_conflict(const or_link *l, const or_link *other) {
+  long m = (long)other->q * other->q * other->q;
+  for (long r = 0; r < l->n; r++)
+    for (long k = 0; k < other->n * m; k++)
+      if (other->donor[k] == l->recv[r]) return 1;
+  return 0;
+}
+
+void or_patch_rk4_step(const or_grid *a, const double *alpha_a,
+                       const double *beta_a, const or_grid *b,
+                       const double *alpha_b, const double *beta_b,
+                       const or_link *la, const or_link *lb, double eta,
+                       double dt, double *ua, double *va, double *ub,
+                       double *vb) {
+  const or_grid *gs[2] = {a, b};
+  const double *al[2] = {alpha_a, alpha_b}, *be[2] = {beta_a, beta_b};
+  double *u[2] = {ua, ub}, *v[2] = {va, vb};
+  double *ku[2][4], *kv[2][4], *us[2], *vs[2];
+  for (int i = 0; i < 2; i++) {
+    long n = gs[i]->npts;
+    double *buf = (double *)malloc(sizeof(double) * (size_t)n * 10);
+    for (int s = 0; s < 4; s++) {
+      ku[i][s] = buf + (2 * s) * n;
+      kv[i][s] = buf + (2 * s + 1) * n;
+    }
+    us[i] = buf + 8 * n;
+    vs[i] = buf + 9 * n;
+  }
+  static const double c[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int s = 0; s < 4; s++) {
+    for (int i = 0; i < 2; i++) {
+      const double *uin = u[i], *vin = v[i];
+      if (s > 0) {
+        for (long p = 0; p < gs[i]->npts; p++) {
+          us[i][p] = u[i][p] + c[s] * dt * ku[i][s - 1][p];
+          vs[i][p] = v[i][p] + c[s] * dt * kv[i][s - 1][p];
+        }
+        uin = us[i];
+        vin = vs[i];
+      }
+      or_rhs(gs[i], al[i], be[i], eta, uin, vin, ku[i][s], kv[i][s]);
+    }
+    /* receivers of a from b, receivers of b from a, then the inner ghosts
+     * again (a receiver may be the image of an inner ghost) */
+    or_link_apply(la, ku[1][s], ku[0][s]);
+    or_link_apply(la, kv[1][s], kv[0][s]);
+    or_link_apply(lb, ku[0][s], ku[1][s]);
+    or_link_apply(lb, kv[0][s], kv[1][s]);
+    for (int i = 0; i < 2; i++) {
+      or_fill_inner_ghosts(gs[i], ku[i][s]);
+      or_fill_inner_ghosts(gs[i], kv[i][s]);
+    }
+  }
+  for (int i = 0; i < 2; i++) {
+    for (long p = 0; p < gs[i]->npts; p++) {
+      u[i][p] += dt / 6.0 * (ku[i][0][p] + 2.0 * ku[i][1][p] + 2.0 * ku[i][2][p] + ku[i][3][p]);
+      v[i][p] += dt / 6.0 * (kv[i][0][p] + 2.0 * kv[i][1][p] + 2.0 * kv[i][2][p] + kv[i][3][p]);
+    }
+    free(ku[i][0]);
+  }
+}
+
+double or_patch_norm(const or_grid *a, const double *Ha, const or_link *la,
+                     const or_grid *b, const double *Hb, const or_link *lb,
+                     double r_int) {
+  const or_grid *gs[2] = {a, b};
+  const double *H[2] = {Ha, Hb};
+  const or_link *ls[2] = {la, lb};
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < 2; i++) {
+    char *recv = (char *)calloc((size_t)gs[i]->npts, 1);
+    for (long r = 0; r < ls[i]->n; r++) recv[ls[i]->recv[r]] = 1;
+    for (long p = 0; p < gs[i]->npts; p++) {
+      if (gs[i]->kind[p] != OR_INTERIOR || recv[p] || !(gs[i]->r[p] < r_int)) continue;
+      double w = fabs(gs[i]->jac[p]);
+      num += H[i][p] * H[i][p] * w;
+      den += w;
+    }
+    free(recv);
+  }
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+int or_patch_relax(const or_grid *a, const double *alpha_a,
+                   const double *beta_a, const or_grid *b,
+                   const double *alpha_b, const double *beta_b,
+                   const or_link *la, const or_link *lb,
+                   const or_relax_params *prm, double *ua, double *va,
+                   double *ub, double *vb, or_relax_result *res) {
+  double *Ha = (double *)malloc(sizeof(double) * (size_t)a->npts);
+  double *Hb = (double *)malloc(sizeof(double) * (size_t)b->npts);
+  if (!Ha || !Hb) {
+    free(Ha);
+    free(Hb);
+    return -1;
+  }
+  long it = 0;
+  int every = prm->check_every > 0 ? prm->check_every : 1;
+  res->status = OR_NOT_CONVERGED;
+  for (;;) {
+    if (it % every == 0) {
+      or_residual(a, alpha_a, beta_a, ua, Ha);
+      or_residual(b, alpha_b, beta_b, ub, Hb);
+      double nrm = or_patch_norm(a, Ha, la, b, Hb, lb, prm->r_int);
+      res->norm = nrm;
+      if (!isfinite(nrm)) {
+        res->status = OR_DIVERGED;
+        break;
+      }
+      if (nrm < prm->tol) {
+        res->status = OR_CONVERGED;
+        break;
+      }
+    }
+    if (it >= prm->max_iters) break;
+    or_patch_rk4_step(a, alpha_a, beta_a, b, alpha_b, beta_b, la, lb, prm->eta,
+                      prm->dt, ua, va, ub, vb);
+    it++;
+  }
+  res->iters = it;
+  free(Ha);
+  free(Hb);
+  return 0;
+}

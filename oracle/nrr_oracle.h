@@ -115,6 +115,58 @@ void or_linear_rhs(const or_grid *g, const double *a, const double *rhat,
 int or_newton(const or_grid *g, const double *alpha, const double *beta,
               double *u, int max_it, double step_tol, double *final_step);
 
+/* Wave speed reference of a patch that is part of a multi-patch system:
+ * c = (local spacing) / ds_ref, with ds_ref the smallest spacing over all
+ * patches, so that one time step dt = cfl ds_ref runs every patch at the
+ * same Courant number (Sec. 2: c proportional to the local spacing). */
+void or_grid_set_speed_reference(or_grid *g, double ds_ref);
+
+/* Two overlapping patches (Sec. 5 multiple patches; Sec. 6 multipatch
+ * grids): values at the receiver points of one patch are interpolated from
+ * a donor patch by tensor-product Lagrange interpolation of q points per
+ * direction in the donor's coordinates xx.  Receivers: kind 0 = every ghost
+ * point of a Cartesian patch (the inner box's boundary); kind 1 = interior
+ * points of the patch with max(|x|,|y|,|z|) < hole (the outer patch's hole
+ * inside the box).  Donor points are evolved points of the donor (inner
+ * ghosts replaced by their images).  NULL on error (message in err). */
+typedef struct or_link or_link;
+or_link *or_link_new(const or_grid *recv, const or_grid *donor, int kind,
+                     double hole, int q, char *err, int errlen);
+void or_link_free(or_link *l);
+long or_link_count(const or_link *l);
+/* receiver flat indices (n), donor flat indices (n*q^3), weights (n*q^3) */
+void or_link_get(const or_link *l, long *recv, long *donor, double *w);
+/* f_recv[r] = sum_j w[r][j] f_donor[donor[r][j]] at every receiver. */
+void or_link_apply(const or_link *l, const double *f_donor, double *f_recv);
+/* 1 if a receiver of `l` is a donor point of `other` (the coupling would
+ * then read interpolated values to interpolate), else 0. */
+int or_link_conflict(const or_link *l, const or_link *other);
+
+/* One RK4 step of the two-patch system: each stage evaluates both patches'
+ * right-hand sides with their boundary conditions, then sets the
+ * right-hand side at the receivers of each link from the donor's (la: the
+ * receivers of patch a, donor b; lb the converse), then the inner ghosts
+ * of both copy their images again. */
+void or_patch_rk4_step(const or_grid *a, const double *alpha_a,
+                       const double *beta_a, const or_grid *b,
+                       const double *alpha_b, const double *beta_b,
+                       const or_link *la, const or_link *lb, double eta,
+                       double dt, double *ua, double *va, double *ub,
+                       double *vb);
+/* Norm of the two-patch residual: sqrt((sum H^2 J over the interior points
+ * of both patches with r < r_int that are not receivers) / (sum J)). */
+double or_patch_norm(const or_grid *a, const double *Ha, const or_link *la,
+                     const or_grid *b, const double *Hb, const or_link *lb,
+                     double r_int);
+/* The relaxation loop of Alg. 1 on the two-patch system (norm every
+ * check_every steps and before the first). */
+int or_patch_relax(const or_grid *a, const double *alpha_a,
+                   const double *beta_a, const or_grid *b,
+                   const double *alpha_b, const double *beta_b,
+                   const or_link *la, const or_link *lb,
+                   const or_relax_params *prm, double *ua, double *va,
+                   double *ub, double *vb, or_relax_result *res);
+
 #ifdef __cplusplus
 }
 #endif
