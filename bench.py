@@ -40,8 +40,10 @@ CHECK_EVERY = 50
 # nrr_set_launch's curvilinear stage-kernel variants
 STAGE_VARIANTS = {0: "column", 1: "tiled", 2: "persistent", 3: "tensor-copy tiled",
                   4: "multi-stage column", 5: "multi-stage tensor-copy tiled"}
-# FP64 peak of the GB300 from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop
-SMS, FP64_FMA_PER_CLK = 152, 2
+# FP64 FMA units: 2 FMA per clock per SM on GB300 (the SM count is read from
+# the device)
+FP64_FMA_PER_CLK = 2
+MAX_SM_MHZ = 2070.0
 
 
 # DRAM bytes (read + write) per launch of the FP64 stage kernel at
@@ -51,12 +53,36 @@ STAGE_FP64_DRAM_BYTES = 16.36e6
 
 
 def flops_per_point(ng: int) -> int:
-    """Algorithmic FP64 flops per interior point per fused stage launch, as
-    the folded operator is evaluated: centre weight (1 mul), 2*ng FMAs in
+    """Algorithmic flops per interior point per fused RHS + RK4 stage, the
+    count the roofline uses: 3 (2p + 6) for the Laplacian's three directions
+    at FD order p = 2 ng, plus about 11 for the source and the RK4 terms
+    (FMA = 2 flops; 77 at order 8)."""
+    return 3 * (4 * ng + 6) + 11
+
+
+def folded_flops_per_point(ng: int) -> int:
+    """The same work as the folded operator evaluates it (c^2 and the metric
+    folded into per-column weights): centre weight (1 mul), 2*ng FMAs in
     each of xx0 and xx1 (8 ng), ng adds + ng FMAs in phi (3 ng), the source
     term (fma, divide, 4 mul, fma: 9), k_u (fma: 2) and the RK4 update
-    (7 on average over the four stages)."""
+    (7 on average over the four stages): 63 at order 8."""
     return 11 * ng + 1 + 9 + 2 + 7
+
+
+# Algorithmic bytes per evolved point of one fused FP32 stage: read u, v
+# (stage), y_n (u, v), acc (u, v), alpha, beta; write stage (u, v) and
+# acc (u, v) -- 12 words.
+FP32_STAGE_BYTES = 48
+FP64_STAGE_BYTES = 96
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    """The measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def rank_info():
@@ -120,10 +146,9 @@ def oracle_rate(desc, punc, seconds: float):
     same grid from zero data, sized to about `seconds` of host time."""
     import numpy as np  # noqa: F401
     import oracle as O
-    from tests.helpers import default_dt_eta, oracle_grid
-    og = oracle_grid(desc)
+    og = O.grid_from_desc(desc)
     alpha, beta = og.source(punc)
-    dt, eta = default_dt_eta(og)
+    dt, eta = O.default_dt_eta(og)
     u, v = og.zeros(), og.zeros()
     t = time.perf_counter()
     og.rk4_step(alpha, beta, eta, dt, u, v)
@@ -249,15 +274,21 @@ def run_ours(args):
     t_max_s, _, value = job_rate(total_ms / 1e3, float(n_int * 4 * iters), dist,
                                  device="cuda")
 
-    # ---- dominant kernel: the fused RK4 stage, timed on its own stream
+    # ---- dominant kernel: the fused RK4 stage.  Its time per launch inside
+    # the timed solves: the solve's device time over its 4 stage launches per
+    # RK4 step (the residual checks, one per 50 steps, are left in: an upper
+    # bound on the stage's time).  Also timed alone on its work stream.
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = nrr.probe_peaks()
     dt, eta = g.timestep(0.5)
     g.set_punctures(punc)
     g.relax(mode="fp64", tol=1e-10, check_every=CHECK_EVERY)
-    ms_launch = g.profile_stages(200, dt, eta, mode="fp64")
+    ms_isolated = g.profile_stages(200, dt, eta, mode="fp64")
+    ms_launch = t_max_s * 1e3 / args.steps / (4 * results[-1][0]["iters"])
     ng = g.ng
     flops = flops_per_point(ng) * n_int
     achieved = flops / (ms_launch * 1e-3) / 1e12
-    peak = SMS * FP64_FMA_PER_CLK * 2 * 2070e6 / 1e12
+    peak = sms * FP64_FMA_PER_CLK * 2 * MAX_SM_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": STAGE_FP64_DRAM_BYTES,
@@ -267,12 +298,21 @@ def run_ours(args):
                                 "L2-resident in the timed run",
                 "kernel": "stage_curvi_kernel<double,4,*> (fused RHS + BC + RK4 stage)",
                 "ms_per_launch": ms_launch,
+                "ms_per_launch_basis": "in-solve: timed solve / (4 x RK4 steps)",
+                "ms_per_launch_isolated": ms_isolated,
                 "flops_per_launch": flops,
-                "peak_basis": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz "
-                              "(unit counts and max clock)"}
+                "flops_per_point": flops_per_point(ng),
+                "flops_basis": "3 (2p + 6) + 11 per interior point at FD order p",
+                "folded_flops_per_point": folded_flops_per_point(ng),
+                "frac_folded_count": folded_flops_per_point(ng) * n_int /
+                (ms_launch * 1e-3) / 1e12 / peak,
+                "peak_basis": "FP64: %d SMs (device property) x 2 FMA/clk x 2 flop "
+                              "x %.0f MHz (unit counts and max clock)" % (sms, MAX_SM_MHZ),
+                "peak_probe_measured": peaks["fp64_tflops"],
+                "frac_of_probe": achieved / peaks["fp64_tflops"]}
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (
-            SMS * FP64_FMA_PER_CLK * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+            sms * FP64_FMA_PER_CLK * 2 * clk["sm_mhz"] * 1e6 / 1e12)
 
     # ---- FP32 relaxation inside the FP64 defect-correction loop, same
     # workload (context beside the FP64 headline)
@@ -296,7 +336,7 @@ def run_ours(args):
     g.get_state(udc)
     dc_err = float(np.abs(udc - u64).max() / np.abs(u64).max())
     ms32 = g.profile_stages(200, dt, eta, mode="fp32")
-    bytes32 = 40 * n_int  # 10 FP32 words per point, averaged over the stages
+    bytes32 = FP32_STAGE_BYTES * n_int
 
     # ---- end to end through the public API with host buffers
     pinned_u = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -324,10 +364,15 @@ def run_ours(args):
                   max_iters=iters // max(1, args.steps), raise_on_error=False)
 
     batch = None if args.no_batch else run_batch(args, nrr, W, torch)
-    # warm start from the learned surrogate, compact: 2048 training solves,
-    # 800 training steps, 128 held-out solves cold vs warm (the full
-    # 8192 / 1024 pipeline is `--surrogate`)
-    warm = None if args.no_surrogate else surrogate_pipeline(nrr, W, torch, 2048, 128, 100)
+    # the larger grids and the other coordinate families, FP64 against
+    # defect correction
+    big = None if args.no_configs2 else configs2_section(nrr, W, torch, peaks, sms)
+    # warm start from the learned surrogate: 8192 training solves at
+    # 64x32x8, 1024 held-out solves at 128x128x16 cold vs warm
+    # (--compact-surrogate: 2048 / 128)
+    n_tr, n_held = (2048, 128) if args.compact_surrogate else (8192, 1024)
+    warm = None if args.no_surrogate else surrogate_pipeline(nrr, W, torch, n_tr,
+                                                            n_held, 100)
 
     line = None
     if rank == 0:
@@ -365,8 +410,18 @@ def run_ours(args):
                 "speedup_vs_fp64": (t_max_s / args.steps) / (statistics.median(dc_ms) / 1e3),
                 "max_rel_diff_u_vs_fp64_solution": dc_err,
                 "fp32_stage_us_per_launch": ms32 * 1e3,
-                "fp32_stage_GBps_algorithmic": bytes32 / (ms32 * 1e-3) / 1e9},
+                "fp32_stage_GBps_algorithmic": bytes32 / (ms32 * 1e-3) / 1e9,
+                "fp32_stage_roofline": {
+                    "bound": "l2", "achieved": bytes32 / (ms32 * 1e-3) / 1e9,
+                    "peak": peaks["l2_gbs"], "unit": "GB/s",
+                    "frac": bytes32 / (ms32 * 1e-3) / 1e9 / peaks["l2_gbs"],
+                    "bytes_per_point": FP32_STAGE_BYTES,
+                    "peak_basis": "L2 read bandwidth measured by the library's "
+                                  "probe kernel (the FP32 working set of "
+                                  "128x128x16 stays in L2)"}},
+            "measured_peaks": dict(peaks, sms=sms),
             "batch_512": batch,
+            "larger_grids": big,
             "surrogate_warm_start": warm,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -592,21 +647,21 @@ def run_profile_batch(args):
     return 0
 
 
-def run_configs2(args):
+def configs2_section(nrr, W, torch, peaks, sms, tight_tol: float = 1e-12):
     """The q=4 spinning pair on SinhSymTP 256x256x32, Spherical 128x64x32 and
-    Cartesian 256^3 (order 8), and on the added SinhSpherical 128x64x16 grid:
-    FP32 relaxation inside the FP64
-    defect-correction loop against the plain FP64 relaxation, with the
-    difference of the two solutions and the oracle's residual of the
-    defect-corrected one (r < 100)."""
-    import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2501_14030_gb300 import nrr, workloads as W
-    from tests.helpers import oracle_grid
-    torch.cuda.set_device(0)
+    Cartesian 256^3 (order 8), and on the added SinhSpherical 128x64x16
+    grid: plain FP64 relaxation against FP32 relaxation inside the FP64
+    defect-correction loop, both to residual 1e-10, with the relative
+    difference of the two u and the oracle's residual of the defect-corrected
+    u.  Both solves are then continued to `tight_tol`, where the difference
+    of u is stated again (the 1e-10 residual fixes u only up to the
+    operator's conditioning).  Rooflines: the FP64 stage's time per launch
+    inside its solve against the FP64 peak; the FP32 stage, timed alone,
+    against the HBM copy bandwidth."""
+    from oracle import grid_from_desc as oracle_grid
     stream = torch.cuda.current_stream()
+    hbm, hbm_basis = hbm_peak_gbs()
+    fp64_peak = sms * FP64_FMA_PER_CLK * 2 * MAX_SM_MHZ * 1e6 / 1e12
     out = {}
     for name, mk in [("sinhsymtp_256x256x32", W.q4_sinhsymtp_256),
                      ("spherical_128x64x32", W.q4_spherical_128),
@@ -627,32 +682,79 @@ def run_configs2(args):
             e1.record(stream)
             e1.synchronize()
             u = torch.empty(g.shape, dtype=torch.float64, device="cuda")
-            g.get_state(u)
-            res[mode] = (r, e0.elapsed_time(e1) / 1e3, u)
+            v = torch.empty_like(u)
+            g.get_state(u, v)
+            res[mode] = (r, e0.elapsed_time(e1) / 1e3, u, v)
         udc, u64 = res["fp32_dc"][2], res["fp64"][2]
         diff = float((udc - u64).abs().max() / u64.abs().max())
-        entry = {"launch": tuned,
+        n_int = g.interior_points
+        r64, t64 = res["fp64"][0], res["fp64"][1]
+        ms64 = t64 * 1e3 / (4 * max(1, r64["iters"]))
+        ach64 = flops_per_point(g.ng) * n_int / (ms64 * 1e-3) / 1e12
+        dt, eta = g.timestep(0.5)
+        ms32 = g.profile_stages(20, dt, eta, mode="fp32")
+        ach32 = FP32_STAGE_BYTES * n_int / (ms32 * 1e-3) / 1e9
+        entry = {"launch": tuned, "interior_points": n_int,
                  "fp32_dc": {"seconds": res["fp32_dc"][1],
                              "rk4_steps": res["fp32_dc"][0]["iters"],
                              "norm": res["fp32_dc"][0]["norm"],
                              "status": res["fp32_dc"][0]["status"]},
-                 "fp64": {"seconds": res["fp64"][1],
-                          "rk4_steps": res["fp64"][0]["iters"],
-                          "norm": res["fp64"][0]["norm"],
-                          "status": res["fp64"][0]["status"]},
-                 "speedup_dc_vs_fp64": res["fp64"][1] / res["fp32_dc"][1],
+                 "fp64": {"seconds": t64, "rk4_steps": r64["iters"],
+                          "norm": r64["norm"], "status": r64["status"]},
+                 "speedup_dc_vs_fp64": t64 / res["fp32_dc"][1],
                  "max_rel_diff_u_dc_vs_fp64": diff,
-                 "gridpoint_rhs_per_s_fp64": g.interior_points * 4 *
-                 res["fp64"][0]["iters"] / res["fp64"][1]}
-        if g.interior_points <= 4_000_000:
-            og = oracle_grid(desc)
-            alpha, beta = og.source(punc)
-            entry["oracle_residual_of_dc_u"] = og.norm(
-                og.residual(alpha, beta, udc.cpu().numpy()))
+                 "gridpoint_rhs_per_s_fp64": n_int * 4 * r64["iters"] / t64,
+                 "roofline_fp64_stage": {
+                     "bound": "alu", "achieved": ach64, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+                     "ms_per_launch": ms64,
+                     "basis": "in-solve: FP64 solve time / (4 x RK4 steps); "
+                              "%d flops per point" % flops_per_point(g.ng)},
+                 "roofline_fp32_stage": {
+                     "bound": "hbm", "achieved": ach32, "peak": hbm,
+                     "unit": "GB/s", "frac": ach32 / hbm, "ms_per_launch": ms32,
+                     "basis": "stage timed alone on its work stream; %d B per "
+                              "point; peak %s" % (FP32_STAGE_BYTES, hbm_basis)}}
+        # both solves continued from their 1e-10 states to tight_tol
+        tight = {}
+        for mode in ("fp32_dc", "fp64"):
+            g.set_state(res[mode][2], res[mode][3])
+            r = g.relax(mode=mode, tol=tight_tol, max_iters=400000,
+                        initial=nrr.INIT_CURRENT, raise_on_error=False)
+            u = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+            g.get_state(u)
+            tight[mode] = (r, u)
+        entry["to_tight_tol"] = {
+            "tol": tight_tol,
+            "fp64_extra_rk4_steps": tight["fp64"][0]["iters"],
+            "fp64_norm": tight["fp64"][0]["norm"],
+            "fp32_dc_extra_rk4_steps": tight["fp32_dc"][0]["iters"],
+            "fp32_dc_norm": tight["fp32_dc"][0]["norm"],
+            "max_rel_diff_u_dc_vs_fp64": float(
+                (tight["fp32_dc"][1] - tight["fp64"][1]).abs().max()
+                / tight["fp64"][1].abs().max())}
+        og = oracle_grid(desc)
+        alpha, beta = og.source(punc)
+        entry["oracle_residual_of_dc_u"] = og.norm(
+            og.residual(alpha, beta, og.fill_inner_ghosts(udc.cpu().numpy())))
+        del og
         out[name] = entry
+        print(json.dumps({name: entry}), file=sys.stderr, flush=True)
         g.close()
-        del udc, u64, res
+        del udc, u64, res, tight
         torch.cuda.empty_cache()
+    return out
+
+
+def run_configs2(args):
+    """The larger and other-coordinate variants on their own."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = configs2_section(nrr, W, torch, nrr.probe_peaks(), sms)
     print(json.dumps({"configs2": out}), flush=True)
     return 0
 
@@ -809,6 +911,11 @@ def main():
                          "autotuning if it exists, else written after it")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-solve batch in the default run")
+    ap.add_argument("--no-configs2", action="store_true",
+                    help="skip the larger-grid section in the default run")
+    ap.add_argument("--compact-surrogate", action="store_true",
+                    help="2048 training / 128 held-out solves instead of "
+                         "8192 / 1024 in the default run")
     args = ap.parse_args()
     if args.surrogate:
         return run_surrogate(args)

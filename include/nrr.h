@@ -54,7 +54,8 @@ typedef enum {
                              /* punctures are set)                          */
 } nrr_status;
 
-enum { NRR_SINHSYMTP = 0, NRR_SPHERICAL = 1, NRR_CARTESIAN = 2, NRR_SINHSPHERICAL = 3 };
+enum { NRR_SINHSYMTP = 0, NRR_SPHERICAL = 1, NRR_CARTESIAN = 2, NRR_SINHSPHERICAL = 3,
+       NRR_SINHCYLINDRICAL = 4 };
 enum { NRR_FP64 = 0, NRR_FP32 = 1, NRR_FP32_DC = 2 };
 enum { NRR_INIT_ZERO = 0, NRR_INIT_CURRENT = 1, NRR_INIT_HOST = 2,
        NRR_INIT_DEVICE = 3 };
@@ -71,8 +72,15 @@ enum { NRR_INIT_ZERO = 0, NRR_INIT_CURRENT = 1, NRR_INIT_HOST = 2,
  *             NRR_SINHSPHERICAL: xx0 in [0,1], r = amax sinh(xx0/w)/sinh(1/w),
  *             theta and phi as above (a sinh-stretched spherical grid, one of
  *             the further families of Sec. 6).
+ *             NRR_SINHCYLINDRICAL (the cylindrical-like family of Sec. 6),
+ *             stored as (rho, z, phi): xx0 in [0,1],
+ *             rho = amax sinh(xx0/w)/sinh(1/w); xx1 in [-1,1],
+ *             z = zmax sinh(xx1/wz)/sinh(1/wz), wz = sinhwz; xx2 = phi in
+ *             [-pi,pi).  Points beyond rho = amax and beyond both ends
+ *             |z| = zmax are outer (radiation) points; rho < 0 is imaged.
  *   n[3]      interior points per direction (n[2] even for curvilinear grids).
- *   fd_order  4, 8 or 10.                                                    */
+ *   fd_order  4, 8 or 10.
+ *   zmax, sinhwz  SinhCylindrical only (ignored otherwise).                  */
 typedef struct {
   int coord;
   int n[3];
@@ -80,6 +88,7 @@ typedef struct {
   double amax, bscale, sinhwaa;
   double rmax;
   double xmax;
+  double zmax, sinhwz;
 } nrr_grid_desc;
 
 /* One puncture (paper Sec. 2, Brandt-Bruegmann data with Bowen-York
@@ -273,7 +282,8 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * variant 4 instead). Single stage launches of variants 4 and 5 run variants 0
  * and 3. Cartesian grids: variant 1 = the tensor-copy kernel under the same
  * conditions, any other variant the column kernel (zc planes per thread,
- * `block` threads). Results do not depend on the shape beyond rounding order.
+ * `block` threads). SinhCylindrical grids: variant 0 only. Results do not
+ * depend on the shape beyond rounding order.
  * Errors: NRR_ERR_INVALID_ARG for other values. */
 nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block);
 
@@ -293,6 +303,18 @@ nrr_status nrr_get_launch(const nrr_grid *g, int mode, int *variant, int *zc,
  * relaxation graphs (rebuilt on the next nrr_relax).
  * Errors: NRR_ERR_INVALID_ARG for a null grid or on not 0/1. */
 nrr_status nrr_set_pdl(nrr_grid *g, int on);
+
+/* Where the stop test of the relaxation loop runs (paper Alg. 1: the norm is
+ * evaluated every check_every steps and the loop stops below tol).  on = 1
+ * (the default): on the device -- each nrr_relax is one graph launch in
+ * which a conditional WHILE node repeats chunks of check_every RK4 steps (or
+ * defect-correction outer iterations) followed by the norm and a control
+ * kernel, and the host reads the outcome once at the end; the wall-clock
+ * limit is then measured on the device.  on = 0: the host launches one
+ * chunk's graph at a time and reads the norm after each.  Both take the same
+ * steps and give identical states.
+ * Errors: NRR_ERR_INVALID_ARG for a null grid or on not 0/1. */
+nrr_status nrr_set_device_loop(nrr_grid *g, int on);
 
 /* The autotuner's cache as a file (JSON; no paper counterpart): every launch
  * shape chosen in this process by nrr_autotune (or loaded), keyed by
@@ -517,6 +539,32 @@ int64_t nrr_kernel_launches(void);
  * Errors: NRR_ERR_INVALID_ARG, NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_selftest_wait_expiry(int which, void *stream, int *expired);
 
+/* Diagnostic of the source term's reciprocal (paper Sec. 2 source
+ * (psi_s + u)^-7, evaluated as (1 + alpha u)^-1 and products; the paper's
+ * Sec. 4 intrinsics discussion is the counterpart): out[i] = the stage
+ * kernels' reciprocal of s[i] -- the hardware approximation refined by one
+ * third-order step in FP64 (fp32 = 0) or one Newton step in FP32 (fp32 = 1).
+ * s, out: device arrays of n doubles (or floats), caller-owned.  Tests
+ * compare it with correctly rounded division.  Synchronous on `stream`.
+ * Errors: NRR_ERR_INVALID_ARG (null pointer, n < 0, fp32 not 0/1),
+ * NRR_ERR_CUDA. */
+nrr_status nrr_selftest_recip(const void *s, void *out, int64_t n, int fp32,
+                              void *stream);
+
+/* Measurement hook for the rooflines (the paper's Sec. 5 roofline uses the
+ * vendor's peaks; here they are measured): kernels of this library, timed
+ * with CUDA events on `stream` (best of five), report
+ *   fp64_tflops  FP64 FMA throughput (2 flops per FMA) with eight
+ *                independent chains per thread on every SM;
+ *   fp32_tflops  the same in FP32;
+ *   l2_gbs       read bandwidth from a buffer of l2_bytes (0: 48 MiB) that
+ *                stays in L2, read 20 times over.
+ * Allocates and frees its buffer.  Outputs host, nullable.
+ * Errors: NRR_ERR_INVALID_ARG (l2_bytes not 0 and outside [1 MiB, 4 GiB]),
+ * NRR_ERR_OOM, NRR_ERR_CUDA. */
+nrr_status nrr_probe_peaks(int64_t l2_bytes, void *stream, double *fp64_tflops,
+                           double *fp32_tflops, double *l2_gbs);
+
 /* Residual norm without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc,
  * for instance an application whose memory manager already owns the whole
@@ -543,7 +591,8 @@ nrr_status nrr_selftest_wait_expiry(int which, void *stream, int *expired);
  * another context is current (after cudaDeviceReset, for instance).
  * The caller's buffers cannot be checked here: u and h_out must hold
  * s0*s1*s2 doubles and norm_out at least one.
- * Coordinates: SinhSymTP, Spherical and Cartesian (not SinhSpherical).
+ * Coordinates: SinhSymTP, Spherical and Cartesian (not SinhSpherical or
+ * SinhCylindrical).
  * Errors: NRR_ERR_INVALID_ARG (null pointer, a descriptor the grid calls
  * reject -- see nrr_create_grid --, SinhSpherical, punctures, r_int <= 0,
  * n0*n1 beyond the scratch), NRR_ERR_CUDA (lookup or launch failure). */

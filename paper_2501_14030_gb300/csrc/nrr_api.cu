@@ -7,6 +7,7 @@
 // only host<->device traffic per chunk is the 8-byte norm.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -72,6 +73,57 @@ struct GraphKey {
   }
 };
 
+// Control block of a relaxation whose stop test runs on the device (Alg. 1:
+// evaluate the norm, stop below tol, else take more RK steps): the host
+// writes the first three fields, the control kernel the rest.
+struct RelaxCtl {
+  double tol;
+  long long max_chunks;            // chunks of check_every steps allowed
+  unsigned long long timeout_ns;   // 0: no limit
+  long long chunks;                // chunks completed
+  double norm;                     // the last norm
+  unsigned long long t0_ns;        // %globaltimer at the first test
+  int timed_out;
+  int pad;
+};
+
+namespace {
+
+// After each norm evaluation: counts the chunk, keeps the norm, and lets the
+// WHILE node run the body again while the norm is finite and >= tol, the
+// chunk limit is not reached and the device-timed limit has not passed.
+__global__ void relax_control_kernel(const double *norm, RelaxCtl *c,
+                                     cudaGraphConditionalHandle h, int first) {
+  unsigned long long now;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+  if (first) {
+    c->t0_ns = now;
+    c->chunks = 0;
+    c->timed_out = 0;
+  } else {
+    c->chunks += 1;
+  }
+  const double n = *norm;
+  c->norm = n;
+  bool go = isfinite(n) && n >= c->tol && c->chunks < c->max_chunks;
+  if (go && c->timeout_ns > 0 && now - c->t0_ns > c->timeout_ns) {
+    c->timed_out = 1;
+    go = false;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// The defect correction's increment (d, w) starts from rest.
+__global__ void zero2_kernel(float *a, float *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = 0.f;
+    b[i] = 0.f;
+  }
+}
+
+}  // namespace
+
 struct nrr_grid {
   nrr_grid_desc desc{};
   Geo geo{};
@@ -107,6 +159,12 @@ struct nrr_grid {
   int state_prec = 64;  // which FieldSet holds the current state
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, int64_t> graph_kernels;
+  // whole-solve graphs (conditional WHILE node): kernels of the prologue and
+  // of one chunk of the loop body
+  std::map<GraphKey, std::pair<int64_t, int64_t>> loop_kernels;
+  int device_loop = 1;          // stop test on the device (one graph launch)
+  struct RelaxCtl *ctl = nullptr;       // device control block
+  struct RelaxCtl *ctl_host = nullptr;  // pinned mirror
 };
 
 namespace {
@@ -201,7 +259,7 @@ size_t footprint_bytes(const Geo &geo) {
   b += n * (10 * 8 + 10 * 4);          // FP64 + FP32 field sets
   b += n * (8 + 8 + 4 + 4 + 4);        // defect-correction buffers
   b += nc * 8 * (3 + 2 + 4);           // column geometry
-  b += nc * (8 + 4) * (ncoef(geo.ng) + 4);
+  b += nc * (8 + 4) * (ncoef(geo.ng) + 5);
   b += (size_t)(geo.ncol / 32 + 16) * 16 * ((geo.n2 + 1)) + (1 << 20);
   return b;
 }
@@ -210,7 +268,7 @@ size_t footprint_bytes(const Geo &geo) {
 
 nrr_status nrr::check_grid_desc(const nrr_grid_desc *d) {
   if (!d) return fail(NRR_ERR_INVALID_ARG, "null grid descriptor");
-  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_SINHSPHERICAL)
+  if (d->coord < NRR_SINHSYMTP || d->coord > NRR_SINHCYLINDRICAL)
     return fail(NRR_ERR_INVALID_ARG, "unknown coordinate system %d", d->coord);
   if (d->fd_order != 4 && d->fd_order != 8 && d->fd_order != 10)
     return fail(NRR_ERR_INVALID_ARG, "fd_order must be 4, 8 or 10 (got %d)",
@@ -246,6 +304,10 @@ nrr_status nrr::check_grid_desc(const nrr_grid_desc *d) {
     return fail(NRR_ERR_INVALID_ARG, "SinhSpherical needs amax > 0, sinhwaa > 0");
   if (d->coord == NRR_CARTESIAN && !(d->xmax > 0))
     return fail(NRR_ERR_INVALID_ARG, "Cartesian needs xmax > 0");
+  if (d->coord == NRR_SINHCYLINDRICAL &&
+      !(d->amax > 0 && d->sinhwaa > 0 && d->zmax > 0 && d->sinhwz > 0))
+    return fail(NRR_ERR_INVALID_ARG,
+                "SinhCylindrical needs amax, sinhwaa, zmax, sinhwz > 0");
   return NRR_OK;
 }
 
@@ -269,10 +331,10 @@ Geo nrr::grid_geo(const nrr_grid_desc *d) {
     }
   } else {
     xmin[0] = 0.0;
-    xmax[0] = (d->coord == NRR_SINHSYMTP || d->coord == NRR_SINHSPHERICAL) ? 1.0
-                                                                         : d->rmax;
-    xmin[1] = 0.0;
-    xmax[1] = M_PI;
+    xmax[0] = (d->coord == NRR_SINHSYMTP || d->coord == NRR_SINHSPHERICAL ||
+               d->coord == NRR_SINHCYLINDRICAL) ? 1.0 : d->rmax;
+    xmin[1] = d->coord == NRR_SINHCYLINDRICAL ? -1.0 : 0.0;
+    xmax[1] = d->coord == NRR_SINHCYLINDRICAL ? 1.0 : M_PI;
     xmin[2] = -M_PI;
     xmax[2] = M_PI;
   }
@@ -284,6 +346,8 @@ Geo nrr::grid_geo(const nrr_grid_desc *d) {
   g.amax = d->amax;
   g.bscale = d->bscale;
   g.sinhwaa = d->sinhwaa;
+  g.zmax = d->zmax;
+  g.sinhwz = d->sinhwz;
   return g;
 }
 
@@ -339,7 +403,8 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
                       int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
   const LaunchCfg &cfg = g->stage_cfg[sizeof(R) == 4];
-  if ((cfg.variant == 4 || cfg.variant == 5) && g->geo.coord != CARTESIAN) {
+  if ((cfg.variant == 4 || cfg.variant == 5) && g->geo.coord != CARTESIAN &&
+      g->geo.coord != SINHCYLINDRICAL) {
     // all steps in one cooperative launch (grid barriers between stages)
     StageArgs<R> sa[4];
     for (int k = 0; k < 4; k++) sa[k] = stage_args<R>(g, f, c, k, dt, eta);
@@ -518,6 +583,176 @@ nrr_status relax_chunks(nrr_grid *g, int mode, double dt, double eta,
   return NRR_OK;
 }
 
+// The start of one defect-correction outer iteration: the FP64 defect
+// F = the relaxation system's right-hand side at (u, v) (into the FP64 t
+// buffers), the FP32 coefficient c^2 a and forcings from it, and the
+// increment (d, w) set to rest.
+void launch_dc_outer_prep(const nrr_grid *g, double eta) {
+  const Geo &geo = g->geo;
+  double *Fu = g->f64.t[0], *Fv = g->f64.t[1];
+  StageArgs<double> ra{};
+  ra.su = g->f64.y[0];
+  ra.sv = g->f64.y[1];
+  ra.ou = Fu;
+  ra.ov = Fv;
+  ra.alpha = g->f64.alpha;
+  ra.bc2 = g->f64.bc2;
+  ra.col = g->c64;
+  ra.cart = g->cart;
+  ra.eta = eta;
+  launch_stage<double>(geo, STAGE_RAW, ra, g->stage_cfg[0], g->stream);
+  launch_dc_prepare(geo, g->f64.y[0], g->f64.alpha, g->f64.bc2, Fu, Fv,
+                    g->acoef32, g->fu32, g->rhs32, g->stream);
+  const int64_t n = geo.npts;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  zero2_kernel<<<blocks, 256, 0, g->stream>>>(g->f32.y[0], g->f32.y[1], n);
+  g_launches += 3;
+}
+
+// One whole solve as one graph: the norm of the current state and the stop
+// test (prologue), then a conditional WHILE node whose body is one chunk --
+// check_every RK4 steps (FP64 or FP32), or one defect-correction outer
+// iteration of `every` FP32 steps with its FP64 update -- followed by the
+// norm and the stop test.  The control block's tol, chunk limit and timeout
+// are read on the device at each replay.
+nrr_status get_loop_graph(nrr_grid *g, int mode, int every, double dt,
+                          double eta, double r_int, cudaGraphExec_t *out,
+                          std::pair<int64_t, int64_t> *kernels) {
+  GraphKey key{mode + 100, every, dt, eta, r_int};
+  auto it = g->graphs.find(key);
+  if (it != g->graphs.end()) {
+    *out = it->second;
+    *kernels = g->loop_kernels[key];
+    return NRR_OK;
+  }
+  cudaGraph_t graph;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1,
+                                                   cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(NRR_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e));
+  }
+  int64_t before = g_launches.load();
+  e = cudaStreamBeginCaptureToGraph(g->stream, graph, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(NRR_ERR_CUDA, "prologue capture: %s", cudaGetErrorString(e));
+  }
+  if (mode == NRR_FP32)
+    launch_norm<float>(g, g->f32, g->c32, r_int, nullptr);
+  else
+    launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
+  relax_control_kernel<<<1, 1, 0, g->stream>>>(g->scalars + 1, g->ctl, handle, 1);
+  g_launches += 1;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(g->stream, &captured);
+  const int64_t n_pro = g_launches.load() - before;
+  if (e != cudaSuccess) {
+    g_launches -= n_pro;
+    cudaGraphDestroy(graph);
+    return fail(NRR_ERR_CUDA, "prologue capture: %s", cudaGetErrorString(e));
+  }
+  // the WHILE node after the prologue's last node
+  size_t nn = 0;
+  std::vector<cudaGraphNode_t> nodes, sinks;
+  e = cudaGraphGetNodes(graph, nullptr, &nn);
+  if (e == cudaSuccess) {
+    nodes.resize(nn);
+    e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+  }
+  for (size_t i = 0; e == cudaSuccess && i < nn; i++) {
+    size_t nout = 0;
+    e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nout);
+    if (e == cudaSuccess && nout == 0) sinks.push_back(nodes[i]);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess)
+    e = cudaGraphAddNode(&wnode, graph, sinks.data(), nullptr, sinks.size(), &cp);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(g->stream, cp.conditional.phGraph_out[0],
+                                      nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    g_launches -= n_pro;
+    cudaGraphDestroy(graph);
+    return fail(NRR_ERR_CUDA, "loop graph: %s", cudaGetErrorString(e));
+  }
+  const int64_t before_body = g_launches.load();
+  if (mode == NRR_FP32_DC) {
+    launch_dc_outer_prep(g, eta);
+    FieldSet<float> dc = dc_fields(g);
+    launch_rk4_steps<float>(g, dc, g->c32, dt, eta, every);
+    launch_dc_update(g->f64.y[0], g->f64.y[1], g->f32.y[0], g->f32.y[1],
+                     g->geo.npts, g->stream);
+    g_launches += 1;
+    launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
+  } else if (mode == NRR_FP32) {
+    launch_rk4_steps<float>(g, g->f32, g->c32, dt, eta, every);
+    launch_norm<float>(g, g->f32, g->c32, r_int, nullptr);
+  } else {
+    launch_rk4_steps<double>(g, g->f64, g->c64, dt, eta, every);
+    launch_norm<double>(g, g->f64, g->c64, r_int, nullptr);
+  }
+  relax_control_kernel<<<1, 1, 0, g->stream>>>(g->scalars + 1, g->ctl, handle, 0);
+  g_launches += 1;
+  e = cudaStreamEndCapture(g->stream, &captured);
+  const int64_t n_body = g_launches.load() - before_body;
+  g_launches -= n_pro + n_body;  // captured, not executed
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(NRR_ERR_CUDA, "loop body capture: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return fail(NRR_ERR_CUDA, "loop graph instantiate: %s", cudaGetErrorString(e));
+  g->graphs[key] = exec;
+  g->loop_kernels[key] = {n_pro, n_body};
+  *out = exec;
+  *kernels = {n_pro, n_body};
+  return NRR_OK;
+}
+
+// Up to max_chunks chunks of `every` steps with the stop test on the device,
+// in one graph launch and one read-back of the control block.  *chunks,
+// *norm: chunks done and the last norm; *timed_out: the device-timed limit
+// stopped it.
+nrr_status relax_device_loop(nrr_grid *g, int mode, int every, double dt,
+                             double eta, double tol, double r_int,
+                             int64_t max_chunks, int64_t timeout_ms,
+                             double t_start, int64_t *chunks, double *norm,
+                             bool *timed_out) {
+  cudaGraphExec_t exec;
+  std::pair<int64_t, int64_t> kern;
+  TRY(get_loop_graph(g, mode, every, dt, eta, r_int, &exec, &kern));
+  RelaxCtl *h = g->ctl_host;
+  memset(h, 0, sizeof *h);
+  h->tol = tol;
+  h->max_chunks = max_chunks;
+  if (timeout_ms > 0) {
+    const double left_ms = (double)timeout_ms - (now_s() - t_start) * 1e3;
+    h->timeout_ns = left_ms > 1e-3 ? (unsigned long long)(left_ms * 1e6) : 1ull;
+  }
+  CUDA_TRY(cudaMemcpyAsync(g->ctl, h, sizeof *h, cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaGraphLaunch(exec, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(h, g->ctl, sizeof *h, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  *chunks = h->chunks;
+  *norm = h->norm;
+  *timed_out = h->timed_out != 0;
+  g_launches += kern.first + h->chunks * kern.second;
+  return NRR_OK;
+}
+
 // Defect correction of the relaxation itself.  Outer iteration, in FP64:
 // the full right-hand side F of the relaxation system (with its boundary
 // conditions) at the current state (u, v) -- the defect -- and the
@@ -532,18 +767,32 @@ nrr_status relax_defect_correction(nrr_grid *g, const nrr_relax_opts *o,
                                    double dt, double eta, double t_start,
                                    nrr_relax_result *res) {
   const Geo &geo = g->geo;
-  const size_t n = (size_t)geo.npts;
   TRY(ensure_state(g, 64));
   const int64_t inner = o->inner_steps > 0 ? o->inner_steps : o->check_every;
-  launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
   double norm64 = 0.0;
-  TRY(sync_read_norm(g, &norm64));
   int64_t steps_total = 0;
   int64_t outer = 0;
   nrr_status status = NRR_ERR_NOT_CONVERGED;
+  bool timed_out = false;
+  if (g->device_loop) {
+    // every whole outer iteration that max_iters and max_outer allow, with
+    // the stop test on the device; the host loop below finishes a shorter
+    // last one, if any
+    int64_t max_chunks = o->max_iters / inner;
+    if (o->max_outer > 0) max_chunks = std::min<int64_t>(max_chunks, o->max_outer);
+    int64_t chunks = 0;
+    TRY(relax_device_loop(g, NRR_FP32_DC, (int)inner, dt, eta, o->tol, o->r_int,
+                          max_chunks, o->timeout_ms, t_start, &chunks, &norm64,
+                          &timed_out));
+    steps_total = chunks * inner;
+    outer = chunks;
+    if (timed_out) status = NRR_ERR_TIMEOUT;
+  } else {
+    launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+    TRY(sync_read_norm(g, &norm64));
+  }
   FieldSet<float> dc = dc_fields(g);
-  double *Fu = g->f64.t[0], *Fv = g->f64.t[1];  // FP64 defect (scratch)
-  for (;;) {
+  for (; !timed_out;) {
     if (!std::isfinite(norm64)) {
       status = NRR_ERR_DIVERGED;
       break;
@@ -560,23 +809,7 @@ nrr_status relax_defect_correction(nrr_grid *g, const nrr_relax_opts *o,
     }
     int64_t m = inner;
     if (o->max_iters - steps_total < m) m = o->max_iters - steps_total;
-    // FP64 defect at (u, v), then the FP32 forcing and coefficient
-    StageArgs<double> ra{};
-    ra.su = g->f64.y[0];
-    ra.sv = g->f64.y[1];
-    ra.ou = Fu;
-    ra.ov = Fv;
-    ra.alpha = g->f64.alpha;
-    ra.bc2 = g->f64.bc2;
-    ra.col = g->c64;
-    ra.cart = g->cart;
-    ra.eta = eta;
-    launch_stage<double>(geo, STAGE_RAW, ra, g->stage_cfg[0], g->stream);
-    launch_dc_prepare(geo, g->f64.y[0], g->f64.alpha, g->f64.bc2, Fu, Fv,
-                      g->acoef32, g->fu32, g->rhs32, g->stream);
-    CUDA_TRY(cudaMemsetAsync(g->f32.y[0], 0, n * sizeof(float), g->stream));
-    CUDA_TRY(cudaMemsetAsync(g->f32.y[1], 0, n * sizeof(float), g->stream));
-    g_launches += 2;
+    launch_dc_outer_prep(g, eta);
     if (m == inner) {
       cudaGraphExec_t exec;
       TRY(get_graph(g, NRR_FP32_DC, (int)m, dt, eta, o->r_int, &exec));
@@ -703,10 +936,10 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
     TRY(dev_alloc(g, &g->jac, nc));
     TRY(dev_alloc(g, &g->dsmin, nc));
     TRY(dev_alloc(g, &g->c64.coef, (size_t)nco * nc));
-    TRY(dev_alloc(g, &g->c64.somm, 3 * (size_t)nc));
+    TRY(dev_alloc(g, &g->c64.somm, 4 * (size_t)nc));
     TRY(dev_alloc(g, &g->c64.c2inv, nc));
     TRY(dev_alloc(g, &g->c32.coef, (size_t)nco * nc));
-    TRY(dev_alloc(g, &g->c32.somm, 3 * (size_t)nc));
+    TRY(dev_alloc(g, &g->c32.somm, 4 * (size_t)nc));
     TRY(dev_alloc(g, &g->c32.c2inv, nc));
     TRY(dev_alloc(g, &g->scalars, 8));
     int nb = residual_blocks(geo, g->res_cfg);
@@ -715,6 +948,9 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
     TRY(dev_alloc(g, &g->flag, 4));
     CUDA_TRY(cudaMemsetAsync(g->flag, 0, 4 * sizeof(int), g->stream));
     CUDA_TRY(cudaMallocHost(&g->host_pinned, 8 * sizeof(double)));
+    TRY(dev_alloc(g, reinterpret_cast<double **>(&g->ctl),
+                  (sizeof(RelaxCtl) + 7) / 8));
+    CUDA_TRY(cudaMallocHost(&g->ctl_host, sizeof(RelaxCtl)));
     // zero all state so unset regions are finite
     for (int c = 0; c < 2; c++) {
       double *f64s[4] = {g->f64.y[c], g->f64.s[c], g->f64.t[c], g->f64.a[c]};
@@ -787,6 +1023,7 @@ nrr_status nrr_destroy_grid(nrr_grid *g) {
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   for (void *p : g->allocs) cudaFree(p);
   if (g->host_pinned) cudaFreeHost(g->host_pinned);
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
   if (g->order_ev) cudaEventDestroy(g->order_ev);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -992,12 +1229,16 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block)
     return fail(NRR_ERR_INVALID_ARG,
                 "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled, tensor-copy), "
                 "1 (persistent, multi-stage)");
+  if (g->geo.coord == SINHCYLINDRICAL && variant != 0)
+    return fail(NRR_ERR_INVALID_ARG,
+                "SinhCylindrical grids run the column kernel (variant 0) only");
   g->stage_cfg[mode == NRR_FP32].variant = variant;
   g->stage_cfg[mode == NRR_FP32].zc = zc;
   if (block) g->stage_cfg[mode == NRR_FP32].block = block;
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
+  g->loop_kernels.clear();
   return NRR_OK;
 }
 
@@ -1021,6 +1262,14 @@ nrr_status nrr_set_pdl(nrr_grid *g, int on) {
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
+  g->loop_kernels.clear();
+  return NRR_OK;
+}
+
+nrr_status nrr_set_device_loop(nrr_grid *g, int on) {
+  TRY(check_grid(g));
+  if (on != 0 && on != 1) return fail(NRR_ERR_INVALID_ARG, "on must be 0 or 1");
+  g->device_loop = on;
   return NRR_OK;
 }
 
@@ -1134,6 +1383,8 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
                                {256, 4, 3},  {256, 8, 3},  {256, 16, 3}, {128, 1, 4},
                                {128, 4, 5},  {128, 8, 5},  {128, 16, 5}};
   for (const LaunchCfg &cand0 : cands) {
+    // SinhCylindrical grids have the column kernel only
+    if (g->geo.coord == SINHCYLINDRICAL && cand0.variant != 0) continue;
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;
     cfg = cand;
@@ -1172,6 +1423,7 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   g->graph_kernels.clear();
+  g->loop_kernels.clear();
   if (best_variant) *best_variant = best.variant;
   if (best_zc) *best_zc = best.zc;
   if (best_ms_per_launch) *best_ms_per_launch = best_ms;
@@ -1254,15 +1506,32 @@ nrr_status nrr_relax(nrr_grid *g, const nrr_relax_opts *o,
   } else {
     int prec = o->mode == NRR_FP32 ? 32 : 64;
     TRY(ensure_state(g, prec));
-    if (prec == 32)
-      launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
-    else
-      launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
-    CUDA_TRY(cudaGetLastError());
-    TRY(sync_read_norm(g, &nrm));
-    TRY(relax_chunks(g, o->mode, dt, eta, o->tol, o->r_int, o->check_every,
-                     o->max_iters, t_start, o->timeout_ms, &it, &nrm,
-                     &status));
+    bool timed_out = false;
+    int64_t it0 = 0;
+    if (g->device_loop) {
+      // whole chunks with the stop test on the device; relax_chunks below
+      // finishes a shorter last chunk, if max_iters leaves one
+      int64_t chunks = 0;
+      TRY(relax_device_loop(g, o->mode, o->check_every, dt, eta, o->tol,
+                            o->r_int, o->max_iters / o->check_every,
+                            o->timeout_ms, t_start, &chunks, &nrm, &timed_out));
+      it0 = chunks * o->check_every;
+    } else {
+      if (prec == 32)
+        launch_norm<float>(g, g->f32, g->c32, o->r_int, nullptr);
+      else
+        launch_norm<double>(g, g->f64, g->c64, o->r_int, nullptr);
+      CUDA_TRY(cudaGetLastError());
+      TRY(sync_read_norm(g, &nrm));
+    }
+    if (timed_out) {
+      status = NRR_ERR_TIMEOUT;
+    } else {
+      TRY(relax_chunks(g, o->mode, dt, eta, o->tol, o->r_int, o->check_every,
+                       o->max_iters - it0, t_start, o->timeout_ms, &it, &nrm,
+                       &status));
+    }
+    it += it0;
     res.iters = it;
     res.outer_iters = 0;
     res.final_norm = nrm;

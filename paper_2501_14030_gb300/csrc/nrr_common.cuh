@@ -16,7 +16,8 @@
 
 namespace nrr {
 
-enum Coord { SINHSYMTP = 0, SPHERICAL = 1, CARTESIAN = 2, SINHSPHERICAL = 3 };
+enum Coord { SINHSYMTP = 0, SPHERICAL = 1, CARTESIAN = 2, SINHSPHERICAL = 3,
+             SINHCYLINDRICAL = 4 };
 
 // Spherical-like maps (radius odd in xx0): the xx0 < 0 image also reflects
 // theta.
@@ -35,6 +36,7 @@ struct Geo {
   double xxmin[3];
   double dxx[3];
   double amax, bscale, sinhwaa;
+  double zmax, sinhwz;  // SinhCylindrical: z = zmax sinh(xx1/sinhwz)/sinh(1/sinhwz)
 };
 
 NRR_HD int64_t flat(const Geo &g, int i0, int i1, int i2) {
@@ -54,6 +56,8 @@ NRR_HD int wrap_phi(const Geo &g, int i2) {
 //   SinhSymTP: (xx0,th,ph) with xx0<0 -> (-xx0, th, ph+pi)   [A odd, Z even]
 //              th<0 -> (-th, ph+pi); th>pi -> (2pi-th, ph+pi)
 //   Spherical, SinhSpherical: r<0 -> (-r, pi-th, ph+pi); theta rules as above
+//   SinhCylindrical (rho, z, ph): rho<0 -> (-rho, z, ph+pi); points beyond
+//              the ends in z are evolved (outer), not images
 //   phi periodic.
 // Evolved points (interior and the outer shell) map to themselves.
 NRR_HD void image_of(const Geo &g, int &i0, int &i1, int &i2) {
@@ -62,6 +66,10 @@ NRR_HD void image_of(const Geo &g, int &i0, int &i1, int &i2) {
     i0 = 2 * g.ng - 1 - i0;
     flip ^= 1;
     if (spherical_like(g.coord)) i1 = g.n1 + 2 * g.ng - 1 - i1;
+  }
+  if (g.coord == SINHCYLINDRICAL) {
+    i2 = wrap_phi(g, i2 + (flip ? g.n2 / 2 : 0));
+    return;
   }
   if (i1 < g.ng) {
     i1 = 2 * g.ng - 1 - i1;

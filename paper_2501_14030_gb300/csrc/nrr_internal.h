@@ -40,7 +40,8 @@ inline int ncoef(int ng) { return 5 * ng + 1; }
 template <typename R>
 struct ColumnSet {
   R *coef = nullptr;   // [ncoef][ncol] c^2-scaled Laplacian weights
-  R *somm = nullptr;   // [3][ncol]: c, 1/(2 dxx0 dr/dxx0), 1/r
+  R *somm = nullptr;   // [3][ncol]: c, 1/(2 dxx0 dr/dxx0), 1/r; SinhCylindrical
+                       // [4][ncol]: c, rho/(2 dxx0 r rho'), 1/r, z/(2 dxx1 r z')
   R *c2inv = nullptr;  // [ncol] 1/c^2
 };
 

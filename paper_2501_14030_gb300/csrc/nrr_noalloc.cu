@@ -268,7 +268,7 @@ extern "C" nrr_status nrr_residual_noalloc(const nrr_grid_desc *d, int npunct,
     nrr_status s = check_grid_desc(d);  // the check every entry point shares
     if (s != NRR_OK) return s;
   }
-  if (d->coord == NRR_SINHSPHERICAL)
+  if (d->coord == NRR_SINHSPHERICAL || d->coord == NRR_SINHCYLINDRICAL)
     return fail(NRR_ERR_INVALID_ARG,
                 "the allocation-free residual takes SinhSymTP, Spherical or Cartesian grids");
   if (npunct < 1 || npunct > 8)

@@ -1,9 +1,8 @@
 // nrr_setup.cu -- device set-up of one grid (arXiv 2501.14030, Alg. 1 set-up:
 // coordinate arrays, reference-metric precompute, constant source terms).
 //
-// Curvilinear grids (SinhSymTP, Spherical, SinhSpherical) have a reference
-// metric that does
-// not depend on phi, so everything except the source lives in per-column
+// Curvilinear grids (SinhSymTP, Spherical, SinhSpherical, SinhCylindrical)
+// have a reference metric that does not depend on phi, so everything except the source lives in per-column
 // arrays indexed col = i0 + s0*i1.
 #include <cuda_runtime.h>
 
@@ -28,8 +27,27 @@ struct ColGeom {
 // Spherical: h = (1, r, r sin th), g0 = 2/r, g1 = cot th / r^2.
 // SinhSpherical, r = amax sinh(xx0/w)/sinh(1/w): h = (r', r, r sin th),
 //   g0 = 2/(r r') - r''/r'^3, g1 = cot th / r^2.
+// SinhCylindrical, columns (rho(xx0), z(xx1)) with sinh-stretched rho and z:
+//   h = (rho', z', rho), g0 = 1/(rho rho') - rho''/rho'^3, g1 = -z''/z'^3.
 __device__ ColGeom column_geom(const Geo &g, double xx0, double th) {
   ColGeom o;
+  if (g.coord == SINHCYLINDRICAL) {
+    const double w = g.sinhwaa, wz = g.sinhwz;
+    const double rho = g.amax * sinh(xx0 / w) / sinh(1.0 / w);
+    const double rhop = g.amax * cosh(xx0 / w) / (w * sinh(1.0 / w));
+    const double rhopp = rho / (w * w);
+    const double z = g.zmax * sinh(th / wz) / sinh(1.0 / wz);
+    const double zp = g.zmax * cosh(th / wz) / (wz * sinh(1.0 / wz));
+    const double zpp = z / (wz * wz);
+    o.h[0] = rhop;
+    o.h[1] = zp;
+    o.h[2] = rho;
+    o.gl[0] = 1.0 / (rho * rhop) - rhopp / (rhop * rhop * rhop);
+    o.gl[1] = -zpp / (zp * zp * zp);
+    o.r = sqrt(rho * rho + z * z);
+    o.drdxx0 = rhop;
+    return o;
+  }
   double st, ct;
   sincos(th, &st, &ct);
   if (g.coord == SINHSYMTP) {
@@ -157,6 +175,19 @@ __global__ void column_coefs_kernel(Geo g, const double *h, const double *gl,
     c32.coef[j * nc + col] = (float)vals[j];
   }
   double sm[3] = {c, 1.0 / (2.0 * g.dxx[0] * drdxx0[col]), 1.0 / rad[col]};
+  if (g.coord == SINHCYLINDRICAL) {
+    // d_r f = (rho/r)(1/rho') D_xx0 f + (z/r)(1/z') D_xx1 f, both D with
+    // the 1/(2 dxx) of the second-order differences folded in: row 1 holds
+    // the rho factor, row 3 (SinhCylindrical only) the z factor
+    const int i1 = col / g.s0;
+    const double xx1 = g.xxmin[1] + (i1 - ng + 0.5) * g.dxx[1];
+    const double z = g.zmax * sinh(xx1 / g.sinhwz) / sinh(1.0 / g.sinhwz);
+    const double rho = h[2 * nc + col];
+    sm[1] = rho / (rad[col] * 2.0 * g.dxx[0] * h[col]);
+    const double kz = z / (rad[col] * 2.0 * g.dxx[1] * h[nc + col]);
+    c64.somm[3 * nc + col] = kz;
+    c32.somm[3 * nc + col] = (float)kz;
+  }
   for (int j = 0; j < 3; j++) {
     c64.somm[j * nc + col] = sm[j];
     c32.somm[j * nc + col] = (float)sm[j];
@@ -180,6 +211,13 @@ __device__ void cart_position(const Geo &g, int i0, int i1, int i2,
   double st, ct, sp, cp;
   sincos(xx1, &st, &ct);
   sincos(xx2, &sp, &cp);
+  if (g.coord == SINHCYLINDRICAL) {
+    const double rho = g.amax * sinh(xx0 / g.sinhwaa) / sinh(1.0 / g.sinhwaa);
+    x[0] = rho * cp;
+    x[1] = rho * sp;
+    x[2] = g.zmax * sinh(xx1 / g.sinhwz) / sinh(1.0 / g.sinhwz);
+    return;
+  }
   if (g.coord == SINHSYMTP) {
     double A = g.amax * sinh(xx0 / g.sinhwaa) / sinh(1.0 / g.sinhwaa);
     double Z = sqrt(A * A + g.bscale * g.bscale);

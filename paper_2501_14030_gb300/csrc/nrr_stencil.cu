@@ -62,6 +62,18 @@ __global__ void __launch_bounds__(256)
   stage_curvi_item<R, NG, KIND, ZC>(g, a, e, NG + blockIdx.y * ZC);
 }
 
+// SinhCylindrical column kernel: the interior columns as above (with the z
+// direction read as stored), then the outer shell beyond the side and both
+// ends; ZC phi planes per thread.
+template <typename R, int NG, int KIND, int ZC>
+__global__ void __launch_bounds__(256)
+    stage_cyl_kernel(Geo g, StageArgs<R> a) {
+  pdl_trigger();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.n0 * g.n1 + NG * g.n1 + 2 * NG * (g.n0 + NG)) return;
+  stage_curvi_item<R, NG, KIND, ZC, false, true>(g, a, e, NG + blockIdx.y * ZC);
+}
+
 // Persistent column kernel: exactly (resident blocks x SMs) blocks stride
 // over single (column, plane) items, so the remainder of the work is spread
 // evenly over all SMs instead of forming a partial last wave.
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 4 : 1)
 
 // Residual H at interior points and the block partials of H^2 J, J over
 // r < r_int (the volume-weighted L2 norm of Alg. 1's residual).
-template <typename R, int NG>
+template <typename R, int NG, bool CYL = false>
 __global__ void __launch_bounds__(128)
     residual_curvi_kernel(Geo g, const R *__restrict__ su,
                           const R *__restrict__ alpha, const R *__restrict__ bc2,
@@ -604,8 +616,8 @@ __global__ void __launch_bounds__(128)
     const int col = (e % g.n0 + NG) + g.s0 * (e / g.n0 + NG);
     const double wt = rad[col] < r_int ? jac[col] : 0.0;
     const int z0 = NG + blockIdx.y * zc;
-    residual_curvi_item<R, NG>(g, su, alpha, bc2, col_set, wt, e, z0,
-                               min(z0 + zc, NG + g.n2), lin, h_out, num, den);
+    residual_curvi_item<R, NG, CYL>(g, su, alpha, bc2, col_set, wt, e, z0,
+                                    min(z0 + zc, NG + g.n2), lin, h_out, num, den);
   }
   block_sum2(num, den, partials + 2 * (blockIdx.x + gridDim.x * blockIdx.y));
 }
@@ -664,8 +676,10 @@ __global__ void fill_ghosts_kernel(Geo g, R *f) {
   int i0 = (int)(p % g.s0);
   int i1 = (int)((p / g.s0) % g.s1);
   int i2 = (int)(p / g.ncol);
-  bool evolved = i0 >= g.ng && i1 >= g.ng && i1 < g.n1 + g.ng && i2 >= g.ng &&
-                 i2 < g.n2 + g.ng;
+  // (SinhCylindrical rows beyond the ends in z are evolved outer points)
+  bool evolved = i0 >= g.ng &&
+                 (g.coord == SINHCYLINDRICAL || (i1 >= g.ng && i1 < g.n1 + g.ng)) &&
+                 i2 >= g.ng && i2 < g.n2 + g.ng;
   if (evolved) return;
   int j0 = i0, j1 = i1, j2 = i2;
   image_of(g, j0, j1, j2);
@@ -748,6 +762,25 @@ void launch_column_zc(const Geo &g, const StageArgs<R> &a, int block, int pdl,
   dim3 grid(((g.n0 + NG) * g.n1 + block - 1) / block, (g.n2 + ZC - 1) / ZC);
   launch_stage_kernel(stage_curvi_kernel<R, NG, KIND, ZC>, grid, dim3(block), st,
                       pdl, g, a);
+}
+
+template <typename R, int NG, int KIND, int ZC>
+void launch_cyl_zc(const Geo &g, const StageArgs<R> &a, int block, int pdl,
+                   cudaStream_t st) {
+  const int ncols = g.n0 * g.n1 + NG * g.n1 + 2 * NG * (g.n0 + NG);
+  dim3 grid((ncols + block - 1) / block, (g.n2 + ZC - 1) / ZC);
+  launch_stage_kernel(stage_cyl_kernel<R, NG, KIND, ZC>, grid, dim3(block), st,
+                      pdl, g, a);
+}
+
+template <typename R, int NG, int KIND>
+void launch_cyl_kind(const Geo &g, const StageArgs<R> &a, int zc, int block,
+                     int pdl, cudaStream_t st) {
+  switch (zc) {
+    case 1: launch_cyl_zc<R, NG, KIND, 1>(g, a, block, pdl, st); break;
+    case 4: launch_cyl_zc<R, NG, KIND, 4>(g, a, block, pdl, st); break;
+    default: launch_cyl_zc<R, NG, KIND, 2>(g, a, block, pdl, st); break;
+  }
 }
 
 template <typename R, int NG, int KIND>
@@ -1052,6 +1085,19 @@ void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
     }
     return;
   }
+  if (g.coord == SINHCYLINDRICAL) {
+    // the column kernel only (the other stage-kernel variants treat the
+    // second direction as theta)
+    const int zc = (cfg.variant == 0 && (cfg.zc == 1 || cfg.zc == 2 || cfg.zc == 4))
+                       ? cfg.zc : 1;
+    switch (kind) {
+      case STAGE_FIRST: launch_cyl_kind<R, NG, STAGE_FIRST>(g, a, zc, cfg.block, cfg.pdl, st); break;
+      case STAGE_MID: launch_cyl_kind<R, NG, STAGE_MID>(g, a, zc, cfg.block, cfg.pdl, st); break;
+      case STAGE_LAST: launch_cyl_kind<R, NG, STAGE_LAST>(g, a, zc, cfg.block, cfg.pdl, st); break;
+      default: launch_cyl_kind<R, NG, STAGE_RAW>(g, a, zc, cfg.block, cfg.pdl, st); break;
+    }
+    return;
+  }
   launch_curvi<R, NG>(g, kind, a, cfg, st);
 }
 
@@ -1066,6 +1112,9 @@ void launch_residual_ng(const Geo &g, const R *u, const R *alpha, const R *bc2,
   if (g.coord == CARTESIAN)
     residual_cart_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
         g, u, alpha, bc2, cart, r_int, h_out, partials, cfg.zc, lin);
+  else if (g.coord == SINHCYLINDRICAL)
+    residual_curvi_kernel<R, NG, true><<<grid, cfg.block, 0, st>>>(
+        g, u, alpha, bc2, col, jac, rad, r_int, h_out, partials, cfg.zc, lin);
   else
     residual_curvi_kernel<R, NG><<<grid, cfg.block, 0, st>>>(
         g, u, alpha, bc2, col, jac, rad, r_int, h_out, partials, cfg.zc, lin);

@@ -12,20 +12,35 @@
 namespace nrr {
 namespace dev {
 
+// Solve-constant data (folded stencil weights, boundary factors): the
+// read-only path.  These are the only arrays a stage kernel reads before
+// pdl_wait().
+template <typename R>
+__device__ __forceinline__ R ldc(const R *p) {
+  return __ldg(p);
+}
+
+// Everything a preceding kernel may have written (stage and base state, the
+// accumulator, the defect correction's coefficient and forcings): plain
+// coherent loads.  A read-only load counts as invariant for the whole
+// kernel, so the compiler may issue it ahead of the griddepcontrol.wait
+// statement -- before the preceding stage has finished writing -- and with
+// programmatic dependent launch that reads stale state.  A plain load stays
+// behind the wait's memory clobber.
 template <typename R>
 __device__ __forceinline__ R ld(const R *p) {
-  return __ldg(p);
+  return *p;
 }
 
 // Loads of state written earlier in the same launch (the multi-stage kernel
 // below, after a grid barrier) go through L2 (ld.global.cg); everything
-// else through the read-only path.
+// else with plain loads (ld above).
 template <bool COH, typename R>
 __device__ __forceinline__ R lds(const R *p) {
   if constexpr (COH)
     return __ldcg(p);
   else
-    return __ldg(p);
+    return ld(p);
 }
 
 // Programmatic dependent launch: a stage kernel launched with the
@@ -92,7 +107,11 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
 // warp instruction every 64 cycles per SM sub-partition) latency is hidden
 // by the other warps, and a second chain would cost its own multiply and
 // the add that joins the two.
-template <typename R, int NG, int ZC, bool COH = false>
+//
+// CYL (SinhCylindrical, columns (rho, z)): the second direction is z, whose
+// ghost rows beyond both ends are evolved outer points read as stored
+// instead of theta reflections.
+template <typename R, int NG, int ZC, bool COH = false, bool CYL = false>
 __device__ __forceinline__ void curvi_operator(
     const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
     int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
@@ -124,7 +143,7 @@ __device__ __forceinline__ void curvi_operator(
 #pragma unroll
   for (int k = 1; k <= NG; k++) {
     const int ip = i1 + k, im = i1 - k;
-    const bool rp = ip >= g.n1 + NG, rm = im < NG;
+    const bool rp = !CYL && ip >= g.n1 + NG, rm = !CYL && im < NG;
     const int cp = i0 + s0 * (rp ? 2 * g.n1 + 2 * NG - 1 - ip : ip);
     const int cm = i0 + s0 * (rm ? 2 * NG - 1 - im : im);
 #pragma unroll
@@ -204,11 +223,77 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
 // interior ones (i0 fastest); the NG n1 columns after them form the outer
 // shell i0 >= n0+ng.  Numbering the shell last keeps the short radiation
 // path out of the interior warps (except the one warp at the seam).
-template <typename R, int NG, int KIND, int ZC, bool COH = false>
+// SinhCylindrical outer shell, item s of NG n1 + 2 NG (n0 + NG) columns: first
+// the side beyond rho = amax (i0 >= n0+NG, interior i1), then the rows beyond
+// both ends in z (i1 < NG or i1 >= n1+NG, i0 from NG).  Radiation condition
+// df/dt = -c (d_r f + f/r) with d_r f = (rho/r)(1/rho') D_xx0 f +
+// (z/r)(1/z') D_xx1 f; each second-order difference one-sided inward where
+// the point lies beyond that direction's boundary, centred otherwise.  At
+// i0 = NG the centred xx0 difference reaches the rho < 0 image: the same
+// column at phi + pi.
+template <typename R, int NG, int KIND, int ZC>
+__device__ __forceinline__ void stage_cyl_shell(const Geo &g, const StageArgs<R> &a,
+                                                int s, int z0) {
+  const int nside = NG * g.n1;
+  int i0, i1;
+  if (s < nside) {
+    i0 = g.n0 + NG + s % NG;
+    i1 = NG + s / NG;
+  } else {
+    const int t = s - nside, wdt = g.n0 + NG, row = t / wdt;
+    i0 = NG + t % wdt;
+    i1 = row < NG ? row : g.n1 + row;
+  }
+  const int col = i0 + g.s0 * i1;
+  const int nc = g.ncol, s0 = g.s0;
+  const int zend = NG + g.n2;
+  const R c = ldc(a.col.somm + col), kr = ldc(a.col.somm + nc + col),
+          rinv = ldc(a.col.somm + 2 * nc + col), kz = ldc(a.col.somm + 3 * nc + col);
+  const bool out0 = i0 >= g.n0 + NG;
+  const int side1 = i1 >= g.n1 + NG ? 1 : (i1 < NG ? -1 : 0);
+  pdl_wait();
+#pragma unroll
+  for (int j = 0; j < ZC; j++) {
+    const int z = z0 + j;
+    if (z >= zend) break;
+    const int64_t p = col + (int64_t)nc * z;
+    const int64_t pm = i0 == NG ? col + (int64_t)nc * wrap_plane<NG>(g, z + g.n2 / 2)
+                                : p - 1;
+    R k2[2];
+#pragma unroll
+    for (int f = 0; f < 2; f++) {
+      const R *q = f == 0 ? a.su : a.sv;
+      const R f0 = ld(q + p);
+      const R d0 = out0 ? fma(R(3), f0, fma(R(-4), ld(q + p - 1), ld(q + p - 2)))
+                        : ld(q + p + 1) - ld(q + pm);
+      R d1;
+      if (side1 > 0)
+        d1 = fma(R(3), f0, fma(R(-4), ld(q + p - s0), ld(q + p - 2 * s0)));
+      else if (side1 < 0)
+        d1 = -fma(R(3), f0, fma(R(-4), ld(q + p + s0), ld(q + p + 2 * s0)));
+      else
+        d1 = ld(q + p + s0) - ld(q + p - s0);
+      k2[f] = -c * fma(kr, d0, fma(kz, d1, rinv * f0));
+    }
+    if (linear_mode<R>(a.lin)) {
+      k2[0] += ld(a.fu + p);
+      k2[1] += ld(a.bc2 + p);
+    }
+    stage_epilogue<R, KIND>(a, p, k2[0], k2[1]);
+  }
+}
+
+template <typename R, int NG, int KIND, int ZC, bool COH = false, bool CYL = false>
 __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R> &a,
                                                  int e, int z0) {
   const int nint = g.n0 * g.n1;
   const bool shell = e >= nint;
+  if constexpr (CYL) {
+    if (shell) {
+      stage_cyl_shell<R, NG, KIND, ZC>(g, a, e - nint, z0);
+      return;
+    }
+  }
   const int i0 = shell ? g.n0 + NG + (e - nint) % NG : e % g.n0 + NG;
   const int i1 = (shell ? (e - nint) / NG : e / g.n0) + NG;
   const int col = i0 + g.s0 * i1;
@@ -217,8 +302,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
   if (shell) {
     // Radiation condition, df/dt = -c (d_r f + f/r), d_r from the
     // second-order backward difference along xx0.
-    R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
-      rinv = ld(a.col.somm + 2 * nc + col);
+    R c = ldc(a.col.somm + col), kdb = ldc(a.col.somm + nc + col),
+      rinv = ldc(a.col.somm + 2 * nc + col);
     pdl_wait();
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
@@ -242,7 +327,7 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
   }
   R w[5 * NG + 1];
 #pragma unroll
-  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ldc(a.col.coef + (int64_t)j * nc + col);
   int wp[ZC + 2 * NG], wh[ZC];
   plane_tables<NG, ZC>(g, z0, wp, wh);
   pdl_wait();
@@ -271,8 +356,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
     }
     fu[j] = linear_mode<R>(a.lin) ? ld(a.fu + p) : R(0);
   }
-  curvi_operator<R, NG, ZC, COH>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc, kv,
-                                 a.lin);
+  curvi_operator<R, NG, ZC, COH, CYL>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc,
+                                      kv, a.lin);
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
     if (z0 + j >= zend) break;
@@ -330,7 +415,7 @@ __device__ __forceinline__ void block_sum2(double &x, double &y, double *out) {
 // fastest over the n0 x n1 interior columns) on planes [z0, z1): H at each
 // point (written to h_out if given) and the sums of H^2 wt and wt with the
 // column's norm weight wt.
-template <typename R, int NG>
+template <typename R, int NG, bool CYL = false>
 __device__ __forceinline__ void residual_curvi_item(
     const Geo &g, const R *__restrict__ su, const R *__restrict__ alpha,
     const R *__restrict__ bc2, const ColumnSet<R> &col_set, double wt, int e,
@@ -341,14 +426,15 @@ __device__ __forceinline__ void residual_curvi_item(
   R w[5 * NG + 1];
 #pragma unroll
   for (int j = 0; j < 5 * NG + 1; j++)
-    w[j] = ld(col_set.coef + (int64_t)j * nc + col);
-  R c2inv = ld(col_set.c2inv + col);
+    w[j] = ldc(col_set.coef + (int64_t)j * nc + col);
+  R c2inv = ldc(col_set.c2inv + col);
   for (int i2 = z0; i2 < z1; i2++) {
     int wp[1 + 2 * NG], wh[1];
     plane_tables<NG, 1>(g, i2, wp, wh);
     int64_t p = col + (int64_t)nc * i2;
     R u0[1] = {ld(su + p)}, al[1] = {ld(alpha + p)}, bc[1] = {ld(bc2 + p)}, op[1];
-    curvi_operator<R, NG, 1>(g, su, w, col, i0, i1, wp, wh, u0, al, bc, op, lin);
+    curvi_operator<R, NG, 1, false, CYL>(g, su, w, col, i0, i1, wp, wh, u0, al, bc,
+                                         op, lin);
     double H = (double)(op[0] * c2inv);
     if (h_out) h_out[p] = H;
     num += H * H * wt;
@@ -389,8 +475,8 @@ __device__ __forceinline__ void stage_shell_rows(const Geo &g, const StageArgs<R
   const int nc = g.ncol;
   const int i0 = g.n0 + NG + tx;
   const int col = i0 + g.s0 * i1;
-  const R c = ld(a.col.somm + col), kdb = ld(a.col.somm + nc + col),
-          rinv = ld(a.col.somm + 2 * nc + col);
+  const R c = ldc(a.col.somm + col), kdb = ldc(a.col.somm + nc + col),
+          rinv = ldc(a.col.somm + 2 * nc + col);
   pdl_wait();
 #pragma unroll 4
   for (int i2 = z0; i2 < z1; i2++) {
@@ -466,7 +552,7 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
   R q[2 * NG + 1];
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+    for (int j = 0; j < 5 * NG + 1; j++) w[j] = ldc(a.col.coef + (int64_t)j * nc + col);
   }
   pdl_wait();
   if (active) {
@@ -688,7 +774,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
   }
   R w[5 * NG + 1];
 #pragma unroll
-  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ldc(a.col.coef + (int64_t)j * nc + col);
   __syncthreads();
   pdl_wait();
   // Operands this stage reads (slot mask) and their field indices (the 4th

@@ -72,8 +72,10 @@ extern "C" nrr_status nrr_prolong(const nrr_grid_desc *coarse, const float *uc,
                                   const nrr_grid_desc *fine, double *uf,
                                   void *stream) {
   if (!coarse || !fine || !uc || !uf) return wfail(NRR_ERR_INVALID_ARG, "null argument");
-  if (coarse->coord != fine->coord || coarse->coord == NRR_CARTESIAN)
-    return wfail(NRR_ERR_INVALID_ARG, "prolongation needs two curvilinear grids of one family");
+  if (coarse->coord != fine->coord || coarse->coord == NRR_CARTESIAN ||
+      coarse->coord == NRR_SINHCYLINDRICAL)
+    return wfail(NRR_ERR_INVALID_ARG,
+                 "prolongation needs two SinhSymTP, Spherical or SinhSpherical grids");
   if (coarse->coord == NRR_SINHSYMTP &&
       (coarse->amax != fine->amax || coarse->bscale != fine->bscale ||
        coarse->sinhwaa != fine->sinhwaa))

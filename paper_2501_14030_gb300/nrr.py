@@ -41,7 +41,8 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_surrogate_predict", "nrr_surrogate_gradients",
            "nrr_surrogate_get_params", "nrr_batch_set_u",
            "nrr_batch_get_interior", "nrr_prolong", "nrr_last_error",
-           "nrr_version")
+           "nrr_version", "nrr_selftest_recip", "nrr_probe_peaks",
+           "nrr_set_device_loop")
 
 
 class NrrError(RuntimeError):
@@ -54,7 +55,8 @@ class GridDesc(C.Structure):
     _fields_ = [("coord", C.c_int), ("n", C.c_int * 3), ("fd_order", C.c_int),
                 ("amax", C.c_double), ("bscale", C.c_double),
                 ("sinhwaa", C.c_double), ("rmax", C.c_double),
-                ("xmax", C.c_double)]
+                ("xmax", C.c_double), ("zmax", C.c_double),
+                ("sinhwz", C.c_double)]
 
 
 class Puncture(C.Structure):
@@ -111,6 +113,7 @@ def lib() -> C.CDLL:
         "nrr_get_launch": [V, I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                            C.POINTER(C.c_int)],
         "nrr_set_pdl": [V, I],
+        "nrr_set_device_loop": [V, I],
         "nrr_selftest_wait_expiry": [I, V, C.POINTER(C.c_int)],
         "nrr_autotune_save": [C.c_char_p],
         "nrr_autotune_load": [C.c_char_p],
@@ -143,6 +146,8 @@ def lib() -> C.CDLL:
         "nrr_prolong": [C.POINTER(GridDesc), V, C.POINTER(GridDesc), V, V],
         "nrr_residual_noalloc": [C.POINTER(GridDesc), I, C.POINTER(Puncture),
                                  V, C.c_double, V, V, V],
+        "nrr_selftest_recip": [V, V, C.c_int64, I, V],
+        "nrr_probe_peaks": [C.c_int64, V, D, D, D],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -170,7 +175,8 @@ def make_desc(desc: dict) -> GridDesc:
                     (C.c_int * 3)(*desc["n"]), int(desc["order"]),
                     float(desc["amax"]), float(desc["bscale"]),
                     float(desc["sinhwaa"]), float(desc["rmax"]),
-                    float(desc["xmax"]))
+                    float(desc["xmax"]), float(desc.get("zmax", 1.0e4)),
+                    float(desc.get("sinhwz", 0.07)))
 
 
 def make_punctures(punctures) -> C.Array:
@@ -243,6 +249,36 @@ def residual_noalloc(desc: dict, punctures, u, norm_out, h_out=None,
     _check(lib().nrr_residual_noalloc(
         C.byref(d), len(punctures), arr, C.c_void_p(u.data_ptr()), r_int,
         C.c_void_p(norm_out.data_ptr()), h, C.c_void_p(stream.cuda_stream)))
+
+
+def selftest_recip(s, out, stream=None) -> None:
+    """out = the stage kernels' reciprocal of s (float64 or float32 CUDA
+    tensors of one size and type)."""
+    import torch
+    if s.dtype != out.dtype or s.numel() != out.numel():
+        raise ValueError("s and out need one dtype and size")
+    if s.dtype not in (torch.float64, torch.float32) or not (
+            s.is_cuda and out.is_cuda and s.is_contiguous() and out.is_contiguous()):
+        raise ValueError("contiguous float64/float32 CUDA tensors expected")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().nrr_selftest_recip(C.c_void_p(s.data_ptr()),
+                                    C.c_void_p(out.data_ptr()), s.numel(),
+                                    int(s.dtype == torch.float32),
+                                    C.c_void_p(stream.cuda_stream)))
+
+
+def probe_peaks(l2_bytes: int = 0, stream=None) -> dict:
+    """Measured FP64/FP32 FMA throughput (TFLOP/s) and L2 read bandwidth
+    (GB/s) of the current GPU, from this library's probe kernels."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    f64, f32, l2 = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().nrr_probe_peaks(int(l2_bytes), C.c_void_p(stream.cuda_stream),
+                                 C.byref(f64), C.byref(f32), C.byref(l2)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value,
+            "l2_gbs": l2.value}
 
 
 def gemm_bf16_tn(A, B, D, stream=None) -> None:
@@ -398,6 +434,11 @@ class Grid:
     def set_pdl(self, on: bool):
         """Programmatic dependent launch of the stage kernels (default on)."""
         _check(lib().nrr_set_pdl(self._h, int(bool(on))))
+
+    def set_device_loop(self, on: bool):
+        """Stop test on the device, one graph launch per solve (default on),
+        or one host read of the norm per chunk (off)."""
+        _check(lib().nrr_set_device_loop(self._h, int(bool(on))))
 
     def autotune(self, mode="fp64", trial_steps: int = 20):
         """Pick the fastest stage kernel and launch shape; returns

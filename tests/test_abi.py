@@ -80,6 +80,10 @@ def test_null_handles_are_rejected(lib):
     W.grid_desc("spherical", (40, 22, 8), 8, rmax=64.0),
     W.grid_desc("spherical", (12, 6, 2), 10, rmax=9.0),
     W.grid_desc("cartesian", (10, 12, 14), 4),
+    W.grid_desc("sinhcylindrical", (20, 12, 8), 8, amax=50.0, sinhwaa=0.3,
+                zmax=40.0, sinhwz=0.3),
+    W.grid_desc("sinhcylindrical", (9, 7, 4), 4, amax=20.0, sinhwaa=0.5,
+                zmax=10.0, sinhwz=0.5),
 ])
 def test_host_image_map_matches_oracle_cartesian_matching(lib, oracle_mod,
                                                           desc):
