@@ -39,7 +39,8 @@ WORKLOAD = ("q=4 spinning Bowen-York pair (m 0.8/0.2, z=+-5, P=+-0.09x, "
 CHECK_EVERY = 50
 # nrr_set_launch's curvilinear stage-kernel variants
 STAGE_VARIANTS = {0: "column", 1: "tiled", 2: "persistent", 3: "tensor-copy tiled",
-                  4: "multi-stage column", 5: "multi-stage tensor-copy tiled"}
+                  4: "multi-stage column", 5: "multi-stage tensor-copy tiled",
+                  6: "two stages per launch"}
 # FP64 FMA units: 2 FMA per clock per SM on GB300 (the SM count is read from
 # the device)
 FP64_FMA_PER_CLK = 2

@@ -280,7 +280,11 @@ nrr_status nrr_profile_stages(nrr_grid *g, int mode, double dt, double eta,
  * 5 = the same multi-stage launch over variant 3's tensor-copy tiles, zc (2, 4,
  * 8 or 16) planes per tile, under variant 3's conditions (other grids run
  * variant 4 instead). Single stage launches of variants 4 and 5 run variants 0
- * and 3. Cartesian grids: variant 1 = the tensor-copy kernel under the same
+ * and 3; variant 6 = two RK4 stages per launch (zc = 1; FP32 stages of
+ * SinhSymTP grids of FD order 8 with n0 % 32 == 0, n1 % 4 == 0 and n2 <= 16;
+ * one block per 32 x 4 column tile with every phi plane, the first stage on
+ * the tile and a halo in shared memory; its single-stage launches run
+ * variant 0). Cartesian grids: variant 1 = the tensor-copy kernel under the same
  * conditions, any other variant the column kernel (zc planes per thread,
  * `block` threads). SinhCylindrical grids: variant 0 only. Results do not
  * depend on the shape beyond rounding order.
@@ -345,6 +349,75 @@ nrr_status nrr_autotune_clear(void);
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
                         int *best_variant, int *best_zc,
                         double *best_ms_per_launch);
+
+/* Wave-speed reference of a grid (paper Sec. 2: the wave speed c is
+ * proportional to the local grid spacing so that one time step satisfies the
+ * CFL condition everywhere): c = (local spacing) / ds_ref instead of
+ * (local spacing) / (the grid's own smallest spacing), for a grid that is
+ * one patch of a multi-patch system relaxed with one time step
+ * dt = cfl ds_ref.  Recomputes the c^2-scaled stencil weights and, if the
+ * punctures are set, the c^2-scaled source; the solution of the relaxation
+ * does not depend on c.  nrr_timestep then reports dt = cfl ds_ref.
+ * Errors: NRR_ERR_INVALID_ARG (null grid, ds_ref not positive), NRR_ERR_CUDA. */
+nrr_status nrr_set_speed_reference(nrr_grid *g, double ds_ref);
+
+/* ---- Two overlapping patches (paper Sec. 5: several patches of one solve;
+ * Sec. 6: multipatch grids with interpolation between patches) ----------- */
+typedef struct nrr_patchset nrr_patchset;
+
+/* Couples an outer grid (any family) and an inner Cartesian grid (a box that
+ * overlaps it) into one system.  Receivers: every ghost point of the box,
+ * and every interior point of the outer grid with max(|x|,|y|,|z|) < hole.
+ * A receiver's value is the tensor-product Lagrange interpolation, q points
+ * per direction (q = 2, 4 or 6), of the other patch in that patch's
+ * coordinates xx (inner-boundary ghosts of the donor read through their
+ * images).  Both grids must have their punctures set; both get the wave-speed
+ * reference min(smallest spacing of the two) (nrr_set_speed_reference), which
+ * they keep after the patch set is destroyed.  The grids stay owned by the
+ * caller and must outlive the patch set.
+ * Errors: NRR_ERR_INVALID_ARG (null or equal grids, an inner grid that is not
+ * Cartesian, q, hole <= 0, a receiver whose stencil leaves the donor, a donor
+ * point that is a receiver of the other link -- a hole too large for the
+ * box), NRR_ERR_STATE (punctures not set), NRR_ERR_OOM, NRR_ERR_CUDA. */
+nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole,
+                               int q, nrr_patchset **out);
+nrr_status nrr_patchset_destroy(nrr_patchset *ps);
+
+/* Receiver counts of the two links and the common wave-speed reference
+ * (host outputs, nullable).  Errors: NRR_ERR_INVALID_ARG for a null set. */
+nrr_status nrr_patchset_info(const nrr_patchset *ps, int64_t *outer_receivers,
+                             int64_t *inner_receivers, double *ds_ref);
+
+/* The common time step dt = cfl ds_ref and the default damping
+ * 2 pi cfl / (n0 dt) with n0 of the outer grid (paper Sec. 2).
+ * Errors: NRR_ERR_INVALID_ARG (null set, cfl <= 0). */
+nrr_status nrr_patchset_timestep(const nrr_patchset *ps, double cfl, double *dt,
+                                 double *eta_default);
+
+/* `steps` RK4 steps of the coupled system in FP64 (paper Alg. 1 inner loop):
+ * each stage runs both grids' fused stage kernels, then sets every
+ * receiver of the stage's output from the donor's output.  The state is that
+ * of the two grids (nrr_get_state / nrr_set_state; a state set from outside
+ * should hold interpolated values at the receivers).
+ * Errors: NRR_ERR_INVALID_ARG (null set, dt <= 0, steps < 0), NRR_ERR_CUDA. */
+nrr_status nrr_patchset_step(nrr_patchset *ps, double dt, double eta,
+                             int64_t steps);
+
+/* Norm of the coupled residual (paper Alg. 1 L2 norm): sqrt(sum H^2 J /
+ * sum J) over the interior points of both grids with r < r_int that are not
+ * receivers.  norm_out: host.  Errors: NRR_ERR_INVALID_ARG, NRR_ERR_CUDA. */
+nrr_status nrr_patchset_residual(nrr_patchset *ps, double r_int,
+                                 double *norm_out);
+
+/* Relaxes the coupled system (paper Alg. 1 loop): mode NRR_FP64, initial
+ * NRR_INIT_ZERO or NRR_INIT_CURRENT; norm every check_every steps; dt and
+ * eta as nrr_patchset_timestep (o->eta > 0 overrides eta); returns as
+ * nrr_relax does.  *r (nullable) filled in every case.
+ * Errors: NRR_ERR_INVALID_ARG (other modes or initial data, invalid
+ * options), NRR_ERR_NOT_CONVERGED, NRR_ERR_DIVERGED, NRR_ERR_TIMEOUT,
+ * NRR_ERR_CUDA. */
+nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
+                              nrr_relax_result *r);
 
 /* ---- Batches of independent solves (paper Sec. 5, N independent grids,
  * there on several streams; here one graph launch for all of them) ------- */

@@ -156,6 +156,7 @@ struct nrr_grid {
 
   double dsmin_global = 0.0;
   bool have_source = false;
+  PunctureSet punct{};  // the last set of punctures (source recomputation)
   int state_prec = 64;  // which FieldSet holds the current state
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, int64_t> graph_kernels;
@@ -197,8 +198,8 @@ bool valid_shape(const LaunchCfg &c) {
       c.variant == 0   ? (c.zc == 1 || c.zc == 2 || c.zc == 4)
       : (c.variant == 1 || c.variant == 3 || c.variant == 5)
           ? (c.zc == 2 || c.zc == 4 || c.zc == 8 || c.zc == 16)
-          : (c.variant == 2 || c.variant == 4) && c.zc == 1;
-  return c.variant >= 0 && c.variant <= 5 && zc_ok &&
+          : (c.variant == 2 || c.variant == 4 || c.variant == 6) && c.zc == 1;
+  return c.variant >= 0 && c.variant <= 6 && zc_ok &&
          (c.block == 32 || c.block == 64 || c.block == 128 || c.block == 256) &&
          (c.pdl == 0 || c.pdl == 1);
 }
@@ -357,44 +358,7 @@ template <typename R>
 StageArgs<R> stage_args(const nrr_grid *g, const FieldSet<R> &f,
                         const ColumnSet<R> &c, int stage, double dt,
                         double eta) {
-  // Classical RK4: k1 = F(y); k2 = F(y + dt/2 k1); k3 = F(y + dt/2 k2);
-  // k4 = F(y + dt k3); y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
-  StageArgs<R> a{};
-  a.alpha = f.alpha;
-  a.bc2 = f.bc2;
-  a.err = g->flag + 2;
-  a.col = c;
-  a.cart = g->cart;
-  a.eta = (R)eta;
-  a.lin = f.lin;
-  a.fu = f.fu;
-  a.au = f.a[0];
-  a.av = f.a[1];
-  a.bu = f.y[0];
-  a.bv = f.y[1];
-  switch (stage) {
-    case 0:  // in y; acc = y + dt/6 k1; s = y + dt/2 k1
-      a.su = f.y[0]; a.sv = f.y[1];
-      a.ou = f.s[0]; a.ov = f.s[1];
-      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 6.0);
-      break;
-    case 1:  // in s; acc += dt/3 k2; t = y + dt/2 k2
-      a.su = f.s[0]; a.sv = f.s[1];
-      a.ou = f.t[0]; a.ov = f.t[1];
-      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 3.0);
-      break;
-    case 2:  // in t; acc += dt/3 k3; s = y + dt k3
-      a.su = f.t[0]; a.sv = f.t[1];
-      a.ou = f.s[0]; a.ov = f.s[1];
-      a.wa = (R)dt; a.wb = (R)(dt / 3.0);
-      break;
-    default:  // in s; y = acc + dt/6 k4
-      a.su = f.s[0]; a.sv = f.s[1];
-      a.ou = f.y[0]; a.ov = f.y[1];
-      a.wa = (R)0; a.wb = (R)(dt / 6.0);
-      break;
-  }
-  return a;
+  return rk4_stage_args<R>(f, c, g->cart, g->flag + 2, stage, dt, eta);
 }
 
 template <typename R>
@@ -403,6 +367,25 @@ void launch_rk4_steps(const nrr_grid *g, const FieldSet<R> &f,
                       int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
   const LaunchCfg &cfg = g->stage_cfg[sizeof(R) == 4];
+  if constexpr (sizeof(R) == 4) {
+    if (cfg.variant == 6 && stage2_ok(g->geo)) {
+      // two stages per launch over an even number of steps (the state
+      // returns to f.y), then one step of single-stage launches if odd
+      const int64_t pairs = steps - (steps & 1);
+      g_launches += 2 * pairs;
+      launch_stage2_steps(g->geo, f, c, dt, eta, pairs, cfg.pdl, g->stream);
+      if (steps & 1) {
+        LaunchCfg col = cfg;
+        col.variant = 0;
+        col.zc = 2;
+        g_launches += 4;
+        for (int k = 0; k < 4; k++)
+          launch_stage<R>(g->geo, kinds[k], stage_args<R>(g, f, c, k, dt, eta), col,
+                          g->stream);
+      }
+      return;
+    }
+  }
   if ((cfg.variant == 4 || cfg.variant == 5) && g->geo.coord != CARTESIAN &&
       g->geo.coord != SINHCYLINDRICAL) {
     // all steps in one cooperative launch (grid barriers between stages)
@@ -837,6 +820,25 @@ nrr_status relax_defect_correction(nrr_grid *g, const nrr_relax_opts *o,
 
 }  // namespace
 
+GridView nrr::grid_view(nrr_grid *g) {
+  GridView v{};
+  v.geo = g->geo;
+  v.stream = g->stream;
+  v.f64 = g->f64;
+  v.c64 = g->c64;
+  v.cart = g->cart;
+  v.cfg64 = g->stage_cfg[0];
+  v.res_cfg = g->res_cfg;
+  v.jac = g->jac;
+  v.rad = g->rad;
+  v.scratch = g->res64;
+  v.partials = g->partials;
+  v.err = g->flag + 2;
+  v.dsmin = g->dsmin_global;
+  v.have_source = g->have_source;
+  return v;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -979,6 +981,7 @@ nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
       g->dsmin_global = ds;
       CartCoef cc{};
       cc.cc = 0.0;
+      cc.speed = 1.0;
       for (int dd = 0; dd < 3; dd++) {
         double inv = 1.0 / (geo.dxx[dd] * geo.dxx[dd]);
         cc.cc += w2[0] * inv;
@@ -1088,6 +1091,54 @@ nrr_status nrr_set_punctures(nrr_grid *g, int n, const nrr_puncture *p) {
     return fail(NRR_ERR_INVALID_ARG, "a puncture lies on a grid point");
   }
   g->have_source = true;
+  g->punct = ps;
+  return NRR_OK;
+}
+
+nrr_status nrr_set_speed_reference(nrr_grid *g, double ds_ref) {
+  TRY(check_grid(g));
+  if (!(ds_ref > 0.0) || !std::isfinite(ds_ref))
+    return fail(NRR_ERR_INVALID_ARG, "ds_ref must be positive");
+  TRY(set_device(g));
+  const Geo &geo = g->geo;
+  g->dsmin_global = ds_ref;
+  CUDA_TRY(cudaMemcpyAsync(g->scalars, &g->dsmin_global, sizeof(double),
+                           cudaMemcpyHostToDevice, g->stream));
+  int m = geo.ng;
+  double w1[7] = {0}, w2[7] = {0};
+  for (int k = 0; k <= m; k++) {
+    w1[k] = k == 0 ? 0.0 : fd_first(m, k);
+    w2[k] = fd_second(m, k);
+  }
+  if (geo.coord == CARTESIAN) {
+    const double ds = fmin(geo.dxx[0], fmin(geo.dxx[1], geo.dxx[2]));
+    const double c = ds / ds_ref, c2 = c * c;
+    CartCoef cc{};
+    cc.speed = c;
+    for (int dd = 0; dd < 3; dd++) {
+      double inv = 1.0 / (geo.dxx[dd] * geo.dxx[dd]);
+      cc.cc += c2 * w2[0] * inv;
+      for (int k = 1; k <= m; k++) cc.a[dd][k - 1] = c2 * w2[k] * inv;
+    }
+    g->cart = cc;
+  } else {
+    launch_column_coefs(geo, g->h, g->gl, g->rad, g->drdxx0, g->dsmin,
+                        g->scalars, w1, w2, g->c64, g->c32, g->stream);
+    g_launches += 1;
+  }
+  if (g->have_source) {
+    // c^2 beta with the new wave speed
+    launch_source(geo, g->punct, g->dsmin, g->scalars, g->f64.alpha, g->f64.bc2,
+                  g->f32.alpha, g->f32.bc2, g->flag, g->stream);
+    g_launches += 1;
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  // captured graphs hold the old coefficients (kernel parameters)
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  g->graphs.clear();
+  g->graph_kernels.clear();
+  g->loop_kernels.clear();
   return NRR_OK;
 }
 
@@ -1217,18 +1268,22 @@ nrr_status nrr_set_launch(nrr_grid *g, int mode, int variant, int zc, int block)
     return fail(NRR_ERR_INVALID_ARG, "block must be 0 (keep), 32, 64, 128 or 256");
   if (mode != NRR_FP64 && mode != NRR_FP32)
     return fail(NRR_ERR_INVALID_ARG, "mode must be NRR_FP64 or NRR_FP32");
-  if (variant < 0 || variant > 5)
+  if (variant < 0 || variant > 6)
     return fail(NRR_ERR_INVALID_ARG,
                 "variant must be 0 (column), 1 (tiled), 2 (persistent column), "
-                "3 (tensor-copy tiled), 4 (multi-stage) or 5 (multi-stage "
-                "tensor-copy)");
+                "3 (tensor-copy tiled), 4 (multi-stage), 5 (multi-stage "
+                "tensor-copy) or 6 (two stages per launch)");
   if ((variant == 0 && zc != 1 && zc != 2 && zc != 4) ||
       ((variant == 1 || variant == 3 || variant == 5) && zc != 2 && zc != 4 &&
        zc != 8 && zc != 16) ||
-      ((variant == 2 || variant == 4) && zc != 1))
+      ((variant == 2 || variant == 4 || variant == 6) && zc != 1))
     return fail(NRR_ERR_INVALID_ARG,
                 "zc must be 1, 2 or 4 (column), 2, 4, 8 or 16 (tiled, tensor-copy), "
-                "1 (persistent, multi-stage)");
+                "1 (persistent, multi-stage, two-stage)");
+  if (variant == 6 && (mode != NRR_FP32 || !stage2_ok(g->geo)))
+    return fail(NRR_ERR_INVALID_ARG,
+                "variant 6 runs FP32 stages of SinhSymTP grids of FD order 8 with "
+                "n0 %% 32 == 0, n1 %% 4 == 0 and n2 <= 16");
   if (g->geo.coord == SINHCYLINDRICAL && variant != 0)
     return fail(NRR_ERR_INVALID_ARG,
                 "SinhCylindrical grids run the column kernel (variant 0) only");
@@ -1376,15 +1431,17 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[24] = {{128, 1, 0},  {32, 1, 0},   {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
+  const LaunchCfg cands[25] = {{128, 1, 0},  {32, 1, 0},   {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
                                {64, 2, 0},   {128, 4, 0},  {128, 2, 1},  {128, 4, 1},
                                {128, 8, 1},  {128, 16, 1}, {128, 1, 2},  {128, 2, 3},
                                {128, 4, 3},  {128, 8, 3},  {128, 16, 3}, {256, 2, 3},
                                {256, 4, 3},  {256, 8, 3},  {256, 16, 3}, {128, 1, 4},
-                               {128, 4, 5},  {128, 8, 5},  {128, 16, 5}};
+                               {128, 4, 5},  {128, 8, 5},  {128, 16, 5}, {512, 1, 6}};
   for (const LaunchCfg &cand0 : cands) {
-    // SinhCylindrical grids have the column kernel only
+    // SinhCylindrical grids have the column kernel only; the two-stage
+    // kernel runs eligible FP32 grids
     if (g->geo.coord == SINHCYLINDRICAL && cand0.variant != 0) continue;
+    if (cand0.variant == 6 && (prec != 32 || !stage2_ok(g->geo))) continue;
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;
     cfg = cand;

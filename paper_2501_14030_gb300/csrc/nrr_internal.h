@@ -68,16 +68,20 @@ struct LaunchCfg {
   int variant = 0;  // curvilinear stages: 0 column kernel, 1 tiled kernel,
                     // 2 persistent column kernel, 3 tensor-copy tiled
                     // kernel, 4 multi-stage cooperative kernel, 5 its
-                    // tensor-copy tiled form; Cartesian
+                    // tensor-copy tiled form, 6 two stages per launch
+                    // (FP32, small SinhSymTP grids); Cartesian
                     // stages: 0 column kernel, 1 tensor-copy tiled kernel
   int pdl = 1;      // stage kernels: programmatic dependent launch (the next
                     // stage's blocks start while this one drains)
 };
 
-// Cartesian grids use constant coefficients (uniform spacing, c = 1).
+// Cartesian grids use constant coefficients (uniform spacing, so the wave
+// speed c = spacing / reference spacing is one constant: 1 on its own, other
+// values in a multi-patch system).  c^2 is folded into the weights.
 struct CartCoef {
   double cc;          // centre weight, all three directions
   double a[3][6];     // a[dir][k] for k = 1..ng, symmetric
+  double speed;       // c, multiplies the radiation condition
 };
 
 // ----------------------------------------------------------------- set-up
@@ -134,6 +138,71 @@ template <typename R>
 void launch_stage(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st);
 
+// Arguments of RK4 stage `stage` (0..3) of one field set: classical RK4,
+// k1 = F(y); k2 = F(y + dt/2 k1); k3 = F(y + dt/2 k2); k4 = F(y + dt k3);
+// y += dt/6 (k1 + 2 k2 + 2 k3 + k4), through the buffers y -> s -> t -> s -> y
+// with the accumulator a.
+template <typename R>
+StageArgs<R> rk4_stage_args(const FieldSet<R> &f, const ColumnSet<R> &c,
+                            const CartCoef &cart, int *err, int stage,
+                            double dt, double eta) {
+  StageArgs<R> a{};
+  a.alpha = f.alpha;
+  a.bc2 = f.bc2;
+  a.err = err;
+  a.col = c;
+  a.cart = cart;
+  a.eta = (R)eta;
+  a.lin = f.lin;
+  a.fu = f.fu;
+  a.au = f.a[0];
+  a.av = f.a[1];
+  a.bu = f.y[0];
+  a.bv = f.y[1];
+  switch (stage) {
+    case 0:  // in y; acc = y + dt/6 k1; s = y + dt/2 k1
+      a.su = f.y[0]; a.sv = f.y[1];
+      a.ou = f.s[0]; a.ov = f.s[1];
+      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 6.0);
+      break;
+    case 1:  // in s; acc += dt/3 k2; t = y + dt/2 k2
+      a.su = f.s[0]; a.sv = f.s[1];
+      a.ou = f.t[0]; a.ov = f.t[1];
+      a.wa = (R)(0.5 * dt); a.wb = (R)(dt / 3.0);
+      break;
+    case 2:  // in t; acc += dt/3 k3; s = y + dt k3
+      a.su = f.t[0]; a.sv = f.t[1];
+      a.ou = f.s[0]; a.ov = f.s[1];
+      a.wa = (R)dt; a.wb = (R)(dt / 3.0);
+      break;
+    default:  // in s; y = acc + dt/6 k4
+      a.su = f.s[0]; a.sv = f.s[1];
+      a.ou = f.y[0]; a.ov = f.y[1];
+      a.wa = (R)0; a.wb = (R)(dt / 6.0);
+      break;
+  }
+  return a;
+}
+
+// The FP64 device data of one grid, for drivers outside nrr_api.cu (the
+// multi-patch system).  Pointers are owned by the grid.
+struct GridView {
+  Geo geo;
+  cudaStream_t stream;     // the grid's work stream
+  FieldSet<double> f64;
+  ColumnSet<double> c64;
+  CartCoef cart;
+  LaunchCfg cfg64;         // FP64 stage launch shape
+  LaunchCfg res_cfg;       // residual kernels
+  const double *jac, *rad; // per column (curvilinear grids)
+  double *scratch;         // s0*s1*s2 doubles free for the caller
+  double *partials;        // residual partial sums (residual_blocks pairs)
+  int *err;                // stage kernels' bounded-wait flag
+  double dsmin;            // the wave speed's reference spacing
+  bool have_source;
+};
+GridView grid_view(nrr_grid *g);
+
 // `steps` RK4 steps (stage arguments FIRST, MID, MID, LAST) in one
 // cooperative launch of a multi-stage curvilinear kernel (variant 5: the
 // tensor-copy tiled form where the grid allows it, else variant 4's
@@ -143,6 +212,16 @@ template <typename R>
 cudaError_t launch_stage_steps(const Geo &g, const StageArgs<R> (&sa)[4], int steps,
                                unsigned *count, const LaunchCfg &cfg,
                                cudaStream_t st);
+
+// Two RK4 stages per launch (stage variant 6; FP32 SinhSymTP grids of FD
+// order 8 with n0 % 32 == 0, n1 % 4 == 0 and n2 <= 16): stage2_ok tells
+// whether a grid is eligible; launch_stage2_steps takes `steps` RK4 steps
+// (2 launches each), the state alternating between f.y and f.s from step to
+// step, so an even count leaves it in f.y.
+bool stage2_ok(const Geo &g);
+cudaError_t launch_stage2_steps(const Geo &g, const FieldSet<float> &f,
+                                const ColumnSet<float> &c, double dt, double eta,
+                                int64_t steps, int pdl, cudaStream_t st);
 
 // Residual H (c^-2 times the scaled operator) at interior points and the
 // per-block partial sums of H^2 J and J over r < r_int.  h_out nullable.

@@ -1,0 +1,543 @@
+// nrr_patch.cu -- two overlapping patches relaxed as one system (arXiv
+// 2501.14030, Sec. 5: several patches of one solve on one GPU; Sec. 6:
+// multipatch grids with interpolation between the patches).
+//
+// An outer patch (any coordinate family) and an inner Cartesian box.  The
+// box's ghost points receive their values by tensor-product Lagrange
+// interpolation of q points per direction in the outer patch's coordinates;
+// the outer patch's interior points inside a smaller cube (the hole) receive
+// theirs from the box in the same way.  Both patches share one time step and
+// one wave-speed reference, the smaller of their smallest spacings, so that
+// both run at the same Courant number (Sec. 2: wave speed proportional to the
+// local spacing).  Each RK4 stage runs both patches' fused stage kernels and
+// then one kernel per link that sets the receivers of the stage's output from
+// the donor's output: RK4 combines stages linearly, so this is the coupling
+// applied to the right-hand side at every stage.
+//
+// Links are built on the host (inverse coordinate maps, Lagrange weights,
+// inner-ghost images) and kept in device memory; a donor point may never be
+// a receiver of the other link, which the set-up checks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <new>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/nrr.h"
+#include "nrr_internal.h"
+#include "nrr_stencil.cuh"
+
+using namespace nrr;
+
+namespace {
+
+nrr_status pfail(nrr_status s, const char *fmt, ...) {
+  char buf[384];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return s;
+}
+
+#define PCUDA(call)                                                         \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return pfail(NRR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Cartesian position of padded point (i0, i1, i2) of a grid.
+void host_position(const Geo &g, int i0, int i1, int i2, double x[3]) {
+  const double xx0 = g.xxmin[0] + (i0 - g.ng + 0.5) * g.dxx[0];
+  const double xx1 = g.xxmin[1] + (i1 - g.ng + 0.5) * g.dxx[1];
+  const double xx2 = g.xxmin[2] + (i2 - g.ng + 0.5) * g.dxx[2];
+  const double s = [&] {
+    if (g.coord == SINHSYMTP || g.coord == SINHSPHERICAL || g.coord == SINHCYLINDRICAL)
+      return g.amax * std::sinh(xx0 / g.sinhwaa) / std::sinh(1.0 / g.sinhwaa);
+    return xx0;
+  }();
+  switch (g.coord) {
+    case CARTESIAN:
+      x[0] = xx0, x[1] = xx1, x[2] = xx2;
+      return;
+    case SINHCYLINDRICAL:
+      x[0] = s * std::cos(xx2), x[1] = s * std::sin(xx2);
+      x[2] = g.zmax * std::sinh(xx1 / g.sinhwz) / std::sinh(1.0 / g.sinhwz);
+      return;
+    case SINHSYMTP:
+      x[0] = s * std::sin(xx1) * std::cos(xx2), x[1] = s * std::sin(xx1) * std::sin(xx2);
+      x[2] = std::sqrt(s * s + g.bscale * g.bscale) * std::cos(xx1);
+      return;
+    default:  // spherical-like: s = r
+      x[0] = s * std::sin(xx1) * std::cos(xx2), x[1] = s * std::sin(xx1) * std::sin(xx2);
+      x[2] = s * std::cos(xx1);
+      return;
+  }
+}
+
+// Coordinates xx of a Cartesian point in a grid's family, in the canonical
+// range (xx0 >= 0, theta in [0, pi], phi in (-pi, pi]).
+void host_coords(const Geo &g, const double x[3], double xx[3]) {
+  const double rho2 = x[0] * x[0] + x[1] * x[1], rho = std::sqrt(rho2);
+  if (g.coord == CARTESIAN) {
+    xx[0] = x[0], xx[1] = x[1], xx[2] = x[2];
+    return;
+  }
+  xx[2] = std::atan2(x[1], x[0]);
+  const double z = x[2];
+  if (g.coord == SINHCYLINDRICAL) {
+    xx[0] = g.sinhwaa * std::asinh(rho * std::sinh(1.0 / g.sinhwaa) / g.amax);
+    xx[1] = g.sinhwz * std::asinh(z * std::sinh(1.0 / g.sinhwz) / g.zmax);
+    return;
+  }
+  if (g.coord == SINHSYMTP) {
+    // rho = A sin(th), z = sqrt(A^2 + b^2) cos(th): A^2 is the positive root
+    // of X^2 - (rho^2 + z^2 - b^2) X - rho^2 b^2 = 0 (written in a form that
+    // does not cancel when the linear coefficient is negative)
+    const double b2 = g.bscale * g.bscale, q = rho2 + z * z - b2;
+    const double d = std::sqrt(q * q + 4.0 * rho2 * b2);
+    const double A2 = q >= 0.0 ? 0.5 * (q + d) : (d > 0.0 ? 2.0 * rho2 * b2 / (d - q) : 0.0);
+    const double A = std::sqrt(A2);
+    xx[0] = g.sinhwaa * std::asinh(A * std::sinh(1.0 / g.sinhwaa) / g.amax);
+    xx[1] = std::atan2(rho * std::sqrt(A2 + b2), z * A);
+    return;
+  }
+  const double r = std::sqrt(rho2 + z * z);
+  xx[0] = g.coord == SINHSPHERICAL
+              ? g.sinhwaa * std::asinh(r * std::sinh(1.0 / g.sinhwaa) / g.amax)
+              : r;
+  xx[1] = std::atan2(rho, z);
+}
+
+// Lagrange weights of nodes base .. base+q-1 at position f (grid-index units).
+void lagrange(int q, int base, double f, double *w) {
+  for (int j = 0; j < q; j++) {
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m < q; m++) {
+      if (m == j) continue;
+      num *= f - (double)(base + m);
+      den *= (double)(j - m);
+    }
+    w[j] = num / den;
+  }
+}
+
+struct HostLink {
+  std::vector<int64_t> recv, donor;
+  std::vector<double> w;
+};
+
+// Receivers (flat indices in `rg`) with their donor stencils in `dg`.
+nrr_status build_link(const Geo &rg, const Geo &dg, const std::vector<int64_t> &recv,
+                      int q, HostLink *out) {
+  const int m = q * q * q;
+  out->recv = recv;
+  out->donor.resize(recv.size() * (size_t)m);
+  out->w.resize(recv.size() * (size_t)m);
+  const int sd[3] = {dg.s0, dg.s1, dg.s2};
+  for (size_t r = 0; r < recv.size(); r++) {
+    const int64_t p = recv[r];
+    const int i0 = (int)(p % rg.s0), i1 = (int)((p / rg.s0) % rg.s1),
+              i2 = (int)(p / rg.ncol);
+    double x[3], xx[3];
+    host_position(rg, i0, i1, i2, x);
+    host_coords(dg, x, xx);
+    int base[3];
+    double wd[3][6];
+    for (int d = 0; d < 3; d++) {
+      const double f = (xx[d] - dg.xxmin[d]) / dg.dxx[d] - 0.5 + dg.ng;
+      base[d] = (int)std::floor(f) - (q / 2 - 1);
+      if (base[d] < 0 || base[d] + q - 1 >= sd[d])
+        return pfail(NRR_ERR_INVALID_ARG,
+                     "receiver at (%.3g, %.3g, %.3g): its stencil leaves the donor patch",
+                     x[0], x[1], x[2]);
+      lagrange(q, base[d], f, wd[d]);
+    }
+    int k = 0;
+    for (int c = 0; c < q; c++)
+      for (int b = 0; b < q; b++)
+        for (int a = 0; a < q; a++, k++) {
+          int j0 = base[0] + a, j1 = base[1] + b, j2 = base[2] + c;
+          if (dg.coord != CARTESIAN) image_of(dg, j0, j1, j2);
+          out->donor[r * m + k] = flat(dg, j0, j1, j2);
+          out->w[r * m + k] = wd[0][a] * wd[1][b] * wd[2][c];
+        }
+  }
+  return NRR_OK;
+}
+
+// One link on the device.
+struct DevLink {
+  int64_t n = 0;
+  int64_t *recv = nullptr, *donor = nullptr;
+  double *w = nullptr;
+};
+
+// Receivers of the stage output (du, dv) from the donor's output (su, sv):
+// one thread per receiver, the q^3 products summed in a fixed order.
+__global__ void link_apply_kernel(int64_t n, int m, const int64_t *__restrict__ recv,
+                                  const int64_t *__restrict__ donor,
+                                  const double *__restrict__ w, const double *su,
+                                  const double *sv, double *du, double *dv) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < m; k++) {
+    const int64_t i = r * m + k;
+    const double wk = w[i];
+    const int64_t d = donor[i];
+    a = fma(wk, su[d], a);
+    b = fma(wk, sv[d], b);
+  }
+  du[recv[r]] = a;
+  dv[recv[r]] = b;
+}
+
+// Partial sums (H^2 J, J) of one patch over its interior points that are
+// not receivers and lie within r < r_int; J = h0 h1 h2 per column
+// (curvilinear) or 1 (Cartesian).
+__global__ void masked_norm_kernel(Geo g, const double *__restrict__ H,
+                                   const unsigned char *__restrict__ mask,
+                                   const double *__restrict__ jac,
+                                   const double *__restrict__ rad, double r_int,
+                                   double *partials) {
+  const int64_t nint = (int64_t)g.n0 * g.n1 * g.n2;
+  double num = 0.0, den = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nint;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e % g.n0) + g.ng, i1 = (int)((e / g.n0) % g.n1) + g.ng,
+              i2 = (int)(e / ((int64_t)g.n0 * g.n1)) + g.ng;
+    const int64_t p = flat(g, i0, i1, i2);
+    if (mask[p]) continue;
+    double wt;
+    if (g.coord == CARTESIAN) {
+      const double x0 = g.xxmin[0] + (i0 - g.ng + 0.5) * g.dxx[0];
+      const double x1 = g.xxmin[1] + (i1 - g.ng + 0.5) * g.dxx[1];
+      const double x2 = g.xxmin[2] + (i2 - g.ng + 0.5) * g.dxx[2];
+      wt = std::sqrt(x0 * x0 + x1 * x1 + x2 * x2) < r_int ? 1.0 : 0.0;
+    } else {
+      const int col = i0 + g.s0 * i1;
+      wt = rad[col] < r_int ? jac[col] : 0.0;
+    }
+    const double h = H[p];
+    num += h * h * wt;
+    den += wt;
+  }
+  dev::block_sum2(num, den, partials + 2 * blockIdx.x);
+}
+
+constexpr int kNormBlocks = 512;  // per patch
+
+}  // namespace
+
+struct nrr_patchset {
+  nrr_grid *grid[2] = {nullptr, nullptr};  // outer, inner
+  DevLink link[2];                          // receivers of grid[i]
+  unsigned char *mask[2] = {nullptr, nullptr};
+  double *partials = nullptr;               // 2 * kNormBlocks pairs
+  double *norm = nullptr;                   // [3]
+  double *host = nullptr;                   // pinned read-back
+  int q = 4;
+  double ds_ref = 0.0;
+  int device = 0;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T>
+nrr_status palloc(nrr_patchset *ps, T **p, size_t count) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T) + 16);
+  if (e != cudaSuccess)
+    return pfail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
+                 cudaGetErrorString(e));
+  ps->allocs.push_back(ptr);
+  *p = static_cast<T *>(ptr);
+  return NRR_OK;
+}
+
+// Every RK4 stage on both patches, then the links; `steps` steps on the
+// outer grid's work stream.
+void launch_patch_steps(nrr_patchset *ps, double dt, double eta, int64_t steps) {
+  static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
+  GridView v[2] = {grid_view(ps->grid[0]), grid_view(ps->grid[1])};
+  cudaStream_t st = v[0].stream;
+  const int m = ps->q * ps->q * ps->q;
+  for (int64_t s = 0; s < steps; s++)
+    for (int k = 0; k < 4; k++) {
+      StageArgs<double> a[2];
+      for (int i = 0; i < 2; i++) {
+        a[i] = rk4_stage_args<double>(v[i].f64, v[i].c64, v[i].cart, v[i].err, k, dt, eta);
+        launch_stage<double>(v[i].geo, kinds[k], a[i], v[i].cfg64, st);
+      }
+      for (int i = 0; i < 2; i++) {
+        const DevLink &l = ps->link[i];
+        if (l.n == 0) continue;
+        const int j = 1 - i;  // donor
+        link_apply_kernel<<<(unsigned)((l.n + 127) / 128), 128, 0, st>>>(
+            l.n, m, l.recv, l.donor, l.w, a[j].ou, a[j].ov, a[i].ou, a[i].ov);
+      }
+    }
+}
+
+// The two-patch residual norm of the current state into ps->norm[0].
+void launch_patch_norm(nrr_patchset *ps, double r_int) {
+  GridView v[2] = {grid_view(ps->grid[0]), grid_view(ps->grid[1])};
+  cudaStream_t st = v[0].stream;
+  for (int i = 0; i < 2; i++) {
+    int nb = 0;
+    launch_residual<double>(v[i].geo, v[i].f64.y[0], v[i].f64.alpha, v[i].f64.bc2,
+                            v[i].c64, v[i].cart, v[i].jac, v[i].rad, r_int,
+                            v[i].scratch, v[i].partials, &nb, v[i].res_cfg, st);
+    masked_norm_kernel<<<kNormBlocks, 128, 0, st>>>(
+        v[i].geo, v[i].scratch, ps->mask[i], v[i].jac, v[i].rad, r_int,
+        ps->partials + 2 * kNormBlocks * i);
+  }
+  launch_norm_finalize(ps->partials, 2 * kNormBlocks, ps->norm, st);
+}
+
+nrr_status read_norm(nrr_patchset *ps, double *out) {
+  cudaStream_t st = grid_view(ps->grid[0]).stream;
+  PCUDA(cudaGetLastError());
+  PCUDA(cudaMemcpyAsync(ps->host, ps->norm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PCUDA(cudaStreamSynchronize(st));
+  *out = ps->host[0];
+  return NRR_OK;
+}
+
+// Both grids' streams drained, so the outer grid's stream may take over
+// both patches' state.
+nrr_status begin(nrr_patchset *ps) {
+  PCUDA(cudaSetDevice(ps->device));
+  PCUDA(cudaStreamSynchronize(grid_view(ps->grid[1]).stream));
+  PCUDA(cudaStreamSynchronize(grid_view(ps->grid[0]).stream));
+  return NRR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole, int q,
+                               nrr_patchset **out) {
+  if (!out) return pfail(NRR_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  if (!outer || !inner || outer == inner)
+    return pfail(NRR_ERR_INVALID_ARG, "two distinct grids are needed");
+  if (q != 2 && q != 4 && q != 6) return pfail(NRR_ERR_INVALID_ARG, "q must be 2, 4 or 6");
+  if (!(hole > 0.0)) return pfail(NRR_ERR_INVALID_ARG, "hole must be positive");
+  GridView vo = grid_view(outer), vi = grid_view(inner);
+  if (vi.geo.coord != CARTESIAN)
+    return pfail(NRR_ERR_INVALID_ARG, "the inner patch must be Cartesian");
+  if (!vo.have_source || !vi.have_source)
+    return pfail(NRR_ERR_STATE, "punctures must be set on both patches");
+  if (q / 2 > vo.geo.ng || q / 2 > vi.geo.ng)
+    return pfail(NRR_ERR_INVALID_ARG, "q/2 exceeds a patch's ghost width");
+  // the inner box's receivers: all its ghost points
+  std::vector<int64_t> recv_in, recv_out;
+  const Geo &gi = vi.geo, &go = vo.geo;
+  for (int i2 = 0; i2 < gi.s2; i2++)
+    for (int i1 = 0; i1 < gi.s1; i1++)
+      for (int i0 = 0; i0 < gi.s0; i0++) {
+        const bool in = i0 >= gi.ng && i0 < gi.ng + gi.n0 && i1 >= gi.ng &&
+                        i1 < gi.ng + gi.n1 && i2 >= gi.ng && i2 < gi.ng + gi.n2;
+        if (!in) recv_in.push_back(flat(gi, i0, i1, i2));
+      }
+  // the outer patch's hole: interior points with max(|x|, |y|, |z|) < hole
+  for (int i2 = go.ng; i2 < go.ng + go.n2; i2++)
+    for (int i1 = go.ng; i1 < go.ng + go.n1; i1++)
+      for (int i0 = go.ng; i0 < go.ng + go.n0; i0++) {
+        double x[3];
+        host_position(go, i0, i1, i2, x);
+        if (std::fmax(std::fabs(x[0]), std::fmax(std::fabs(x[1]), std::fabs(x[2]))) < hole)
+          recv_out.push_back(flat(go, i0, i1, i2));
+      }
+  HostLink hl[2];
+  nrr_status s = build_link(go, gi, recv_out, q, &hl[0]);
+  if (s != NRR_OK) return s;
+  s = build_link(gi, go, recv_in, q, &hl[1]);
+  if (s != NRR_OK) return s;
+  // no donor point of one link may be a receiver of the other
+  std::vector<unsigned char> mk[2] = {std::vector<unsigned char>((size_t)go.npts, 0),
+                                      std::vector<unsigned char>((size_t)gi.npts, 0)};
+  for (int i = 0; i < 2; i++)
+    for (int64_t p : hl[i].recv) mk[i][(size_t)p] = 1;
+  for (int i = 0; i < 2; i++)
+    for (int64_t d : hl[i].donor)
+      if (mk[1 - i][(size_t)d])
+        return pfail(NRR_ERR_INVALID_ARG,
+                     "a donor point of the %s patch's receivers is itself a receiver "
+                     "(make the hole smaller)", i == 0 ? "outer" : "inner");
+  nrr_patchset *ps = new (std::nothrow) nrr_patchset();
+  if (!ps) return pfail(NRR_ERR_OOM, "host allocation failed");
+  ps->grid[0] = outer;
+  ps->grid[1] = inner;
+  ps->q = q;
+  nrr_status st = [&]() -> nrr_status {
+    PCUDA(cudaGetDevice(&ps->device));
+    // one wave-speed reference and so one time step for both patches
+    ps->ds_ref = std::fmin(vo.dsmin, vi.dsmin);
+    nrr_status e = nrr_set_speed_reference(outer, ps->ds_ref);
+    if (e != NRR_OK) return e;
+    e = nrr_set_speed_reference(inner, ps->ds_ref);
+    if (e != NRR_OK) return e;
+    const int m = q * q * q;
+    for (int i = 0; i < 2; i++) {
+      DevLink &l = ps->link[i];
+      l.n = (int64_t)hl[i].recv.size();
+      const size_t nm = (size_t)l.n * m;
+      e = palloc(ps, &l.recv, (size_t)l.n);
+      if (e == NRR_OK) e = palloc(ps, &l.donor, nm);
+      if (e == NRR_OK) e = palloc(ps, &l.w, nm);
+      if (e == NRR_OK) e = palloc(ps, &ps->mask[i], mk[i].size());
+      if (e != NRR_OK) return e;
+      PCUDA(cudaMemcpy(l.recv, hl[i].recv.data(), l.n * sizeof(int64_t),
+                       cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.donor, hl[i].donor.data(), nm * sizeof(int64_t),
+                       cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.w, hl[i].w.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(ps->mask[i], mk[i].data(), mk[i].size(), cudaMemcpyHostToDevice));
+    }
+    e = palloc(ps, &ps->partials, 4 * (size_t)kNormBlocks);
+    if (e == NRR_OK) e = palloc(ps, &ps->norm, 4);
+    if (e != NRR_OK) return e;
+    PCUDA(cudaMallocHost(&ps->host, 4 * sizeof(double)));
+    return NRR_OK;
+  }();
+  if (st != NRR_OK) {
+    nrr_patchset_destroy(ps);
+    return st;
+  }
+  *out = ps;
+  return NRR_OK;
+}
+
+nrr_status nrr_patchset_destroy(nrr_patchset *ps) {
+  if (!ps) return NRR_OK;
+  cudaSetDevice(ps->device);
+  for (void *p : ps->allocs) cudaFree(p);
+  if (ps->host) cudaFreeHost(ps->host);
+  delete ps;
+  return NRR_OK;
+}
+
+nrr_status nrr_patchset_info(const nrr_patchset *ps, int64_t *outer_receivers,
+                             int64_t *inner_receivers, double *ds_ref) {
+  if (!ps) return pfail(NRR_ERR_INVALID_ARG, "null patch set");
+  if (outer_receivers) *outer_receivers = ps->link[0].n;
+  if (inner_receivers) *inner_receivers = ps->link[1].n;
+  if (ds_ref) *ds_ref = ps->ds_ref;
+  return NRR_OK;
+}
+
+nrr_status nrr_patchset_timestep(const nrr_patchset *ps, double cfl, double *dt,
+                                 double *eta_default) {
+  if (!ps || !(cfl > 0.0)) return pfail(NRR_ERR_INVALID_ARG, "null patch set or cfl <= 0");
+  const double d = cfl * ps->ds_ref;
+  if (dt) *dt = d;
+  if (eta_default)
+    *eta_default = 2.0 * M_PI * cfl / (grid_view(ps->grid[0]).geo.n0 * d);
+  return NRR_OK;
+}
+
+nrr_status nrr_patchset_step(nrr_patchset *ps, double dt, double eta, int64_t steps) {
+  if (!ps || !(dt > 0.0) || steps < 0)
+    return pfail(NRR_ERR_INVALID_ARG, "null patch set, dt <= 0 or steps < 0");
+  nrr_status s = begin(ps);
+  if (s != NRR_OK) return s;
+  launch_patch_steps(ps, dt, eta, steps);
+  cudaStream_t st = grid_view(ps->grid[0]).stream;
+  PCUDA(cudaGetLastError());
+  PCUDA(cudaStreamSynchronize(st));
+  return NRR_OK;
+}
+
+nrr_status nrr_patchset_residual(nrr_patchset *ps, double r_int, double *norm_out) {
+  if (!ps || !norm_out || !(r_int > 0.0))
+    return pfail(NRR_ERR_INVALID_ARG, "null argument or r_int <= 0");
+  nrr_status s = begin(ps);
+  if (s != NRR_OK) return s;
+  launch_patch_norm(ps, r_int);
+  return read_norm(ps, norm_out);
+}
+
+nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
+                              nrr_relax_result *r) {
+  if (!ps || !o) return pfail(NRR_ERR_INVALID_ARG, "null argument");
+  if (o->mode != NRR_FP64)
+    return pfail(NRR_ERR_INVALID_ARG, "patch sets relax in NRR_FP64");
+  if (!(o->tol > 0.0) || o->check_every < 1 || o->max_iters < 0 || !(o->cfl > 0.0) ||
+      !(o->r_int > 0.0))
+    return pfail(NRR_ERR_INVALID_ARG, "invalid relax options");
+  if (o->initial != NRR_INIT_ZERO && o->initial != NRR_INIT_CURRENT)
+    return pfail(NRR_ERR_INVALID_ARG, "patch sets start from zero or the current state");
+  using clk = std::chrono::steady_clock;
+  const auto t_start = clk::now();
+  auto elapsed_ms = [&] {
+    return std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+  };
+  nrr_status s = begin(ps);
+  if (s != NRR_OK) return s;
+  cudaStream_t st = grid_view(ps->grid[0]).stream;
+  if (o->initial == NRR_INIT_ZERO)
+    for (int i = 0; i < 2; i++) {
+      GridView v = grid_view(ps->grid[i]);
+      for (int c = 0; c < 2; c++)
+        PCUDA(cudaMemsetAsync(v.f64.y[c], 0, (size_t)v.geo.npts * sizeof(double), st));
+    }
+  double dt = 0.0, eta_def = 0.0;
+  nrr_patchset_timestep(ps, o->cfl, &dt, &eta_def);
+  const double eta = o->eta > 0.0 ? o->eta : eta_def;
+  double nrm = 0.0;
+  launch_patch_norm(ps, o->r_int);
+  s = read_norm(ps, &nrm);
+  if (s != NRR_OK) return s;
+  int64_t it = 0;
+  nrr_status why = NRR_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (!std::isfinite(nrm)) {
+      why = NRR_ERR_DIVERGED;
+      break;
+    }
+    if (nrm < o->tol) {
+      why = NRR_OK;
+      break;
+    }
+    if (it >= o->max_iters) break;
+    if (o->timeout_ms > 0 && elapsed_ms() > (double)o->timeout_ms) {
+      why = NRR_ERR_TIMEOUT;
+      break;
+    }
+    const int64_t m = std::min<int64_t>(o->check_every, o->max_iters - it);
+    launch_patch_steps(ps, dt, eta, m);
+    launch_patch_norm(ps, o->r_int);
+    s = read_norm(ps, &nrm);
+    if (s != NRR_OK) return s;
+    it += m;
+  }
+  if (r) {
+    r->iters = it;
+    r->outer_iters = 0;
+    r->final_norm = nrm;
+    r->seconds = elapsed_ms() * 1e-3;
+    r->status = why;
+  }
+  if (why == NRR_ERR_NOT_CONVERGED)
+    return pfail(why, "patch set not converged after %lld steps (norm %.3e)",
+                 (long long)it, nrm);
+  if (why == NRR_ERR_DIVERGED)
+    return pfail(why, "patch set residual not finite after %lld steps", (long long)it);
+  if (why == NRR_ERR_TIMEOUT)
+    return pfail(why, "patch set timeout after %lld steps", (long long)it);
+  return NRR_OK;
+}
+
+}  // extern "C"

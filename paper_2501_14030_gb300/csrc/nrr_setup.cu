@@ -286,6 +286,11 @@ __global__ void source_kernel(Geo g, PunctureSet ps, const double *dsmin,
   if (g.coord != CARTESIAN) {
     double c = dsmin[i0 + g.s0 * i1] / dsmin_global[0];
     c2 = c * c;
+  } else {
+    // uniform spacing: c = spacing / reference spacing, exactly 1 unless the
+    // grid is a patch of a multi-patch system with a smaller reference
+    double c = fmin(g.dxx[0], fmin(g.dxx[1], g.dxx[2])) / dsmin_global[0];
+    c2 = c * c;
   }
   alpha[p] = al;
   bc2[p] = c2 * beta;

@@ -88,9 +88,12 @@ __global__ void __launch_bounds__(128)
     stage_curvi_item<R, NG, KIND, 1>(g, a, it % ncols, NG + it / ncols);
 }
 
-// Cartesian: uniform spacing, c = 1, every ghost is an outer ghost evolved by
-// the radiation condition with d_r f = sum_i (x^i/r) D_i f (one-sided inward
-// along directions in which the point lies outside, centred otherwise).
+// Cartesian: uniform spacing, so the wave speed is one constant (1 on a lone
+// grid; c^2 is in the folded weights, c multiplies the radiation term at the
+// call sites); every ghost is an outer ghost evolved by the radiation
+// condition with d_r f = sum_i (x^i/r) D_i f (one-sided inward along
+// directions in which the point lies outside, centred otherwise).  Returns
+// -(d_r f + f/r).
 template <typename R, int NG>
 __device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ f,
                                             int i0, int i1, int i2, int64_t p) {
@@ -171,8 +174,9 @@ __global__ void __launch_bounds__(256)
       ku = fma(-a.eta, u0, v0);
       if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
     } else {
-      ku = cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
-      kv = cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
+      const R c = R(a.cart.speed);
+      ku = c * cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
+      kv = c * cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
       if (linear_mode<R>(a.lin)) {
         ku += ld(a.fu + p);
         kv += ld(a.bc2 + p);
@@ -252,8 +256,9 @@ __device__ __forceinline__ void cart_shell_point(const Geo &g, const StageArgs<R
     dru = fma(nx, Du, dru);
     drv = fma(nx, Dv, drv);
   }
-  ku = -(dru + u0 * rinv);
-  kv = -(drv + v0 * rinv);
+  const R c = R(a.cart.speed);
+  ku = -c * (dru + u0 * rinv);
+  kv = -c * (drv + v0 * rinv);
   if (linear_mode<R>(a.lin)) {
     ku += ld(a.fu + p);
     kv += ld(a.bc2 + p);
@@ -640,8 +645,10 @@ __global__ void __launch_bounds__(128)
     for (int i2 = z0; i2 < z1; i2++) {
       int64_t p = i0 + (int64_t)g.s0 * (i1 + (int64_t)g.s1 * i2);
       R u0 = ld(su + p);
+      // the operator carries the folded c^2 (exactly 1 on a lone grid)
       double H = (double)cart_operator<R, NG>(g, su, w, p, u0, ld(alpha + p),
-                                              ld(bc2 + p), lin);
+                                              ld(bc2 + p), lin) /
+                 (cc.speed * cc.speed);
       if (h_out) h_out[p] = H;
       double x2 = g.xxmin[2] + (i2 - NG + 0.5) * g.dxx[2];
       double wt = sqrt(x0 * x0 + x1 * x1 + x2 * x2) < r_int ? 1.0 : 0.0;
@@ -994,6 +1001,14 @@ template <typename R, int NG>
 void launch_curvi(const Geo &g, int kind, const StageArgs<R> &a,
                   const LaunchCfg &cfg, cudaStream_t st) {
   const int zc = cfg.zc, pdl = cfg.pdl;
+  if (cfg.variant == 6) {
+    // single stage launches of the two-stage shape: the column kernel
+    LaunchCfg col = cfg;
+    col.variant = 0;
+    col.zc = 2;
+    launch_curvi<R, NG>(g, kind, a, col, st);
+    return;
+  }
   if (cfg.variant == 4) {
     // single stage launches of the multi-stage shape: the column kernel
     LaunchCfg col = cfg;

@@ -42,7 +42,10 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_surrogate_get_params", "nrr_batch_set_u",
            "nrr_batch_get_interior", "nrr_prolong", "nrr_last_error",
            "nrr_version", "nrr_selftest_recip", "nrr_probe_peaks",
-           "nrr_set_device_loop")
+           "nrr_set_device_loop", "nrr_set_speed_reference",
+           "nrr_patchset_create", "nrr_patchset_destroy", "nrr_patchset_info",
+           "nrr_patchset_timestep", "nrr_patchset_step",
+           "nrr_patchset_residual", "nrr_patchset_relax")
 
 
 class NrrError(RuntimeError):
@@ -114,6 +117,14 @@ def lib() -> C.CDLL:
                            C.POINTER(C.c_int)],
         "nrr_set_pdl": [V, I],
         "nrr_set_device_loop": [V, I],
+        "nrr_set_speed_reference": [V, C.c_double],
+        "nrr_patchset_create": [V, V, C.c_double, I, C.POINTER(V)],
+        "nrr_patchset_destroy": [V],
+        "nrr_patchset_info": [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64), D],
+        "nrr_patchset_timestep": [V, C.c_double, D, D],
+        "nrr_patchset_step": [V, C.c_double, C.c_double, C.c_int64],
+        "nrr_patchset_residual": [V, C.c_double, D],
+        "nrr_patchset_relax": [V, C.POINTER(RelaxOpts), C.POINTER(RelaxResult)],
         "nrr_selftest_wait_expiry": [I, V, C.POINTER(C.c_int)],
         "nrr_autotune_save": [C.c_char_p],
         "nrr_autotune_load": [C.c_char_p],
@@ -435,6 +446,11 @@ class Grid:
         """Programmatic dependent launch of the stage kernels (default on)."""
         _check(lib().nrr_set_pdl(self._h, int(bool(on))))
 
+    def set_speed_reference(self, ds_ref: float):
+        """Wave speed = local spacing / ds_ref (a patch of a multi-patch
+        system)."""
+        _check(lib().nrr_set_speed_reference(self._h, float(ds_ref)))
+
     def set_device_loop(self, on: bool):
         """Stop test on the device, one graph launch per solve (default on),
         or one host read of the norm per chunk (off)."""
@@ -452,6 +468,61 @@ class Grid:
     def step(self, steps: int, dt: float, eta: float, mode="fp64"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         _check(lib().nrr_step(self._h, m, dt, eta, int(steps)))
+
+
+class PatchSet:
+    """An outer grid and an inner Cartesian box relaxed as one system
+    (receivers interpolated from the other patch).  The grids stay owned by
+    the caller and must outlive the patch set."""
+
+    def __init__(self, outer: "Grid", inner: "Grid", hole: float, q: int = 4):
+        h = C.c_void_p()
+        _check(lib().nrr_patchset_create(outer._h, inner._h, float(hole), int(q),
+                                         C.byref(h)))
+        self._h = h
+        self.outer, self.inner = outer, inner
+        no, ni, ds = C.c_int64(), C.c_int64(), C.c_double()
+        _check(lib().nrr_patchset_info(h, C.byref(no), C.byref(ni), C.byref(ds)))
+        self.outer_receivers, self.inner_receivers = no.value, ni.value
+        self.ds_ref = ds.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrr_patchset_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def timestep(self, cfl: float = 0.5):
+        dt, eta = C.c_double(), C.c_double()
+        _check(lib().nrr_patchset_timestep(self._h, cfl, C.byref(dt), C.byref(eta)))
+        return dt.value, eta.value
+
+    def step(self, steps: int, dt: float, eta: float):
+        _check(lib().nrr_patchset_step(self._h, dt, eta, int(steps)))
+
+    def residual(self, r_int: float = 100.0) -> float:
+        n = C.c_double()
+        _check(lib().nrr_patchset_residual(self._h, r_int, C.byref(n)))
+        return n.value
+
+    def relax(self, tol=1e-10, max_iters=1_000_000, check_every=50, cfl=0.5,
+              eta=0.0, r_int=100.0, initial=None, timeout_ms=0,
+              raise_on_error=True) -> dict:
+        o = RelaxOpts()
+        _check(lib().nrr_default_opts(C.byref(o)))
+        o.tol, o.max_iters, o.check_every = tol, max_iters, check_every
+        o.cfl, o.eta, o.r_int, o.timeout_ms = cfl, eta, r_int, timeout_ms
+        o.initial = INIT_ZERO if initial is None else int(initial)
+        r = RelaxResult()
+        st = lib().nrr_patchset_relax(self._h, C.byref(o), C.byref(r))
+        if raise_on_error:
+            _check(st)
+        return _result(r, st)
 
 
 def _result(r: RelaxResult, st: int | None = None) -> dict:

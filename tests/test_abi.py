@@ -100,7 +100,7 @@ def test_bench_names_every_documented_stage_variant():
     doc = re.sub(r"\s*\n\s*\*\s*", " ", doc)  # comment lines joined
     documented = {int(v) for v in re.findall(r"variant (\d)", doc)}
     import bench
-    assert documented == set(range(6))
+    assert documented == set(range(7))
     assert documented <= set(bench.STAGE_VARIANTS)
 
 

@@ -573,3 +573,66 @@ def test_loaded_autotune_entry_sets_new_grids_shape(gpu, tmp_path):
     assert g2.get_launch("fp64")[0] == 0
     g2.close()
     nrr.autotune_clear()
+
+
+TWO_STAGE_CASES = {
+    "sinh_32x16x2_o8": (W.grid_desc("sinhsymtp", (32, 16, 2), 8), Q4),
+    "sinh_64x32x8_o8": (W.grid_desc("sinhsymtp", (64, 32, 8), 8), Q4),
+    "sinh_96x20x16_o8": (W.grid_desc("sinhsymtp", (96, 20, 16), 8),
+                         W.equal_mass_pair()),
+    "sinh_128x128x16_o8": W.q4_sinhsymtp_128(),
+}
+
+
+@pytest.mark.parametrize("name", list(TWO_STAGE_CASES))
+def test_two_stage_kernel_equals_column_kernel(gpu, name):
+    """Variant 6 evaluates two RK4 stages per launch (the first on the tile
+    with a halo, from shared memory) with the per-stage kernels' arithmetic:
+    FP32 trajectories of an odd and an even number of steps, a plain FP32
+    solve and a defect-correction solve give the column kernel's states
+    bit for bit."""
+    desc, punc = TWO_STAGE_CASES[name]
+    out = {}
+    for variant in (0, 6):
+        g = nrr.Grid(desc)
+        g.set_punctures(punc)
+        g.set_launch(1, "fp32", variant)
+        dt, eta = g.timestep(0.5)
+        u0 = torch.from_numpy(W.smooth_random_field(desc, seed=51, amplitude=0.1)).cuda()
+        res = []
+        for steps in (7, 30):
+            g.set_state(u0.clone(), torch.zeros_like(u0))
+            g.step(steps, dt, eta, mode="fp32")
+            u, v = torch.empty_like(u0), torch.empty_like(u0)
+            g.get_state(u, v)
+            res.append((u, v))
+        r32 = g.relax(mode="fp32", tol=1e-5, check_every=50, max_iters=2000,
+                      raise_on_error=False)
+        u32 = torch.empty_like(u0)
+        g.get_state(u32)
+        rdc = g.relax(mode="fp32_dc", tol=1e-10, check_every=50)
+        udc = torch.empty_like(u0)
+        g.get_state(udc)
+        out[variant] = (res, r32, u32, rdc, udc)
+        g.close()
+    (res0, r0, u0_, d0, ud0), (res6, r6, u6, d6, ud6) = out[0], out[6]
+    for (a, b), (c, d) in zip(res0, res6):
+        assert torch.equal(a, c) and torch.equal(b, d)
+    assert r0["iters"] == r6["iters"] and torch.equal(u0_, u6)
+    assert d0["status"] == d6["status"] == 0 and d0["iters"] == d6["iters"]
+    assert torch.equal(ud0, ud6)
+
+
+def test_two_stage_kernel_eligibility(gpu):
+    g = nrr.Grid(W.grid_desc("sinhsymtp", (64, 32, 8), 8))
+    with pytest.raises(nrr.NrrError):
+        g.set_launch(1, "fp64", 6)            # FP32 stages only
+    g.close()
+    for desc in (W.grid_desc("sinhsymtp", (48, 32, 8), 8),     # n0 % 32
+                 W.grid_desc("sinhsymtp", (64, 32, 32), 8),    # n2 > 16
+                 W.grid_desc("sinhsymtp", (64, 32, 8), 4),     # order
+                 W.grid_desc("spherical", (64, 32, 8), 8)):    # family
+        g = nrr.Grid(desc)
+        with pytest.raises(nrr.NrrError):
+            g.set_launch(1, "fp32", 6)
+        g.close()
