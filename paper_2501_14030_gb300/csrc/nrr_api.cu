@@ -1431,17 +1431,17 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaEventCreate(&e1));
   LaunchCfg best = keep;
   double best_ms = 1e30;
-  const LaunchCfg cands[25] = {{128, 1, 0},  {32, 1, 0},   {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
+  // (variant 6, two stages per launch, measured 4-7x slower than these on
+  // every eligible grid, is left to nrr_set_launch)
+  const LaunchCfg cands[24] = {{128, 1, 0},  {32, 1, 0},   {64, 1, 0},   {256, 1, 0},  {128, 2, 0},
                                {64, 2, 0},   {128, 4, 0},  {128, 2, 1},  {128, 4, 1},
                                {128, 8, 1},  {128, 16, 1}, {128, 1, 2},  {128, 2, 3},
                                {128, 4, 3},  {128, 8, 3},  {128, 16, 3}, {256, 2, 3},
                                {256, 4, 3},  {256, 8, 3},  {256, 16, 3}, {128, 1, 4},
-                               {128, 4, 5},  {128, 8, 5},  {128, 16, 5}, {512, 1, 6}};
+                               {128, 4, 5},  {128, 8, 5},  {128, 16, 5}};
   for (const LaunchCfg &cand0 : cands) {
-    // SinhCylindrical grids have the column kernel only; the two-stage
-    // kernel runs eligible FP32 grids
+    // SinhCylindrical grids have the column kernel only
     if (g->geo.coord == SINHCYLINDRICAL && cand0.variant != 0) continue;
-    if (cand0.variant == 6 && (prec != 32 || !stage2_ok(g->geo))) continue;
     LaunchCfg cand = cand0;
     cand.pdl = keep.pdl;
     cfg = cand;
