@@ -594,34 +594,69 @@ def run_surrogate(args):
 
 
 def run_profile_gemm(args):
-    """The surrogate's largest GEMM shapes once each (profiler captures):
-    forward/backward of the 512 -> 16384 layer at batch 256 and a larger
-    M for the tensor-core rate."""
+    """The surrogate's GEMM shapes (forward of the 512 -> 16384 layer at batch
+    256, its input gradient with K = 16384, its weight gradient, a hidden
+    layer) and a large M for the tensor-core rate: each tile width and K
+    split that applies, timed with CUDA events (operands stay L2-resident
+    between calls) two ways: 20 calls enqueued from Python with one status
+    read-back (`ms_enqueued`, host-bound for the small shapes), and the same
+    20 calls captured in a CUDA graph and replayed (`ms`, device time per
+    call).  The chosen plan (bn = splits = 0) is listed first."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_14030_gb300 import nrr
     torch.cuda.set_device(0)
     g = torch.Generator(device="cuda").manual_seed(0)
-    # network shapes at batch 256 (forward of the 512 -> 16384 layer, its
-    # input gradient with K = 16384, its weight gradient, a hidden layer) and
-    # a large M for the tensor-core rate
+    hbm, _ = hbm_peak_gbs()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        bf16 = 1900.0  # fallback burst figure
     for (M, N, K) in [(256, 16384, 512), (256, 512, 16384), (16384, 512, 256),
                       (256, 512, 512), (8192, 16384, 512)]:
         A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
         D = torch.empty((M, N), dtype=torch.float32, device="cuda")
-        nrr.gemm_bf16_tn(A, B, D)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            nrr.gemm_bf16_tn(A, B, D)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / 10
-        print(json.dumps({"gemm": [M, N, K], "ms": ms,
-                          "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}))
+        combos = [(0, 0)] + [(bn, 1) for bn in (64, 128, 256) if N % bn == 0]
+        if K >= 4096:
+            combos += [(128, sp) for sp in (8, 19, 38)] + [(64, 19)]
+        for bn, sp in combos:
+            for _ in range(3):
+                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+            nrr.gemm_status()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+            e1.record()
+            e1.synchronize()
+            nrr.gemm_status()
+            ms_enq = e0.elapsed_time(e1) / 20
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+                for _ in range(20):
+                    nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+            graph.replay()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(5):
+                graph.replay()
+            e1.record()
+            e1.synchronize()
+            nrr.gemm_status()
+            ms = e0.elapsed_time(e1) / 100
+            del graph
+            nbytes = 2 * (M * K + N * K) + 4 * M * N
+            tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            print(json.dumps({"gemm": [M, N, K], "bn": bn, "splits": sp, "ms": ms,
+                              "ms_enqueued": ms_enq,
+                              "tflops": tf, "frac_bf16": tf / bf16,
+                              "GBps_operands_and_output": gbs,
+                              "frac_hbm": gbs / hbm}), flush=True)
     return 0
 
 

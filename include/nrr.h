@@ -514,11 +514,38 @@ nrr_status nrr_batch_autotune(nrr_batch *b, int mode, int64_t trial_steps,
  * D[m][n] = sum_k A[m][k] B[n][k] for row-major BF16 A (M x K) and B
  * (N x K) -- both K-major -- and row-major FP32 D (M x N).  All device
  * pointers, 16-byte aligned; M % 128 == 0, N % 64 == 0, K % 64 == 0.
- * Synchronous on `stream`; NRR_ERR_TIMEOUT if a pipeline wait expired.
+ * Tile width and K splits are chosen from the shape (as
+ * nrr_gemm_bf16_tn_async with bn = splits = 0).  Synchronous on `stream`:
+ * it ends with nrr_gemm_status, so NRR_ERR_TIMEOUT if a pipeline wait of
+ * this or an earlier unchecked call expired.
  * Errors: NRR_ERR_INVALID_ARG (null or misaligned pointer, a size that is
- * not a multiple of the tile), NRR_ERR_CUDA. */
+ * not a multiple of the tile), NRR_ERR_OOM (split-K workspace),
+ * NRR_ERR_CUDA. */
 nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
                             int N, int K, void *stream);
+
+/* The same product, only enqueued on `stream` (no host synchronisation).
+ * bn: output tile width 64, 128 or 256 (must divide N), 0 to choose (256
+ * when it divides N and the (N / 256) x (M / 128) tiles fit one per SM,
+ * else 128 when it divides N, else 64).  splits: number of equal K ranges
+ * computed by separate CTAs into a stream-ordered FP32 workspace
+ * (splits x M x N, cudaMallocAsync on `stream`, freed on it after use) and
+ * summed by a second kernel in a fixed order, so results are deterministic;
+ * 1 = no split, 0 = choose (split only when the output tiles fill fewer
+ * than half the SMs and K / 64 >= 32, into about one CTA per SM, at least
+ * eight k-blocks each); at most K / 64.  A pipeline wait that expires is only
+ * recorded in a device flag: nrr_gemm_status reads it.
+ * Errors (host-side, nothing enqueued): NRR_ERR_INVALID_ARG (as
+ * nrr_gemm_bf16_tn, or bn / splits outside the ranges above), NRR_ERR_OOM,
+ * NRR_ERR_CUDA. */
+nrr_status nrr_gemm_bf16_tn_async(const void *A, const void *B, float *D, int M,
+                                  int N, int K, int bn, int splits, void *stream);
+
+/* Waits for `stream` and reads the GEMM error flag, which every GEMM of the
+ * library (nrr_gemm_*, the surrogate) sets when a pipeline wait expires;
+ * clears it.  NRR_OK, NRR_ERR_TIMEOUT (a wait expired since the last
+ * check: that call's output is incomplete), NRR_ERR_CUDA. */
+nrr_status nrr_gemm_status(void *stream);
 
 /* ---- Warm-start surrogate (trained on solutions the solver generates) ---- */
 typedef struct nrr_surrogate nrr_surrogate;

@@ -172,8 +172,7 @@ __host__ __device__ constexpr int shell_rows() { return 32 * kTileY / NG; }
 // phi chunks).  VAR 0: planes staged
 // through registers (stage_tile_block); VAR 1: planes streamed by tensor
 // copies through a ring of shared-memory slots (stage_tma_block; order 8,
-// aligned grids), which records an expired copy wait in *err; VAR 2: one
-// thread per column of evolved points and zc planes (stage_curvi_item).
+// aligned grids), which records an expired copy wait in *err.
 template <typename R, int NG, int KIND, int VAR>
 __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 1)
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
@@ -184,20 +183,6 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 
   const SolveDev &sd = sds[bm.x];
   const Geo g = sd.g;
   const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
-  if constexpr (VAR == 2) {
-    // column kernel: thread = one (i0, i1) column of evolved points (shell
-    // columns last) and zc phi planes
-    const int ncols = (g.n0 + NG) * g.n1, ncb = (ncols + 32 * kTileY - 1) / (32 * kTileY);
-    const int e = (bm.y % ncb) * 32 * kTileY + threadIdx.x;
-    if (e >= ncols) return;
-    const int z0 = NG + (bm.y / ncb) * zc;
-    switch (zc) {
-      case 1: dev::stage_curvi_item<R, NG, KIND, 1>(g, a, e, z0); break;
-      case 2: dev::stage_curvi_item<R, NG, KIND, 2>(g, a, e, z0); break;
-      default: dev::stage_curvi_item<R, NG, KIND, 4>(g, a, e, z0); break;
-    }
-    return;
-  }
   const int nx = dev::tiles_x(g), ny = dev::tiles_y<kTileY>(g);
   const int nint = nx * ny * dev::chunks_z(g, zc);
   if (bm.y >= nint) {
@@ -214,7 +199,7 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 
   }
   const int tile_x = bm.y % nx, tile_y = (bm.y / nx) % ny, chunk = bm.y / (nx * ny);
   if constexpr (VAR == 1) {
-    __shared__ __align__(128) dev::TmaSlot<R, NG, kTileY, kTmaPZ> ring[tma_slots<R>()];
+    __shared__ __align__(128) dev::TmaSlot<R, NG, kTileY, kTmaPZ, sizeof(R) == 4> ring[tma_slots<R>()];
     __shared__ __align__(8) uint64_t full[tma_slots<R>()];
     dev::stage_tma_block<R, NG, KIND, kTileY, tma_slots<R>(), kTmaPZ>(
         g, a, tile_x, tile_y, chunk, zc, sizeof(R) == 4 ? sd.tf32 : sd.tf64, ring,
@@ -223,6 +208,27 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 
     __shared__ R tile[2][kTileY + 2 * NG][32 + 2 * NG];
     dev::stage_tile_block<R, NG, KIND, kTileY>(g, a, tile_x, tile_y, chunk, zc, tile);
   }
+}
+
+// Column variant of the stage kernel (as the single-grid column kernel):
+// thread = one (i0, i1) column of evolved points (shell columns last) and ZC
+// phi planes; block b covers 32 * kTileY columns of solve map[b].x, chunk
+// map[b].y.  ZC is a template parameter and the register budget is capped
+// (several blocks per SM), so that the FP64 pipe sees as many warps as in the
+// single-grid kernel.
+template <typename R, int NG, int KIND, int ZC>
+__global__ void __launch_bounds__(32 * kTileY, ZC == 4 ? 4 : 6)
+    batch_col_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
+                     const int *__restrict__ active, int stage, int mode) {
+  const int2 bm = map[blockIdx.x];
+  if (!active[bm.x]) return;
+  const SolveDev &sd = sds[bm.x];
+  const Geo g = sd.g;
+  const StageArgs<R> a = batch_stage_args<R>(sd, stage, mode);
+  const int ncols = (g.n0 + NG) * g.n1, ncb = (ncols + 32 * kTileY - 1) / (32 * kTileY);
+  const int e = (bm.y % ncb) * 32 * kTileY + threadIdx.x;
+  if (e >= ncols) return;
+  dev::stage_curvi_item<R, NG, KIND, ZC>(g, a, e, NG + (bm.y / ncb) * ZC);
 }
 
 // FP64 residual partial sums over all solves (2 phi planes per item).
@@ -508,8 +514,17 @@ template <typename R, int NG, int KIND>
 void launch_bstage_kind(nrr_batch *b, int zc, int stage, int mode,
                         cudaStream_t st) {
   if (b->variant[sizeof(R) == 4] == 2) {
-    batch_stage_kernel<R, NG, KIND, 2><<<b->nblk_col[col_index(zc)], 32 * kTileY, 0, st>>>(
-        b->d_sd, b->d_map_col[col_index(zc)], b->d_active, stage, mode, zc, b->d_err);
+    const int nb = b->nblk_col[col_index(zc)];
+    const int2 *map = b->d_map_col[col_index(zc)];
+    if (zc <= 1)
+      batch_col_kernel<R, NG, KIND, 1><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
+                                                                  stage, mode);
+    else if (zc == 2)
+      batch_col_kernel<R, NG, KIND, 2><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
+                                                                  stage, mode);
+    else
+      batch_col_kernel<R, NG, KIND, 4><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
+                                                                  stage, mode);
     return;
   }
   const int2 *map = b->d_map_stage[zc_index(zc)];

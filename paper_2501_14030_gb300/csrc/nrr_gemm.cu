@@ -2,19 +2,25 @@
 // the surrogate network: D[M,N] (FP32) = sum_k A[m,k] B[n,k], both operands
 // K-major BF16 in global memory.
 //
-// One CTA computes a 128 x BN tile.  Warp 0 (one lane) streams 128x64 and
-// BNx64 operand tiles into a STAGES-deep (3) shared-memory ring with TMA
-// (128-byte swizzle); warp 1 (one lane) issues tcgen05.mma (M=128, N=BN,
-// K=16 per instruction) into an FP32 accumulator in tensor memory and
-// releases each stage with tcgen05.commit; then all four warps read the
-// accumulator back with tcgen05.ld (warp w owns rows 32w..32w+31) and store
-// it.  Every mbarrier wait is bounded: on expiry the kernel records an error,
-// skips the remaining work, frees its tensor memory and returns.
+// One CTA computes a 128 x BN tile (BN = 64, 128 or 256) over a range of K.
+// Warp 0 (one lane) streams 128x64 and BNx64 operand tiles into a shared-
+// memory ring (3 stages for BN <= 128, two CTAs per SM; 4 stages for
+// BN = 256, one CTA per SM) with TMA (128-byte swizzle); warp 1 (one lane)
+// issues tcgen05.mma (M=128, N=BN, K=16 per instruction) into an FP32
+// accumulator in tensor memory and releases each stage with tcgen05.commit;
+// then all four warps read the accumulator back with tcgen05.ld (warp w owns
+// rows 32w..32w+31) and store it.  Split-K: blockIdx.z takes one of S equal
+// ranges of K and writes its partial tile to slice z of a workspace, and a
+// second kernel sums the S slices in a fixed order (deterministic).  Every
+// mbarrier wait is bounded: on expiry the kernel records an error in a device
+// flag, skips the remaining work, frees its tensor memory and returns; the
+// flag is read back only when the caller asks (nrr_gemm_status).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -27,10 +33,16 @@ namespace nrr {
 namespace {
 
 constexpr int BM = 128, BK = 64;
-// Pipeline depth: three 128 x 64 + BN x 64 stages leave room for two CTAs
-// per SM (one CTA's epilogue overlaps another's main loop), and the freed
-// stages hold the accumulator tile for the coalesced store.
-constexpr int STAGES = 3;
+// Pipeline depth: for BN <= 128 three 128 x 64 + BN x 64 stages leave room
+// for two CTAs per SM (one CTA's epilogue overlaps another's main loop); the
+// 48 KB stages of BN = 256 take four and one CTA per SM.  The freed stages
+// hold the accumulator tile for the coalesced store.
+template <int BN>
+__host__ __device__ constexpr int gemm_stages() { return BN == 256 ? 4 : 3; }
+template <int BN>
+__host__ __device__ constexpr int gemm_smem() {
+  return gemm_stages<BN>() * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+}
 constexpr long long kWaitLimit = 1ll << 18;  // try_wait polls (about a second)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -98,11 +110,14 @@ __device__ __forceinline__ uint32_t mma_idesc() {
          ((uint32_t)(BM >> 4) << 24);
 }
 
+// D + z * split_stride receives the partial product over K range z of
+// gridDim.z (the whole K when gridDim.z == 1).
 template <int BN>
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(128, BN == 256 ? 1 : 2)
     gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap map_a,
                         const __grid_constant__ CUtensorMap map_b, float *D,
-                        int M, int N, int K, int ldd, int *err) {
+                        int M, int K, int ldd, int64_t split_stride, int *err) {
+  constexpr int STAGES = gemm_stages<BN>();
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   static_assert((size_t)BM * (BN + 4) * 4 <= (size_t)STAGES * (A_BYTES + B_BYTES),
                 "the epilogue's row staging must fit in the pipeline buffers");
@@ -119,7 +134,12 @@ __global__ void __launch_bounds__(128, 2)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = K / BK;
+  // K range of this split: k-blocks kb0 .. kb0 + nk - 1 (nk >= 1, the host
+  // keeps gridDim.z <= K / BK)
+  const int nk_all = K / BK;
+  const int kb0 = (int)((int64_t)nk_all * blockIdx.z / gridDim.z);
+  const int nk = (int)((int64_t)nk_all * (blockIdx.z + 1) / gridDim.z) - kb0;
+  D += (int64_t)blockIdx.z * split_stride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -151,8 +171,8 @@ __global__ void __launch_bounds__(128, 2)
           !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err, 1))
         break;
       mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-      tma_load_2d(sA + s * A_BYTES, &map_a, &full[s], kb * BK, m0);
-      tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], kb * BK, n0);
+      tma_load_2d(sA + s * A_BYTES, &map_a, &full[s], (kb0 + kb) * BK, m0);
+      tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], (kb0 + kb) * BK, n0);
       *issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -322,10 +342,40 @@ bool cached_map(CUtensorMap *out, const void *base, int rows, int cols,
 int *g_err = nullptr;
 std::once_flag g_err_once;
 
+// Sum of the S split-K slices ws[z][m][n] (row stride N) into D[m][n] (row
+// stride ldd), in the order z = 0 .. S-1; four columns per thread.
+__global__ void splitk_reduce_kernel(const float4 *__restrict__ ws, float *D,
+                                     int M, int N, int ldd, int S) {
+  const int64_t n4 = N / 4, total = (int64_t)M * n4;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 acc = ws[i];
+    for (int z = 1; z < S; z++) {
+      const float4 v = ws[(int64_t)z * total + i];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    const int64_t m = i / n4, c = i - m * n4;
+    reinterpret_cast<float4 *>(D + m * ldd)[c] = acc;
+  }
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    return 1;
+  return sms;
+}
+
 template <int BN>
 cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, float *D,
-                        int M, int N, int K, int ldd, cudaStream_t st) {
-  constexpr int smem = STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+                        int M, int N, int K, int ldd, int splits,
+                        int64_t split_stride, cudaStream_t st) {
+  constexpr int smem = gemm_smem<BN>();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN>,
@@ -334,8 +384,9 @@ cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, float *D,
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(N / BN, M / BM);
-  gemm_bf16_tn_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, D, M, N, K, ldd, g_err);
+  dim3 grid(N / BN, M / BM, splits);
+  gemm_bf16_tn_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, D, M, K, ldd, split_stride,
+                                                  g_err);
   return cudaGetLastError();
 }
 
@@ -348,8 +399,38 @@ int *gemm_error_flag() {
   return g_err;
 }
 
+// Tile width and K splits for a shape, each where the caller passed 0
+// (measured on GB300 at the surrogate's shapes):
+// - 256 wide when it divides N and the 128 x 256 tiles fit in one wave of
+//   one CTA per SM (fewer operand bytes per flop, no second wave that would
+//   need the epilogue overlap of two CTAs per SM); else 128 when it divides
+//   N, else 64;
+// - K split when the output tiles fill fewer than half the SMs and K is
+//   long (K / 64 >= 32): about one CTA per SM, at least eight k-blocks per
+//   split, so that the partial-sum traffic and the second kernel stay small
+//   against the main loop.
+void gemm_plan(int M, int N, int K, int *bn, int *splits) {
+  const int sms = device_sms();
+  if (*bn == 0) {
+    if (N % 256 == 0 && (int64_t)(N / 256) * (M / BM) <= sms)
+      *bn = 256;
+    else
+      *bn = (N % 128 == 0) ? 128 : 64;
+  }
+  if (*splits != 0) return;
+  const int tiles = (N / *bn) * (M / BM), nk = K / BK;
+  int sp = 1;
+  if (2 * tiles <= sms && nk >= 32) sp = std::max(1, std::min(nk / 8, sms / tiles));
+  *splits = sp;
+}
+
+size_t gemm_workspace_bytes(int M, int N, int splits) {
+  return splits > 1 ? (size_t)splits * M * N * sizeof(float) : 0;
+}
+
 nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
-                        int K, int ldd, cudaStream_t st, char *msg, int msglen) {
+                        int K, int ldd, cudaStream_t st, char *msg, int msglen,
+                        int bn, int splits, float *ws, size_t ws_bytes) {
   if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || M % BM || K % BK ||
       (N % 64) || ldd < N || (ldd % 4) ||
       (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
@@ -360,18 +441,50 @@ nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
              M, N, K, ldd);
     return NRR_ERR_INVALID_ARG;
   }
+  if ((bn != 0 && bn != 64 && bn != 128 && bn != 256) || (bn != 0 && N % bn) ||
+      splits < 0 || splits > K / BK || splits > 65535) {
+    snprintf(msg, msglen,
+             "gemm: tile width must be 0 (chosen), 64, 128 or 256 and divide N; "
+             "splits 0 (chosen) .. K/64 (bn=%d splits=%d N=%d K=%d)",
+             bn, splits, N, K);
+    return NRR_ERR_INVALID_ARG;
+  }
   if (!gemm_error_flag()) {
     snprintf(msg, msglen, "gemm: error flag allocation failed");
     return NRR_ERR_OOM;
   }
-  const int bn = (N % 128 == 0) ? 128 : 64;
+  gemm_plan(M, N, K, &bn, &splits);
   CUtensorMap ma, mb;
   if (!cached_map(&ma, A, M, K, BM) || !cached_map(&mb, B, N, K, bn)) {
     snprintf(msg, msglen, "gemm: tensor map encoding failed");
     return NRR_ERR_CUDA;
   }
-  cudaError_t e = bn == 128 ? launch_gemm<128>(ma, mb, D, M, N, K, ldd, st)
-                            : launch_gemm<64>(ma, mb, D, M, N, K, ldd, st);
+  const size_t need = gemm_workspace_bytes(M, N, splits);
+  bool own = false;
+  if (splits > 1 && (!ws || ws_bytes < need)) {
+    // stream-ordered temporary for the partial products
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ws), need, st);
+    if (e != cudaSuccess) {
+      snprintf(msg, msglen, "gemm: split-K workspace of %zu bytes: %s", need,
+               cudaGetErrorString(e));
+      return NRR_ERR_OOM;
+    }
+    own = true;
+  }
+  float *dst = splits > 1 ? ws : D;
+  const int ld = splits > 1 ? N : ldd;
+  const int64_t stride = (int64_t)M * N;
+  cudaError_t e = bn == 256 ? launch_gemm<256>(ma, mb, dst, M, N, K, ld, splits, stride, st)
+                  : bn == 128 ? launch_gemm<128>(ma, mb, dst, M, N, K, ld, splits, stride, st)
+                              : launch_gemm<64>(ma, mb, dst, M, N, K, ld, splits, stride, st);
+  if (e == cudaSuccess && splits > 1) {
+    const int64_t n4 = (int64_t)M * (N / 4);
+    const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 8 * device_sms());
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(ws),
+                                                 D, M, N, ldd, splits);
+    e = cudaGetLastError();
+  }
+  if (own) cudaFreeAsync(ws, st);
   if (e != cudaSuccess) {
     snprintf(msg, msglen, "gemm launch: %s", cudaGetErrorString(e));
     return NRR_ERR_CUDA;
@@ -398,16 +511,28 @@ nrr_status gemm_check_error(cudaStream_t st, char *msg, int msglen) {
 
 }  // namespace nrr
 
-extern "C" nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D,
-                                       int M, int N, int K, void *stream) {
+extern "C" {
+
+nrr_status nrr_gemm_bf16_tn_async(const void *A, const void *B, float *D, int M,
+                                  int N, int K, int bn, int splits, void *stream) {
   char msg[256] = {0};
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  nrr_status s = nrr::gemm_bf16_tn(A, B, D, M, N, K, N, st, msg, sizeof msg);
-  if (s != NRR_OK) {
-    nrr::set_last_error(msg);
-    return s;
-  }
-  s = nrr::gemm_check_error(st, msg, sizeof msg);
+  nrr_status s = nrr::gemm_bf16_tn(A, B, D, M, N, K, N, static_cast<cudaStream_t>(stream),
+                                   msg, sizeof msg, bn, splits, nullptr, 0);
   if (s != NRR_OK) nrr::set_last_error(msg);
   return s;
 }
+
+nrr_status nrr_gemm_status(void *stream) {
+  char msg[256] = {0};
+  nrr_status s = nrr::gemm_check_error(static_cast<cudaStream_t>(stream), msg, sizeof msg);
+  if (s != NRR_OK) nrr::set_last_error(msg);
+  return s;
+}
+
+nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
+                            int K, void *stream) {
+  nrr_status s = nrr_gemm_bf16_tn_async(A, B, D, M, N, K, 0, 0, stream);
+  return s != NRR_OK ? s : nrr_gemm_status(stream);
+}
+
+}  // extern "C"

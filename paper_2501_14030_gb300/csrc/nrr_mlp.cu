@@ -27,8 +27,11 @@
 
 namespace nrr {
 nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
-                        int K, int ldd, cudaStream_t st, char *msg, int msglen);
+                        int K, int ldd, cudaStream_t st, char *msg, int msglen,
+                        int bn, int splits, float *ws, size_t ws_bytes);
 nrr_status gemm_check_error(cudaStream_t st, char *msg, int msglen);
+void gemm_plan(int M, int N, int K, int *bn, int *splits);
+size_t gemm_workspace_bytes(int M, int N, int splits);
 }  // namespace nrr
 
 using namespace nrr;
@@ -309,6 +312,8 @@ struct nrr_surrogate {
   std::vector<float *> z;
   std::vector<bf16 *> a, at;
   float *da = nullptr, *dz32 = nullptr, *yb = nullptr;
+  float *ws = nullptr;  // split-K partial products
+  size_t ws_bytes = 0;
   bf16 *dzb = nullptr, *dzt = nullptr;
   float *mean = nullptr, *stdv = nullptr;
   int32_t *order_id = nullptr;  // identity order
@@ -340,7 +345,8 @@ nrr_status sbegin(nrr_surrogate *s) {
 nrr_status gemm(nrr_surrogate *s, const void *A, const void *B, float *D, int M,
                 int N, int K) {
   char msg[256];
-  nrr_status st = gemm_bf16_tn(A, B, D, M, N, K, N, s->stream, msg, sizeof msg);
+  nrr_status st = gemm_bf16_tn(A, B, D, M, N, K, N, s->stream, msg, sizeof msg, 0, 0,
+                               s->ws, s->ws_bytes);
   if (st != NRR_OK) set_last_error(msg);
   return st;
 }
@@ -549,6 +555,20 @@ nrr_status nrr_surrogate_create(int n_in, int hidden, int depth, int n_out,
     MTRY(malloc_s(s, &s->mean, n_out));
     MTRY(malloc_s(s, &s->stdv, n_out));
     MTRY(malloc_s(s, &s->order_id, batch));
+    // split-K workspace of the largest split GEMM of a training step (the
+    // weight gradients contract over the batch, the input gradients and
+    // the forward over a layer's width)
+    for (int l = 0; l < s->L; l++) {
+      const int shapes[3][3] = {{batch, s->dout[l], s->din[l]},
+                                {s->dout[l], s->din[l], batch},
+                                {batch, s->din[l], s->dout[l]}};
+      for (const auto &sh : shapes) {
+        int bn = 0, sp = 0;
+        gemm_plan(sh[0], sh[1], sh[2], &bn, &sp);
+        s->ws_bytes = std::max(s->ws_bytes, gemm_workspace_bytes(sh[0], sh[1], sp));
+      }
+    }
+    if (s->ws_bytes) MTRY(malloc_s(s, &s->ws, s->ws_bytes / sizeof(float)));
     MTRY(malloc_s(s, &s->partials, (size_t)((n_out + 31) / 32) * ((batch + 31) / 32) + 64));
     s->loss_cap = 1 << 16;
     MTRY(malloc_s(s, &s->loss, (size_t)s->loss_cap));

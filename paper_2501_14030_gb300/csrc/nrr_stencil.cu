@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(R) == 4 ? 24 / TY : 1)
                                     min(z0 + zc, NG + g.n2));
     return;
   }
-  __shared__ __align__(128) TmaSlot<R, NG, TY, PZ> ring[NS];
+  __shared__ __align__(128) TmaSlot<R, NG, TY, PZ, sizeof(R) == 4> ring[NS];
   __shared__ __align__(8) uint64_t full[NS];
   stage_tma_block<R, NG, KIND, TY, NS, PZ>(g, a, blockIdx.x % ntx,
                                             (blockIdx.x / ntx) % nty,
@@ -893,6 +893,7 @@ bool stage_field_maps(FieldSrc *m, const Geo &g, const StageArgs<R> &a, int b0u,
   const bool use_b = KIND == STAGE_MID, use_acc = KIND == STAGE_MID || KIND == STAGE_LAST;
   const bool need[8] = {true, true, true, use_fu, use_b, use_b, use_acc, use_acc};
   if (!field_map(&m->u, a.su, es, g, b0u, b1u)) return false;
+  if (!field_map(&m->ph, a.su, es, g, 32, ty)) return false;
   for (int o = 0; o < 8; o++) {
     if (need[o]) {
       if (!field_map(&m->op[o], ops[o], es, g, 32, ty)) return false;

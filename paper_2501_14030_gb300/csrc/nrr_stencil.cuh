@@ -684,10 +684,17 @@ struct ArenaSrc {
                                           int y, int z, int f) const {
     tma_load_4d(dst, map_op, bar, x, y, z, f);
   }
+  // u without halo (the planes entering the phi queue): the operand box of
+  // the u field
+  __device__ __forceinline__ void load_ph(void *dst, uint64_t *bar, int x, int y,
+                                          int z, int f) const {
+    tma_load_4d(dst, map_op, bar, x, y, z, f);
+  }
 };
 struct FieldSrc {
   CUtensorMap u;      // su, box (32 + 2 NG, TY + 2 NG, PZ)
   CUtensorMap op[8];  // operand arrays by TmaOp slot, box (32, TY, PZ)
+  CUtensorMap ph;     // su, box (32, TY, PZ): planes entering the phi queue
   template <typename R>
   __device__ __forceinline__ int field(const R *) const { return 0; }
   __device__ __forceinline__ void load_u(void *dst, uint64_t *bar, int x, int y,
@@ -698,22 +705,50 @@ struct FieldSrc {
                                           int y, int z, int) const {
     tma_load_3d(dst, &op[o], bar, x, y, z);
   }
+  __device__ __forceinline__ void load_ph(void *dst, uint64_t *bar, int x, int y,
+                                          int z, int) const {
+    tma_load_3d(dst, &ph, bar, x, y, z);
+  }
 };
 
-template <typename R, int NG, int TY, int PZ>
+// One ring slot.  Every member is a tensor-copy destination and starts on a
+// 128-byte boundary (checked where the ring is used).  PH: the slot also
+// carries, without halo, the PZ planes of u that enter the phi queue (NG
+// planes ahead of the slot's own), so that no thread loads them itself.
+template <typename R, int NG, int TY, int PZ, bool PH = false>
 struct TmaSlot {
   R u[PZ][TY + 2 * NG][32 + 2 * NG];  // PZ planes of u with halo
   R op[8][PZ][TY][32];                // operand rows, slots below
 };
+template <typename R, int NG, int TY, int PZ>
+struct TmaSlot<R, NG, TY, PZ, true> {
+  R u[PZ][TY + 2 * NG][32 + 2 * NG];
+  R op[8][PZ][TY][32];
+  R ph[PZ][TY][32];  // phi-queue planes of u, no halo
+};
+// Shared-memory destinations of tensor copies: 128-byte aligned slots and
+// members, so that a ring of slots keeps every copy aligned.
+template <typename R, int NG, int TY, int PZ, bool PH>
+constexpr bool tma_slot_aligned() {
+  return sizeof(TmaSlot<R, NG, TY, PZ, PH>) % 128 == 0 &&
+         (PZ * (TY + 2 * NG) * (32 + 2 * NG) * sizeof(R)) % 128 == 0 &&
+         (PZ * TY * 32 * sizeof(R)) % 128 == 0;
+}
 enum TmaOp { OP_SV = 0, OP_AL, OP_BC, OP_FU, OP_BU, OP_BV, OP_AU, OP_AV };
 
 template <typename R, int NG, int KIND, int TY, int NS, int PZ, typename Src,
-          bool COH = false>
+          bool COH = false, bool PH = false>
 __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R> &a,
                                                  int tile_x, int tile_y, int chunk,
                                                  int zc, const Src &src,
-                                                 TmaSlot<R, NG, TY, PZ> *ring,
+                                                 TmaSlot<R, NG, TY, PZ, PH> *ring,
                                                  uint64_t *full, int *err) {
+  // With PH the phi box of a slot (planes i2 + NG .. i2 + NG + PZ - 1,
+  // wrapped) must not straddle the periodic seam: PZ == 2 with even NG, even
+  // n2 and slots starting on even local planes keep it whole.
+  static_assert(!PH || (PZ == 2 && NG % 2 == 0), "phi box needs PZ 2, even NG");
+  static_assert(tma_slot_aligned<R, NG, TY, PZ, PH>(),
+                "tensor-copy destinations must start on 128-byte boundaries");
   static_assert((NG * sizeof(R)) % 16 == 0,
                 "operand boxes start at x = NG: 16-byte aligned");
   constexpr int TW = 32 + 2 * NG, TH = TY + 2 * NG;
@@ -784,7 +819,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
                           (use_b ? (1u << OP_BU) | (1u << OP_BV) : 0u) |
                           (use_acc ? (1u << OP_AU) | (1u << OP_AV) : 0u);
   const uint32_t slot_bytes =
-      (uint32_t)(PZ * (TW * TH + __popc(opmask) * TY * 32) * sizeof(R));
+      (uint32_t)(PZ * (TW * TH + (__popc(opmask) + (PH ? 1 : 0)) * TY * 32) * sizeof(R));
   // Source coordinate (field index for an arena) of u (fidx[8]) and of
   // each operand: thread 0 only.
   int fidx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -797,6 +832,9 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
       if ((opmask >> o) & 1u)
         src.load_op(o, &ring[sl].op[o][0][0][0], &full[sl], NG + j0b, NG + j1b,
                     pl, fidx[o]);
+    if constexpr (PH)
+      src.load_ph(&ring[sl].ph[0][0][0], &full[sl], NG + j0b, NG + j1b,
+                  wrap_plane<NG>(g, pl + NG), fidx[8]);
   };
   if (threadIdx.x == 0) {
     const R *optr[8] = {a.sv, a.alpha, a.bc2, a.fu, a.bu, a.bv, a.au, a.av};
@@ -813,9 +851,11 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
   for (int k = 0; k < 2 * NG; k++)
     q[k + PZ] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 - NG + k));
   R nq[PZ];
+  if constexpr (!PH) {
 #pragma unroll
-  for (int j = 0; j < PZ; j++)
-    nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 + NG + j));
+    for (int j = 0; j < PZ; j++)
+      nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, z0 + NG + j));
+  }
   R ireg[PZ][NST];
   auto fetch_images = [&](int pl) {
     if (!has_img) return;
@@ -839,7 +879,7 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
       if (it >= nslots) break;
       const int i2 = z0 + PZ * it;
       const bool ok = mbar_wait_parity(&full[sl], (uint32_t)phase);
-      TmaSlot<R, NG, TY, PZ> &S = ring[sl];
+      TmaSlot<R, NG, TY, PZ, PH> &S = ring[sl];
       if (has_img) {
 #pragma unroll
         for (int j = 0; j < PZ; j++) {
@@ -853,8 +893,13 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
       }
 #pragma unroll
       for (int k = 0; k < 2 * NG; k++) q[k] = q[k + PZ];
+      if constexpr (PH) {
 #pragma unroll
-      for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
+        for (int j = 0; j < PZ; j++) q[2 * NG + j] = S.ph[j][ty][tx];
+      } else {
+#pragma unroll
+        for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
+      }
       if (__syncthreads_or(!ok)) {
         // A copy did not complete in time: record it, let the copies still in
         // flight (slots it .. it + NS - 2) land, bounded, and leave.
@@ -870,9 +915,11 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
         issue(i2 + PZ * (NS - 1), (sl + NS - 1) % NS);
       if (it + 1 < nslots) {
         fetch_images(i2 + PZ);
+        if constexpr (!PH) {
 #pragma unroll
-        for (int j = 0; j < PZ; j++)
-          nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
+          for (int j = 0; j < PZ; j++)
+            nq[j] = lds<COH>(a.su + col + (int64_t)nc * wrap_plane<NG>(g, i2 + PZ + NG + j));
+        }
       }
 #pragma unroll
       for (int j = 0; j < PZ; j++) {

@@ -35,7 +35,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_set_pdl",
            "nrr_autotune", "nrr_batch_create", "nrr_batch_destroy",
            "nrr_batch_info", "nrr_batch_relax", "nrr_batch_get_u",
-           "nrr_batch_autotune", "nrr_batch_set_launch", "nrr_gemm_bf16_tn", "nrr_surrogate_create",
+           "nrr_batch_autotune", "nrr_batch_set_launch", "nrr_gemm_bf16_tn", "nrr_gemm_bf16_tn_async", "nrr_gemm_status", "nrr_surrogate_create",
            "nrr_surrogate_destroy", "nrr_surrogate_num_params",
            "nrr_surrogate_fit_scaling", "nrr_surrogate_train",
            "nrr_surrogate_predict", "nrr_surrogate_gradients",
@@ -143,6 +143,8 @@ def lib() -> C.CDLL:
                                C.POINTER(C.c_int)],
         "nrr_batch_set_launch": [V, I, I, I],
         "nrr_gemm_bf16_tn": [V, V, V, I, I, I, V],
+        "nrr_gemm_bf16_tn_async": [V, V, V, I, I, I, I, I, V],
+        "nrr_gemm_status": [V],
         "nrr_surrogate_create": [I, I, I, I, I, C.POINTER(C.c_float), V,
                                  C.POINTER(V)],
         "nrr_surrogate_destroy": [V],
@@ -292,17 +294,53 @@ def probe_peaks(l2_bytes: int = 0, stream=None) -> dict:
             "l2_gbs": l2.value}
 
 
+def _gemm_shape(A, B, D):
+    import torch
+    for t in (A, B):
+        if t.dtype != torch.bfloat16 or t.dim() != 2 or not t.is_contiguous():
+            raise NrrError(ERR_INVALID_ARG, "gemm operands: contiguous 2-D bfloat16")
+    if D.dtype != torch.float32 or not D.is_contiguous():
+        raise NrrError(ERR_INVALID_ARG, "gemm output: contiguous float32")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or tuple(D.shape) != (M, N):
+        raise NrrError(ERR_INVALID_ARG, "gemm: shapes A (M, K), B (N, K), D (M, N)")
+    return M, N, K
+
+
 def gemm_bf16_tn(A, B, D, stream=None) -> None:
-    """D (float32, M x N) = A (bf16, M x K) @ B (bf16, N x K)^T on device."""
+    """D (float32, M x N) = A (bf16, M x K) @ B (bf16, N x K)^T on device;
+    synchronous, raises on a pipeline timeout."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    M, K = A.shape
-    N = B.shape[0]
+    M, N, K = _gemm_shape(A, B, D)
     _check(lib().nrr_gemm_bf16_tn(C.c_void_p(A.data_ptr()),
                                   C.c_void_p(B.data_ptr()),
                                   C.c_void_p(D.data_ptr()), M, N, K,
                                   C.c_void_p(stream.cuda_stream)))
+
+
+def gemm_bf16_tn_async(A, B, D, bn=0, splits=0, stream=None) -> None:
+    """The same product only enqueued; bn / splits 0 = chosen from the shape.
+    Check with gemm_status()."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    M, N, K = _gemm_shape(A, B, D)
+    _check(lib().nrr_gemm_bf16_tn_async(C.c_void_p(A.data_ptr()),
+                                        C.c_void_p(B.data_ptr()),
+                                        C.c_void_p(D.data_ptr()), M, N, K,
+                                        int(bn), int(splits),
+                                        C.c_void_p(stream.cuda_stream)))
+
+
+def gemm_status(stream=None) -> None:
+    """Wait for the stream and raise if a GEMM pipeline wait expired."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().nrr_gemm_status(C.c_void_p(stream.cuda_stream)))
 
 
 def prolong(coarse: dict, uc, fine: dict, uf, stream=None) -> None:

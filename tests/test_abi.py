@@ -164,3 +164,21 @@ def test_noalloc_binding_checks_tensors_before_the_call(lib):
     for u, n, h, msg in cases:
         with pytest.raises(ValueError, match=msg):
             nrr.residual_noalloc(desc, W.spinning_q4_pair(), u, n, h)
+
+
+@pytest.mark.parametrize("M,N,K,bn,splits", [
+    (128, 128, 512, 32, 1),      # tile width not offered
+    (128, 128, 512, 256, 1),     # 256 does not divide N
+    (128, 192, 512, 128, 0),     # 128 does not divide N
+    (128, 128, 512, 128, 9),     # more splits than k-blocks (8)
+    (128, 128, 512, 128, -1),
+    (100, 128, 512, 0, 0),       # M not a multiple of 128
+    (128, 96, 512, 0, 0),        # N not a multiple of 64
+    (128, 128, 500, 0, 0),       # K not a multiple of 64
+])
+def test_gemm_async_rejects_bad_shapes_and_tiles_on_host(lib, M, N, K, bn, splits):
+    """Shape, tile-width and split checks happen on the host, before any
+    device call (the pointers are never dereferenced)."""
+    p = C.c_void_p(1 << 20)
+    st = lib.nrr_gemm_bf16_tn_async(p, p, p, M, N, K, bn, splits, None)
+    assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()

@@ -44,3 +44,66 @@ def test_gemm_rejects_bad_shapes(gpu):
     with pytest.raises(nrr.NrrError) as e:
         nrr.gemm_bf16_tn(A, B, D)
     assert e.value.status == nrr.ERR_INVALID_ARG
+
+
+def _operands(M, N, K, seed):
+    rng = np.random.default_rng(seed)
+    A = bf16_round(rng.standard_normal((M, K)).astype(np.float32))
+    B = bf16_round(rng.standard_normal((N, K)).astype(np.float32))
+    return A, B
+
+
+@pytest.mark.parametrize("M,N,K,bn,splits", [
+    (256, 512, 16384, 128, 0),    # the input gradient of a 16384-wide layer
+    (256, 512, 16384, 128, 19),
+    (256, 512, 4096, 64, 5),      # k-block ranges of unequal length
+    (128, 256, 512, 256, 1),
+    (256, 16384, 512, 256, 1),
+    (384, 768, 1024, 256, 3),
+    (128, 128, 512, 128, 8),      # one k-block per split
+])
+def test_gemm_tiles_and_splits_match_fp64_product(gpu, M, N, K, bn, splits):
+    A, B = _operands(M, N, K, M + N + K + bn + splits)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=splits)
+    nrr.gemm_status()
+    out = D.cpu().numpy().astype(np.float64)
+    # each split and the final sum add FP32 roundings: still within K eps32
+    bound = K * 6e-8 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T)
+    assert np.all(np.isfinite(out))
+    assert np.all(np.abs(out - ref) <= bound + 1e-30)
+
+
+def test_gemm_split_k_is_deterministic(gpu):
+    """The split partial sums are added in a fixed order: repeated calls give
+    identical bits."""
+    M, N, K = 256, 512, 8192
+    A, B = _operands(M, N, K, 5)
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    outs = []
+    for _ in range(3):
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=128, splits=16)
+        outs.append(D)
+    nrr.gemm_status()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_gemm_async_calls_need_one_status_check(gpu):
+    """Many enqueued products, one read-back of the error flag at the end."""
+    M, N, K = 256, 1024, 512
+    A, B = _operands(M, N, K, 9)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    Ds = [torch.empty((M, N), dtype=torch.float32, device="cuda") for _ in range(8)]
+    for i, D in enumerate(Ds):
+        nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=(64, 128, 256)[i % 3])
+    nrr.gemm_status()
+    bound = K * 6e-8 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T)
+    for D in Ds:
+        assert np.all(np.abs(D.cpu().numpy().astype(np.float64) - ref) <= bound)
