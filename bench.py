@@ -614,23 +614,36 @@ def run_profile_gemm(args):
             bf16 = float(json.load(f)["bf16_tflops"])
     except (OSError, KeyError, ValueError):
         bf16 = 1900.0  # fallback burst figure
-    for (M, N, K) in [(256, 16384, 512), (256, 512, 16384), (16384, 512, 256),
-                      (256, 512, 512), (8192, 16384, 512)]:
+    shapes = [(256, 16384, 512), (256, 512, 16384), (16384, 512, 256),
+              (256, 512, 512), (8192, 16384, 512)]
+    if args.gemm_shape:
+        # one shape, the chosen plan, three plain calls (profiler captures)
+        M, N, K = (int(x) for x in args.gemm_shape.split(","))
         A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
         D = torch.empty((M, N), dtype=torch.float32, device="cuda")
-        combos = [(0, 0)] + [(bn, 1) for bn in (64, 128, 256) if N % bn == 0]
+        for _ in range(3):
+            nrr.gemm_bf16_tn_async(A, B, D)
+        nrr.gemm_status()
+        print(json.dumps({"gemm": [M, N, K], "calls": 3}))
+        return 0
+    for (M, N, K) in shapes:
+        A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        combos = [(0, 0, -1)] + [(bn, 1, 0) for bn in (64, 128, 256) if N % bn == 0]
+        combos += [(bn, 1, 1) for bn in (128, 256) if N % bn == 0]
         if K >= 4096:
-            combos += [(128, sp) for sp in (8, 19, 38)] + [(64, 19)]
-        for bn, sp in combos:
+            combos += [(128, sp, 0) for sp in (8, 19, 38)] + [(64, 19, 0)]
+        for bn, sp, pers in combos:
             for _ in range(3):
-                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp, persistent=pers)
             nrr.gemm_status()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(20):
-                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+                nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp, persistent=pers)
             e1.record()
             e1.synchronize()
             nrr.gemm_status()
@@ -638,7 +651,8 @@ def run_profile_gemm(args):
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, capture_error_mode="thread_local"):
                 for _ in range(20):
-                    nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp)
+                    nrr.gemm_bf16_tn_async(A, B, D, bn=bn, splits=sp,
+                                           persistent=pers)
             graph.replay()
             torch.cuda.synchronize()
             e0.record()
@@ -652,7 +666,8 @@ def run_profile_gemm(args):
             nbytes = 2 * (M * K + N * K) + 4 * M * N
             tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
             gbs = nbytes / (ms * 1e-3) / 1e9
-            print(json.dumps({"gemm": [M, N, K], "bn": bn, "splits": sp, "ms": ms,
+            print(json.dumps({"gemm": [M, N, K], "bn": bn, "splits": sp,
+                              "persistent": pers, "ms": ms,
                               "ms_enqueued": ms_enq,
                               "tflops": tf, "frac_bf16": tf / bf16,
                               "GBps_operands_and_output": gbs,
@@ -977,6 +992,9 @@ def main():
                     help="with --profile-steps: phi planes per thread/block")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run only the surrogate GEMM shapes (captures)")
+    ap.add_argument("--gemm-shape", default="",
+                    help="with --profile-gemm: only M,N,K, three calls of the "
+                         "chosen plan")
     ap.add_argument("--surrogate", action="store_true",
                     help="run the learned warm-start pipeline instead")
     ap.add_argument("--surrogate-train", type=int, default=8192)

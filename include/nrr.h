@@ -525,21 +525,29 @@ nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
                             int N, int K, void *stream);
 
 /* The same product, only enqueued on `stream` (no host synchronisation).
- * bn: output tile width 64, 128 or 256 (must divide N), 0 to choose (256
- * when it divides N and the (N / 256) x (M / 128) tiles fit one per SM,
- * else 128 when it divides N, else 64).  splits: number of equal K ranges
- * computed by separate CTAs into a stream-ordered FP32 workspace
- * (splits x M x N, cudaMallocAsync on `stream`, freed on it after use) and
- * summed by a second kernel in a fixed order, so results are deterministic;
- * 1 = no split, 0 = choose (split only when the output tiles fill fewer
- * than half the SMs and K / 64 >= 32, into about one CTA per SM, at least
- * eight k-blocks each); at most K / 64.  A pipeline wait that expires is only
- * recorded in a device flag: nrr_gemm_status reads it.
+ * persistent: 1 = one CTA per SM walks all output tiles with two tensor-
+ * memory accumulators (a tile's epilogue, stored by TMA, overlaps the next
+ * tile's main loop); 0 = one CTA per output tile; -1 = choose (persistent
+ * when there are more 128 x 128 output tiles than SMs and K is not split).
+ * bn: output tile width 64, 128 or 256 (must divide N), 0 to choose
+ * (persistent: 256 when it divides N, else 128, else 64; K split: 128 when
+ * it divides N, else 64; otherwise the widest that divides N and gives at
+ * least half as many tiles as SMs, else 64).  splits (one CTA per tile
+ * only): number of equal K ranges computed by separate CTAs into a
+ * stream-ordered FP32 workspace (splits x M x N, cudaMallocAsync on
+ * `stream`, freed on it after use) and summed by a second kernel in a fixed
+ * order, so results are deterministic; 1 = no split, 0 = choose (split only
+ * when the 128-wide output tiles fill fewer than half the SMs and
+ * K / 64 >= 32, into about one CTA per SM, at least eight k-blocks each);
+ * at most K / 64.  A
+ * pipeline wait that expires is only recorded in a device flag:
+ * nrr_gemm_status reads it.
  * Errors (host-side, nothing enqueued): NRR_ERR_INVALID_ARG (as
- * nrr_gemm_bf16_tn, or bn / splits outside the ranges above), NRR_ERR_OOM,
- * NRR_ERR_CUDA. */
+ * nrr_gemm_bf16_tn, or bn / splits / persistent outside the ranges above,
+ * or persistent = 1 with splits > 1), NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_gemm_bf16_tn_async(const void *A, const void *B, float *D, int M,
-                                  int N, int K, int bn, int splits, void *stream);
+                                  int N, int K, int bn, int splits, int persistent,
+                                  void *stream);
 
 /* Waits for `stream` and reads the GEMM error flag, which every GEMM of the
  * library (nrr_gemm_*, the surrogate) sets when a pipeline wait expires;

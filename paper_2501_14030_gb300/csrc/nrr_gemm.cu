@@ -267,6 +267,232 @@ __global__ void __launch_bounds__(128, BN == 256 ? 1 : 2)
                  "r"(BN));
 }
 
+// ---- persistent variant (many output tiles, no K split) -------------------
+//
+// One CTA per SM walks the output tiles t = blockIdx.x, + gridDim.x, ...
+// (N-tiles fastest, so the CTAs of a wave share the rows of A and stream all
+// of B through L2).  Roles: warp 0 lane 0 loads operand stages with TMA into
+// a ring that runs across tiles; warp 1 lane 0 issues the MMAs of tile i into
+// accumulator buffer i % 2 of tensor memory (2 x BN columns); warps 2-5 read
+// the other buffer back (tcgen05.ld, warp w owns TMEM lanes 32 (w % 4) ..
+// + 31), write 32 x 32 FP32 boxes into 128-byte-swizzled staging buffers and
+// store them with TMA, so a tile's epilogue overlaps the next tile's main
+// loop.  Barriers: full/empty per ring stage, acc_full (MMA commit) and
+// acc_empty (four epilogue warps) per accumulator buffer.  Every wait is
+// bounded; on expiry the kernel records an error, every role stops, copies
+// in flight are allowed to land and tensor memory is freed.
+constexpr int PST_STAGES = 4;
+constexpr int PST_THREADS = 192;
+template <int BN>
+__host__ __device__ constexpr int pst_smem() {
+  return PST_STAGES * (BM * BK * 2 + BN * BK * 2) + 4 * 2 * 4096 + 1024 + 256;
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src,
+                                             int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_addr(src)), "r"(x), "r"(y)
+      : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(PST_THREADS, 1)
+    gemm_bf16_tn_persistent_kernel(const __grid_constant__ CUtensorMap map_a,
+                                   const __grid_constant__ CUtensorMap map_b,
+                                   const __grid_constant__ CUtensorMap map_d, int M,
+                                   int N, int K, int *err) {
+  constexpr int STAGES = PST_STAGES;
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + STAGES * A_BYTES;
+  uint8_t *sOut = sB + STAGES * B_BYTES;  // 4 warps x 2 buffers x 4 KB
+  uint64_t *full = reinterpret_cast<uint64_t *>(sOut + 4 * 2 * 4096);
+  uint64_t *empty = full + STAGES;
+  uint64_t *acc_full = empty + STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *mma_done = acc_empty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+  int *issued = reinterpret_cast<int *>(tmem_slot + 1);  // k-blocks loaded
+  int *abort_flag = issued + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntn = N / BN, tiles = ntn * (M / BM), nk = K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(mma_done, 1);
+    *issued = 0;
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_addr(tmem_slot)),
+        "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  volatile int *vabort = abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer: k-block g (counted over all of this CTA's tiles) goes
+    // to stage g % STAGES
+    int g = 0;
+    for (int t = blockIdx.x; t < tiles && !*vabort; t += gridDim.x) {
+      const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+      for (int kb = 0; kb < nk && !*vabort; kb++, g++) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, err, 11)) {
+          *vabort = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        tma_load_2d(sA + s * A_BYTES, &map_a, &full[s], kb * BK, m0);
+        tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], kb * BK, n0);
+        *issued = g + 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: tile i of this CTA into accumulator buffer i % 2
+    const uint32_t idesc = mma_idesc<BN>();
+    int g = 0, i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, i++) {
+      const int buf = i & 1;
+      if (i >= 2 && !mbar_wait(&acc_empty[buf], ((i >> 1) - 1) & 1, err, 12)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dtm = tmem + (uint32_t)(buf * BN);
+      for (int kb = 0; kb < nk; kb++, g++) {
+        const int s = g % STAGES;
+        if (*vabort || !mbar_wait(&full[s], (g / STAGES) & 1, err, 13)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t da = sw128_desc(smem_addr(sA + s * A_BYTES));
+        const uint64_t db = sw128_desc(smem_addr(sB + s * B_BYTES));
+#pragma unroll
+        for (int k = 0; k < BK / 16; k++) {
+          const uint64_t off = (uint64_t)(k * 2);
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
+              "l"(da + off), "l"(db + off), "r"(idesc), "r"(acc));
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+            "[%0];" ::"r"(smem_addr(&empty[s]))
+            : "memory");
+      }
+      if (!ok) break;
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+          "[%0];" ::"r"(smem_addr(&acc_full[buf]))
+          : "memory");
+    }
+    if (!ok) *vabort = 1;
+    // every MMA issued so far has completed once this barrier flips
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+        "[%0];" ::"r"(smem_addr(mma_done))
+        : "memory");
+  } else if (warp >= 2) {
+    // Epilogue: TMEM lanes 32 q .. 32 q + 31 are output rows m0 + 32 q + lane
+    const int q = warp & 3;
+    uint8_t *stg0 = sOut + (warp - 2) * 2 * 4096;
+    int nst = 0;  // boxes stored by this warp (staging buffer nst % 2)
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, i++) {
+      const int buf = i & 1;
+      const bool ready = mbar_wait(&acc_full[buf], (i >> 1) & 1, err, 14);
+      if (!__all_sync(0xffffffffu, ready && !*vabort)) {
+        if (lane == 0) *vabort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32, nst++) {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, "
+            "%8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, "
+            "%23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+              "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+              "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + (uint32_t)c));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // the staging buffer written two boxes ago must have been read out
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        uint8_t *stg = stg0 + (nst & 1) * 4096;
+        // row `lane`, 16-byte chunk j at (j ^ (lane & 7)): the 128-byte
+        // swizzle of the output tensor map
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+          *reinterpret_cast<uint4 *>(stg + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+              make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&map_d, stg, n0 + c, m0 + 32 * q);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
+      // this warp has read its lanes of buffer buf
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                      smem_addr(&acc_empty[buf]))
+                                  : "memory");
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // no copy may still be landing in shared memory, and no MMA may still
+    // be writing tensor memory, when the CTA frees them and exits
+    const int n_iss = *issued;
+    for (int g = n_iss - STAGES < 0 ? 0 : n_iss - STAGES; g < n_iss; g++)
+      mbar_wait(&full[g % STAGES], (g / STAGES) & 1, err, 15);
+    mbar_wait(mma_done, 0, err, 16);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * BN));
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                               void *, const cuuint64_t *, const cuuint64_t *,
                               const cuuint32_t *, const cuuint32_t *,
@@ -313,27 +539,47 @@ bool make_map(CUtensorMap *m, const void *base, int rows, int cols,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of a row-major [rows][ld] FP32 matrix (cols used) written in
+// 32 x 32 boxes with 128-byte swizzle (the persistent kernel's output).
+bool make_out_map(CUtensorMap *m, const void *base, int rows, int cols, int ld) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// kind 0: BF16 operand map (box rows x 64); kind 1: FP32 output map (box
+// 32 x 32, row stride `box` elements)
 struct MapKey {
   const void *p;
-  int rows, cols, box;
+  int rows, cols, box, kind;
   bool operator<(const MapKey &o) const {
-    return std::tie(p, rows, cols, box) < std::tie(o.p, o.rows, o.cols, o.box);
+    return std::tie(p, rows, cols, box, kind) <
+           std::tie(o.p, o.rows, o.cols, o.box, o.kind);
   }
 };
 std::mutex g_map_mu;
 std::map<MapKey, CUtensorMap> g_maps;
 
-bool cached_map(CUtensorMap *out, const void *base, int rows, int cols,
-                int box) {
+bool cached_map(CUtensorMap *out, const void *base, int rows, int cols, int box,
+                int kind = 0) {
   std::lock_guard<std::mutex> lock(g_map_mu);
-  MapKey k{base, rows, cols, box};
+  MapKey k{base, rows, cols, box, kind};
   auto it = g_maps.find(k);
   if (it != g_maps.end()) {
     *out = it->second;
     return true;
   }
   CUtensorMap m;
-  if (!make_map(&m, base, rows, cols, box)) return false;
+  if (!(kind == 0 ? make_map(&m, base, rows, cols, box)
+                  : make_out_map(&m, base, rows, cols, box)))
+    return false;
   g_maps[k] = m;
   *out = m;
   return true;
@@ -390,6 +636,24 @@ cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, float *D,
   return cudaGetLastError();
 }
 
+template <int BN>
+cudaError_t launch_gemm_persistent(const CUtensorMap &ma, const CUtensorMap &mb,
+                                   const CUtensorMap &md, int M, int N, int K,
+                                   int ctas, cudaStream_t st) {
+  constexpr int smem = pst_smem<BN>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_persistent_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  gemm_bf16_tn_persistent_kernel<BN><<<ctas, PST_THREADS, smem, st>>>(ma, mb, md, M, N,
+                                                                      K, g_err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int *gemm_error_flag() {
@@ -399,28 +663,48 @@ int *gemm_error_flag() {
   return g_err;
 }
 
-// Tile width and K splits for a shape, each where the caller passed 0
-// (measured on GB300 at the surrogate's shapes):
-// - 256 wide when it divides N and the 128 x 256 tiles fit in one wave of
-//   one CTA per SM (fewer operand bytes per flop, no second wave that would
-//   need the epilogue overlap of two CTAs per SM); else 128 when it divides
-//   N, else 64;
-// - K split when the output tiles fill fewer than half the SMs and K is
-//   long (K / 64 >= 32): about one CTA per SM, at least eight k-blocks per
-//   split, so that the partial-sum traffic and the second kernel stay small
-//   against the main loop.
-void gemm_plan(int M, int N, int K, int *bn, int *splits) {
+// Kernel, tile width and K splits for a shape, each where the caller passed
+// 0 (persistent: -1), as measured on GB300 at the surrogate's shapes:
+// - more 128 x 128 output tiles than SMs and no K split: the persistent
+//   kernel (the epilogue of one tile overlaps the next tile's main loop),
+//   256 wide when that divides N, else 128 (else 64);
+// - few output tiles and a long K (K / 64 >= 32): 128 wide (64 if it does
+//   not divide N) and K split into about one CTA per SM, at least eight
+//   k-blocks per split, so that the partial-sum traffic and the second
+//   kernel stay small against the main loop;
+// - otherwise one CTA per tile, the widest tile (256, 128, 64) that divides
+//   N and still gives at least half as many CTAs as SMs (else 64): wide
+//   tiles read fewer operand bytes per flop, narrow ones put more SMs on a
+//   small product.
+void gemm_plan(int M, int N, int K, int *bn, int *splits, int *persistent) {
   const int sms = device_sms();
+  const int nk = K / BK;
+  auto tiles = [&](int w) { return (int64_t)(N / w) * (M / BM); };
+  const int64_t tiles128 = N >= 128 ? tiles(128) : tiles(64);
+  if (*persistent < 0)
+    *persistent = (*splits <= 1 && tiles128 > sms) ? 1 : 0;
+  if (*persistent) {
+    *splits = 1;
+    if (*bn == 0) *bn = N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : 64;
+    return;
+  }
+  const bool split_k = *splits != 1 && 2 * tiles128 <= sms && nk >= 32;
   if (*bn == 0) {
-    if (N % 256 == 0 && (int64_t)(N / 256) * (M / BM) <= sms)
-      *bn = 256;
-    else
-      *bn = (N % 128 == 0) ? 128 : 64;
+    if (split_k) {
+      *bn = N % 128 == 0 ? 128 : 64;
+    } else {
+      *bn = 64;
+      for (int w : {256, 128}) {
+        if (N % w == 0 && 2 * tiles(w) >= sms) {
+          *bn = w;
+          break;
+        }
+      }
+    }
   }
   if (*splits != 0) return;
-  const int tiles = (N / *bn) * (M / BM), nk = K / BK;
   int sp = 1;
-  if (2 * tiles <= sms && nk >= 32) sp = std::max(1, std::min(nk / 8, sms / tiles));
+  if (split_k) sp = std::max(1, std::min(nk / 8, (int)(sms / tiles(*bn))));
   *splits = sp;
 }
 
@@ -430,7 +714,8 @@ size_t gemm_workspace_bytes(int M, int N, int splits) {
 
 nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
                         int K, int ldd, cudaStream_t st, char *msg, int msglen,
-                        int bn, int splits, float *ws, size_t ws_bytes) {
+                        int bn, int splits, float *ws, size_t ws_bytes,
+                        int persistent) {
   if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || M % BM || K % BK ||
       (N % 64) || ldd < N || (ldd % 4) ||
       (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
@@ -442,22 +727,42 @@ nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
     return NRR_ERR_INVALID_ARG;
   }
   if ((bn != 0 && bn != 64 && bn != 128 && bn != 256) || (bn != 0 && N % bn) ||
-      splits < 0 || splits > K / BK || splits > 65535) {
+      splits < 0 || splits > K / BK || splits > 65535 || persistent < -1 ||
+      persistent > 1 || (persistent == 1 && splits > 1)) {
     snprintf(msg, msglen,
              "gemm: tile width must be 0 (chosen), 64, 128 or 256 and divide N; "
-             "splits 0 (chosen) .. K/64 (bn=%d splits=%d N=%d K=%d)",
-             bn, splits, N, K);
+             "splits 0 (chosen) .. K/64; persistent -1 (chosen), 0 or 1, and not "
+             "with splits > 1 (bn=%d splits=%d persistent=%d N=%d K=%d)",
+             bn, splits, persistent, N, K);
     return NRR_ERR_INVALID_ARG;
   }
   if (!gemm_error_flag()) {
     snprintf(msg, msglen, "gemm: error flag allocation failed");
     return NRR_ERR_OOM;
   }
-  gemm_plan(M, N, K, &bn, &splits);
+  gemm_plan(M, N, K, &bn, &splits, &persistent);
   CUtensorMap ma, mb;
   if (!cached_map(&ma, A, M, K, BM) || !cached_map(&mb, B, N, K, bn)) {
     snprintf(msg, msglen, "gemm: tensor map encoding failed");
     return NRR_ERR_CUDA;
+  }
+  if (persistent) {
+    CUtensorMap md;
+    if (!cached_map(&md, D, M, N, ldd, 1)) {
+      snprintf(msg, msglen, "gemm: output tensor map encoding failed");
+      return NRR_ERR_CUDA;
+    }
+    const int tiles = (N / bn) * (M / BM);
+    const int ctas = std::min(tiles, device_sms());
+    cudaError_t e =
+        bn == 256 ? launch_gemm_persistent<256>(ma, mb, md, M, N, K, ctas, st)
+        : bn == 128 ? launch_gemm_persistent<128>(ma, mb, md, M, N, K, ctas, st)
+                    : launch_gemm_persistent<64>(ma, mb, md, M, N, K, ctas, st);
+    if (e != cudaSuccess) {
+      snprintf(msg, msglen, "gemm launch: %s", cudaGetErrorString(e));
+      return NRR_ERR_CUDA;
+    }
+    return NRR_OK;
   }
   const size_t need = gemm_workspace_bytes(M, N, splits);
   bool own = false;
@@ -514,10 +819,11 @@ nrr_status gemm_check_error(cudaStream_t st, char *msg, int msglen) {
 extern "C" {
 
 nrr_status nrr_gemm_bf16_tn_async(const void *A, const void *B, float *D, int M,
-                                  int N, int K, int bn, int splits, void *stream) {
+                                  int N, int K, int bn, int splits, int persistent,
+                                  void *stream) {
   char msg[256] = {0};
   nrr_status s = nrr::gemm_bf16_tn(A, B, D, M, N, K, N, static_cast<cudaStream_t>(stream),
-                                   msg, sizeof msg, bn, splits, nullptr, 0);
+                                   msg, sizeof msg, bn, splits, nullptr, 0, persistent);
   if (s != NRR_OK) nrr::set_last_error(msg);
   return s;
 }
@@ -531,7 +837,7 @@ nrr_status nrr_gemm_status(void *stream) {
 
 nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
                             int K, void *stream) {
-  nrr_status s = nrr_gemm_bf16_tn_async(A, B, D, M, N, K, 0, 0, stream);
+  nrr_status s = nrr_gemm_bf16_tn_async(A, B, D, M, N, K, 0, 0, -1, stream);
   return s != NRR_OK ? s : nrr_gemm_status(stream);
 }
 

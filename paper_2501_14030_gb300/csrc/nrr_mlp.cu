@@ -28,9 +28,10 @@
 namespace nrr {
 nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
                         int K, int ldd, cudaStream_t st, char *msg, int msglen,
-                        int bn, int splits, float *ws, size_t ws_bytes);
+                        int bn, int splits, float *ws, size_t ws_bytes,
+                        int persistent);
 nrr_status gemm_check_error(cudaStream_t st, char *msg, int msglen);
-void gemm_plan(int M, int N, int K, int *bn, int *splits);
+void gemm_plan(int M, int N, int K, int *bn, int *splits, int *persistent);
 size_t gemm_workspace_bytes(int M, int N, int splits);
 }  // namespace nrr
 
@@ -346,7 +347,7 @@ nrr_status gemm(nrr_surrogate *s, const void *A, const void *B, float *D, int M,
                 int N, int K) {
   char msg[256];
   nrr_status st = gemm_bf16_tn(A, B, D, M, N, K, N, s->stream, msg, sizeof msg, 0, 0,
-                               s->ws, s->ws_bytes);
+                               s->ws, s->ws_bytes, -1);
   if (st != NRR_OK) set_last_error(msg);
   return st;
 }
@@ -563,8 +564,8 @@ nrr_status nrr_surrogate_create(int n_in, int hidden, int depth, int n_out,
                                 {s->dout[l], s->din[l], batch},
                                 {batch, s->din[l], s->dout[l]}};
       for (const auto &sh : shapes) {
-        int bn = 0, sp = 0;
-        gemm_plan(sh[0], sh[1], sh[2], &bn, &sp);
+        int bn = 0, sp = 0, pers = -1;
+        gemm_plan(sh[0], sh[1], sh[2], &bn, &sp, &pers);
         s->ws_bytes = std::max(s->ws_bytes, gemm_workspace_bytes(sh[0], sh[1], sp));
       }
     }

@@ -143,7 +143,7 @@ def lib() -> C.CDLL:
                                C.POINTER(C.c_int)],
         "nrr_batch_set_launch": [V, I, I, I],
         "nrr_gemm_bf16_tn": [V, V, V, I, I, I, V],
-        "nrr_gemm_bf16_tn_async": [V, V, V, I, I, I, I, I, V],
+        "nrr_gemm_bf16_tn_async": [V, V, V, I, I, I, I, I, I, V],
         "nrr_gemm_status": [V],
         "nrr_surrogate_create": [I, I, I, I, I, C.POINTER(C.c_float), V,
                                  C.POINTER(V)],
@@ -321,9 +321,9 @@ def gemm_bf16_tn(A, B, D, stream=None) -> None:
                                   C.c_void_p(stream.cuda_stream)))
 
 
-def gemm_bf16_tn_async(A, B, D, bn=0, splits=0, stream=None) -> None:
-    """The same product only enqueued; bn / splits 0 = chosen from the shape.
-    Check with gemm_status()."""
+def gemm_bf16_tn_async(A, B, D, bn=0, splits=0, persistent=-1, stream=None) -> None:
+    """The same product only enqueued; bn / splits 0 and persistent -1 =
+    chosen from the shape.  Check with gemm_status()."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -331,7 +331,7 @@ def gemm_bf16_tn_async(A, B, D, bn=0, splits=0, stream=None) -> None:
     _check(lib().nrr_gemm_bf16_tn_async(C.c_void_p(A.data_ptr()),
                                         C.c_void_p(B.data_ptr()),
                                         C.c_void_p(D.data_ptr()), M, N, K,
-                                        int(bn), int(splits),
+                                        int(bn), int(splits), int(persistent),
                                         C.c_void_p(stream.cuda_stream)))
 
 

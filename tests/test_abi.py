@@ -180,5 +180,13 @@ def test_gemm_async_rejects_bad_shapes_and_tiles_on_host(lib, M, N, K, bn, split
     """Shape, tile-width and split checks happen on the host, before any
     device call (the pointers are never dereferenced)."""
     p = C.c_void_p(1 << 20)
-    st = lib.nrr_gemm_bf16_tn_async(p, p, p, M, N, K, bn, splits, None)
+    st = lib.nrr_gemm_bf16_tn_async(p, p, p, M, N, K, bn, splits, -1, None)
+    assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()
+
+
+@pytest.mark.parametrize("persistent,splits", [(2, 1), (-2, 1), (1, 4)])
+def test_gemm_async_rejects_bad_kernel_choice_on_host(lib, persistent, splits):
+    p = C.c_void_p(1 << 20)
+    st = lib.nrr_gemm_bf16_tn_async(p, p, p, 256, 256, 4096, 128, splits,
+                                    persistent, None)
     assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()

@@ -68,7 +68,7 @@ def test_gemm_tiles_and_splits_match_fp64_product(gpu, M, N, K, bn, splits):
     Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
     Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
     D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
-    nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=splits)
+    nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=splits, persistent=0)
     nrr.gemm_status()
     out = D.cpu().numpy().astype(np.float64)
     # each split and the final sum add FP32 roundings: still within K eps32
@@ -107,3 +107,40 @@ def test_gemm_async_calls_need_one_status_check(gpu):
     bound = K * 6e-8 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T)
     for D in Ds:
         assert np.all(np.abs(D.cpu().numpy().astype(np.float64) - ref) <= bound)
+
+
+@pytest.mark.parametrize("M,N,K,bn", [
+    (2048, 4096, 512, 256),   # 256 tiles: some CTAs take two
+    (4096, 4096, 256, 256),   # 512 tiles: both accumulators reused
+    (4096, 2048, 512, 128),
+    (1024, 1024, 1024, 64),   # fewer tiles than SMs: one each
+    (384, 192, 320, 64),
+])
+def test_persistent_gemm_matches_fp64_product(gpu, M, N, K, bn):
+    A, B = _operands(M, N, K, M + 3 * N + K + bn)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=1, persistent=1)
+    nrr.gemm_status()
+    out = D.cpu().numpy().astype(np.float64)
+    bound = K * 6e-8 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T)
+    assert np.all(np.isfinite(out))
+    assert np.all(np.abs(out - ref) <= bound + 1e-30)
+
+
+@pytest.mark.parametrize("bn", [128, 256])
+def test_persistent_gemm_equals_one_cta_per_tile_bitwise(gpu, bn):
+    """Both kernels issue the same MMAs over K in the same order into an FP32
+    accumulator: identical bits, whatever the tile-to-CTA assignment."""
+    M, N, K = 2048, 2048, 512
+    A, B = _operands(M, N, K, 77 + bn)
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    D1 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    D2 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    nrr.gemm_bf16_tn_async(Ad, Bd, D1, bn=bn, splits=1, persistent=1)
+    nrr.gemm_bf16_tn_async(Ad, Bd, D2, bn=bn, splits=1, persistent=0)
+    nrr.gemm_status()
+    assert torch.equal(D1, D2)
