@@ -659,6 +659,22 @@ nrr_status nrr_selftest_wait_expiry(int which, void *stream, int *expired);
 nrr_status nrr_selftest_recip(const void *s, void *out, int64_t n, int fp32,
                               void *stream);
 
+/* Address checks of the debug build (no paper counterpart; a stand-in for
+ * a memory checker where none can run).  libnrr_debug.so, built with
+ * NRR_DEBUG=1, checks every load and store of the stencil, boundary and
+ * residual kernels against the device allocations the library owns (grids,
+ * batches, patch systems, surrogates): an access outside all of them is
+ * skipped (a load reads zero, a store is dropped) and recorded, and nothing
+ * traps.  This call waits for the device, then reports *enabled = 1 for the
+ * debug build (0 for the release build, whose kernels check nothing),
+ * *first_bad = the first refused device address since the previous call
+ * (0: none) and *refused = how many accesses were refused since then, and
+ * clears the record.  Outputs host, nullable.  Errors: NRR_ERR_STATE if more
+ * allocations were alive at once than the check's table holds (the check
+ * was then incomplete), NRR_ERR_CUDA. */
+nrr_status nrr_debug_check(int *enabled, unsigned long long *first_bad,
+                           unsigned long long *refused);
+
 /* Measurement hook for the rooflines (the paper's Sec. 5 roofline uses the
  * vendor's peaks; here they are measured): kernels of this library, timed
  * with CUDA events on `stream` (best of five), report

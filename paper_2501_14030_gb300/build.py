@@ -16,6 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrr.so")
+# The NRR_DEBUG build (address checks in the stencil kernels' loads and
+# stores) goes to its own folder and library name.
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libnrr_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
@@ -42,37 +46,43 @@ def _deps() -> list[str]:
     return out
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra: list[str], out_dir: str, defs: list[str]) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
     newest_dep = max(os.path.getmtime(p) for p in _deps() + [src])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defs, *extra, "-c", src, "-o", obj]
     subprocess.run(cmd, check=True)
     return obj
 
 
-def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    """Compile every CUDA source and link ``_build/libnrr.so``."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose_ptxas: bool = False, force: bool = False,
+          debug: bool = False) -> str:
+    """Compile every CUDA source and link ``_build/libnrr.so`` (with
+    debug=True: ``_build_debug/libnrr_debug.so``, compiled with
+    -DNRR_DEBUG=1)."""
+    out_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    defs = ["-DNRR_DEBUG=1"] if debug else []
+    os.makedirs(out_dir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     if force:
-        for f in os.listdir(BUILD):
+        for f in os.listdir(out_dir):
             if f.endswith(".o"):
-                os.remove(os.path.join(BUILD, f))
+                os.remove(os.path.join(out_dir, f))
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if (not os.path.exists(LIB) or force or extra
-            or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(LIB)):
-        tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, out_dir, defs), srcs))
+    if (not os.path.exists(lib) or force or extra
+            or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(lib)):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static",
                "-lrt", "-lpthread", "-ldl"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(verbose_ptxas="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose_ptxas="-v" in sys.argv, force="-f" in sys.argv,
+                debug="--debug" in sys.argv))

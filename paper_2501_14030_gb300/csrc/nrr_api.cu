@@ -22,9 +22,80 @@
 #include <vector>
 
 #include "../../include/nrr.h"
+#include "nrr_debug.cuh"
 #include "nrr_internal.h"
 
 using namespace nrr;
+
+// ---- NRR_DEBUG address registry (no-ops in the release build) --------------
+namespace nrr {
+namespace dbgreg {
+struct DbgRegistry {
+  std::mutex mu;
+  std::vector<std::pair<uintptr_t, uintptr_t>> ranges;
+  std::vector<std::pair<DbgSync, DbgRead>> units;
+  bool overflow = false;
+};
+DbgRegistry &dbg_registry() {
+  static DbgRegistry r;
+  return r;
+}
+#if NRR_DEBUG
+// Copies the range list into every translation unit's device table; the
+// device is idle first, so that no kernel reads a half-written table.
+void dbg_publish(DbgRegistry &r) {
+  DbgTable t{};
+  t.n = (int)std::min<size_t>(r.ranges.size(), kDbgRanges);
+  for (int i = 0; i < t.n; i++) {
+    t.lo[i] = r.ranges[i].first;
+    t.hi[i] = r.ranges[i].second;
+  }
+  cudaDeviceSynchronize();
+  for (auto &u : r.units) u.first(t);
+}
+#endif
+}  // namespace dbgreg
+using dbgreg::DbgRegistry;
+using dbgreg::dbg_registry;
+
+void dbg_add_unit(DbgSync sync, DbgRead read) {
+  DbgRegistry &r = dbg_registry();
+  std::lock_guard<std::mutex> lock(r.mu);
+  r.units.emplace_back(sync, read);
+}
+
+void dbg_register(const void *p, size_t bytes) {
+#if NRR_DEBUG
+  // NaN poison (all bits set is a NaN in FP32 and FP64): a kernel that reads
+  // memory the library never wrote then produces NaN instead of plausible
+  // numbers
+  cudaMemset(const_cast<void *>(p), 0xFF, bytes);
+  DbgRegistry &r = dbg_registry();
+  std::lock_guard<std::mutex> lock(r.mu);
+  if (r.ranges.size() >= (size_t)kDbgRanges) r.overflow = true;
+  r.ranges.emplace_back((uintptr_t)p, (uintptr_t)p + bytes);
+  dbgreg::dbg_publish(r);
+#else
+  (void)p;
+  (void)bytes;
+#endif
+}
+
+void dbg_unregister(const void *p) {
+#if NRR_DEBUG
+  DbgRegistry &r = dbg_registry();
+  std::lock_guard<std::mutex> lock(r.mu);
+  for (size_t i = 0; i < r.ranges.size(); i++)
+    if (r.ranges[i].first == (uintptr_t)p) {
+      r.ranges.erase(r.ranges.begin() + (long)i);
+      break;
+    }
+  dbgreg::dbg_publish(r);
+#else
+  (void)p;
+#endif
+}
+}  // namespace nrr
 
 namespace {
 
@@ -250,6 +321,7 @@ nrr_status dev_alloc(nrr_grid *g, T **p, size_t count) {
     return fail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
                 cudaGetErrorString(e));
   g->allocs.push_back(ptr);
+  dbg_register(ptr, count * sizeof(T));
   *p = static_cast<T *>(ptr);
   return NRR_OK;
 }
@@ -845,7 +917,32 @@ extern "C" {
 
 const char *nrr_last_error(void) { return g_last_error.c_str(); }
 int64_t nrr_kernel_launches(void) { return g_launches.load(); }
-const char *nrr_version(void) { return "nrr 0.1 (sm_103a)"; }
+const char *nrr_version(void) {
+  return NRR_DEBUG ? "nrr 0.1 (sm_103a, NRR_DEBUG address checks)" : "nrr 0.1 (sm_103a)";
+}
+
+nrr_status nrr_debug_check(int *enabled, unsigned long long *first_bad,
+                           unsigned long long *refused) {
+  unsigned long long bad = 0, cnt = 0;
+  bool overflow = false;
+  if (NRR_DEBUG) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+      return fail(NRR_ERR_CUDA, "cudaDeviceSynchronize: %s", cudaGetErrorString(e));
+    DbgRegistry &r = dbg_registry();
+    std::lock_guard<std::mutex> lock(r.mu);
+    for (auto &u : r.units) u.second(&bad, &cnt);
+    overflow = r.overflow;
+    r.overflow = false;
+  }
+  if (enabled) *enabled = NRR_DEBUG ? 1 : 0;
+  if (first_bad) *first_bad = bad;
+  if (refused) *refused = cnt;
+  if (overflow)
+    return fail(NRR_ERR_STATE, "more than %d allocations were alive: the address "
+                "check missed some", kDbgRanges);
+  return NRR_OK;
+}
 
 nrr_status nrr_default_opts(nrr_relax_opts *o) {
   if (!o) return fail(NRR_ERR_INVALID_ARG, "null opts");
@@ -1024,7 +1121,10 @@ nrr_status nrr_destroy_grid(nrr_grid *g) {
   cudaSetDevice(g->device);
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
-  for (void *p : g->allocs) cudaFree(p);
+  for (void *p : g->allocs) {
+    dbg_unregister(p);
+    cudaFree(p);
+  }
   if (g->host_pinned) cudaFreeHost(g->host_pinned);
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   if (g->order_ev) cudaEventDestroy(g->order_ev);

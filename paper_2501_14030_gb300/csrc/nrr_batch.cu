@@ -443,6 +443,7 @@ nrr_status balloc(nrr_batch *b, T **p, size_t count) {
     return bfail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
                  cudaGetErrorString(e));
   b->allocs.push_back(ptr);
+  dbg_register(ptr, std::max<size_t>(count, 1) * sizeof(T));
   *p = static_cast<T *>(ptr);
   return NRR_OK;
 }
@@ -940,7 +941,10 @@ nrr_status nrr_batch_destroy(nrr_batch *b) {
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  for (void *p : b->allocs) cudaFree(p);
+  for (void *p : b->allocs) {
+    dbg_unregister(p);
+    cudaFree(p);
+  }
   if (b->order_ev) cudaEventDestroy(b->order_ev);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/nrr.h"
+#include "nrr_debug.cuh"
 #include "nrr_internal.h"
 
 namespace nrr {
@@ -332,6 +333,7 @@ nrr_status malloc_s(nrr_surrogate *s, T **p, size_t count) {
     return mfail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
                  cudaGetErrorString(e));
   s->allocs.push_back(ptr);
+  dbg_register(ptr, std::max<size_t>(count, 1) * sizeof(T));
   *p = static_cast<T *>(ptr);
   return NRR_OK;
 }
@@ -606,7 +608,10 @@ nrr_status nrr_surrogate_destroy(nrr_surrogate *s) {
   if (!s) return NRR_OK;
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (void *p : s->allocs) cudaFree(p);
+  for (void *p : s->allocs) {
+    dbg_unregister(p);
+    cudaFree(p);
+  }
   if (s->order_ev) cudaEventDestroy(s->order_ev);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128)
       double w;
       double H = residual_point<NG>(g, pz, fw, u, i0, i1, i2, &w, r_int);
       if (h_out) h_out[nrr::flat(g, i0, i1, i2)] = H;
-      num += H * H * w;
+      num = fma(H * H, w, num);
       den += w;
     }
   }

@@ -260,6 +260,7 @@ nrr_status palloc(nrr_patchset *ps, T **p, size_t count) {
     return pfail(NRR_ERR_OOM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
                  cudaGetErrorString(e));
   ps->allocs.push_back(ptr);
+  dbg_register(ptr, count * sizeof(T) + 16);
   *p = static_cast<T *>(ptr);
   return NRR_OK;
 }
@@ -423,7 +424,10 @@ nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole, in
 nrr_status nrr_patchset_destroy(nrr_patchset *ps) {
   if (!ps) return NRR_OK;
   cudaSetDevice(ps->device);
-  for (void *p : ps->allocs) cudaFree(p);
+  for (void *p : ps->allocs) {
+    dbg_unregister(p);
+    cudaFree(p);
+  }
   if (ps->host) cudaFreeHost(ps->host);
   delete ps;
   return NRR_OK;

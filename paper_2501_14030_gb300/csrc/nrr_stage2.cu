@@ -198,8 +198,8 @@ __global__ void __launch_bounds__(NT2, 1)
       // tile of a row, the shell columns)
       const int bx = aj0 - c0, by = aj1 - c1;
       if (bx >= 0 && bx < BW && by >= 0 && by < TY2 && (bx < TX2 || last_x)) {
-        const float accu = PAIR == 0 ? yb0 : a.au[p];
-        const float accv = PAIR == 0 ? yb1 : a.av[p];
+        const float accu = PAIR == 0 ? yb0 : ld(a.au + p);
+        const float accv = PAIR == 0 ? yb1 : ld(a.av + p);
         float *ACz = AC + z * TY2 * BW + by * BW + bx;
         ACz[0] = fmaf(a.wbA, ku, accu);
         ACz[nz * TY2 * BW] = fmaf(a.wbA, kv, accv);
@@ -272,14 +272,14 @@ __global__ void __launch_bounds__(NT2, 1)
     const float acu = ACz[0], acv = ACz[nz * TY2 * BW];
     if (PAIR == 0) {
       // stage 2 (MID): accumulator and its output t
-      a.au[p] = fmaf(a.wbB, ku, acu);
-      a.av[p] = fmaf(a.wbB, kv, acv);
-      a.ou[p] = fmaf(a.waB, ku, ld(a.yu + p));
-      a.ov[p] = fmaf(a.waB, kv, ld(a.yv + p));
+      st(a.au + p, fmaf(a.wbB, ku, acu));
+      st(a.av + p, fmaf(a.wbB, kv, acv));
+      st(a.ou + p, fmaf(a.waB, ku, ld(a.yu + p)));
+      st(a.ov + p, fmaf(a.waB, kv, ld(a.yv + p)));
     } else {
       // stage 4 (LAST): the new state
-      a.ou[p] = fmaf(a.wbB, ku, acu);
-      a.ov[p] = fmaf(a.wbB, kv, acv);
+      st(a.ou + p, fmaf(a.wbB, ku, acu));
+      st(a.ov + p, fmaf(a.wbB, kv, acv));
     }
   }
 }

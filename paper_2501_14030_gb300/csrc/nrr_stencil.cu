@@ -103,25 +103,27 @@ __device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ 
   R x[3], r2 = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    x[d] = R(g.xxmin[d] + (ii[d] - NG + 0.5) * g.dxx[d]);
+    x[d] = R(fma((double)(ii[d] - NG) + 0.5, g.dxx[d], g.xxmin[d]));
     r2 = fma(x[d], x[d], r2);
   }
   R rinv = R(1) / sqrt(r2);
   R f0 = ld(f + p);
   R dr = R(0);
+  // every operation explicit (fma, or rounded on its own), so that the
+  // result does not depend on the compiler's contraction choices
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     R D;
     R inv2 = R(0.5 / g.dxx[d]);
     if (ii[d] >= nn[d] + NG)
-      D = (R(3) * f0 - R(4) * ld(f + p - st[d]) + ld(f + p - 2 * st[d])) * inv2;
+      D = mul_rn(fma(R(3), f0, fma(R(-4), ld(f + p - st[d]), ld(f + p - 2 * st[d]))), inv2);
     else if (ii[d] < NG)
-      D = -(R(3) * f0 - R(4) * ld(f + p + st[d]) + ld(f + p + 2 * st[d])) * inv2;
+      D = -mul_rn(fma(R(3), f0, fma(R(-4), ld(f + p + st[d]), ld(f + p + 2 * st[d]))), inv2);
     else
-      D = (ld(f + p + st[d]) - ld(f + p - st[d])) * inv2;
-    dr = fma(x[d] * rinv, D, dr);
+      D = mul_rn(sub_rn(ld(f + p + st[d]), ld(f + p - st[d])), inv2);
+    dr = fma(mul_rn(x[d], rinv), D, dr);
   }
-  return -(dr + f0 * rinv);
+  return -fma(f0, rinv, dr);
 }
 
 // Cartesian operator weights in the working precision, converted once per
@@ -175,8 +177,8 @@ __global__ void __launch_bounds__(256)
       if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
     } else {
       const R c = R(a.cart.speed);
-      ku = c * cart_radiation<R, NG>(g, a.su, i0, i1, i2, p);
-      kv = c * cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p);
+      ku = mul_rn(c, cart_radiation<R, NG>(g, a.su, i0, i1, i2, p));
+      kv = mul_rn(c, cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p));
       if (linear_mode<R>(a.lin)) {
         ku += ld(a.fu + p);
         kv += ld(a.bc2 + p);
@@ -241,24 +243,24 @@ __device__ __forceinline__ void cart_shell_point(const Geo &g, const StageArgs<R
   R dru = R(0), drv = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    const R nx = x[d] * rinv, inv2 = sc.inv2[d];
+    const R nx = mul_rn(x[d], rinv), inv2 = sc.inv2[d];
     R Du, Dv;
     if (ii[d] >= nn[d] + NG) {
-      Du = (R(3) * u0 - R(4) * ld(a.su + p - st[d]) + ld(a.su + p - 2 * st[d])) * inv2;
-      Dv = (R(3) * v0 - R(4) * ld(a.sv + p - st[d]) + ld(a.sv + p - 2 * st[d])) * inv2;
+      Du = mul_rn(fma(R(3), u0, fma(R(-4), ld(a.su + p - st[d]), ld(a.su + p - 2 * st[d]))), inv2);
+      Dv = mul_rn(fma(R(3), v0, fma(R(-4), ld(a.sv + p - st[d]), ld(a.sv + p - 2 * st[d]))), inv2);
     } else if (ii[d] < NG) {
-      Du = -(R(3) * u0 - R(4) * ld(a.su + p + st[d]) + ld(a.su + p + 2 * st[d])) * inv2;
-      Dv = -(R(3) * v0 - R(4) * ld(a.sv + p + st[d]) + ld(a.sv + p + 2 * st[d])) * inv2;
+      Du = -mul_rn(fma(R(3), u0, fma(R(-4), ld(a.su + p + st[d]), ld(a.su + p + 2 * st[d]))), inv2);
+      Dv = -mul_rn(fma(R(3), v0, fma(R(-4), ld(a.sv + p + st[d]), ld(a.sv + p + 2 * st[d]))), inv2);
     } else {
-      Du = (ld(a.su + p + st[d]) - ld(a.su + p - st[d])) * inv2;
-      Dv = (ld(a.sv + p + st[d]) - ld(a.sv + p - st[d])) * inv2;
+      Du = mul_rn(sub_rn(ld(a.su + p + st[d]), ld(a.su + p - st[d])), inv2);
+      Dv = mul_rn(sub_rn(ld(a.sv + p + st[d]), ld(a.sv + p - st[d])), inv2);
     }
     dru = fma(nx, Du, dru);
     drv = fma(nx, Dv, drv);
   }
   const R c = R(a.cart.speed);
-  ku = -c * (dru + u0 * rinv);
-  kv = -c * (drv + v0 * rinv);
+  ku = mul_rn(-c, fma(u0, rinv, dru));
+  kv = mul_rn(-c, fma(v0, rinv, drv));
   if (linear_mode<R>(a.lin)) {
     ku += ld(a.fu + p);
     kv += ld(a.bc2 + p);
@@ -409,21 +411,21 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
         R ku = fma(-a.eta, u0, v0);
         if (use_fu) ku += S.op[OP_FU][j][ty][tx];
         if (KIND == STAGE_FIRST) {
-          a.au[p] = fma(a.wb, ku, u0);
-          a.av[p] = fma(a.wb, kv, v0);
-          a.ou[p] = fma(a.wa, ku, u0);
-          a.ov[p] = fma(a.wa, kv, v0);
+          st(a.au + p, fma(a.wb, ku, u0));
+          st(a.av + p, fma(a.wb, kv, v0));
+          st(a.ou + p, fma(a.wa, ku, u0));
+          st(a.ov + p, fma(a.wa, kv, v0));
         } else if (KIND == STAGE_MID) {
-          a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-          a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
-          a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
-          a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
+          st(a.au + p, fma(a.wb, ku, S.op[OP_AU][j][ty][tx]));
+          st(a.av + p, fma(a.wb, kv, S.op[OP_AV][j][ty][tx]));
+          st(a.ou + p, fma(a.wa, ku, S.op[OP_BU][j][ty][tx]));
+          st(a.ov + p, fma(a.wa, kv, S.op[OP_BV][j][ty][tx]));
         } else if (KIND == STAGE_LAST) {
-          a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-          a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+          st(a.ou + p, fma(a.wb, ku, S.op[OP_AU][j][ty][tx]));
+          st(a.ov + p, fma(a.wb, kv, S.op[OP_AV][j][ty][tx]));
         } else {
-          a.ou[p] = ku;
-          a.ov[p] = kv;
+          st(a.ou + p, ku);
+          st(a.ov + p, kv);
         }
       }
     }
@@ -652,7 +654,7 @@ __global__ void __launch_bounds__(128)
       if (h_out) h_out[p] = H;
       double x2 = g.xxmin[2] + (i2 - NG + 0.5) * g.dxx[2];
       double wt = sqrt(x0 * x0 + x1 * x1 + x2 * x2) < r_int ? 1.0 : 0.0;
-      num += H * H * wt;
+      num = fma(H * H, wt, num);
       den += wt;
     }
   }
@@ -690,7 +692,7 @@ __global__ void fill_ghosts_kernel(Geo g, R *f) {
   if (evolved) return;
   int j0 = i0, j1 = i1, j2 = i2;
   image_of(g, j0, j1, j2);
-  f[p] = f[flat(g, j0, j1, j2)];
+  dev::st(f + p, dev::ld(f + flat(g, j0, j1, j2)));
 }
 
 // Defect correction, set-up of one outer iteration at the FP64 state (u, v)

@@ -7,16 +7,31 @@
 #include <cuda_runtime.h>
 
 #include "nrr_async.cuh"
+#include "nrr_debug.cuh"
 #include "nrr_internal.h"
 
 namespace nrr {
 namespace dev {
+
+// In the NRR_DEBUG build every helper below first checks the address against
+// the library's registered allocations (nrr_debug.cuh) and skips the access
+// if it lies outside them; in the release build the check is absent.
+#if NRR_DEBUG
+#define NRR_DBG_LOAD(p) \
+  if (!dbg_ok((p), sizeof(*(p)))) return decltype(+*(p))(0)
+#define NRR_DBG_STORE(p) \
+  if (!dbg_ok((p), sizeof(*(p)))) return
+#else
+#define NRR_DBG_LOAD(p) (void)0
+#define NRR_DBG_STORE(p) (void)0
+#endif
 
 // Solve-constant data (folded stencil weights, boundary factors): the
 // read-only path.  These are the only arrays a stage kernel reads before
 // pdl_wait().
 template <typename R>
 __device__ __forceinline__ R ldc(const R *p) {
+  NRR_DBG_LOAD(p);
   return __ldg(p);
 }
 
@@ -29,7 +44,15 @@ __device__ __forceinline__ R ldc(const R *p) {
 // behind the wait's memory clobber.
 template <typename R>
 __device__ __forceinline__ R ld(const R *p) {
+  NRR_DBG_LOAD(p);
   return *p;
+}
+
+// Stores of the stage and residual kernels to global memory.
+template <typename R>
+__device__ __forceinline__ void st(R *p, R v) {
+  NRR_DBG_STORE(p);
+  *p = v;
 }
 
 // Loads of state written earlier in the same launch (the multi-stage kernel
@@ -37,11 +60,22 @@ __device__ __forceinline__ R ld(const R *p) {
 // else with plain loads (ld above).
 template <bool COH, typename R>
 __device__ __forceinline__ R lds(const R *p) {
-  if constexpr (COH)
+  if constexpr (COH) {
+    NRR_DBG_LOAD(p);
     return __ldcg(p);
-  else
+  } else {
     return ld(p);
+  }
 }
+
+// A product or sum rounded on its own: the compiler may not fuse it with a
+// neighbouring operation into an FMA, so that the result does not depend on
+// how the surrounding code was optimised (the debug build must agree with
+// the release build bit for bit).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 // Programmatic dependent launch: a stage kernel launched with the
 // programmatic-serialisation attribute may start while the preceding kernel
@@ -199,22 +233,22 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<R> &a, int64_t p,
                                                R ku, R kv) {
   if (KIND == STAGE_FIRST) {
     R yu = lds<COH>(a.bu + p), yv = lds<COH>(a.bv + p);
-    a.au[p] = fma(a.wb, ku, yu);
-    a.av[p] = fma(a.wb, kv, yv);
-    a.ou[p] = fma(a.wa, ku, yu);
-    a.ov[p] = fma(a.wa, kv, yv);
+    st(a.au + p, fma(a.wb, ku, yu));
+    st(a.av + p, fma(a.wb, kv, yv));
+    st(a.ou + p, fma(a.wa, ku, yu));
+    st(a.ov + p, fma(a.wa, kv, yv));
   } else if (KIND == STAGE_MID) {
     R yu = lds<COH>(a.bu + p), yv = lds<COH>(a.bv + p);
-    a.au[p] = fma(a.wb, ku, a.au[p]);
-    a.av[p] = fma(a.wb, kv, a.av[p]);
-    a.ou[p] = fma(a.wa, ku, yu);
-    a.ov[p] = fma(a.wa, kv, yv);
+    st(a.au + p, fma(a.wb, ku, ld(a.au + p)));
+    st(a.av + p, fma(a.wb, kv, ld(a.av + p)));
+    st(a.ou + p, fma(a.wa, ku, yu));
+    st(a.ov + p, fma(a.wa, kv, yv));
   } else if (KIND == STAGE_LAST) {
-    a.ou[p] = fma(a.wb, ku, a.au[p]);
-    a.ov[p] = fma(a.wb, kv, a.av[p]);
+    st(a.ou + p, fma(a.wb, ku, ld(a.au + p)));
+    st(a.ov + p, fma(a.wb, kv, ld(a.av + p)));
   } else {
-    a.ou[p] = ku;
-    a.ov[p] = kv;
+    st(a.ou + p, ku);
+    st(a.ov + p, kv);
   }
 }
 
@@ -273,7 +307,7 @@ __device__ __forceinline__ void stage_cyl_shell(const Geo &g, const StageArgs<R>
         d1 = -fma(R(3), f0, fma(R(-4), ld(q + p + s0), ld(q + p + 2 * s0)));
       else
         d1 = ld(q + p + s0) - ld(q + p - s0);
-      k2[f] = -c * fma(kr, d0, fma(kz, d1, rinv * f0));
+      k2[f] = mul_rn(-c, fma(kr, d0, fma(kz, d1, mul_rn(rinv, f0))));
     }
     if (linear_mode<R>(a.lin)) {
       k2[0] += ld(a.fu + p);
@@ -315,8 +349,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
         v2 = lds<COH>(a.sv + p - 2);
       R du = fma(R(3), u0, fma(R(-4), u1, u2));
       R dv = fma(R(3), v0, fma(R(-4), v1, v2));
-      R ku = -c * fma(kdb, du, rinv * u0);
-      R kv = -c * fma(kdb, dv, rinv * v0);
+      R ku = mul_rn(-c, fma(kdb, du, mul_rn(rinv, u0)));
+      R kv = mul_rn(-c, fma(kdb, dv, mul_rn(rinv, v0)));
       if (linear_mode<R>(a.lin)) {
         ku += ld(a.fu + p);
         kv += ld(a.bc2 + p);
@@ -351,8 +385,8 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
       yb[1][j] = lds<COH>(a.bv + p);
     }
     if (KIND == STAGE_MID || KIND == STAGE_LAST) {
-      ac[0][j] = a.au[p];
-      ac[1][j] = a.av[p];
+      ac[0][j] = ld(a.au + p);
+      ac[1][j] = ld(a.av + p);
     }
     fu[j] = linear_mode<R>(a.lin) ? ld(a.fu + p) : R(0);
   }
@@ -365,21 +399,21 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
     R ku = fma(-a.eta, u0[j], v0[j]);
     if (linear_mode<R>(a.lin)) ku += fu[j];
     if (KIND == STAGE_FIRST) {
-      a.au[p] = fma(a.wb, ku, yb[0][j]);
-      a.av[p] = fma(a.wb, kv[j], yb[1][j]);
-      a.ou[p] = fma(a.wa, ku, yb[0][j]);
-      a.ov[p] = fma(a.wa, kv[j], yb[1][j]);
+      st(a.au + p, fma(a.wb, ku, yb[0][j]));
+      st(a.av + p, fma(a.wb, kv[j], yb[1][j]));
+      st(a.ou + p, fma(a.wa, ku, yb[0][j]));
+      st(a.ov + p, fma(a.wa, kv[j], yb[1][j]));
     } else if (KIND == STAGE_MID) {
-      a.au[p] = fma(a.wb, ku, ac[0][j]);
-      a.av[p] = fma(a.wb, kv[j], ac[1][j]);
-      a.ou[p] = fma(a.wa, ku, yb[0][j]);
-      a.ov[p] = fma(a.wa, kv[j], yb[1][j]);
+      st(a.au + p, fma(a.wb, ku, ac[0][j]));
+      st(a.av + p, fma(a.wb, kv[j], ac[1][j]));
+      st(a.ou + p, fma(a.wa, ku, yb[0][j]));
+      st(a.ov + p, fma(a.wa, kv[j], yb[1][j]));
     } else if (KIND == STAGE_LAST) {
-      a.ou[p] = fma(a.wb, ku, ac[0][j]);
-      a.ov[p] = fma(a.wb, kv[j], ac[1][j]);
+      st(a.ou + p, fma(a.wb, ku, ac[0][j]));
+      st(a.ov + p, fma(a.wb, kv[j], ac[1][j]));
     } else {
-      a.ou[p] = ku;
-      a.ov[p] = kv[j];
+      st(a.ou + p, ku);
+      st(a.ov + p, kv[j]);
     }
   }
 }
@@ -437,7 +471,7 @@ __device__ __forceinline__ void residual_curvi_item(
                                          op, lin);
     double H = (double)(op[0] * c2inv);
     if (h_out) h_out[p] = H;
-    num += H * H * wt;
+    num = fma(H * H, wt, num);
     den += wt;
   }
 }
@@ -483,8 +517,8 @@ __device__ __forceinline__ void stage_shell_rows(const Geo &g, const StageArgs<R
     const int64_t p = col + (int64_t)nc * i2;
     R u0 = lds<COH>(a.su + p), u1 = lds<COH>(a.su + p - 1), u2 = lds<COH>(a.su + p - 2);
     R v0 = lds<COH>(a.sv + p), v1 = lds<COH>(a.sv + p - 1), v2 = lds<COH>(a.sv + p - 2);
-    R ku = -c * fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), rinv * u0);
-    R kv = -c * fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), rinv * v0);
+    R ku = mul_rn(-c, fma(kdb, fma(R(3), u0, fma(R(-4), u1, u2)), mul_rn(rinv, u0)));
+    R kv = mul_rn(-c, fma(kdb, fma(R(3), v0, fma(R(-4), v1, v2)), mul_rn(rinv, v0)));
     if (linear_mode<R>(a.lin)) {
       ku += ld(a.fu + p);
       kv += ld(a.bc2 + p);
@@ -583,8 +617,8 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
         nyb1 = ld(a.bv + p_);                                                    \
       }                                                                          \
       if (KIND == STAGE_MID || KIND == STAGE_LAST) {                             \
-        nac0 = a.au[p_];                                                         \
-        nac1 = a.av[p_];                                                         \
+        nac0 = ld(a.au + p_);                                                         \
+        nac1 = ld(a.av + p_);                                                         \
       }                                                                          \
       if (linear_mode<R>(a.lin)) nfu = ld(a.fu + p_);                            \
       nq = ld(a.su + col + (int64_t)nc * wrap_plane<NG>(g, pl_ + NG));           \
@@ -627,21 +661,21 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
       R ku = fma(-a.eta, u0, v0);
       if (linear_mode<R>(a.lin)) ku += fu;
       if (KIND == STAGE_FIRST) {
-        a.au[p] = fma(a.wb, ku, yb0);
-        a.av[p] = fma(a.wb, kv, yb1);
-        a.ou[p] = fma(a.wa, ku, yb0);
-        a.ov[p] = fma(a.wa, kv, yb1);
+        st(a.au + p, fma(a.wb, ku, yb0));
+        st(a.av + p, fma(a.wb, kv, yb1));
+        st(a.ou + p, fma(a.wa, ku, yb0));
+        st(a.ov + p, fma(a.wa, kv, yb1));
       } else if (KIND == STAGE_MID) {
-        a.au[p] = fma(a.wb, ku, ac0);
-        a.av[p] = fma(a.wb, kv, ac1);
-        a.ou[p] = fma(a.wa, ku, yb0);
-        a.ov[p] = fma(a.wa, kv, yb1);
+        st(a.au + p, fma(a.wb, ku, ac0));
+        st(a.av + p, fma(a.wb, kv, ac1));
+        st(a.ou + p, fma(a.wa, ku, yb0));
+        st(a.ov + p, fma(a.wa, kv, yb1));
       } else if (KIND == STAGE_LAST) {
-        a.ou[p] = fma(a.wb, ku, ac0);
-        a.ov[p] = fma(a.wb, kv, ac1);
+        st(a.ou + p, fma(a.wb, ku, ac0));
+        st(a.ov + p, fma(a.wb, kv, ac1));
       } else {
-        a.ou[p] = ku;
-        a.ov[p] = kv;
+        st(a.ou + p, ku);
+        st(a.ov + p, kv);
       }
     }
   }
@@ -947,21 +981,21 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
         R ku = fma(-a.eta, u0, v0);
         if (use_fu) ku += S.op[OP_FU][j][ty][tx];
         if (KIND == STAGE_FIRST) {
-          a.au[p] = fma(a.wb, ku, u0);
-          a.av[p] = fma(a.wb, kv, v0);
-          a.ou[p] = fma(a.wa, ku, u0);
-          a.ov[p] = fma(a.wa, kv, v0);
+          st(a.au + p, fma(a.wb, ku, u0));
+          st(a.av + p, fma(a.wb, kv, v0));
+          st(a.ou + p, fma(a.wa, ku, u0));
+          st(a.ov + p, fma(a.wa, kv, v0));
         } else if (KIND == STAGE_MID) {
-          a.au[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-          a.av[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
-          a.ou[p] = fma(a.wa, ku, S.op[OP_BU][j][ty][tx]);
-          a.ov[p] = fma(a.wa, kv, S.op[OP_BV][j][ty][tx]);
+          st(a.au + p, fma(a.wb, ku, S.op[OP_AU][j][ty][tx]));
+          st(a.av + p, fma(a.wb, kv, S.op[OP_AV][j][ty][tx]));
+          st(a.ou + p, fma(a.wa, ku, S.op[OP_BU][j][ty][tx]));
+          st(a.ov + p, fma(a.wa, kv, S.op[OP_BV][j][ty][tx]));
         } else if (KIND == STAGE_LAST) {
-          a.ou[p] = fma(a.wb, ku, S.op[OP_AU][j][ty][tx]);
-          a.ov[p] = fma(a.wb, kv, S.op[OP_AV][j][ty][tx]);
+          st(a.ou + p, fma(a.wb, ku, S.op[OP_AU][j][ty][tx]));
+          st(a.ov + p, fma(a.wb, kv, S.op[OP_AV][j][ty][tx]));
         } else {
-          a.ou[p] = ku;
-          a.ov[p] = kv;
+          st(a.ou + p, ku);
+          st(a.ov + p, kv);
         }
       }
     }

@@ -16,7 +16,11 @@ import numpy as np
 from . import workloads
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libnrr.so")
+# NRR_DEBUG=1 in the environment selects the address-checking debug build
+# (build.build(debug=True) makes it).
+DEBUG = os.environ.get("NRR_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG else "_build",
+                        "libnrr_debug.so" if DEBUG else "libnrr.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA = 0, 1, 2, 3
 ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE = 4, 5, 6, 7
@@ -42,6 +46,7 @@ EXPORTS = ("nrr_default_opts", "nrr_create_grid", "nrr_destroy_grid",
            "nrr_surrogate_get_params", "nrr_batch_set_u",
            "nrr_batch_get_interior", "nrr_prolong", "nrr_last_error",
            "nrr_version", "nrr_selftest_recip", "nrr_probe_peaks",
+           "nrr_debug_check",
            "nrr_set_device_loop", "nrr_set_speed_reference",
            "nrr_patchset_create", "nrr_patchset_destroy", "nrr_patchset_info",
            "nrr_patchset_timestep", "nrr_patchset_step",
@@ -92,8 +97,8 @@ def lib() -> C.CDLL:
         return _lib
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(
-            "libnrr.so is missing (%s): build it with __graft_entry__.build()"
-            % LIB_PATH)
+            "%s is missing: build it with __graft_entry__.build()%s"
+            % (LIB_PATH, " and build.build(debug=True)" if DEBUG else ""))
     L = C.CDLL(LIB_PATH)
     V, D, I = C.c_void_p, C.POINTER(C.c_double), C.c_int
     sig = {
@@ -161,6 +166,8 @@ def lib() -> C.CDLL:
                                  V, C.c_double, V, V, V],
         "nrr_selftest_recip": [V, V, C.c_int64, I, V],
         "nrr_probe_peaks": [C.c_int64, V, D, D, D],
+        "nrr_debug_check": [C.POINTER(C.c_int), C.POINTER(C.c_ulonglong),
+                            C.POINTER(C.c_ulonglong)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -333,6 +340,17 @@ def gemm_bf16_tn_async(A, B, D, bn=0, splits=0, persistent=-1, stream=None) -> N
                                         C.c_void_p(D.data_ptr()), M, N, K,
                                         int(bn), int(splits), int(persistent),
                                         C.c_void_p(stream.cuda_stream)))
+
+
+def debug_check() -> dict:
+    """Address-check record of the debug build since the previous call:
+    {"enabled", "first_bad", "refused"} (enabled False for the release
+    build)."""
+    en = C.c_int(0)
+    bad = C.c_ulonglong(0)
+    cnt = C.c_ulonglong(0)
+    _check(lib().nrr_debug_check(C.byref(en), C.byref(bad), C.byref(cnt)))
+    return {"enabled": bool(en.value), "first_bad": bad.value, "refused": cnt.value}
 
 
 def gemm_status(stream=None) -> None:

@@ -190,3 +190,15 @@ def test_gemm_async_rejects_bad_kernel_choice_on_host(lib, persistent, splits):
     st = lib.nrr_gemm_bf16_tn_async(p, p, p, 256, 256, 4096, 128, splits,
                                     persistent, None)
     assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()
+
+
+def test_release_build_reports_no_address_checks(lib):
+    """nrr_debug_check on the release build: checks disabled, nothing
+    recorded, no device call needed."""
+    en = C.c_int(-1)
+    bad = C.c_ulonglong(7)
+    cnt = C.c_ulonglong(7)
+    assert lib.nrr_debug_check(C.byref(en), C.byref(bad), C.byref(cnt)) == nrr.OK
+    assert (en.value, bad.value, cnt.value) == (0, 0, 0)
+    assert lib.nrr_debug_check(None, None, None) == nrr.OK
+    assert b"NRR_DEBUG" not in lib.nrr_version()
