@@ -378,7 +378,11 @@ typedef struct nrr_patchset nrr_patchset;
  * Errors: NRR_ERR_INVALID_ARG (null or equal grids, an inner grid that is not
  * Cartesian, q, hole <= 0, a receiver whose stencil leaves the donor, a donor
  * point that is a receiver of the other link -- a hole too large for the
- * box), NRR_ERR_STATE (punctures not set), NRR_ERR_OOM, NRR_ERR_CUDA. */
+ * box, a grid of 2^31 points or more), NRR_ERR_STATE (punctures not set),
+ * NRR_ERR_OOM, NRR_ERR_CUDA.  nrr_patchset_relax replays each full chunk of
+ * check_every steps (both patches' stages, the inner patch's on a side
+ * stream, the links, the norm) as one CUDA graph, captured on first use and
+ * again when dt, eta, r_int or a grid's launch shape changes. */
 nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole,
                                int q, nrr_patchset **out);
 nrr_status nrr_patchset_destroy(nrr_patchset *ps);

@@ -174,30 +174,53 @@ nrr_status build_link(const Geo &rg, const Geo &dg, const std::vector<int64_t> &
 }
 
 // One link on the device.
+// Device form of a link: donor index and weight k of receiver r at
+// [k * n + r] (stencil-point-major, so that the threads of a warp read
+// consecutive entries), donor indices 32-bit (patches of fewer than 2^31
+// points).
 struct DevLink {
   int64_t n = 0;
-  int64_t *recv = nullptr, *donor = nullptr;
+  int64_t *recv = nullptr;
+  int32_t *donor = nullptr;
   double *w = nullptr;
 };
 
 // Receivers of the stage output (du, dv) from the donor's output (su, sv):
-// one thread per receiver, the q^3 products summed in a fixed order.
+// one thread per receiver, the q^3 products summed in a fixed order (k = 0
+// .. M-1).  M = q^3 is a template parameter for the usual q, so the loop
+// unrolls and a thread's loads are all in flight at once; M = 0 reads m
+// at run time.
+template <int M>
 __global__ void link_apply_kernel(int64_t n, int m, const int64_t *__restrict__ recv,
-                                  const int64_t *__restrict__ donor,
+                                  const int32_t *__restrict__ donor,
                                   const double *__restrict__ w, const double *su,
                                   const double *sv, double *du, double *dv) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   double a = 0.0, b = 0.0;
-  for (int k = 0; k < m; k++) {
-    const int64_t i = r * m + k;
+  const int mm = M > 0 ? M : m;
+#pragma unroll
+  for (int k = 0; k < mm; k++) {
+    const int64_t i = (int64_t)k * n + r;
     const double wk = w[i];
-    const int64_t d = donor[i];
+    const int32_t d = donor[i];
     a = fma(wk, su[d], a);
     b = fma(wk, sv[d], b);
   }
   du[recv[r]] = a;
   dv[recv[r]] = b;
+}
+
+void launch_link(const DevLink &l, int q, const double *su, const double *sv, double *du,
+                 double *dv, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((l.n + 127) / 128);
+  const int m = q * q * q;
+  switch (q) {
+    case 2: link_apply_kernel<8><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
+    case 4: link_apply_kernel<64><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
+    case 6: link_apply_kernel<216><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
+    default: link_apply_kernel<0><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
+  }
 }
 
 // Partial sums (H^2 J, J) of one patch over its interior points that are
@@ -237,8 +260,22 @@ constexpr int kNormBlocks = 512;  // per patch
 
 }  // namespace
 
+// One relaxation chunk (m RK4 steps of both patches with their links, then
+// the residual norm) captured as a CUDA graph, with what it was captured for.
+struct PatchChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t m = 0;
+  double dt = 0.0, eta = 0.0, r_int = 0.0;
+  LaunchCfg cfg[2];
+};
+
 struct nrr_patchset {
   nrr_grid *grid[2] = {nullptr, nullptr};  // outer, inner
+  PatchChunkGraph chunk;
+  // the inner patch's stage kernels run on `side`, concurrently with the
+  // outer patch's on the outer grid's stream; fork / join order them
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   DevLink link[2];                          // receivers of grid[i]
   unsigned char *mask[2] = {nullptr, nullptr};
   double *partials = nullptr;               // 2 * kNormBlocks pairs
@@ -266,25 +303,35 @@ nrr_status palloc(nrr_patchset *ps, T **p, size_t count) {
 }
 
 // Every RK4 stage on both patches, then the links; `steps` steps on the
-// outer grid's work stream.
+// outer grid's work stream.  The two patches' stage kernels of one stage
+// are independent (each reads and writes only its own patch), so the inner
+// patch's runs on a side stream that forks from the outer grid's stream
+// before the stage and joins it before the links, which read both.  (Stage
+// kernels launched this way go without programmatic dependent launch: the
+// node before each is an event, not the previous stage.)
 void launch_patch_steps(nrr_patchset *ps, double dt, double eta, int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
   GridView v[2] = {grid_view(ps->grid[0]), grid_view(ps->grid[1])};
   cudaStream_t st = v[0].stream;
-  const int m = ps->q * ps->q * ps->q;
+  const cudaStream_t on[2] = {st, ps->side};
+  LaunchCfg cfg[2] = {v[0].cfg64, v[1].cfg64};
+  cfg[0].pdl = cfg[1].pdl = 0;
   for (int64_t s = 0; s < steps; s++)
     for (int k = 0; k < 4; k++) {
       StageArgs<double> a[2];
+      cudaEventRecord(ps->fork, st);
+      cudaStreamWaitEvent(ps->side, ps->fork, 0);
       for (int i = 0; i < 2; i++) {
         a[i] = rk4_stage_args<double>(v[i].f64, v[i].c64, v[i].cart, v[i].err, k, dt, eta);
-        launch_stage<double>(v[i].geo, kinds[k], a[i], v[i].cfg64, st);
+        launch_stage<double>(v[i].geo, kinds[k], a[i], cfg[i], on[i]);
       }
+      cudaEventRecord(ps->join, ps->side);
+      cudaStreamWaitEvent(st, ps->join, 0);
       for (int i = 0; i < 2; i++) {
         const DevLink &l = ps->link[i];
         if (l.n == 0) continue;
         const int j = 1 - i;  // donor
-        link_apply_kernel<<<(unsigned)((l.n + 127) / 128), 128, 0, st>>>(
-            l.n, m, l.recv, l.donor, l.w, a[j].ou, a[j].ov, a[i].ou, a[i].ov);
+        launch_link(l, ps->q, a[j].ou, a[j].ov, a[i].ou, a[i].ov, st);
       }
     }
 }
@@ -311,6 +358,48 @@ nrr_status read_norm(nrr_patchset *ps, double *out) {
   PCUDA(cudaMemcpyAsync(ps->host, ps->norm, sizeof(double), cudaMemcpyDeviceToHost, st));
   PCUDA(cudaStreamSynchronize(st));
   *out = ps->host[0];
+  return NRR_OK;
+}
+
+bool same_cfg(const LaunchCfg &a, const LaunchCfg &b) {
+  return a.block == b.block && a.zc == b.zc && a.variant == b.variant && a.pdl == b.pdl;
+}
+
+// The graph of one chunk for (m, dt, eta, r_int) and the grids' current
+// launch shapes: the cached one, or a new capture of the same launches the
+// host loop issues.  One graph launch then replaces 16 m + 5 launches.
+nrr_status chunk_graph(nrr_patchset *ps, int64_t m, double dt, double eta,
+                       double r_int, cudaGraphExec_t *out) {
+  const GridView v0 = grid_view(ps->grid[0]), v1 = grid_view(ps->grid[1]);
+  PatchChunkGraph &c = ps->chunk;
+  if (c.exec && c.m == m && c.dt == dt && c.eta == eta && c.r_int == r_int &&
+      same_cfg(c.cfg[0], v0.cfg64) && same_cfg(c.cfg[1], v1.cfg64)) {
+    *out = c.exec;
+    return NRR_OK;
+  }
+  if (c.exec) {
+    cudaGraphExecDestroy(c.exec);
+    c.exec = nullptr;
+  }
+  cudaStream_t st = v0.stream;
+  cudaGraph_t graph = nullptr;
+  PCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  launch_patch_steps(ps, dt, eta, m);
+  launch_patch_norm(ps, r_int);
+  PCUDA(cudaStreamEndCapture(st, &graph));
+  const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c.exec = nullptr;
+    return pfail(NRR_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  c.m = m;
+  c.dt = dt;
+  c.eta = eta;
+  c.r_int = r_int;
+  c.cfg[0] = v0.cfg64;
+  c.cfg[1] = v1.cfg64;
+  *out = c.exec;
   return NRR_OK;
 }
 
@@ -342,6 +431,8 @@ nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole, in
     return pfail(NRR_ERR_STATE, "punctures must be set on both patches");
   if (q / 2 > vo.geo.ng || q / 2 > vi.geo.ng)
     return pfail(NRR_ERR_INVALID_ARG, "q/2 exceeds a patch's ghost width");
+  if (vo.geo.npts >= (int64_t)1 << 31 || vi.geo.npts >= (int64_t)1 << 31)
+    return pfail(NRR_ERR_INVALID_ARG, "patches must have fewer than 2^31 points");
   // the inner box's receivers: all its ghost points
   std::vector<int64_t> recv_in, recv_out;
   const Geo &gi = vi.geo, &go = vo.geo;
@@ -402,15 +493,25 @@ nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole, in
       if (e != NRR_OK) return e;
       PCUDA(cudaMemcpy(l.recv, hl[i].recv.data(), l.n * sizeof(int64_t),
                        cudaMemcpyHostToDevice));
-      PCUDA(cudaMemcpy(l.donor, hl[i].donor.data(), nm * sizeof(int64_t),
-                       cudaMemcpyHostToDevice));
-      PCUDA(cudaMemcpy(l.w, hl[i].w.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+      // stencil-point-major on the device (k * n + r)
+      std::vector<int32_t> dT(nm);
+      std::vector<double> wT(nm);
+      for (int64_t r = 0; r < l.n; r++)
+        for (int k = 0; k < m; k++) {
+          dT[(size_t)k * l.n + r] = (int32_t)hl[i].donor[(size_t)r * m + k];
+          wT[(size_t)k * l.n + r] = hl[i].w[(size_t)r * m + k];
+        }
+      PCUDA(cudaMemcpy(l.donor, dT.data(), nm * sizeof(int32_t), cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.w, wT.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
       PCUDA(cudaMemcpy(ps->mask[i], mk[i].data(), mk[i].size(), cudaMemcpyHostToDevice));
     }
     e = palloc(ps, &ps->partials, 4 * (size_t)kNormBlocks);
     if (e == NRR_OK) e = palloc(ps, &ps->norm, 4);
     if (e != NRR_OK) return e;
     PCUDA(cudaMallocHost(&ps->host, 4 * sizeof(double)));
+    PCUDA(cudaStreamCreateWithFlags(&ps->side, cudaStreamNonBlocking));
+    PCUDA(cudaEventCreateWithFlags(&ps->fork, cudaEventDisableTiming));
+    PCUDA(cudaEventCreateWithFlags(&ps->join, cudaEventDisableTiming));
     return NRR_OK;
   }();
   if (st != NRR_OK) {
@@ -429,6 +530,10 @@ nrr_status nrr_patchset_destroy(nrr_patchset *ps) {
     cudaFree(p);
   }
   if (ps->host) cudaFreeHost(ps->host);
+  if (ps->chunk.exec) cudaGraphExecDestroy(ps->chunk.exec);
+  if (ps->fork) cudaEventDestroy(ps->fork);
+  if (ps->join) cudaEventDestroy(ps->join);
+  if (ps->side) cudaStreamDestroy(ps->side);
   delete ps;
   return NRR_OK;
 }
@@ -521,8 +626,15 @@ nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
       break;
     }
     const int64_t m = std::min<int64_t>(o->check_every, o->max_iters - it);
-    launch_patch_steps(ps, dt, eta, m);
-    launch_patch_norm(ps, o->r_int);
+    if (m == o->check_every) {
+      cudaGraphExec_t exec = nullptr;
+      s = chunk_graph(ps, m, dt, eta, o->r_int, &exec);
+      if (s != NRR_OK) return s;
+      PCUDA(cudaGraphLaunch(exec, st));
+    } else {  // a last, shorter chunk: launched one kernel at a time
+      launch_patch_steps(ps, dt, eta, m);
+      launch_patch_norm(ps, o->r_int);
+    }
     s = read_norm(ps, &nrm);
     if (s != NRR_OK) return s;
     it += m;
