@@ -130,8 +130,9 @@ void lagrange(int q, int base, double f, double *w) {
 }
 
 struct HostLink {
-  std::vector<int64_t> recv, donor;
-  std::vector<double> w;
+  std::vector<int64_t> recv, donor;  // donor[r q^3 + k], k = a + q (b + q c)
+  std::vector<double> w;             // w[r q^3 + k] = wxy[a + q b] wz[c]
+  std::vector<double> wxy, wz;       // per receiver: q^2 and q factors
 };
 
 // Receivers (flat indices in `rg`) with their donor stencils in `dg`.
@@ -141,6 +142,8 @@ nrr_status build_link(const Geo &rg, const Geo &dg, const std::vector<int64_t> &
   out->recv = recv;
   out->donor.resize(recv.size() * (size_t)m);
   out->w.resize(recv.size() * (size_t)m);
+  out->wxy.resize(recv.size() * (size_t)q * q);
+  out->wz.resize(recv.size() * (size_t)q);
   const int sd[3] = {dg.s0, dg.s1, dg.s2};
   for (size_t r = 0; r < recv.size(); r++) {
     const int64_t p = recv[r];
@@ -160,6 +163,9 @@ nrr_status build_link(const Geo &rg, const Geo &dg, const std::vector<int64_t> &
                      x[0], x[1], x[2]);
       lagrange(q, base[d], f, wd[d]);
     }
+    for (int b = 0; b < q; b++)
+      for (int a = 0; a < q; a++) out->wxy[r * q * q + a + q * b] = wd[0][a] * wd[1][b];
+    for (int c = 0; c < q; c++) out->wz[r * q + c] = wd[2][c];
     int k = 0;
     for (int c = 0; c < q; c++)
       for (int b = 0; b < q; b++)
@@ -167,60 +173,140 @@ nrr_status build_link(const Geo &rg, const Geo &dg, const std::vector<int64_t> &
           int j0 = base[0] + a, j1 = base[1] + b, j2 = base[2] + c;
           if (dg.coord != CARTESIAN) image_of(dg, j0, j1, j2);
           out->donor[r * m + k] = flat(dg, j0, j1, j2);
-          out->w[r * m + k] = wd[0][a] * wd[1][b] * wd[2][c];
+          // the same product as the kernel forms: (wx wy) wz
+          out->w[r * m + k] = out->wxy[r * q * q + a + q * b] * wd[2][c];
         }
   }
   return NRR_OK;
 }
 
 // One link on the device.
-// Device form of a link: donor index and weight k of receiver r at
-// [k * n + r] (stencil-point-major, so that the threads of a warp read
-// consecutive entries), donor indices 32-bit (patches of fewer than 2^31
-// points).
+// Device form of a link, stencil-point-major ([j * n + r] for entry j of
+// receiver r, so that the threads of a warp read consecutive entries), in
+// the tensor-product structure of the stencil: the donor of stencil point
+// (a, b, c) is column col[a + q b] (32-bit; patches of fewer than 2^31
+// points) on plane planes[c] -- or planes[q + c], the plane at phi + pi, where
+// bit a + q b of flip is set (columns whose image lies across the axis or
+// the origin) -- and its weight is wxy[a + q b] wz[c].
 struct DevLink {
   int64_t n = 0;
+  int64_t ncol = 0;  // donor grid's points per plane
   int64_t *recv = nullptr;
-  int32_t *donor = nullptr;
-  double *w = nullptr;
+  int32_t *col = nullptr;
+  unsigned long long *flip = nullptr;
+  int32_t *planes = nullptr;
+  double *wxy = nullptr, *wz = nullptr;
 };
 
 // Receivers of the stage output (du, dv) from the donor's output (su, sv):
-// one thread per receiver, the q^3 products summed in a fixed order (k = 0
-// .. M-1).  M = q^3 is a template parameter for the usual q, so the loop
-// unrolls and a thread's loads are all in flight at once; M = 0 reads m
-// at run time.
-template <int M>
-__global__ void link_apply_kernel(int64_t n, int m, const int64_t *__restrict__ recv,
-                                  const int32_t *__restrict__ donor,
-                                  const double *__restrict__ w, const double *su,
-                                  const double *sv, double *du, double *dv) {
+// one thread per receiver.  Each plane c of the stencil has its own
+// accumulator (q independent FMA chains per field: the FP64 pipe needs them,
+// since a small link gives few warps per SM), the q^2 products of a plane
+// summed in order (b outer, then a), the planes' sums then added in order c
+// = 0 .. q-1.
+template <int Q>
+__global__ void __launch_bounds__(128)
+    link_apply_kernel(int64_t n, int64_t ncol, const int64_t *__restrict__ recv,
+                      const int32_t *__restrict__ col,
+                      const unsigned long long *__restrict__ flip,
+                      const int32_t *__restrict__ planes,
+                      const double *__restrict__ wxy, const double *__restrict__ wz,
+                      const double *su, const double *sv, double *du, double *dv) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
-  double a = 0.0, b = 0.0;
-  const int mm = M > 0 ? M : m;
+  int32_t cl[Q * Q];
+  double wab[Q * Q];
 #pragma unroll
-  for (int k = 0; k < mm; k++) {
-    const int64_t i = (int64_t)k * n + r;
-    const double wk = w[i];
-    const int32_t d = donor[i];
-    a = fma(wk, su[d], a);
-    b = fma(wk, sv[d], b);
+  for (int ab = 0; ab < Q * Q; ab++) {
+    cl[ab] = col[(int64_t)ab * n + r];
+    wab[ab] = wxy[(int64_t)ab * n + r];
   }
-  du[recv[r]] = a;
-  dv[recv[r]] = b;
+  const unsigned long long fm = flip[r];
+  double a[Q], b[Q];
+#pragma unroll
+  for (int c = 0; c < Q; c++) {
+    const double wc = wz[(int64_t)c * n + r];
+    const int64_t o0 = ncol * planes[(int64_t)c * n + r];
+    const int64_t o1 = ncol * planes[(int64_t)(Q + c) * n + r];
+    a[c] = 0.0;
+    b[c] = 0.0;
+#pragma unroll
+    for (int ab = 0; ab < Q * Q; ab++) {
+      const double w = wab[ab] * wc;
+      const int64_t d = cl[ab] + (((fm >> ab) & 1ull) ? o1 : o0);
+      a[c] = fma(w, su[d], a[c]);
+      b[c] = fma(w, sv[d], b[c]);
+    }
+  }
+  double sa = a[0], sb = b[0];
+#pragma unroll
+  for (int c = 1; c < Q; c++) {
+    sa += a[c];
+    sb += b[c];
+  }
+  du[recv[r]] = sa;
+  dv[recv[r]] = sb;
 }
 
 void launch_link(const DevLink &l, int q, const double *su, const double *sv, double *du,
                  double *dv, cudaStream_t st) {
   const unsigned blocks = (unsigned)((l.n + 127) / 128);
-  const int m = q * q * q;
+#define NRR_LINK(Q)                                                                    \
+  link_apply_kernel<Q><<<blocks, 128, 0, st>>>(l.n, l.ncol, l.recv, l.col, l.flip,    \
+                                               l.planes, l.wxy, l.wz, su, sv, du, dv)
   switch (q) {
-    case 2: link_apply_kernel<8><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
-    case 4: link_apply_kernel<64><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
-    case 6: link_apply_kernel<216><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
-    default: link_apply_kernel<0><<<blocks, 128, 0, st>>>(l.n, m, l.recv, l.donor, l.w, su, sv, du, dv); break;
+    case 2: NRR_LINK(2); break;
+    case 6: NRR_LINK(6); break;
+    default: NRR_LINK(4); break;
   }
+#undef NRR_LINK
+}
+
+// The device form of host link `h` whose donor grid is `dg`: columns,
+// flip bits and planes read off the donor list (and checked against it
+// entry by entry), arrays transposed to stencil-point-major order.
+bool compress_link(const HostLink &h, const Geo &dg, int q, std::vector<int32_t> &col,
+                   std::vector<unsigned long long> &flip, std::vector<int32_t> &planes,
+                   std::vector<double> &wxy, std::vector<double> &wz) {
+  const int64_t n = (int64_t)h.recv.size(), nc = dg.ncol;
+  const int q2 = q * q, m = q2 * q;
+  col.assign((size_t)q2 * n, 0);
+  flip.assign((size_t)n, 0ull);
+  planes.assign((size_t)2 * q * n, 0);
+  wxy.assign((size_t)q2 * n, 0.0);
+  wz.assign((size_t)q * n, 0.0);
+  for (int64_t r = 0; r < n; r++) {
+    const int64_t *d = &h.donor[(size_t)r * m];
+    // planes of column (0, 0) and their phi + pi partners; a flip bit says
+    // that a column sits on the partner planes (its image lies across the
+    // axis or the origin while column (0, 0)'s does not, or the reverse)
+    int pl[2][6];
+    for (int c = 0; c < q; c++) {
+      const int z = (int)(d[q2 * c] / nc);
+      const int zf = dg.coord == CARTESIAN ? z : wrap_phi(dg, z + dg.n2 / 2);
+      pl[0][c] = z;
+      pl[1][c] = zf;
+    }
+    unsigned long long fm = 0ull;
+    for (int ab = 0; ab < q2; ab++) {
+      const int64_t c0 = d[ab] % nc;
+      const int z0 = (int)(d[ab] / nc);
+      const int f = z0 == pl[0][0] ? 0 : (z0 == pl[1][0] ? 1 : -1);
+      if (f < 0 || c0 > INT32_MAX) return false;
+      col[(size_t)ab * n + r] = (int32_t)c0;
+      if (f) fm |= 1ull << ab;
+      for (int c = 0; c < q; c++)
+        if (d[ab + q2 * c] != c0 + nc * pl[f][c]) return false;
+      wxy[(size_t)ab * n + r] = h.wxy[(size_t)r * q2 + ab];
+    }
+    flip[(size_t)r] = fm;
+    for (int c = 0; c < q; c++) {
+      planes[(size_t)c * n + r] = pl[0][c];
+      planes[(size_t)(q + c) * n + r] = pl[1][c];
+      wz[(size_t)c * n + r] = h.wz[(size_t)r * q + c];
+    }
+  }
+  return true;
 }
 
 // Partial sums (H^2 J, J) of one patch over its interior points that are
@@ -481,28 +567,35 @@ nrr_status nrr_patchset_create(nrr_grid *outer, nrr_grid *inner, double hole, in
     if (e != NRR_OK) return e;
     e = nrr_set_speed_reference(inner, ps->ds_ref);
     if (e != NRR_OK) return e;
-    const int m = q * q * q;
     for (int i = 0; i < 2; i++) {
       DevLink &l = ps->link[i];
+      const Geo &dg = i == 0 ? gi : go;  // donor of link i
       l.n = (int64_t)hl[i].recv.size();
-      const size_t nm = (size_t)l.n * m;
+      l.ncol = dg.ncol;
+      std::vector<int32_t> col, planes;
+      std::vector<unsigned long long> flip;
+      std::vector<double> wxy, wz;
+      if (!compress_link(hl[i], dg, q, col, flip, planes, wxy, wz))
+        return pfail(NRR_ERR_INVALID_ARG,
+                     "a receiver's donor stencil does not have the tensor-product "
+                     "form (columns x planes) the device link uses");
       e = palloc(ps, &l.recv, (size_t)l.n);
-      if (e == NRR_OK) e = palloc(ps, &l.donor, nm);
-      if (e == NRR_OK) e = palloc(ps, &l.w, nm);
+      if (e == NRR_OK) e = palloc(ps, &l.col, col.size());
+      if (e == NRR_OK) e = palloc(ps, &l.flip, flip.size());
+      if (e == NRR_OK) e = palloc(ps, &l.planes, planes.size());
+      if (e == NRR_OK) e = palloc(ps, &l.wxy, wxy.size());
+      if (e == NRR_OK) e = palloc(ps, &l.wz, wz.size());
       if (e == NRR_OK) e = palloc(ps, &ps->mask[i], mk[i].size());
       if (e != NRR_OK) return e;
       PCUDA(cudaMemcpy(l.recv, hl[i].recv.data(), l.n * sizeof(int64_t),
                        cudaMemcpyHostToDevice));
-      // stencil-point-major on the device (k * n + r)
-      std::vector<int32_t> dT(nm);
-      std::vector<double> wT(nm);
-      for (int64_t r = 0; r < l.n; r++)
-        for (int k = 0; k < m; k++) {
-          dT[(size_t)k * l.n + r] = (int32_t)hl[i].donor[(size_t)r * m + k];
-          wT[(size_t)k * l.n + r] = hl[i].w[(size_t)r * m + k];
-        }
-      PCUDA(cudaMemcpy(l.donor, dT.data(), nm * sizeof(int32_t), cudaMemcpyHostToDevice));
-      PCUDA(cudaMemcpy(l.w, wT.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.flip, flip.data(), flip.size() * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.planes, planes.data(), planes.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.wxy, wxy.data(), wxy.size() * sizeof(double), cudaMemcpyHostToDevice));
+      PCUDA(cudaMemcpy(l.wz, wz.data(), wz.size() * sizeof(double), cudaMemcpyHostToDevice));
       PCUDA(cudaMemcpy(ps->mask[i], mk[i].data(), mk[i].size(), cudaMemcpyHostToDevice));
     }
     e = palloc(ps, &ps->partials, 4 * (size_t)kNormBlocks);

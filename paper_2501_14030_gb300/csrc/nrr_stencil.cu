@@ -88,44 +88,6 @@ __global__ void __launch_bounds__(128)
     stage_curvi_item<R, NG, KIND, 1>(g, a, it % ncols, NG + it / ncols);
 }
 
-// Cartesian: uniform spacing, so the wave speed is one constant (1 on a lone
-// grid; c^2 is in the folded weights, c multiplies the radiation term at the
-// call sites); every ghost is an outer ghost evolved by the radiation
-// condition with d_r f = sum_i (x^i/r) D_i f (one-sided inward along
-// directions in which the point lies outside, centred otherwise).  Returns
-// -(d_r f + f/r).
-template <typename R, int NG>
-__device__ __forceinline__ R cart_radiation(const Geo &g, const R *__restrict__ f,
-                                            int i0, int i1, int i2, int64_t p) {
-  const int ii[3] = {i0, i1, i2};
-  const int nn[3] = {g.n0, g.n1, g.n2};
-  const int64_t st[3] = {1, g.s0, (int64_t)g.ncol};
-  R x[3], r2 = R(0);
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    x[d] = R(fma((double)(ii[d] - NG) + 0.5, g.dxx[d], g.xxmin[d]));
-    r2 = fma(x[d], x[d], r2);
-  }
-  R rinv = R(1) / sqrt(r2);
-  R f0 = ld(f + p);
-  R dr = R(0);
-  // every operation explicit (fma, or rounded on its own), so that the
-  // result does not depend on the compiler's contraction choices
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    R D;
-    R inv2 = R(0.5 / g.dxx[d]);
-    if (ii[d] >= nn[d] + NG)
-      D = mul_rn(fma(R(3), f0, fma(R(-4), ld(f + p - st[d]), ld(f + p - 2 * st[d]))), inv2);
-    else if (ii[d] < NG)
-      D = -mul_rn(fma(R(3), f0, fma(R(-4), ld(f + p + st[d]), ld(f + p + 2 * st[d]))), inv2);
-    else
-      D = mul_rn(sub_rn(ld(f + p + st[d]), ld(f + p - st[d])), inv2);
-    dr = fma(mul_rn(x[d], rinv), D, dr);
-  }
-  return -fma(f0, rinv, dr);
-}
-
 // Cartesian operator weights in the working precision, converted once per
 // thread (a conversion from FP64 per use would run on the FP64 pipe).
 template <typename R, int NG>
@@ -154,72 +116,31 @@ __device__ __forceinline__ R cart_operator(const Geo &g, const R *__restrict__ s
   return add_source(lap, u0, al, bc2, lin);
 }
 
-template <typename R, int NG, int KIND>
-__global__ void __launch_bounds__(256)
-    stage_cart_kernel(Geo g, StageArgs<R> a, int zc) {
-  pdl_trigger();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.ncol) return;
-  pdl_wait();
-  const int i0 = e % g.s0, i1 = e / g.s0;
-  const int z0 = blockIdx.y * zc;
-  const int z1 = min(z0 + zc, g.s2);
-  const bool in01 = i0 >= NG && i0 < g.n0 + NG && i1 >= NG && i1 < g.n1 + NG;
-  const CartW<R, NG> w(a.cart);
-  for (int i2 = z0; i2 < z1; i2++) {
-    int64_t p = e + (int64_t)g.ncol * i2;
-    R ku, kv;
-    if (in01 && i2 >= NG && i2 < g.n2 + NG) {
-      R u0 = ld(a.su + p), v0 = ld(a.sv + p);
-      kv = cart_operator<R, NG>(g, a.su, w, p, u0, ld(a.alpha + p),
-                                ld(a.bc2 + p), a.lin);
-      ku = fma(-a.eta, u0, v0);
-      if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
-    } else {
-      const R c = R(a.cart.speed);
-      ku = mul_rn(c, cart_radiation<R, NG>(g, a.su, i0, i1, i2, p));
-      kv = mul_rn(c, cart_radiation<R, NG>(g, a.sv, i0, i1, i2, p));
-      if (linear_mode<R>(a.lin)) {
-        ku += ld(a.fu + p);
-        kv += ld(a.bc2 + p);
-      }
-    }
-    stage_epilogue<R, KIND>(a, p, ku, kv);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Cartesian stage fed by tensor copies (variant 1; order 8, n0 % 32 == 0,
-// n1 % 4 == 0, n2 and the plane chunk even).  Interior blocks: a 32 x 4
-// column tile streams its chunk of planes, two per slot, through a 2-slot
-// shared-memory ring (one 40 x 12 x 2 box of u with its halo, one 32 x 4 x 2
-// box per operand array, completing on the slot's mbarrier; thread 0 issues
-// two slots ahead).  Cartesian ghosts are all outer ghosts, stored and
-// evolved, so the halo box needs no images; the i2 neighbours come from a
-// register queue.  Extra blocks evolve the ghost shell with the radiation
-// condition, one point per thread: first the two i2 slabs, then the ring of
-// ghost columns on the interior planes.
-// ---------------------------------------------------------------------------
-using CartMaps = FieldSrc;  // su box (40, 12, 2), operand boxes (32, 4, 2)
-
-constexpr int kCartTY = 4, kCartPZ = 2;
-template <typename R>
-__host__ __device__ constexpr int cart_slots() { return 2; }
-
-__host__ __device__ __forceinline__ int64_t cart_shell_points(const Geo &g) {
-  const int ng = g.ng;
-  return 2 * (int64_t)ng * g.ncol +
-         ((int64_t)g.ncol - (int64_t)g.n0 * g.n1) * g.n2;
-}
-
-// Grid constants of the shell points in the working precision, converted on
-// the host (a conversion from FP64 per point would run on the FP64 pipe).
+// Cartesian: uniform spacing, so the wave speed is one constant (1 on a lone
+// grid; c^2 is in the folded weights, c multiplies the radiation term); every
+// ghost is an outer ghost evolved by the radiation condition with
+// d_r f = sum_i (x^i/r) D_i f (one-sided inward along directions in which the
+// point lies outside, centred otherwise).  The per-launch constants
+// (positions, 1 / (2 dxx)) are computed once on the host, and u and v share
+// one 1/r: the FP64 division and square root are long instruction sequences
+// on the FP64 pipe.
 template <typename R>
 struct CartShellC {
   R xmin[3];  // coordinate of padded index 0 + half a cell, per direction
   R dxx[3];   // spacing
   R inv2[3];  // 1 / (2 dxx)
 };
+
+template <typename R, int NG>
+CartShellC<R> cart_shell_consts(const Geo &g) {
+  CartShellC<R> sc;
+  for (int d = 0; d < 3; d++) {
+    sc.xmin[d] = (R)(g.xxmin[d] + (0.5 - NG) * g.dxx[d]);
+    sc.dxx[d] = (R)g.dxx[d];
+    sc.inv2[d] = (R)(0.5 / g.dxx[d]);
+  }
+  return sc;
+}
 
 // Radiation condition at ghost point (i0, i1, i2) for u and v together:
 // k_f = -(d_r f + f / r) with d_r f = sum_d (x_d / r) D_d f, in the working
@@ -267,6 +188,60 @@ __device__ __forceinline__ void cart_shell_point(const Geo &g, const StageArgs<R
   }
 }
 
+template <typename R, int NG, int KIND>
+__global__ void __launch_bounds__(256)
+    stage_cart_kernel(Geo g, StageArgs<R> a, CartShellC<R> sc, int zc) {
+  pdl_trigger();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ncol) return;
+  pdl_wait();
+  const int i0 = e % g.s0, i1 = e / g.s0;
+  const int z0 = blockIdx.y * zc;
+  const int z1 = min(z0 + zc, g.s2);
+  const bool in01 = i0 >= NG && i0 < g.n0 + NG && i1 >= NG && i1 < g.n1 + NG;
+  const CartW<R, NG> w(a.cart);
+  for (int i2 = z0; i2 < z1; i2++) {
+    int64_t p = e + (int64_t)g.ncol * i2;
+    R ku, kv;
+    if (in01 && i2 >= NG && i2 < g.n2 + NG) {
+      R u0 = ld(a.su + p), v0 = ld(a.sv + p);
+      kv = cart_operator<R, NG>(g, a.su, w, p, u0, ld(a.alpha + p),
+                                ld(a.bc2 + p), a.lin);
+      ku = fma(-a.eta, u0, v0);
+      if (linear_mode<R>(a.lin)) ku += ld(a.fu + p);
+    } else {
+      cart_shell_point<R, NG>(g, a, sc, i0, i1, i2, ku, kv);
+    }
+    stage_epilogue<R, KIND>(a, p, ku, kv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cartesian stage fed by tensor copies (variant 1; order 8, n0 % 32 == 0,
+// n1 % 4 == 0, n2 and the plane chunk even).  Interior blocks: a 32 x 4
+// column tile streams its chunk of planes, two per slot, through a 2-slot
+// shared-memory ring (one 40 x 12 x 2 box of u with its halo, one 32 x 4 x 2
+// box per operand array, completing on the slot's mbarrier; thread 0 issues
+// two slots ahead).  Cartesian ghosts are all outer ghosts, stored and
+// evolved, so the halo box needs no images; the i2 neighbours come from a
+// register queue.  Extra blocks evolve the ghost shell with the radiation
+// condition, one point per thread: first the two i2 slabs, then the ring of
+// ghost columns on the interior planes.
+// ---------------------------------------------------------------------------
+using CartMaps = FieldSrc;  // su box (40, 12, 2), operand boxes (32, 4, 2)
+
+constexpr int kCartTY = 4, kCartPZ = 2;
+template <typename R>
+__host__ __device__ constexpr int cart_slots() { return 2; }
+
+__host__ __device__ __forceinline__ int64_t cart_shell_points(const Geo &g) {
+  const int ng = g.ng;
+  return 2 * (int64_t)ng * g.ncol +
+         ((int64_t)g.ncol - (int64_t)g.n0 * g.n1) * g.n2;
+}
+
+// Grid constants of the shell points in the working precision, converted on
+// the host (a conversion from FP64 per point would run on the FP64 pipe).
 template <typename R, int NG, int KIND>
 __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
     stage_cart_tma_kernel(Geo g, StageArgs<R> a, const __grid_constant__ CartMaps maps,
@@ -927,12 +902,7 @@ bool launch_cart_tma_kind(const Geo &g, const StageArgs<R> &a, int zc, int pdl,
   CartMaps maps;
   if (!stage_field_maps<R, NG, KIND>(&maps, g, a, 32 + 2 * NG, kCartTY + 2 * NG))
     return false;
-  CartShellC<R> sc;
-  for (int d = 0; d < 3; d++) {
-    sc.xmin[d] = (R)(g.xxmin[d] + (0.5 - NG) * g.dxx[d]);
-    sc.dxx[d] = (R)g.dxx[d];
-    sc.inv2[d] = (R)(0.5 / g.dxx[d]);
-  }
+  const CartShellC<R> sc = cart_shell_consts<R, NG>(g);
   const int nint = (g.n0 / 32) * (g.n1 / kCartTY) * ((g.n2 + zc - 1) / zc);
   const int nshell = (int)((cart_shell_points(g) + 32 * kCartTY - 1) / (32 * kCartTY));
   launch_stage_kernel(stage_cart_tma_kernel<R, NG, KIND>, dim3(nint + nshell),
@@ -1095,11 +1065,12 @@ void launch_stage_ng(const Geo &g, int kind, const StageArgs<R> &a,
       return;
     dim3 grid((g.ncol + cfg.block - 1) / cfg.block, (g.s2 + cfg.zc - 1) / cfg.zc);
     dim3 blk(cfg.block);
+    const CartShellC<R> sc = cart_shell_consts<R, NG>(g);
     switch (kind) {
-      case STAGE_FIRST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_FIRST>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
-      case STAGE_MID: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_MID>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
-      case STAGE_LAST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_LAST>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
-      default: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_RAW>, grid, blk, st, cfg.pdl, g, a, cfg.zc); break;
+      case STAGE_FIRST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_FIRST>, grid, blk, st, cfg.pdl, g, a, sc, cfg.zc); break;
+      case STAGE_MID: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_MID>, grid, blk, st, cfg.pdl, g, a, sc, cfg.zc); break;
+      case STAGE_LAST: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_LAST>, grid, blk, st, cfg.pdl, g, a, sc, cfg.zc); break;
+      default: launch_stage_kernel(stage_cart_kernel<R, NG, STAGE_RAW>, grid, blk, st, cfg.pdl, g, a, sc, cfg.zc); break;
     }
     return;
   }
