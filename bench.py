@@ -539,11 +539,13 @@ def surrogate_pipeline(nrr, W, torch, n_train: int, n_held: int, epochs: int):
     held = W.batch_parameters(n_held, seed=2)
     fdesc = [W.grid_desc("sinhsymtp", fine_n, 8, bscale=p["d"] / 2) for p in held]
     cold = nrr.Batch(fdesc, [p["punctures"] for p in held])
+    cold.autotune("fp32_dc", 3)
     cold.relax(mode="fp32_dc", tol=1e-10, max_iters=50, raise_on_error=False)
     (per_c, tot_c), t_cold = timed(lambda: cold.relax(mode="fp32_dc", tol=1e-10,
                                                       raise_on_error=False))
     cold.close()
     warm = nrr.Batch(fdesc, [p["punctures"] for p in held])
+    warm.autotune("fp32_dc", 3)
     warm.relax(mode="fp32_dc", tol=1e-10, max_iters=50, raise_on_error=False)
     Xh = torch.from_numpy(W.surrogate_inputs(held)).cuda()
     shape = W.padded_shape(fdesc[0])

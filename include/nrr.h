@@ -497,7 +497,8 @@ nrr_status nrr_batch_get_interior(nrr_batch *b, float *dst);
  * 8 with every solve's n0 % 32 == 0 and n1 % 4 == 0); both take zc (2, 4, 8
  * or 16) phi planes per block and give bitwise identical results.  Variant
  * 2 = one thread per column of evolved points and zc (1, 2 or 4) planes.
- * Defaults: variant 2, zc 1 for FP64; variant 0, zc 4 for FP32.
+ * Defaults: variant 2, zc 1 for FP64; for FP32 variant 1, zc 16 where the
+ * batch allows variant 1, else variant 0, zc 4.
  * Errors: NRR_ERR_INVALID_ARG for other values or an ineligible batch. */
 nrr_status nrr_batch_set_launch(nrr_batch *b, int mode, int variant, int zc);
 

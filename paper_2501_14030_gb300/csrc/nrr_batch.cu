@@ -407,6 +407,7 @@ struct nrr_batch {
   int nblk_col[3] = {};
   int zc[2] = {1, 4};  // phi planes per block chunk: [0] FP64, [1] FP32
   // stage kernel: 0 register-staged tiles, 1 tensor-copy tiles, 2 columns
+  // (FP32: 1 with zc 16 where the batch allows it, set at creation)
   int variant[2] = {2, 0};
   int tma_ok = 0;           // every solve meets the tensor-copy variant's shape
   int *d_err = nullptr;     // set by a stage kernel whose copy wait expired
@@ -912,6 +913,14 @@ nrr_status nrr_batch_create(int n, const nrr_grid_desc *descs,
       if (b->tma_ok)
         BCUDA(cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                          cudaMemcpyHostToDevice));
+    }
+    // FP32 stages: the tensor-copy tiles over 16-plane chunks where every
+    // solve allows them (the autotuner's choice on SinhSymTP batches of
+    // 64x32x8 to 128x128x16; about half the time of the register-staged
+    // tiles), else register-staged tiles over 4-plane chunks
+    if (b->tma_ok) {
+      b->variant[1] = 1;
+      b->zc[1] = 16;
     }
     BTRY(balloc(b, &b->d_norms, (size_t)n));
     BTRY(balloc(b, &b->d_steps, (size_t)n));
