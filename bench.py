@@ -842,12 +842,18 @@ def patches_section(nrr, W, torch):
     ps = nrr.PatchSet(go, gi, 3.0, 4)
     ps.relax(tol=1e-10, max_iters=100, raise_on_error=False)
     r2, t2 = timed(lambda: ps.relax(tol=1e-10, raise_on_error=False))
+    ps.relax(tol=1e-10, max_iters=100, mode="fp32_dc", raise_on_error=False)
+    r3, t3 = timed(lambda: ps.relax(tol=1e-10, mode="fp32_dc", raise_on_error=False))
     out = {"outer": "Spherical 64x32x32, rmax 48, order 4",
            "inner": "Cartesian 48^3 over [-8, 8]^3, order 4", "hole": 3.0,
            "interpolation_points": 4,
            "receivers": [ps.outer_receivers, ps.inner_receivers],
            "two_patch": {"seconds": t2, "rk4_steps": r2["iters"],
                          "norm": r2["norm"], "status": r2["status"]},
+           "two_patch_defect_correction": {
+               "seconds": t3, "rk4_steps": r3["iters"],
+               "outer_iters": r3["outer_iters"], "norm": r3["norm"],
+               "status": r3["status"]},
            "outer_alone": {"seconds": t1, "rk4_steps": r1["iters"],
                            "norm": r1["norm"], "status": r1["status"]}}
     ps.close()

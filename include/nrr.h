@@ -413,10 +413,18 @@ nrr_status nrr_patchset_step(nrr_patchset *ps, double dt, double eta,
 nrr_status nrr_patchset_residual(nrr_patchset *ps, double r_int,
                                  double *norm_out);
 
-/* Relaxes the coupled system (paper Alg. 1 loop): mode NRR_FP64, initial
- * NRR_INIT_ZERO or NRR_INIT_CURRENT; norm every check_every steps; dt and
- * eta as nrr_patchset_timestep (o->eta > 0 overrides eta); returns as
- * nrr_relax does.  *r (nullable) filled in every case.
+/* Relaxes the coupled system (paper Alg. 1 loop): initial NRR_INIT_ZERO or
+ * NRR_INIT_CURRENT; dt and eta as nrr_patchset_timestep (o->eta > 0
+ * overrides eta); returns as nrr_relax does.  *r (nullable) filled in
+ * every case.  Modes:
+ *   NRR_FP64: FP64 steps of both patches, norm every check_every steps;
+ *   NRR_FP32_DC: defect correction as nrr_relax does it for one grid, on
+ *   the coupled system.  Each outer iteration takes both patches' FP64
+ *   defects, relaxes their FP32 increments together for inner_steps
+ *   (default check_every) steps, with the links applied to the increments
+ *   in FP32, then adds the increments to the FP64 state.  The coupled FP64
+ *   norm is checked after each outer iteration; max_outer limits the
+ *   iterations (0 = none).
  * Errors: NRR_ERR_INVALID_ARG (other modes or initial data, invalid
  * options), NRR_ERR_NOT_CONVERGED, NRR_ERR_DIVERGED, NRR_ERR_TIMEOUT,
  * NRR_ERR_CUDA. */

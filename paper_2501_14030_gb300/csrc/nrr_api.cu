@@ -642,7 +642,7 @@ nrr_status relax_chunks(nrr_grid *g, int mode, double dt, double eta,
 // F = the relaxation system's right-hand side at (u, v) (into the FP64 t
 // buffers), the FP32 coefficient c^2 a and forcings from it, and the
 // increment (d, w) set to rest.
-void launch_dc_outer_prep(const nrr_grid *g, double eta) {
+void launch_dc_outer_prep(const nrr_grid *g, double eta, cudaStream_t st) {
   const Geo &geo = g->geo;
   double *Fu = g->f64.t[0], *Fv = g->f64.t[1];
   StageArgs<double> ra{};
@@ -655,13 +655,17 @@ void launch_dc_outer_prep(const nrr_grid *g, double eta) {
   ra.col = g->c64;
   ra.cart = g->cart;
   ra.eta = eta;
-  launch_stage<double>(geo, STAGE_RAW, ra, g->stage_cfg[0], g->stream);
+  ra.err = g->flag + 2;  // a tensor-copy variant's bounded-wait flag
+  launch_stage<double>(geo, STAGE_RAW, ra, g->stage_cfg[0], st);
   launch_dc_prepare(geo, g->f64.y[0], g->f64.alpha, g->f64.bc2, Fu, Fv,
-                    g->acoef32, g->fu32, g->rhs32, g->stream);
+                    g->acoef32, g->fu32, g->rhs32, st);
   const int64_t n = geo.npts;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  zero2_kernel<<<blocks, 256, 0, g->stream>>>(g->f32.y[0], g->f32.y[1], n);
+  zero2_kernel<<<blocks, 256, 0, st>>>(g->f32.y[0], g->f32.y[1], n);
   g_launches += 3;
+}
+void launch_dc_outer_prep(const nrr_grid *g, double eta) {
+  launch_dc_outer_prep(g, eta, g->stream);
 }
 
 // One whole solve as one graph: the norm of the current state and the stop
@@ -908,7 +912,19 @@ GridView nrr::grid_view(nrr_grid *g) {
   v.err = g->flag + 2;
   v.dsmin = g->dsmin_global;
   v.have_source = g->have_source;
+  v.dc32 = dc_fields(g);
+  v.c32 = g->c32;
+  v.cfg32 = g->stage_cfg[1];
   return v;
+}
+
+void nrr::dc_outer_prep(nrr_grid *g, double eta, cudaStream_t st) {
+  launch_dc_outer_prep(g, eta, st);
+}
+
+void nrr::dc_outer_update(nrr_grid *g, cudaStream_t st) {
+  launch_dc_update(g->f64.y[0], g->f64.y[1], g->f32.y[0], g->f32.y[1], g->geo.npts, st);
+  g_launches += 1;
 }
 
 // ------------------------------------------------------------------ C ABI

@@ -200,8 +200,19 @@ struct GridView {
   int *err;                // stage kernels' bounded-wait flag
   double dsmin;            // the wave speed's reference spacing
   bool have_source;
+  FieldSet<float> dc32;    // defect correction: the FP32 increment fields
+  ColumnSet<float> c32;
+  LaunchCfg cfg32;         // FP32 stage launch shape
 };
 GridView grid_view(nrr_grid *g);
+
+// Defect correction driven from outside a grid's own relaxation loop (the
+// two-patch system), on stream st: the start of one outer iteration (the FP64
+// right-hand side at the current state as the defect, the FP32 coefficient
+// and forcings from it, the increment at rest) and its end (the FP64 state
+// plus the FP32 increment).
+void dc_outer_prep(nrr_grid *g, double eta, cudaStream_t st);
+void dc_outer_update(nrr_grid *g, cudaStream_t st);
 
 // `steps` RK4 steps (stage arguments FIRST, MID, MID, LAST) in one
 // cooperative launch of a multi-stage curvilinear kernel (variant 5: the

@@ -204,41 +204,43 @@ struct DevLink {
 // since a small link gives few warps per SM), the q^2 products of a plane
 // summed in order (b outer, then a), the planes' sums then added in order c
 // = 0 .. q-1.
-template <int Q>
+// T: the precision of the fields (FP64, or FP32 for the increments of the
+// defect correction, whose weights are rounded to FP32 before the products).
+template <int Q, typename T>
 __global__ void __launch_bounds__(128)
     link_apply_kernel(int64_t n, int64_t ncol, const int64_t *__restrict__ recv,
                       const int32_t *__restrict__ col,
                       const unsigned long long *__restrict__ flip,
                       const int32_t *__restrict__ planes,
                       const double *__restrict__ wxy, const double *__restrict__ wz,
-                      const double *su, const double *sv, double *du, double *dv) {
+                      const T *su, const T *sv, T *du, T *dv) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   int32_t cl[Q * Q];
-  double wab[Q * Q];
+  T wab[Q * Q];
 #pragma unroll
   for (int ab = 0; ab < Q * Q; ab++) {
     cl[ab] = col[(int64_t)ab * n + r];
-    wab[ab] = wxy[(int64_t)ab * n + r];
+    wab[ab] = (T)wxy[(int64_t)ab * n + r];
   }
   const unsigned long long fm = flip[r];
-  double a[Q], b[Q];
+  T a[Q], b[Q];
 #pragma unroll
   for (int c = 0; c < Q; c++) {
-    const double wc = wz[(int64_t)c * n + r];
+    const T wc = (T)wz[(int64_t)c * n + r];
     const int64_t o0 = ncol * planes[(int64_t)c * n + r];
     const int64_t o1 = ncol * planes[(int64_t)(Q + c) * n + r];
-    a[c] = 0.0;
-    b[c] = 0.0;
+    a[c] = T(0);
+    b[c] = T(0);
 #pragma unroll
     for (int ab = 0; ab < Q * Q; ab++) {
-      const double w = wab[ab] * wc;
+      const T w = wab[ab] * wc;
       const int64_t d = cl[ab] + (((fm >> ab) & 1ull) ? o1 : o0);
       a[c] = fma(w, su[d], a[c]);
       b[c] = fma(w, sv[d], b[c]);
     }
   }
-  double sa = a[0], sb = b[0];
+  T sa = a[0], sb = b[0];
 #pragma unroll
   for (int c = 1; c < Q; c++) {
     sa += a[c];
@@ -248,12 +250,13 @@ __global__ void __launch_bounds__(128)
   dv[recv[r]] = sb;
 }
 
-void launch_link(const DevLink &l, int q, const double *su, const double *sv, double *du,
-                 double *dv, cudaStream_t st) {
+template <typename T>
+void launch_link(const DevLink &l, int q, const T *su, const T *sv, T *du, T *dv,
+                 cudaStream_t st) {
   const unsigned blocks = (unsigned)((l.n + 127) / 128);
-#define NRR_LINK(Q)                                                                    \
-  link_apply_kernel<Q><<<blocks, 128, 0, st>>>(l.n, l.ncol, l.recv, l.col, l.flip,    \
-                                               l.planes, l.wxy, l.wz, su, sv, du, dv)
+#define NRR_LINK(Q)                                                                       \
+  link_apply_kernel<Q, T><<<blocks, 128, 0, st>>>(l.n, l.ncol, l.recv, l.col, l.flip,    \
+                                                  l.planes, l.wxy, l.wz, su, sv, du, dv)
   switch (q) {
     case 2: NRR_LINK(2); break;
     case 6: NRR_LINK(6); break;
@@ -350,9 +353,10 @@ constexpr int kNormBlocks = 512;  // per patch
 // the residual norm) captured as a CUDA graph, with what it was captured for.
 struct PatchChunkGraph {
   cudaGraphExec_t exec = nullptr;
+  int mode = -1;
   int64_t m = 0;
   double dt = 0.0, eta = 0.0, r_int = 0.0;
-  LaunchCfg cfg[2];
+  LaunchCfg cfg[2], cfg32[2];
 };
 
 struct nrr_patchset {
@@ -395,21 +399,28 @@ nrr_status palloc(nrr_patchset *ps, T **p, size_t count) {
 // before the stage and joins it before the links, which read both.  (Stage
 // kernels launched this way go without programmatic dependent launch: the
 // node before each is an event, not the previous stage.)
+// R = double: the relaxation system; R = float: the defect correction's
+// increment equation (the grids' FP32 increment fields, FP32 links).
+template <typename R>
 void launch_patch_steps(nrr_patchset *ps, double dt, double eta, int64_t steps) {
   static const int kinds[4] = {STAGE_FIRST, STAGE_MID, STAGE_MID, STAGE_LAST};
   GridView v[2] = {grid_view(ps->grid[0]), grid_view(ps->grid[1])};
   cudaStream_t st = v[0].stream;
   const cudaStream_t on[2] = {st, ps->side};
-  LaunchCfg cfg[2] = {v[0].cfg64, v[1].cfg64};
+  constexpr bool f32 = sizeof(R) == 4;
+  LaunchCfg cfg[2] = {f32 ? v[0].cfg32 : v[0].cfg64, f32 ? v[1].cfg32 : v[1].cfg64};
   cfg[0].pdl = cfg[1].pdl = 0;
   for (int64_t s = 0; s < steps; s++)
     for (int k = 0; k < 4; k++) {
-      StageArgs<double> a[2];
+      StageArgs<R> a[2];
       cudaEventRecord(ps->fork, st);
       cudaStreamWaitEvent(ps->side, ps->fork, 0);
       for (int i = 0; i < 2; i++) {
-        a[i] = rk4_stage_args<double>(v[i].f64, v[i].c64, v[i].cart, v[i].err, k, dt, eta);
-        launch_stage<double>(v[i].geo, kinds[k], a[i], cfg[i], on[i]);
+        if constexpr (f32)
+          a[i] = rk4_stage_args<R>(v[i].dc32, v[i].c32, v[i].cart, v[i].err, k, dt, eta);
+        else
+          a[i] = rk4_stage_args<R>(v[i].f64, v[i].c64, v[i].cart, v[i].err, k, dt, eta);
+        launch_stage<R>(v[i].geo, kinds[k], a[i], cfg[i], on[i]);
       }
       cudaEventRecord(ps->join, ps->side);
       cudaStreamWaitEvent(st, ps->join, 0);
@@ -451,15 +462,45 @@ bool same_cfg(const LaunchCfg &a, const LaunchCfg &b) {
   return a.block == b.block && a.zc == b.zc && a.variant == b.variant && a.pdl == b.pdl;
 }
 
-// The graph of one chunk for (m, dt, eta, r_int) and the grids' current
-// launch shapes: the cached one, or a new capture of the same launches the
-// host loop issues.  One graph launch then replaces 16 m + 5 launches.
-nrr_status chunk_graph(nrr_patchset *ps, int64_t m, double dt, double eta,
+// One chunk on the outer grid's stream: NRR_FP64, m RK4 steps of both patches
+// with their links; NRR_FP32_DC, one defect-correction outer iteration -- the
+// FP64 defect and FP32 coefficients of each patch, m FP32 steps of both
+// patches' increments with FP32 links, the FP64 update of each patch, and
+// then the FP64 links on the updated state: the FP32 links interpolate the
+// increments only to FP32 rounding, and receivers left that far from the
+// FP64 interpolation of their donors would pose a slightly different
+// discrete problem.  Then the coupled norm.
+void launch_chunk(nrr_patchset *ps, int mode, int64_t m, double dt, double eta,
+                  double r_int) {
+  cudaStream_t st = grid_view(ps->grid[0]).stream;
+  if (mode == NRR_FP32_DC) {
+    for (int i = 0; i < 2; i++) dc_outer_prep(ps->grid[i], eta, st);
+    launch_patch_steps<float>(ps, dt, eta, m);
+    GridView v[2] = {grid_view(ps->grid[0]), grid_view(ps->grid[1])};
+    for (int i = 0; i < 2; i++) dc_outer_update(ps->grid[i], st);
+    for (int i = 0; i < 2; i++) {
+      const DevLink &l = ps->link[i];
+      if (l.n == 0) continue;
+      const int j = 1 - i;  // donor
+      launch_link<double>(l, ps->q, v[j].f64.y[0], v[j].f64.y[1], v[i].f64.y[0],
+                          v[i].f64.y[1], st);
+    }
+  } else {
+    launch_patch_steps<double>(ps, dt, eta, m);
+  }
+  launch_patch_norm(ps, r_int);
+}
+
+// The graph of one chunk for (mode, m, dt, eta, r_int) and the grids' current
+// launch shapes: the cached one, or a new capture of the launches
+// launch_chunk issues.  One graph launch then replaces them all.
+nrr_status chunk_graph(nrr_patchset *ps, int mode, int64_t m, double dt, double eta,
                        double r_int, cudaGraphExec_t *out) {
   const GridView v0 = grid_view(ps->grid[0]), v1 = grid_view(ps->grid[1]);
   PatchChunkGraph &c = ps->chunk;
-  if (c.exec && c.m == m && c.dt == dt && c.eta == eta && c.r_int == r_int &&
-      same_cfg(c.cfg[0], v0.cfg64) && same_cfg(c.cfg[1], v1.cfg64)) {
+  if (c.exec && c.mode == mode && c.m == m && c.dt == dt && c.eta == eta &&
+      c.r_int == r_int && same_cfg(c.cfg[0], v0.cfg64) && same_cfg(c.cfg[1], v1.cfg64) &&
+      same_cfg(c.cfg32[0], v0.cfg32) && same_cfg(c.cfg32[1], v1.cfg32)) {
     *out = c.exec;
     return NRR_OK;
   }
@@ -470,8 +511,7 @@ nrr_status chunk_graph(nrr_patchset *ps, int64_t m, double dt, double eta,
   cudaStream_t st = v0.stream;
   cudaGraph_t graph = nullptr;
   PCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  launch_patch_steps(ps, dt, eta, m);
-  launch_patch_norm(ps, r_int);
+  launch_chunk(ps, mode, m, dt, eta, r_int);
   PCUDA(cudaStreamEndCapture(st, &graph));
   const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
   cudaGraphDestroy(graph);
@@ -479,12 +519,15 @@ nrr_status chunk_graph(nrr_patchset *ps, int64_t m, double dt, double eta,
     c.exec = nullptr;
     return pfail(NRR_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   }
+  c.mode = mode;
   c.m = m;
   c.dt = dt;
   c.eta = eta;
   c.r_int = r_int;
   c.cfg[0] = v0.cfg64;
   c.cfg[1] = v1.cfg64;
+  c.cfg32[0] = v0.cfg32;
+  c.cfg32[1] = v1.cfg32;
   *out = c.exec;
   return NRR_OK;
 }
@@ -655,7 +698,7 @@ nrr_status nrr_patchset_step(nrr_patchset *ps, double dt, double eta, int64_t st
     return pfail(NRR_ERR_INVALID_ARG, "null patch set, dt <= 0 or steps < 0");
   nrr_status s = begin(ps);
   if (s != NRR_OK) return s;
-  launch_patch_steps(ps, dt, eta, steps);
+  launch_patch_steps<double>(ps, dt, eta, steps);
   cudaStream_t st = grid_view(ps->grid[0]).stream;
   PCUDA(cudaGetLastError());
   PCUDA(cudaStreamSynchronize(st));
@@ -674,8 +717,10 @@ nrr_status nrr_patchset_residual(nrr_patchset *ps, double r_int, double *norm_ou
 nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
                               nrr_relax_result *r) {
   if (!ps || !o) return pfail(NRR_ERR_INVALID_ARG, "null argument");
-  if (o->mode != NRR_FP64)
-    return pfail(NRR_ERR_INVALID_ARG, "patch sets relax in NRR_FP64");
+  if (o->mode != NRR_FP64 && o->mode != NRR_FP32_DC)
+    return pfail(NRR_ERR_INVALID_ARG, "patch sets relax in NRR_FP64 or NRR_FP32_DC");
+  if (o->mode == NRR_FP32_DC && o->inner_steps < 0)
+    return pfail(NRR_ERR_INVALID_ARG, "inner_steps < 0");
   if (!(o->tol > 0.0) || o->check_every < 1 || o->max_iters < 0 || !(o->cfl > 0.0) ||
       !(o->r_int > 0.0))
     return pfail(NRR_ERR_INVALID_ARG, "invalid relax options");
@@ -702,7 +747,11 @@ nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
   launch_patch_norm(ps, o->r_int);
   s = read_norm(ps, &nrm);
   if (s != NRR_OK) return s;
-  int64_t it = 0;
+  int64_t it = 0, outer = 0;
+  // steps per chunk: FP64, the norm check interval; defect correction, the
+  // FP32 steps of one outer iteration
+  const int64_t every =
+      o->mode == NRR_FP32_DC && o->inner_steps > 0 ? o->inner_steps : o->check_every;
   nrr_status why = NRR_ERR_NOT_CONVERGED;
   for (;;) {
     if (!std::isfinite(nrm)) {
@@ -714,27 +763,28 @@ nrr_status nrr_patchset_relax(nrr_patchset *ps, const nrr_relax_opts *o,
       break;
     }
     if (it >= o->max_iters) break;
+    if (o->mode == NRR_FP32_DC && o->max_outer > 0 && outer >= o->max_outer) break;
     if (o->timeout_ms > 0 && elapsed_ms() > (double)o->timeout_ms) {
       why = NRR_ERR_TIMEOUT;
       break;
     }
-    const int64_t m = std::min<int64_t>(o->check_every, o->max_iters - it);
-    if (m == o->check_every) {
+    const int64_t m = std::min<int64_t>(every, o->max_iters - it);
+    if (m == every) {
       cudaGraphExec_t exec = nullptr;
-      s = chunk_graph(ps, m, dt, eta, o->r_int, &exec);
+      s = chunk_graph(ps, o->mode, m, dt, eta, o->r_int, &exec);
       if (s != NRR_OK) return s;
       PCUDA(cudaGraphLaunch(exec, st));
     } else {  // a last, shorter chunk: launched one kernel at a time
-      launch_patch_steps(ps, dt, eta, m);
-      launch_patch_norm(ps, o->r_int);
+      launch_chunk(ps, o->mode, m, dt, eta, o->r_int);
     }
     s = read_norm(ps, &nrm);
     if (s != NRR_OK) return s;
     it += m;
+    outer++;
   }
   if (r) {
     r->iters = it;
-    r->outer_iters = 0;
+    r->outer_iters = o->mode == NRR_FP32_DC ? outer : 0;
     r->final_norm = nrm;
     r->seconds = elapsed_ms() * 1e-3;
     r->status = why;

@@ -567,12 +567,17 @@ class PatchSet:
         return n.value
 
     def relax(self, tol=1e-10, max_iters=1_000_000, check_every=50, cfl=0.5,
-              eta=0.0, r_int=100.0, initial=None, timeout_ms=0,
-              raise_on_error=True) -> dict:
+              eta=0.0, r_int=100.0, initial=None, timeout_ms=0, mode="fp64",
+              inner_steps=0, max_outer=0, raise_on_error=True) -> dict:
+        """mode "fp64", or "fp32_dc" (FP32 increments of both patches inside
+        the FP64 defect correction, one outer iteration per inner_steps
+        steps, default check_every)."""
         o = RelaxOpts()
         _check(lib().nrr_default_opts(C.byref(o)))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
         o.tol, o.max_iters, o.check_every = tol, max_iters, check_every
         o.cfl, o.eta, o.r_int, o.timeout_ms = cfl, eta, r_int, timeout_ms
+        o.inner_steps, o.max_outer = inner_steps, max_outer
         o.initial = INIT_ZERO if initial is None else int(initial)
         r = RelaxResult()
         st = lib().nrr_patchset_relax(self._h, C.byref(o), C.byref(r))

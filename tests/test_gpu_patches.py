@@ -188,3 +188,47 @@ def test_patch_relax_chunk_graph_equals_kernel_by_kernel_steps(gpu):
         assert np.array_equal(a, b)
     for obj in (ps, go, gi, ps2, go2, gi2):
         obj.close()
+
+
+def test_patch_defect_correction_reaches_the_fp64_coupled_solution(gpu):
+    """Defect correction on the coupled system (FP32 increments of both
+    patches, FP32 links, FP64 defect and update): converges to the coupled
+    residual 1e-10, the oracle confirms that residual on the GPU's state, and
+    driven on to 1e-12 it agrees with the FP64 coupled solution driven to
+    1e-12."""
+    import oracle as O
+    go, gi, ps = _pair(SPH, BOX, HOLE)
+    r = ps.relax(tol=1e-10, mode="fp32_dc")
+    assert r["status"] == nrr.OK and r["norm"] < 1e-10 and r["outer_iters"] > 0
+    uo, _ = _state(go)
+    ui, _ = _state(gi)
+    a, b, sa, sb, la, lb = _oracle_pair(SPH, BOX, HOLE)
+    Ha, Hb = a.residual(*sa, a.fill_inner_ghosts(uo)), b.residual(*sb, ui)
+    onorm = O.patch_norm(a, Ha, la, b, Hb, lb, 100.0)
+    assert onorm < 1e-10 and onorm == pytest.approx(r["norm"], rel=1e-8)
+    r_dc = ps.relax(tol=1e-12, mode="fp32_dc", initial=nrr.INIT_CURRENT)
+    assert r_dc["status"] == nrr.OK
+    dc = _state(go)[0], _state(gi)[0]
+    go2, gi2, ps2 = _pair(SPH, BOX, HOLE)
+    r64 = ps2.relax(tol=1e-12, mode="fp64")
+    assert r64["status"] == nrr.OK
+    ref = _state(go2)[0], _state(gi2)[0]
+    # a residual of 1e-12 fixes u to about 1e-10 of its scale (the box's
+    # difference is a near-uniform offset of ~8e-12 against max |u| = 0.085)
+    scale = max(np.max(np.abs(w)) for w in ref)
+    for u, w in zip(dc, ref):
+        assert np.max(np.abs(u - w)) <= 2e-10 * scale
+    for obj in (ps, go, gi, ps2, go2, gi2):
+        obj.close()
+
+
+def test_patch_relax_modes_refused(gpu):
+    go, gi, ps = _pair(SPH, BOX, HOLE)
+    for mode in ("fp32",):
+        with pytest.raises(nrr.NrrError) as e:
+            ps.relax(tol=1e-10, mode=mode)
+        assert e.value.status == nrr.ERR_INVALID_ARG
+    with pytest.raises(nrr.NrrError):
+        ps.relax(tol=1e-10, mode="fp32_dc", inner_steps=-1)
+    for obj in (ps, go, gi):
+        obj.close()
