@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(32 * kTileY, VAR == 1 && sizeof(R) == 4 ? 6 : 
     batch_stage_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
                        const int *__restrict__ active, int stage, int mode, int zc,
                        int *err) {
+  dev::pdl_trigger();
   const int2 bm = map[blockIdx.x];
   if (!active[bm.x]) return;
   const SolveDev &sd = sds[bm.x];
@@ -220,6 +221,7 @@ template <typename R, int NG, int KIND, int ZC>
 __global__ void __launch_bounds__(32 * kTileY, ZC == 4 ? 4 : 6)
     batch_col_kernel(const SolveDev *__restrict__ sds, const int2 *__restrict__ map,
                      const int *__restrict__ active, int stage, int mode) {
+  dev::pdl_trigger();
   const int2 bm = map[blockIdx.x];
   if (!active[bm.x]) return;
   const SolveDev &sd = sds[bm.x];
@@ -512,34 +514,57 @@ nrr_status stage_map_for(nrr_batch *b, int variant, int zc) {
   return variant == 2 ? col_map(b, zc) : stage_map(b, zc);
 }
 
+// Stage kernels go with programmatic dependent launch: a stage's blocks
+// start while the previous kernel drains, and wait (griddepcontrol.wait, in
+// the stage's device code) before they read anything a kernel of the solve
+// writes.  What a stage reads before that -- its block map, the solves'
+// descriptors and weights, and the active flags -- no kernel launched
+// between two finalize kernels changes, and the kernels that precede a
+// chunk's first stage are launched without the attribute, so the finalize
+// kernel has completed.
+template <typename... P, typename... A>
+void launch_pdl(void (*k)(P...), unsigned blocks, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3(blocks);
+  c.blockDim = dim3(32 * kTileY);
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  c.attrs = at;
+  c.numAttrs = 1;
+  cudaLaunchKernelEx(&c, k, args...);
+}
+
 template <typename R, int NG, int KIND>
 void launch_bstage_kind(nrr_batch *b, int zc, int stage, int mode,
                         cudaStream_t st) {
   if (b->variant[sizeof(R) == 4] == 2) {
     const int nb = b->nblk_col[col_index(zc)];
     const int2 *map = b->d_map_col[col_index(zc)];
+    const SolveDev *sds = b->d_sd;
+    const int *act = b->d_active;
     if (zc <= 1)
-      batch_col_kernel<R, NG, KIND, 1><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
-                                                                  stage, mode);
+      launch_pdl(batch_col_kernel<R, NG, KIND, 1>, nb, st, sds, map, act, stage, mode);
     else if (zc == 2)
-      batch_col_kernel<R, NG, KIND, 2><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
-                                                                  stage, mode);
+      launch_pdl(batch_col_kernel<R, NG, KIND, 2>, nb, st, sds, map, act, stage, mode);
     else
-      batch_col_kernel<R, NG, KIND, 4><<<nb, 32 * kTileY, 0, st>>>(b->d_sd, map, b->d_active,
-                                                                  stage, mode);
+      launch_pdl(batch_col_kernel<R, NG, KIND, 4>, nb, st, sds, map, act, stage, mode);
     return;
   }
   const int2 *map = b->d_map_stage[zc_index(zc)];
   const int nb = b->nblk_stage[zc_index(zc)];
+  const SolveDev *sds = b->d_sd;
+  const int *act = b->d_active;
   if constexpr (NG == 4) {
     if (b->variant[sizeof(R) == 4] == 1) {
-      batch_stage_kernel<R, NG, KIND, 1><<<nb, 32 * kTileY, 0, st>>>(
-          b->d_sd, map, b->d_active, stage, mode, zc, b->d_err);
+      launch_pdl(batch_stage_kernel<R, NG, KIND, 1>, nb, st, sds, map, act, stage, mode,
+                 zc, b->d_err);
       return;
     }
   }
-  batch_stage_kernel<R, NG, KIND, 0><<<nb, 32 * kTileY, 0, st>>>(
-      b->d_sd, map, b->d_active, stage, mode, zc, b->d_err);
+  launch_pdl(batch_stage_kernel<R, NG, KIND, 0>, nb, st, sds, map, act, stage, mode, zc,
+             b->d_err);
 }
 
 template <typename R, int NG>
