@@ -704,6 +704,31 @@ def run_profile_batch(args):
     return 0
 
 
+def run_profile_patches(args):
+    """A short fixed workload for profiler captures of the two-patch kernels:
+    the Spherical 64x32x32 + Cartesian 48^3 system of the bench line,
+    `--profile-patches` RK4 steps launched kernel by kernel (FP64)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_14030_gb300 import nrr, workloads as W
+    torch.cuda.set_device(0)
+    punc = W.spinning_q4_pair()
+    go = nrr.Grid(W.grid_desc("spherical", (64, 32, 32), 4, rmax=48.0))
+    gi = nrr.Grid(W.grid_desc("cartesian", (48, 48, 48), 4, xmax=8.0))
+    go.set_punctures(punc)
+    gi.set_punctures(punc)
+    ps = nrr.PatchSet(go, gi, 3.0, 4)
+    dt, eta = ps.timestep(0.5)
+    ps.step(args.profile_patches, dt, eta)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_patches": args.profile_patches,
+                      "receivers": [ps.outer_receivers, ps.inner_receivers]}))
+    for x in (ps, go, gi):
+        x.close()
+    return 0
+
+
 def configs2_section(nrr, W, torch, peaks, sms, tight_tol: float = 1e-12):
     """The q=4 spinning pair on SinhSymTP 256x256x32, Spherical 128x64x32 and
     Cartesian 256^3 (order 8), and on the added SinhSpherical 128x64x16
@@ -1006,6 +1031,9 @@ def main():
                     help="with --profile-steps: phi planes per thread/block")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run only the surrogate GEMM shapes (captures)")
+    ap.add_argument("--profile-patches", type=int, default=0,
+                    help="run only this many RK4 steps of the two-patch "
+                         "system (profiler captures)")
     ap.add_argument("--gemm-shape", default="",
                     help="with --profile-gemm: only M,N,K, three calls of the "
                          "chosen plan")
@@ -1046,6 +1074,8 @@ def main():
         return run_profile_batch(args)
     if args.profile_gemm:
         return run_profile_gemm(args)
+    if args.profile_patches:
+        return run_profile_patches(args)
     if args.configs2:
         return run_configs2(args)
     if args.streams:

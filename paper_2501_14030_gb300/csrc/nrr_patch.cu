@@ -250,16 +250,67 @@ __global__ void __launch_bounds__(128)
   dv[recv[r]] = sb;
 }
 
+// The same sums with the Q planes of a receiver on Q adjacent lanes (Q = 2
+// or 4, so a receiver's lanes share a warp): Q times the threads and a Q
+// times shorter chain per thread, for links too small to fill the GPU with
+// one thread per receiver.  Each lane sums its plane in the same order, and
+// the first lane adds the planes in order c = 0 .. Q-1: the results equal
+// link_apply_kernel's bit for bit.
+template <int Q, typename T>
+__global__ void __launch_bounds__(128)
+    link_apply_lanes_kernel(int64_t n, int64_t ncol, const int64_t *__restrict__ recv,
+                            const int32_t *__restrict__ col,
+                            const unsigned long long *__restrict__ flip,
+                            const int32_t *__restrict__ planes,
+                            const double *__restrict__ wxy,
+                            const double *__restrict__ wz, const T *su, const T *sv,
+                            T *du, T *dv) {
+  static_assert(32 % Q == 0, "a receiver's lanes stay in one warp");
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t r = t / Q;
+  const int c = (int)(t % Q);
+  const bool live = r < n;
+  T a = T(0), b = T(0);
+  if (live) {
+    const unsigned long long fm = flip[r];
+    const T wc = (T)wz[(int64_t)c * n + r];
+    const int64_t o0 = ncol * planes[(int64_t)c * n + r];
+    const int64_t o1 = ncol * planes[(int64_t)(Q + c) * n + r];
+#pragma unroll
+    for (int ab = 0; ab < Q * Q; ab++) {
+      const T w = (T)wxy[(int64_t)ab * n + r] * wc;
+      const int64_t d = col[(int64_t)ab * n + r] + (((fm >> ab) & 1ull) ? o1 : o0);
+      a = fma(w, su[d], a);
+      b = fma(w, sv[d], b);
+    }
+  }
+  // every lane of the warp takes part in the shuffles (the group of a
+  // receiver past n computes nothing and stores nothing)
+  const int lane = threadIdx.x & 31, base = lane - c;
+  T sa = __shfl_sync(0xffffffffu, a, base), sb = __shfl_sync(0xffffffffu, b, base);
+#pragma unroll
+  for (int k = 1; k < Q; k++) {
+    sa += __shfl_sync(0xffffffffu, a, base + k);
+    sb += __shfl_sync(0xffffffffu, b, base + k);
+  }
+  if (live && c == 0) {
+    du[recv[r]] = sa;
+    dv[recv[r]] = sb;
+  }
+}
+
 template <typename T>
 void launch_link(const DevLink &l, int q, const T *su, const T *sv, T *du, T *dv,
                  cudaStream_t st) {
-  const unsigned blocks = (unsigned)((l.n + 127) / 128);
-#define NRR_LINK(Q)                                                                       \
-  link_apply_kernel<Q, T><<<blocks, 128, 0, st>>>(l.n, l.ncol, l.recv, l.col, l.flip,    \
-                                                  l.planes, l.wxy, l.wz, su, sv, du, dv)
+#define NRR_LINK(Q)                                                                     \
+  link_apply_lanes_kernel<Q, T><<<(unsigned)((l.n * Q + 127) / 128), 128, 0, st>>>(    \
+      l.n, l.ncol, l.recv, l.col, l.flip, l.planes, l.wxy, l.wz, su, sv, du, dv)
   switch (q) {
     case 2: NRR_LINK(2); break;
-    case 6: NRR_LINK(6); break;
+    case 6:
+      link_apply_kernel<6, T><<<(unsigned)((l.n + 127) / 128), 128, 0, st>>>(
+          l.n, l.ncol, l.recv, l.col, l.flip, l.planes, l.wxy, l.wz, su, sv, du, dv);
+      break;
     default: NRR_LINK(4); break;
   }
 #undef NRR_LINK
