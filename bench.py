@@ -862,8 +862,11 @@ def patches_section(nrr, W, torch):
     go, gi = nrr.Grid(sph), nrr.Grid(box)
     go.set_punctures(punc)
     gi.set_punctures(punc)
-    for g in (go, gi):  # not the lone grid's tuned (multi-stage) shape
-        g.set_launch(2, "fp64", 0, 128)
+    # single-stage launch shapes measured for this pair (the lone grid's
+    # tuned shape is the multi-stage kernel, which a patch system does not
+    # use): tiled stages on the sphere, one plane per thread in the box
+    go.set_launch(2, "fp64", 1, 128)
+    gi.set_launch(1, "fp64", 0, 64)
     ps = nrr.PatchSet(go, gi, 3.0, 4)
     ps.relax(tol=1e-10, max_iters=100, raise_on_error=False)
     r2, t2 = timed(lambda: ps.relax(tol=1e-10, raise_on_error=False))

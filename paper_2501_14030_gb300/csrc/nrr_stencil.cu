@@ -195,13 +195,33 @@ __global__ void __launch_bounds__(256)
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ncol) return;
   pdl_wait();
-  const int i0 = e % g.s0, i1 = e / g.s0;
+  // Columns numbered interior first (i0 fastest), then the ring of ghost
+  // columns around them: a warp then takes either the interior operator or
+  // the radiation condition on a plane, not both one after the other.
+  const int nint = g.n0 * g.n1;
+  int i0, i1;
+  if (e < nint) {
+    i0 = NG + e % g.n0;
+    i1 = NG + e / g.n0;
+  } else {
+    const int s = e - nint;
+    if (s < 2 * NG * g.s0) {  // the NG ghost rows below and above
+      const int r = s / g.s0;
+      i0 = s - r * g.s0;
+      i1 = r < NG ? r : g.n1 + r;
+    } else {  // the NG ghost columns left and right of each interior row
+      const int t = s - 2 * NG * g.s0, k = t % (2 * NG);
+      i1 = NG + t / (2 * NG);
+      i0 = k < NG ? k : g.n0 + k;
+    }
+  }
+  const int col = i0 + g.s0 * i1;
   const int z0 = blockIdx.y * zc;
   const int z1 = min(z0 + zc, g.s2);
-  const bool in01 = i0 >= NG && i0 < g.n0 + NG && i1 >= NG && i1 < g.n1 + NG;
+  const bool in01 = e < nint;
   const CartW<R, NG> w(a.cart);
   for (int i2 = z0; i2 < z1; i2++) {
-    int64_t p = e + (int64_t)g.ncol * i2;
+    int64_t p = col + (int64_t)g.ncol * i2;
     R ku, kv;
     if (in01 && i2 >= NG && i2 < g.n2 + NG) {
       R u0 = ld(a.su + p), v0 = ld(a.sv + p);
