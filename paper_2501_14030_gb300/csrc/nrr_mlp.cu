@@ -151,8 +151,12 @@ __global__ void mse_grad_kernel(const float *Z, const float *Y, float *dz32,
   if (t == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
+// out: the loss slot, or (step != nullptr) the base of a ring of `cap`
+// slots indexed by the device step counter.
 __global__ void loss_finalize_kernel(const double *partials, int n,
-                                     double denom, double *out) {
+                                     double denom, double *out,
+                                     const int64_t *step, int cap) {
+  if (step) out += *step % cap;
   __shared__ double red[256];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
@@ -193,9 +197,12 @@ __global__ void colsum_kernel(const float *dz, float *db, int rows, int cols) {
 
 // Minibatch assembly: rows order[0..rows) of X (n_in wide, zero-padded to
 // in_pad) as BF16 and transposed BF16; of Y normalised by (mean, std).
+// order: the rows of this minibatch, or (step != nullptr) of every
+// minibatch, rows * (*step) entries in.
 __global__ void gather_inputs_kernel(const float *X, const int32_t *order,
                                      int n_in, int in_pad, int rows,
-                                     bf16 *xb, bf16 *xt) {
+                                     bf16 *xb, bf16 *xt, const int64_t *step) {
+  if (step) order += *step * rows;
   tile_apply(
       rows, in_pad,
       [&](int r, int c) {
@@ -208,7 +215,9 @@ __global__ void gather_inputs_kernel(const float *X, const int32_t *order,
 }
 __global__ void gather_targets_kernel(const float *Y, const int32_t *order,
                                       const float *mean, const float *std,
-                                      int n_out, int rows, float *yb) {
+                                      int n_out, int rows, float *yb,
+                                      const int64_t *step) {
+  if (step) order += *step * rows;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)rows * n_out) return;
   const int r = (int)(i / n_out), c = (int)(i % n_out);
@@ -260,11 +269,19 @@ __global__ void std_floor_kernel(float *std, int cols) {
 struct AdamArgs {
   float lr, beta1, beta2, eps, wd, c1, c2;  // c1 = 1/(1-beta1^t), c2 likewise
 };
+// corr (nullable): per-step bias corrections (c1, c2) indexed by the device
+// step counter, in place of a.c1 and a.c2.
 __global__ void adamw_kernel(float *p, const float *g, float *m, float *v,
                              int64_t n, AdamArgs a, int dout, int din,
-                             int is_weight, bf16 *wt, bf16 *w) {
+                             int is_weight, bf16 *wt, bf16 *w, const float2 *corr,
+                             const int64_t *step) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (corr) {
+    const float2 c = corr[*step];
+    a.c1 = c.x;
+    a.c2 = c.y;
+  }
   float gi = g[i];
   float mi = a.beta1 * m[i] + (1.f - a.beta1) * gi;
   float vi = a.beta2 * v[i] + (1.f - a.beta2) * gi * gi;
@@ -282,6 +299,8 @@ __global__ void adamw_kernel(float *p, const float *g, float *m, float *v,
     w[(int64_t)k * dout + o] = b;
   }
 }
+
+__global__ void step_advance_kernel(int64_t *step) { *step += 1; }
 
 // BF16 copies of one layer's weights in both layouts.
 __global__ void weights_to_bf16_kernel(const float *p, int dout, int din,
@@ -374,13 +393,16 @@ nrr_status forward(nrr_surrogate *s) {
 
 // Backward pass from the normalised targets yb; gradients into s->grad; the
 // batch loss into loss_slot (device).
-nrr_status backward(nrr_surrogate *s, double *loss_slot) {
+// step (nullable): the device step counter of a captured training step; the
+// loss then goes to loss_slot[*step % s->loss_cap].
+nrr_status backward(nrr_surrogate *s, double *loss_slot, const int64_t *step = nullptr) {
   const int B = s->batch, Lm = s->L - 1;
   dim3 tg = tile_grid(B, s->dout[Lm]);
   mse_grad_kernel<<<tg, dim3(32, 8), 0, s->stream>>>(
       s->z[Lm], s->yb, s->dz32, s->dzb, s->dzt, B, s->dout[Lm], s->partials);
   loss_finalize_kernel<<<1, 256, 0, s->stream>>>(s->partials, (int)(tg.x * tg.y),
-                                                 (double)B * s->dout[Lm], loss_slot);
+                                                 (double)B * s->dout[Lm], loss_slot,
+                                                 step, s->loss_cap);
   for (int l = Lm; l >= 0; l--) {
     const int dout = s->dout[l], din = s->din[l];
     const void *act_t = l == 0 ? (const void *)s->xt : (const void *)s->at[l - 1];
@@ -399,37 +421,53 @@ nrr_status backward(nrr_surrogate *s, double *loss_slot) {
   return NRR_OK;
 }
 
+// step (nullable): the minibatch is order[*step * batch ..] (a captured
+// training step), else order[0 .. batch).
 nrr_status gather(nrr_surrogate *s, const float *X, const float *Y,
-                  const int32_t *order) {
+                  const int32_t *order, const int64_t *step = nullptr) {
   const int B = s->batch;
   gather_inputs_kernel<<<tile_grid(B, s->in_pad), dim3(32, 8), 0, s->stream>>>(
-      X, order, s->n_in, s->in_pad, B, s->xb, s->xt);
+      X, order, s->n_in, s->in_pad, B, s->xb, s->xt, step);
   if (Y)
     gather_targets_kernel<<<(unsigned)(((int64_t)B * s->n_out + 255) / 256), 256,
                             0, s->stream>>>(Y, order, s->mean, s->stdv, s->n_out,
-                                            B, s->yb);
+                                            B, s->yb, step);
   MCUDA(cudaGetLastError());
   return NRR_OK;
 }
 
-nrr_status adam_step(nrr_surrogate *s, double lr, double wd) {
-  s->step++;
+// AdamW's bias corrections after `step` updates.
+float2 bias_corrections(int64_t step) {
+  return make_float2((float)(1.0 / (1.0 - std::pow(0.9, (double)step))),
+                     (float)(1.0 / (1.0 - std::pow(0.999, (double)step))));
+}
+
+// corr, step (nullable): a captured training step reads its corrections from
+// corr[*step]; otherwise the host counter s->step advances here.
+nrr_status adam_step(nrr_surrogate *s, double lr, double wd,
+                     const float2 *corr = nullptr, const int64_t *step = nullptr) {
   AdamArgs a;
   a.lr = (float)lr;
   a.beta1 = 0.9f;
   a.beta2 = 0.999f;
   a.eps = 1e-8f;
   a.wd = (float)wd;
-  a.c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)s->step)));
-  a.c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)s->step)));
+  a.c1 = a.c2 = 0.f;
+  if (!corr) {
+    s->step++;
+    const float2 c = bias_corrections(s->step);
+    a.c1 = c.x;
+    a.c2 = c.y;
+  }
   for (int l = 0; l < s->L; l++) {
     int64_t nw = (int64_t)s->dout[l] * s->din[l];
     adamw_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s->stream>>>(
         s->param + s->offW[l], s->grad + s->offW[l], s->m + s->offW[l],
-        s->v + s->offW[l], nw, a, s->dout[l], s->din[l], 1, s->wt[l], s->w[l]);
+        s->v + s->offW[l], nw, a, s->dout[l], s->din[l], 1, s->wt[l], s->w[l], corr,
+        step);
     adamw_kernel<<<(s->dout[l] + 255) / 256, 256, 0, s->stream>>>(
         s->param + s->offB[l], s->grad + s->offB[l], s->m + s->offB[l],
-        s->v + s->offB[l], s->dout[l], a, 0, 1, 0, nullptr, nullptr);
+        s->v + s->offB[l], s->dout[l], a, 0, 1, 0, nullptr, nullptr, corr, step);
   }
   MCUDA(cudaGetLastError());
   return NRR_OK;
@@ -639,10 +677,74 @@ nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
   if (!s || !X || !Y || !order || n < s->batch || steps < 0 || !(lr > 0.0))
     return mfail(NRR_ERR_INVALID_ARG, "bad arguments (n >= batch, lr > 0)");
   MTRY(sbegin(s));
-  std::vector<double> losses;
+  // Two or more steps: the first runs from the host (it also sets up what a
+  // capture may not: the error flag, kernel attributes, tensor maps); then
+  // one training step (gather, forward, backward, AdamW, counter advance) is
+  // captured as a CUDA graph and replayed for the others.  Its minibatch
+  // offset, loss slot and AdamW corrections come from a device step counter
+  // and a per-step table, so every replay issues the same kernels with the
+  // same arguments as a step launched from the host.
+  cudaGraphExec_t exec = nullptr;
+  int64_t *d_step = nullptr;
+  float2 *d_corr = nullptr;
+  struct Release {
+    cudaGraphExec_t *e;
+    int64_t **st;
+    float2 **c;
+    cudaStream_t stream;
+    ~Release() {
+      if (*e || *st || *c) cudaStreamSynchronize(stream);
+      if (*e) cudaGraphExecDestroy(*e);
+      if (*st) cudaFree(*st);
+      if (*c) cudaFree(*c);
+    }
+  } release{&exec, &d_step, &d_corr, s->stream};
+  int64_t t_first = 0;  // steps already taken from the host
+  if (steps >= 2) {
+    std::vector<float2> corr((size_t)steps);
+    for (int64_t t = 0; t < steps; t++) corr[(size_t)t] = bias_corrections(s->step + 1 + t);
+    MCUDA(cudaMalloc(&d_step, sizeof(int64_t)));
+    MCUDA(cudaMalloc(&d_corr, corr.size() * sizeof(float2)));
+    MCUDA(cudaMemcpyAsync(d_corr, corr.data(), corr.size() * sizeof(float2),
+                          cudaMemcpyHostToDevice, s->stream));
+    MTRY(gather(s, X, Y, order));
+    MTRY(forward(s));
+    MTRY(backward(s, s->loss));
+    MTRY(adam_step(s, lr, weight_decay));
+    t_first = 1;
+    const int64_t one = 1;
+    MCUDA(cudaMemcpyAsync(d_step, &one, sizeof one, cudaMemcpyHostToDevice, s->stream));
+    MCUDA(cudaStreamSynchronize(s->stream));
+    cudaGraph_t graph = nullptr;
+    MCUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    nrr_status cs = [&]() -> nrr_status {
+      MTRY(gather(s, X, Y, order, d_step));
+      MTRY(forward(s));
+      MTRY(backward(s, s->loss, d_step));
+      MTRY(adam_step(s, lr, weight_decay, d_corr, d_step));
+      step_advance_kernel<<<1, 1, 0, s->stream>>>(d_step);
+      return NRR_OK;
+    }();
+    const cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
+    if (cs != NRR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return cs;
+    }
+    if (ce != cudaSuccess)
+      return mfail(NRR_ERR_CUDA, "training step capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess)
+      return mfail(NRR_ERR_CUDA, "training step graph: %s", cudaGetErrorString(ie));
+  }
   for (int64_t t0 = 0; t0 < steps; t0 += s->loss_cap) {
     const int64_t chunk = std::min<int64_t>(s->loss_cap, steps - t0);
     for (int64_t t = 0; t < chunk; t++) {
+      if (t0 + t < t_first) continue;
+      if (exec) {
+        MCUDA(cudaGraphLaunch(exec, s->stream));
+        continue;
+      }
       MTRY(gather(s, X, Y, order + (t0 + t) * s->batch));
       MTRY(forward(s));
       MTRY(backward(s, s->loss + t));
@@ -656,6 +758,7 @@ nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
       for (int64_t t = 0; t < chunk; t++) loss_out[t0 + t] = (float)h[t];
     }
   }
+  if (exec) s->step += steps - t_first;  // the replays' AdamW updates
   MCUDA(cudaStreamSynchronize(s->stream));
   return check_gemm(s);
 }

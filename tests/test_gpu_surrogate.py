@@ -66,3 +66,28 @@ def test_training_lowers_loss_and_predict_matches_reference(gpu):
     got = out[:300].cpu().numpy()
     assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max()
     s.close()
+
+
+def test_replayed_training_steps_equal_host_launched_steps(gpu):
+    """A call of several steps replays one captured training step (device
+    step counter, per-step AdamW corrections); one-step calls launch each
+    step from the host.  Five steps either way: identical parameters and
+    losses, bit for bit."""
+    dims, batch, n = [12, 128, 128, 256], 128, 1024
+    rng = np.random.default_rng(8)
+    X = rng.uniform(-1, 1, (n, 12)).astype(np.float32)
+    Y = rng.standard_normal((n, 256)).astype(np.float32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    order = torch.from_numpy(W.minibatch_order(n, batch, 5, seed=9)).cuda()
+    init = W.mlp_init_params(dims, seed=10)
+    a = nrr.Surrogate(dims, init, batch=batch)
+    b = nrr.Surrogate(dims, init, batch=batch)
+    for s in (a, b):
+        s.fit_scaling(Yd)
+    la = a.train(Xd, Yd, order, 5, lr=2e-3)
+    lb = np.concatenate([b.train(Xd, Yd, order[t * batch:(t + 1) * batch].contiguous(),
+                                 1, lr=2e-3) for t in range(5)])
+    assert np.array_equal(la, lb)
+    assert np.array_equal(a.params(), b.params())
+    a.close()
+    b.close()
