@@ -635,6 +635,8 @@ def run_profile_gemm(args):
         D = torch.empty((M, N), dtype=torch.float32, device="cuda")
         combos = [(0, 0, -1)] + [(bn, 1, 0) for bn in (64, 128, 256) if N % bn == 0]
         combos += [(bn, 1, 1) for bn in (128, 256) if N % bn == 0]
+        if M % 256 == 0:
+            combos += [(bn, 1, 2) for bn in (128, 256) if N % bn == 0]
         if K >= 4096:
             combos += [(128, sp, 0) for sp in (8, 19, 38)] + [(64, 19, 0)]
         for bn, sp, pers in combos:

@@ -297,12 +297,47 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void 
       : "memory");
 }
 
-template <int BN>
+// Tensor copy into the same CTA-relative shared-memory offset of every CTA in
+// `mask` of this cluster, completing bytes on the mbarrier at the same
+// offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map,
+                                               uint64_t *bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CL = 1: one CTA per SM walks the output tiles.  CL = 2: clusters of two CTAs
+// walk pairs of vertically adjacent tiles (rows m0 and m0 + 128, the same
+// columns): each CTA loads its own A rows and half of the shared B tile,
+// multicast into both CTAs' rings, so B is read from L2 once per pair; a
+// ring stage is refilled when both CTAs' MMAs have released it (the MMA
+// commit arrives on the empty barriers of both), and the cluster meets at
+// a barrier after set-up (no copy before the peer's barriers exist) and
+// before exit (no copy into a CTA that has left).  map_b's box is BN / CL
+// rows.
+template <int BN, int CL>
 __global__ void __launch_bounds__(PST_THREADS, 1)
     gemm_bf16_tn_persistent_kernel(const __grid_constant__ CUtensorMap map_a,
                                    const __grid_constant__ CUtensorMap map_b,
                                    const __grid_constant__ CUtensorMap map_d, int M,
                                    int N, int K, int *err) {
+  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   constexpr int STAGES = PST_STAGES;
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   extern __shared__ uint8_t smem_raw[];
@@ -321,12 +356,17 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
   int *abort_flag = issued + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntn = N / BN, tiles = ntn * (M / BM), nk = K / BK;
+  const int ntn = N / BN, nk = K / BK;
+  // work units: tiles (CL = 1) or vertical tile pairs (CL = 2), walked by
+  // CTAs (or clusters) in steps of their number
+  const int rank = CL == 2 ? (int)cluster_rank() : 0;
+  const int units = ntn * (M / BM / CL), unit0 = blockIdx.x / CL,
+            ustep = gridDim.x / CL;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(&acc_full[b], 1);
@@ -348,15 +388,19 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if constexpr (CL == 2) cluster_sync();  // the peer's barriers exist
   const uint32_t tmem = *tmem_slot;
   volatile int *vabort = abort_flag;
+  // the output tile of work unit u for this CTA
+  auto tile_m0 = [&](int u) { return ((u / ntn) * CL + rank) * BM; };
+  auto tile_n0 = [&](int u) { return (u % ntn) * BN; };
 
   if (warp == 0 && lane == 0) {
     // TMA producer: k-block g (counted over all of this CTA's tiles) goes
     // to stage g % STAGES
     int g = 0;
-    for (int t = blockIdx.x; t < tiles && !*vabort; t += gridDim.x) {
-      const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+    for (int u = unit0; u < units && !*vabort; u += ustep) {
+      const int m0 = tile_m0(u), n0 = tile_n0(u);
       for (int kb = 0; kb < nk && !*vabort; kb++, g++) {
         const int s = g % STAGES;
         if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, err, 11)) {
@@ -365,7 +409,11 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
         }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
         tma_load_2d(sA + s * A_BYTES, &map_a, &full[s], kb * BK, m0);
-        tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], kb * BK, n0);
+        if constexpr (CL == 2)
+          tma_load_2d_mc(sB + s * B_BYTES + rank * (B_BYTES / 2), &map_b, &full[s],
+                         kb * BK, n0 + rank * (BN / 2), (uint16_t)0x3);
+        else
+          tma_load_2d(sB + s * B_BYTES, &map_b, &full[s], kb * BK, n0);
         *issued = g + 1;
       }
     }
@@ -374,7 +422,7 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
     const uint32_t idesc = mma_idesc<BN>();
     int g = 0, i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, i++) {
+    for (int u = unit0; u < units && ok; u += ustep, i++) {
       const int buf = i & 1;
       if (i >= 2 && !mbar_wait(&acc_empty[buf], ((i >> 1) - 1) & 1, err, 12)) {
         ok = false;
@@ -400,10 +448,19 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
               "l"(da + off), "l"(db + off), "r"(idesc), "r"(acc));
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-            "[%0];" ::"r"(smem_addr(&empty[s]))
-            : "memory");
+        if constexpr (CL == 2)
+          // release the stage in both CTAs: the peer refills its half of B
+          // in this CTA's ring too
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster"
+              ".multicast::cluster.b64 [%0], %1;" ::"r"(smem_addr(&empty[s])),
+              "h"((uint16_t)0x3)
+              : "memory");
+        else
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+              "[%0];" ::"r"(smem_addr(&empty[s]))
+              : "memory");
       }
       if (!ok) break;
       asm volatile(
@@ -423,7 +480,7 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
     uint8_t *stg0 = sOut + (warp - 2) * 2 * 4096;
     int nst = 0;  // boxes stored by this warp (staging buffer nst % 2)
     int i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, i++) {
+    for (int u = unit0; u < units; u += ustep, i++) {
       const int buf = i & 1;
       const bool ready = mbar_wait(&acc_full[buf], (i >> 1) & 1, err, 14);
       if (!__all_sync(0xffffffffu, ready && !*vabort)) {
@@ -431,7 +488,7 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+      const int m0 = tile_m0(u), n0 = tile_n0(u);
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32, nst++) {
@@ -487,6 +544,8 @@ __global__ void __launch_bounds__(PST_THREADS, 1)
     mbar_wait(mma_done, 0, err, 16);
   }
   __syncthreads();
+  // no CTA leaves while its peer may still copy into it
+  if constexpr (CL == 2) cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -636,22 +695,33 @@ cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, float *D,
   return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, int CL>
 cudaError_t launch_gemm_persistent(const CUtensorMap &ma, const CUtensorMap &mb,
                                    const CUtensorMap &md, int M, int N, int K,
                                    int ctas, cudaStream_t st) {
   constexpr int smem = pst_smem<BN>();
+  auto kern = gemm_bf16_tn_persistent_kernel<BN, CL>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_persistent_kernel<BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  gemm_bf16_tn_persistent_kernel<BN><<<ctas, PST_THREADS, smem, st>>>(ma, mb, md, M, N,
-                                                                      K, g_err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3(ctas);
+  c.blockDim = dim3(PST_THREADS);
+  c.dynamicSmemBytes = smem;
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  c.attrs = at;
+  c.numAttrs = CL > 1 ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&c, kern, ma, mb, md, M, N, K, g_err);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -728,11 +798,13 @@ nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
   }
   if ((bn != 0 && bn != 64 && bn != 128 && bn != 256) || (bn != 0 && N % bn) ||
       splits < 0 || splits > K / BK || splits > 65535 || persistent < -1 ||
-      persistent > 1 || (persistent == 1 && splits > 1)) {
+      persistent > 2 || (persistent >= 1 && splits > 1) ||
+      (persistent == 2 && M % (2 * BM))) {
     snprintf(msg, msglen,
              "gemm: tile width must be 0 (chosen), 64, 128 or 256 and divide N; "
-             "splits 0 (chosen) .. K/64; persistent -1 (chosen), 0 or 1, and not "
-             "with splits > 1 (bn=%d splits=%d persistent=%d N=%d K=%d)",
+             "splits 0 (chosen) .. K/64; persistent -1 (chosen), 0, 1 or 2 (2: M "
+             "%% 256 == 0), and not with splits > 1 (bn=%d splits=%d "
+             "persistent=%d N=%d K=%d)",
              bn, splits, persistent, N, K);
     return NRR_ERR_INVALID_ARG;
   }
@@ -741,8 +813,10 @@ nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
     return NRR_ERR_OOM;
   }
   gemm_plan(M, N, K, &bn, &splits, &persistent);
+  // clusters of two CTAs share B: each loads half of the B box
+  const int cl = persistent == 2 ? 2 : 1;
   CUtensorMap ma, mb;
-  if (!cached_map(&ma, A, M, K, BM) || !cached_map(&mb, B, N, K, bn)) {
+  if (!cached_map(&ma, A, M, K, BM) || !cached_map(&mb, B, N, K, bn / cl)) {
     snprintf(msg, msglen, "gemm: tensor map encoding failed");
     return NRR_ERR_CUDA;
   }
@@ -752,12 +826,17 @@ nrr_status gemm_bf16_tn(const void *A, const void *B, float *D, int M, int N,
       snprintf(msg, msglen, "gemm: output tensor map encoding failed");
       return NRR_ERR_CUDA;
     }
-    const int tiles = (N / bn) * (M / BM);
-    const int ctas = std::min(tiles, device_sms());
-    cudaError_t e =
-        bn == 256 ? launch_gemm_persistent<256>(ma, mb, md, M, N, K, ctas, st)
-        : bn == 128 ? launch_gemm_persistent<128>(ma, mb, md, M, N, K, ctas, st)
-                    : launch_gemm_persistent<64>(ma, mb, md, M, N, K, ctas, st);
+    const int units = (N / bn) * (M / BM / cl);
+    const int ctas = cl * std::min(units, device_sms() / cl);
+    cudaError_t e;
+    if (cl == 2)
+      e = bn == 256 ? launch_gemm_persistent<256, 2>(ma, mb, md, M, N, K, ctas, st)
+          : bn == 128 ? launch_gemm_persistent<128, 2>(ma, mb, md, M, N, K, ctas, st)
+                      : launch_gemm_persistent<64, 2>(ma, mb, md, M, N, K, ctas, st);
+    else
+      e = bn == 256 ? launch_gemm_persistent<256, 1>(ma, mb, md, M, N, K, ctas, st)
+          : bn == 128 ? launch_gemm_persistent<128, 1>(ma, mb, md, M, N, K, ctas, st)
+                      : launch_gemm_persistent<64, 1>(ma, mb, md, M, N, K, ctas, st);
     if (e != cudaSuccess) {
       snprintf(msg, msglen, "gemm launch: %s", cudaGetErrorString(e));
       return NRR_ERR_CUDA;

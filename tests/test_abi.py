@@ -184,10 +184,14 @@ def test_gemm_async_rejects_bad_shapes_and_tiles_on_host(lib, M, N, K, bn, split
     assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()
 
 
-@pytest.mark.parametrize("persistent,splits", [(2, 1), (-2, 1), (1, 4)])
-def test_gemm_async_rejects_bad_kernel_choice_on_host(lib, persistent, splits):
+@pytest.mark.parametrize("M,persistent,splits", [(256, 3, 1), (256, -2, 1),
+                                                 (256, 1, 4), (256, 2, 4),
+                                                 (384, 2, 1)])
+def test_gemm_async_rejects_bad_kernel_choice_on_host(lib, M, persistent, splits):
+    """persistent -1, 0, 1 or 2; no K split with the persistent kernels; the
+    2-CTA clusters take pairs of 128-row tiles (M % 256 == 0)."""
     p = C.c_void_p(1 << 20)
-    st = lib.nrr_gemm_bf16_tn_async(p, p, p, 256, 256, 4096, 128, splits,
+    st = lib.nrr_gemm_bf16_tn_async(p, p, p, M, 256, 4096, 128, splits,
                                     persistent, None)
     assert st == nrr.ERR_INVALID_ARG, lib.nrr_last_error()
 

@@ -130,17 +130,39 @@ def test_persistent_gemm_matches_fp64_product(gpu, M, N, K, bn):
     assert np.all(np.abs(out - ref) <= bound + 1e-30)
 
 
-@pytest.mark.parametrize("bn", [128, 256])
+@pytest.mark.parametrize("bn", [64, 128, 256])
 def test_persistent_gemm_equals_one_cta_per_tile_bitwise(gpu, bn):
-    """Both kernels issue the same MMAs over K in the same order into an FP32
-    accumulator: identical bits, whatever the tile-to-CTA assignment."""
+    """The persistent kernel, alone or in 2-CTA clusters that share B by
+    multicast, issues the same MMAs over K in the same order into an FP32
+    accumulator as one CTA per tile: identical bits, whatever the
+    tile-to-CTA assignment."""
     M, N, K = 2048, 2048, 512
     A, B = _operands(M, N, K, 77 + bn)
     Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
     Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
-    D1 = torch.empty((M, N), dtype=torch.float32, device="cuda")
-    D2 = torch.empty((M, N), dtype=torch.float32, device="cuda")
-    nrr.gemm_bf16_tn_async(Ad, Bd, D1, bn=bn, splits=1, persistent=1)
-    nrr.gemm_bf16_tn_async(Ad, Bd, D2, bn=bn, splits=1, persistent=0)
+    Ds = [torch.empty((M, N), dtype=torch.float32, device="cuda") for _ in range(3)]
+    for D, pers in zip(Ds, (0, 1, 2)):
+        nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=1, persistent=pers)
     nrr.gemm_status()
-    assert torch.equal(D1, D2)
+    assert torch.equal(Ds[1], Ds[0])
+    assert torch.equal(Ds[2], Ds[0])
+
+
+@pytest.mark.parametrize("M,N,K,bn", [
+    (4096, 4096, 256, 256),   # 1024 tile pairs over 76 clusters
+    (768, 512, 1024, 128),    # fewer pairs than clusters
+    (8192, 16384, 512, 256),  # the large shape of the rate table
+])
+def test_cluster_gemm_matches_fp64_product(gpu, M, N, K, bn):
+    A, B = _operands(M, N, K, M + N + K + 2 * bn)
+    Ad = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    Bd = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    nrr.gemm_bf16_tn_async(Ad, Bd, D, bn=bn, splits=1, persistent=2)
+    nrr.gemm_status()
+    rows = np.random.default_rng(3).choice(M, size=min(M, 512), replace=False)
+    ref = A[rows].astype(np.float64) @ B.astype(np.float64).T
+    bound = K * 6e-8 * (np.abs(A[rows]).astype(np.float64) @ np.abs(B).astype(np.float64).T)
+    out = D.cpu().numpy()[rows].astype(np.float64)
+    assert np.all(np.isfinite(D.cpu().numpy()))
+    assert np.all(np.abs(out - ref) <= bound + 1e-30)
