@@ -540,8 +540,12 @@ nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
 /* The same product, only enqueued on `stream` (no host synchronisation).
  * persistent: 1 = one CTA per SM walks all output tiles with two tensor-
  * memory accumulators (a tile's epilogue, stored by TMA, overlaps the next
- * tile's main loop); 0 = one CTA per output tile; -1 = choose (persistent
- * when there are more 128 x 128 output tiles than SMs and K is not split).
+ * tile's main loop); 2 = the same in clusters of two CTAs that take pairs of
+ * vertically adjacent tiles and share their B tile by TMA multicast (M %
+ * 256 == 0; bitwise equal results, measured 9% slower than 1 at
+ * 8192x16384x512, never chosen); 0 = one CTA per output tile; -1 = choose
+ * (persistent 1 when there are more 128 x 128 output tiles than SMs and K
+ * is not split).
  * bn: output tile width 64, 128 or 256 (must divide N), 0 to choose
  * (persistent: 256 when it divides N, else 128, else 64; K split: 128 when
  * it divides N, else 64; otherwise the widest that divides N and gives at
@@ -557,7 +561,7 @@ nrr_status nrr_gemm_bf16_tn(const void *A, const void *B, float *D, int M,
  * nrr_gemm_status reads it.
  * Errors (host-side, nothing enqueued): NRR_ERR_INVALID_ARG (as
  * nrr_gemm_bf16_tn, or bn / splits / persistent outside the ranges above,
- * or persistent = 1 with splits > 1), NRR_ERR_OOM, NRR_ERR_CUDA. */
+ * or persistent 1 or 2 with splits > 1), NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_gemm_bf16_tn_async(const void *A, const void *B, float *D, int M,
                                   int N, int K, int bn, int splits, int persistent,
                                   void *stream);
