@@ -134,8 +134,10 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
 }
 
 // c^2 [lap(u) + source] at ZC interior points of one column (i0, i1) of a
-// curvilinear grid, planes pl[0..ZC).  wp[] holds the wrapped phi planes
-// pl[0]-NG .. pl[ZC-1]+NG, wh[] the planes phi + pi of pl[].  One
+// curvilinear grid, planes pl[0..ZC).  zo[] holds the element offsets
+// (ncol x plane) of the wrapped phi planes pl[0]-NG .. pl[ZC-1]+NG, ho[]
+// those of the planes phi + pi of pl[].  Indices are 32-bit: a grid holds
+// at most 2^31 points.  One
 // accumulation chain per point -- centre, xx0, xx1, phi, then the source --
 // in the order every curvilinear stage kernel uses: on the FP64 pipe (a
 // warp instruction every 64 cycles per SM sub-partition) latency is hidden
@@ -148,27 +150,26 @@ __device__ __forceinline__ R add_source(R acc, R u0, R al, R bc2, int lin) {
 template <typename R, int NG, int ZC, bool COH = false, bool CYL = false>
 __device__ __forceinline__ void curvi_operator(
     const Geo &g, const R *__restrict__ su, const R (&w)[5 * NG + 1], int col,
-    int i0, int i1, const int (&wp)[ZC + 2 * NG], const int (&wh)[ZC],
+    int i0, int i1, const int (&zo)[ZC + 2 * NG], const int (&ho)[ZC],
     const R (&u0)[ZC], const R (&al)[ZC], const R (&bc)[ZC], R (&out)[ZC],
     int lin) {
-  const int64_t nc = g.ncol;
   const int s0 = g.s0;
   R a0[ZC];
 #pragma unroll
   for (int j = 0; j < ZC; j++) a0[j] = w[0] * u0[j];
   // xx0: the + side stays inside the padded box; the - side may cross
   // xx0 = 0 and read the reflected point at phi + pi.
+  const int rrow = s0 * (spherical_like(g.coord) ? g.n1 + 2 * NG - 1 - i1 : i1);
 #pragma unroll
   for (int k = 1; k <= NG; k++) {
     const int im = i0 - k;
     const bool refl = im < NG;
-    const int rcol = (2 * NG - 1 - im) +
-                     s0 * (spherical_like(g.coord) ? g.n1 + 2 * NG - 1 - i1 : i1);
+    const int rcol = (2 * NG - 1 - im) + rrow;
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
-      const int64_t p = col + nc * wp[NG + j];
-      R up = lds<COH>(su + p + k);
-      R um = refl ? lds<COH>(su + rcol + nc * wh[j]) : lds<COH>(su + p - k);
+      const R *pc = su + (col + zo[NG + j]);
+      R up = lds<COH>(pc + k);
+      R um = refl ? lds<COH>(su + (rcol + ho[j])) : lds<COH>(pc - k);
       a0[j] = fma(w[k], up, a0[j]);
       a0[j] = fma(w[NG + k], um, a0[j]);
     }
@@ -182,8 +183,8 @@ __device__ __forceinline__ void curvi_operator(
     const int cm = i0 + s0 * (rm ? 2 * NG - 1 - im : im);
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
-      R up = lds<COH>(su + cp + nc * (rp ? wh[j] : wp[NG + j]));
-      R um = lds<COH>(su + cm + nc * (rm ? wh[j] : wp[NG + j]));
+      R up = lds<COH>(su + (cp + (rp ? ho[j] : zo[NG + j])));
+      R um = lds<COH>(su + (cm + (rm ? ho[j] : zo[NG + j])));
       a0[j] = fma(w[2 * NG + k], up, a0[j]);
       a0[j] = fma(w[3 * NG + k], um, a0[j]);
     }
@@ -193,8 +194,8 @@ __device__ __forceinline__ void curvi_operator(
   for (int k = 1; k <= NG; k++) {
 #pragma unroll
     for (int j = 0; j < ZC; j++) {
-      R sp = lds<COH>(su + col + nc * wp[NG + j + k]);
-      R sm = lds<COH>(su + col + nc * wp[NG + j - k]);
+      R sp = lds<COH>(su + (col + zo[NG + j + k]));
+      R sm = lds<COH>(su + (col + zo[NG + j - k]));
       a0[j] = fma(w[4 * NG + k], sp + sm, a0[j]);
     }
   }
@@ -212,20 +213,19 @@ __device__ __forceinline__ int wrap_plane(const Geo &g, int z) {
   return z;
 }
 
-// Plane tables of one thread: wp[] = wrapped phi planes z0-NG .. z0+ZC-1+NG
-// (planes past the last one are clamped so that loads stay in range), wh[] =
-// the plane at phi + pi of each of the ZC planes.
+// Plane offsets of one thread: zo[j] = ncol x (phi plane z0-NG+j, wrapped;
+// planes past the last one are clamped so that loads stay in range), ho[j]
+// = ncol x (the plane at phi + pi of plane z0+j).  Each plane is wrapped on
+// its own: an incremental form (previous plane plus one) made the stage
+// kernel slower.
 template <int NG, int ZC>
-__device__ __forceinline__ void plane_tables(const Geo &g, int z0, int (&wp)[ZC + 2 * NG],
-                                             int (&wh)[ZC]) {
-  const int last = NG + g.n2 - 1;
+__device__ __forceinline__ void plane_offsets(const Geo &g, int z0, int (&zo)[ZC + 2 * NG],
+                                              int (&ho)[ZC]) {
+  const int nc = g.ncol, last = NG + g.n2 - 1;
 #pragma unroll
-  for (int j = 0; j < ZC + 2 * NG; j++) {
-    int z = min(z0 - NG + j, last + NG);
-    wp[j] = wrap_plane<NG>(g, z);
-  }
+  for (int j = 0; j < ZC + 2 * NG; j++) zo[j] = nc * wrap_plane<NG>(g, min(z0 - NG + j, last + NG));
 #pragma unroll
-  for (int j = 0; j < ZC; j++) wh[j] = wrap_plane<NG>(g, min(z0 + j, last) + g.n2 / 2);
+  for (int j = 0; j < ZC; j++) ho[j] = nc * wrap_plane<NG>(g, min(z0 + j, last) + g.n2 / 2);
 }
 
 template <typename R, int KIND, bool COH = false>
@@ -362,13 +362,13 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
   R w[5 * NG + 1];
 #pragma unroll
   for (int j = 0; j < 5 * NG + 1; j++) w[j] = ldc(a.col.coef + (int64_t)j * nc + col);
-  int wp[ZC + 2 * NG], wh[ZC];
-  plane_tables<NG, ZC>(g, z0, wp, wh);
+  int zo[ZC + 2 * NG], ho[ZC];
+  plane_offsets<NG, ZC>(g, z0, zo, ho);
   pdl_wait();
   R u0[ZC], v0[ZC], al[ZC], bc[ZC], kv[ZC];
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
-    int64_t p = col + (int64_t)nc * wp[NG + j];
+    const int p = col + zo[NG + j];
     u0[j] = lds<COH>(a.su + p);
     v0[j] = lds<COH>(a.sv + p);
     al[j] = ld(a.alpha + p);
@@ -379,7 +379,7 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
   R yb[2][ZC], ac[2][ZC], fu[ZC];
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
-    int64_t p = col + (int64_t)nc * wp[NG + j];
+    const int p = col + zo[NG + j];
     if (KIND == STAGE_FIRST || KIND == STAGE_MID) {
       yb[0][j] = lds<COH>(a.bu + p);
       yb[1][j] = lds<COH>(a.bv + p);
@@ -390,12 +390,14 @@ __device__ __forceinline__ void stage_curvi_item(const Geo &g, const StageArgs<R
     }
     fu[j] = linear_mode<R>(a.lin) ? ld(a.fu + p) : R(0);
   }
-  curvi_operator<R, NG, ZC, COH, CYL>(g, a.su, w, col, i0, i1, wp, wh, u0, al, bc,
+  curvi_operator<R, NG, ZC, COH, CYL>(g, a.su, w, col, i0, i1, zo, ho, u0, al, bc,
                                       kv, a.lin);
+  // Plane z0 + j (< zend) is its own wrapped plane, so its offset is
+  // zo[NG + j].
 #pragma unroll
   for (int j = 0; j < ZC; j++) {
     if (z0 + j >= zend) break;
-    int64_t p = col + (int64_t)nc * (z0 + j);
+    const int p = col + zo[NG + j];
     R ku = fma(-a.eta, u0[j], v0[j]);
     if (linear_mode<R>(a.lin)) ku += fu[j];
     if (KIND == STAGE_FIRST) {
@@ -463,11 +465,11 @@ __device__ __forceinline__ void residual_curvi_item(
     w[j] = ldc(col_set.coef + (int64_t)j * nc + col);
   R c2inv = ldc(col_set.c2inv + col);
   for (int i2 = z0; i2 < z1; i2++) {
-    int wp[1 + 2 * NG], wh[1];
-    plane_tables<NG, 1>(g, i2, wp, wh);
-    int64_t p = col + (int64_t)nc * i2;
+    int zo[1 + 2 * NG], ho[1];
+    plane_offsets<NG, 1>(g, i2, zo, ho);
+    const int p = col + nc * i2;
     R u0[1] = {ld(su + p)}, al[1] = {ld(alpha + p)}, bc[1] = {ld(bc2 + p)}, op[1];
-    curvi_operator<R, NG, 1, false, CYL>(g, su, w, col, i0, i1, wp, wh, u0, al, bc,
+    curvi_operator<R, NG, 1, false, CYL>(g, su, w, col, i0, i1, zo, ho, u0, al, bc,
                                          op, lin);
     double H = (double)(op[0] * c2inv);
     if (h_out) h_out[p] = H;
