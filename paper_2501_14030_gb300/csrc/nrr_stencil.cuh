@@ -708,9 +708,12 @@ struct ArenaSrc {
   const CUtensorMap *map_op;  // box (32, TY, PZ, 1)
   const void *base;           // field 0 of this solve in the arena
   int64_t stride;             // elements between consecutive fields
+  // (p - base) is a whole number f of fields, f at most a few dozen: the
+  // FP32 quotient is within 4e-6 f of f, so rounding recovers f exactly
+  // without a 64-bit integer division.
   template <typename R>
   __device__ __forceinline__ int field(const R *p) const {
-    return (int)((p - static_cast<const R *>(base)) / stride);
+    return __float2int_rn((float)(p - static_cast<const R *>(base)) / (float)stride);
   }
   __device__ __forceinline__ void load_u(void *dst, uint64_t *bar, int x, int y,
                                          int z, int f) const {
@@ -843,9 +846,6 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
     for (int k = 0; k < NS; k++) mbar_init_count(&full[k], 1);
     mbar_init_fence();
   }
-  R w[5 * NG + 1];
-#pragma unroll
-  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ldc(a.col.coef + (int64_t)j * nc + col);
   __syncthreads();
   pdl_wait();
   // Operands this stage reads (slot mask) and their field indices (the 4th
@@ -878,8 +878,15 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
     for (int o = 0; o < 8; o++)
       if ((opmask >> o) & 1u) fidx[o] = src.field(optr[o]);
     fidx[8] = src.field(a.su);
-    for (int k = 0; k < NS - 1 && k < nslots; k++) issue(z0 + PZ * k, k);
+    for (int k = 0; k < NS && k < nslots; k++) issue(z0 + PZ * k, k);
   }
+  // The column's folded weights are loaded while the first copies are in
+  // flight: a block that starts after the preceding stage has finished
+  // would otherwise wait for them before issuing any copy.  Plain loads, so
+  // that the compiler keeps them behind the copies.
+  R w[5 * NG + 1];
+#pragma unroll
+  for (int j = 0; j < 5 * NG + 1; j++) w[j] = ld(a.col.coef + (int64_t)j * nc + col);
   // phi queue of this column (planes i2 - NG .. i2 + NG of the slot's first
   // plane i2) and the image cells of the next slot
   R q[2 * NG + PZ];
@@ -938,17 +945,15 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
       }
       if (__syncthreads_or(!ok)) {
         // A copy did not complete in time: record it, let the copies still in
-        // flight (slots it .. it + NS - 2) land, bounded, and leave.
+        // flight (slots it .. it + NS - 1) land, bounded, and leave.
         if (threadIdx.x == 0) {
           atomicExch(err, 1);
-          for (int j = it; j < nslots && j < it + NS - 1; j++)
+          for (int j = it; j < nslots && j < it + NS; j++)
             mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
         }
         __syncthreads();
         return;
       }
-      if (threadIdx.x == 0 && it + NS - 1 < nslots)
-        issue(i2 + PZ * (NS - 1), (sl + NS - 1) % NS);
       if (it + 1 < nslots) {
         fetch_images(i2 + PZ);
         if constexpr (!PH) {
@@ -999,6 +1004,12 @@ __device__ __forceinline__ void stage_tma_block(const Geo &g, const StageArgs<R>
           st(a.ou + p, ku);
           st(a.ov + p, kv);
         }
+      }
+      // Refill this slot as soon as every thread is done with it, so that
+      // NS copies are in flight while the block waits for the next one.
+      if (it + NS < nslots) {
+        __syncthreads();
+        if (threadIdx.x == 0) issue(i2 + PZ * NS, sl);
       }
     }
   }
