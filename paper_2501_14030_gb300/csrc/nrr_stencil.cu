@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
                     NG + j1b, pl);
   };
   if (threadIdx.x == 0)
-    for (int k = 0; k < NS - 1 && k < nslots; k++) issue(z0 + PZ * k, k);
+    for (int k = 0; k < NS && k < nslots; k++) issue(z0 + PZ * k, k);
   // i2 queue of this column: planes i2 - NG .. i2 + NG of the slot's first
   // plane (ghost planes are stored: no wrap)
   R q[2 * NG + PZ];
@@ -372,17 +372,15 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
       for (int j = 0; j < PZ; j++) q[2 * NG + j] = nq[j];
       if (__syncthreads_or(!ok)) {
         // a copy did not complete in time: record it, let the copies still
-        // in flight (slots it .. it + NS - 2) land, bounded, and leave
+        // in flight (slots it .. it + NS - 1) land, bounded, and leave
         if (threadIdx.x == 0) {
           if (a.err) atomicExch(a.err, 1);
-          for (int j = it; j < nslots && j < it + NS - 1; j++)
+          for (int j = it; j < nslots && j < it + NS; j++)
             mbar_wait_parity(&full[j % NS], (uint32_t)((j / NS) & 1));
         }
         __syncthreads();
         return;
       }
-      if (threadIdx.x == 0 && it + NS - 1 < nslots)
-        issue(i2 + PZ * (NS - 1), (sl + NS - 1) % NS);
       if (it + 1 < nslots) {
 #pragma unroll
         for (int j = 0; j < PZ; j++)
@@ -422,6 +420,12 @@ __global__ void __launch_bounds__(32 * kCartTY, sizeof(R) == 4 ? 6 : 1)
           st(a.ou + p, ku);
           st(a.ov + p, kv);
         }
+      }
+      // refill this slot as soon as every thread is done with it: NS copies
+      // in flight while the block waits for the next one
+      if (it + NS < nslots) {
+        __syncthreads();
+        if (threadIdx.x == 0) issue(i2 + PZ * NS, sl);
       }
     }
   }
