@@ -341,9 +341,10 @@ nrr_status nrr_autotune_clear(void);
  * block 128 or 256, variant 4, variant 5 with zc in {4, 8, 16} -- skips
  * shapes the grid cannot launch, keeps the fastest for this grid and for
  * every later grid of the same coordinates, sizes, order and precision in
- * this process, and restores the state it started from.  Needs the
- * punctures set.  *best_zc and *best_ms_per_launch (nullable) report the
- * choice and its average time per stage launch.
+ * this process, and restores the state it started from, bit for bit and in
+ * the precision it was held in.  Needs the punctures set.  *best_zc and
+ * *best_ms_per_launch (nullable) report the choice and its average time per
+ * stage launch.
  * Errors: NRR_ERR_INVALID_ARG (null grid, unknown mode, trial_steps < 1),
  * NRR_ERR_STATE (punctures not set), NRR_ERR_CUDA. */
 nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,

@@ -1529,6 +1529,9 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   if (trial_steps < 1) return fail(NRR_ERR_INVALID_ARG, "trial_steps >= 1");
   TRY(set_device(g));
   const int prec = mode == NRR_FP32 ? 32 : 64;
+  // The state's own precision: trials in the other precision run on a
+  // converted copy and leave the state's buffers untouched.
+  const int prec0 = g->state_prec;
   TRY(ensure_state(g, prec));
   double dt = 0.0, eta = 0.0;
   TRY(nrr_timestep(g, 0.5, &dt, &eta));
@@ -1592,6 +1595,7 @@ nrr_status nrr_autotune(nrr_grid *g, int mode, int64_t trial_steps,
   CUDA_TRY(cudaMemcpyAsync(yu, save_u, bytes, cudaMemcpyDeviceToDevice, g->stream));
   CUDA_TRY(cudaMemcpyAsync(yv, save_v, bytes, cudaMemcpyDeviceToDevice, g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  g->state_prec = prec0;
   // cached relaxation graphs hold the old shape
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();

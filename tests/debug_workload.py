@@ -34,14 +34,17 @@ def _state(nrr, torch, g):
     return u.cpu().numpy(), v.cpu().numpy()
 
 
-# (family, interior size, FD order, map parameters, stage variants per mode)
+# (family, interior size, FD order, map parameters, stage variants per mode;
+# a variant given as (variant, zc) runs with that plane chunk)
 GRIDS = [
     ("sinhsymtp", (32, 16, 4), 8, {}, {"fp64": [0, 1, 2, 3, 4, 5], "fp32": [0, 1, 2, 3, 4, 5, 6]}),
     ("sinhsymtp", (24, 10, 6), 4, {}, {"fp64": [0, 1, 2, 4], "fp32": [0, 1, 2, 4]}),
     ("spherical", (16, 8, 4), 10, {"rmax": 40.0}, {"fp64": [0, 1, 2], "fp32": [0, 1]}),
     ("sinhspherical", (16, 8, 4), 8, {}, {"fp64": [0, 2], "fp32": [0]}),
     ("sinhcylindrical", (16, 12, 4), 8, {}, {"fp64": [0], "fp32": [0]}),
-    ("cartesian", (32, 32, 32), 8, {"xmax": 20.0}, {"fp64": [0, 3], "fp32": [0, 3]}),
+    # Cartesian variant 1 is the tensor-copy kernel; 16 planes per chunk run
+    # its ring through more slots than it holds
+    ("cartesian", (32, 32, 32), 8, {"xmax": 20.0}, {"fp64": [0, (1, 16)], "fp32": [0, (1, 16)]}),
 ]
 
 
@@ -59,7 +62,10 @@ def run() -> dict:
         dt, eta = g.timestep(0.5)
         for mode, vs in variants.items():
             for var in vs:
-                zc = 2 if var in (1, 3, 5) else 1
+                if isinstance(var, tuple):
+                    var, zc = var
+                else:
+                    zc = 2 if var in (1, 3, 5) else 1
                 try:
                     g.set_launch(zc, mode, var)
                 except nrr.NrrError:
@@ -81,7 +87,7 @@ def run() -> dict:
     # batches: each stage variant, FP64 and defect correction
     descs = [W.grid_desc("sinhsymtp", s, 8) for s in ((32, 16, 4), (64, 8, 4), (32, 32, 8))]
     for mode in ("fp64", "fp32_dc"):
-        for var, zc in ((0, 4), (1, 2), (2, 1), (2, 2)):
+        for var, zc in ((0, 4), (1, 2), (1, 8), (2, 1), (2, 2)):
             b = nrr.Batch(descs, [punc] * 3, with_fp64=(mode == "fp64"))
             try:
                 b.set_launch(var, zc, mode)

@@ -575,6 +575,59 @@ def test_loaded_autotune_entry_sets_new_grids_shape(gpu, tmp_path):
     nrr.autotune_clear()
 
 
+def test_autotune_picks_caches_and_restores(gpu, tmp_path):
+    """nrr_autotune times the candidate launch shapes on the grid, applies
+    the fastest, caches it for later grids of the same key (and in a saved
+    cache file) and leaves the state it started from; a solve with the tuned
+    shapes takes the default shapes' steps to the same u."""
+    import json
+    import math
+    nrr.autotune_clear()
+    desc, punc = W.grid_desc("sinhsymtp", (64, 32, 8), 8), Q4
+    g0 = nrr.Grid(desc)
+    g0.set_punctures(punc)
+    r0 = g0.relax(mode="fp64", tol=1e-10)
+    u_ref = torch.empty(g0.shape, dtype=torch.float64, device="cuda")
+    g0.get_state(u_ref)
+    g0.close()
+
+    g = nrr.Grid(desc)
+    g.set_punctures(punc)
+    u = W.smooth_random_field(desc, seed=5, amplitude=0.1, noise=0.01)
+    v = W.smooth_random_field(desc, seed=6, amplitude=0.1, noise=0.01)
+    g.set_state(_dev(u), _dev(v))
+    before = [torch.empty(g.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    g.get_state(*before)
+    tuned = {}
+    for mode in ("fp64", "fp32"):
+        var, zc, ms = g.autotune(mode, 3)
+        assert ms > 0 and math.isfinite(ms), (mode, ms)
+        tuned[mode] = g.get_launch(mode)
+        assert tuned[mode][:2] == (var, zc), (mode, tuned[mode], var, zc)
+    after = [torch.empty_like(before[0]) for _ in range(2)]
+    g.get_state(*after)
+    assert torch.equal(before[0], after[0]) and torch.equal(before[1], after[1])
+
+    g2 = nrr.Grid(desc)
+    for mode in ("fp64", "fp32"):
+        assert g2.get_launch(mode) == tuned[mode], mode
+    g2.close()
+    nrr.autotune_save(str(tmp_path / "tuned.json"))
+    entries = json.loads((tmp_path / "tuned.json").read_text())["entries"]
+    for mode, prec in (("fp64", 0), ("fp32", 1)):
+        assert any(e["n"] == [64, 32, 8] and e["fp32"] == prec and
+                   (e["variant"], e["zc"], e["block"]) == tuned[mode]
+                   for e in entries), (mode, entries)
+
+    r = g.relax(mode="fp64", tol=1e-10)
+    assert r["iters"] == r0["iters"]
+    u_t = torch.empty_like(u_ref)
+    g.get_state(u_t)
+    assert (u_t - u_ref).abs().max().item() <= 1e-12 * u_ref.abs().max().item()
+    g.close()
+    nrr.autotune_clear()
+
+
 TWO_STAGE_CASES = {
     "sinh_32x16x2_o8": (W.grid_desc("sinhsymtp", (32, 16, 2), 8), Q4),
     "sinh_64x32x8_o8": (W.grid_desc("sinhsymtp", (64, 32, 8), 8), Q4),
