@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(256)
 // n1 % 4 == 0, n2 and the plane chunk even).  Interior blocks: a 32 x 4
 // column tile streams its chunk of planes, two per slot, through a 2-slot
 // shared-memory ring (one 40 x 12 x 2 box of u with its halo, one 32 x 4 x 2
-// box per operand array, completing on the slot's mbarrier; thread 0 issues
-// two slots ahead).  Cartesian ghosts are all outer ghosts, stored and
+// box per operand array, completing on the slot's mbarrier; thread 0 refills
+// a slot as soon as the block has read it).  Cartesian ghosts are all outer ghosts, stored and
 // evolved, so the halo box needs no images; the i2 neighbours come from a
 // register queue.  Extra blocks evolve the ghost shell with the radiation
 // condition, one point per thread: first the two i2 slabs, then the ring of

@@ -690,8 +690,9 @@ __device__ __forceinline__ void stage_tile_block(const Geo &g, const StageArgs<R
 // planes of a block's chunk stream, PZ at a time, through a ring of NS
 // shared-memory slots, each filled by tiled tensor copies -- one
 // (32 + 2 NG) x (TY + 2 NG) x PZ box of u with its halo and one 32 x TY x PZ
-// box per operand array -- that complete on the slot's mbarrier and are
-// issued NS - 1 slots ahead by one thread (maps: ArenaSrc or FieldSrc).  Each
+// box per operand array -- that complete on the slot's mbarrier.  One
+// thread fills all NS slots at the start and refills each as soon as the
+// block has finished reading it (maps: ArenaSrc or FieldSrc).  Each
 // thread evaluates PZ points of its column per slot; it fetches only the
 // inner-boundary image cells itself, one slot ahead, overwriting the box's
 // unmaintained ghost cells.  Requires n0 % 32 == 0, n1 % TY == 0 and the
