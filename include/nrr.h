@@ -157,12 +157,15 @@ nrr_status nrr_default_opts(nrr_relax_opts *o);
 
 /* Creates a grid: computes the full device footprint, fails with
  * NRR_ERR_OOM before allocating if it does not fit, allocates, and runs the
- * coordinate and reference-metric set-up on the device (paper Alg. 1,
- * set-up lines: coordinate arrays, reference-metric precompute, boundary
+ * coordinate and reference-metric set-up on the device (paper Alg. 1, its
+ * set-up: coordinate arrays, reference-metric precompute, boundary
  * containers, storage).  stream: a cudaStream_t, caller-owned, must outlive
  * the grid.  *out receives a handle owned by the caller (nrr_destroy_grid).
+ * The kernels index a grid's arrays with 32-bit offsets, so a padded grid
+ * holds at most 2^31 points.
  * Errors: NRR_ERR_INVALID_ARG (unsupported coord/order, n < 1, odd n2 on a
- * curvilinear grid, n1 < fd_order/2), NRR_ERR_OOM, NRR_ERR_CUDA. */
+ * curvilinear grid, n1 < fd_order/2, more than 2^31 padded points),
+ * NRR_ERR_OOM, NRR_ERR_CUDA. */
 nrr_status nrr_create_grid(const nrr_grid_desc *d, void *stream,
                            nrr_grid **out);
 nrr_status nrr_destroy_grid(nrr_grid *g);

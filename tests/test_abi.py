@@ -67,6 +67,18 @@ def test_create_grid_rejects_bad_descriptors_on_host(lib, bad):
     assert lib.nrr_last_error()
 
 
+def test_create_grid_rejects_more_than_2_31_points_on_host(lib):
+    """The stage kernels index a grid's arrays with 32-bit offsets: a
+    padded grid of more than 2^31 points (here 1284^2 x 1404 = 2.31e9, each
+    plane well inside 32 bits) is refused before any device call, so this
+    runs without a GPU."""
+    d = nrr.make_desc(W.grid_desc("cartesian", (1280, 1280, 1400), 4))
+    h = C.c_void_p()
+    assert lib.nrr_create_grid(C.byref(d), None, C.byref(h)) == nrr.ERR_INVALID_ARG
+    assert not h.value
+    assert b"2^31" in lib.nrr_last_error()
+
+
 def test_null_handles_are_rejected(lib):
     assert lib.nrr_relax(None, None, None) == nrr.ERR_INVALID_ARG
     assert lib.nrr_residual(None, 100.0, None, None, 0) == nrr.ERR_INVALID_ARG
