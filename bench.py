@@ -50,7 +50,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the FP64 stage kernel at
 # 128x128x16, order 8, from one ncu capture of this kernel (dram__bytes_read
 # + dram__bytes_write, mean of a FIRST and a MID launch).
-STAGE_FP64_DRAM_BYTES = 16.36e6
+STAGE_FP64_DRAM_BYTES = 17.0e6
 
 
 def flops_per_point(ng: int) -> int:
