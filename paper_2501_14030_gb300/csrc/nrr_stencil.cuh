@@ -710,8 +710,8 @@ struct ArenaSrc {
   const void *base;           // field 0 of this solve in the arena
   int64_t stride;             // elements between consecutive fields
   // (p - base) is a whole number f of fields, f at most a few dozen: the
-  // FP32 quotient is within 4e-6 f of f, so rounding recovers f exactly
-  // without a 64-bit integer division.
+  // FP32 quotient is within about 2e-7 f of f (three roundings of 2^-24),
+  // so rounding recovers f exactly without a 64-bit integer division.
   template <typename R>
   __device__ __forceinline__ int field(const R *p) const {
     return __float2int_rn((float)(p - static_cast<const R *>(base)) / (float)stride);
