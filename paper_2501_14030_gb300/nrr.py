@@ -220,20 +220,29 @@ def image_map(desc: dict) -> np.ndarray:
     return out
 
 
-def _require_f64(name: str, t, numel: int, exact: bool) -> None:
-    """Raises ValueError unless t is a contiguous float64 tensor with `numel`
-    elements (at least `numel` if not exact).  The C side receives bare
-    pointers and cannot check any of this."""
+def _require_tensor(name: str, t, dtype, numel: int, exact: bool = True,
+                    cuda: bool = True) -> None:
+    """Raises ValueError unless t is a contiguous torch tensor of `dtype`
+    with `numel` elements (at least `numel` if not exact), on the current
+    CUDA device if `cuda`.  The C side receives bare pointers and cannot
+    check any of this."""
     import torch
     if not isinstance(t, torch.Tensor):
         raise ValueError("%s must be a torch tensor" % name)
-    if t.dtype != torch.float64:
-        raise ValueError("%s must be float64 (got %s)" % (name, t.dtype))
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s (got %s)" % (name, dtype, t.dtype))
     if (t.numel() != numel) if exact else (t.numel() < numel):
         raise ValueError("%s has %d elements, needs %s%d" % (
             name, t.numel(), "" if exact else "at least ", numel))
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
+    if cuda:
+        _require_current_device(name, t)
+
+
+def _require_f64(name: str, t, numel: int, exact: bool) -> None:
+    import torch
+    _require_tensor(name, t, torch.float64, numel, exact, cuda=False)
 
 
 def _require_current_device(name: str, t) -> None:
@@ -368,6 +377,11 @@ def prolong(coarse: dict, uc, fine: dict, uf, stream=None) -> None:
     if stream is None:
         stream = torch.cuda.current_stream()
     dc, df = make_desc(coarse), make_desc(fine)
+    _require_tensor("uc", uc, torch.float32, int(np.prod(coarse["n"])), cuda=False)
+    _require_tensor("uf", uf, torch.float64,
+                    int(np.prod(workloads.padded_shape(fine))), cuda=False)
+    _require_current_device("uc", uc)
+    _require_current_device("uf", uf)
     _check(lib().nrr_prolong(C.byref(dc), C.c_void_p(uc.data_ptr()), C.byref(df),
                              C.c_void_p(uf.data_ptr()),
                              C.c_void_p(stream.cuda_stream)))
@@ -378,12 +392,20 @@ def kernel_launches() -> int:
     return int(lib().nrr_kernel_launches())
 
 
-def _ptr(x):
-    """(pointer, on_device) of a torch tensor or numpy array of float64."""
+def _ptr(x, numel: int, name: str = "array"):
+    """(pointer, on_device) of a padded FP64 array: a C-contiguous float64
+    numpy array, or a contiguous float64 torch tensor (on the current
+    device if on a GPU), with exactly `numel` elements.  Checked here: the
+    C side receives the bare pointer."""
     if isinstance(x, np.ndarray):
-        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != numel:
+            raise ValueError("%s must be a C-contiguous float64 array of %d "
+                             "elements (got %s, %d)" % (name, numel, x.dtype, x.size))
         return C.c_void_p(x.ctypes.data), 0
-    assert x.dtype.is_floating_point and x.is_contiguous()
+    import torch
+    _require_tensor(name, x, torch.float64, numel, cuda=False)
+    if x.is_cuda:
+        _require_current_device(name, x)
     return C.c_void_p(x.data_ptr()), int(x.is_cuda)
 
 
@@ -409,6 +431,7 @@ class Grid:
         self.ng = ng.value
         self.interior_points = ni.value
         self.shape = (s[2], s[1], s[0])
+        self.npts = s[0] * s[1] * s[2]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -441,7 +464,7 @@ class Grid:
         o.cfl, o.eta, o.r_int = cfl, eta, r_int
         o.timeout_ms, o.inner_steps, o.max_outer = timeout_ms, inner_steps, max_outer
         if u0 is not None:
-            p, on_dev = _ptr(u0)
+            p, on_dev = _ptr(u0, self.npts, "u0")
             o.initial = INIT_DEVICE if on_dev else INIT_HOST
             o.u0 = C.cast(p, C.POINTER(C.c_double))
         else:
@@ -458,24 +481,41 @@ class Grid:
         if h_out is None:
             _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), None, 0))
         else:
-            p, on_dev = _ptr(h_out)
+            p, on_dev = _ptr(h_out, self.npts, "h_out")
             _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), p, on_dev))
         return nrm.value
 
+    def _pair(self, u, v, names):
+        """Pointers of u and (nullable) v, both padded FP64 arrays of this
+        grid on the same side (host or device)."""
+        pu, on_dev = _ptr(u, self.npts, names[0])
+        if v is None:
+            return pu, None, on_dev
+        pv, on_dev_v = _ptr(v, self.npts, names[1])
+        if on_dev_v != on_dev:
+            raise ValueError("%s and %s must both be on the host or both on "
+                             "the device" % names)
+        return pu, pv, on_dev
+
     def get_state(self, u_out, v_out=None):
-        pu, on_dev = _ptr(u_out)
-        pv = _ptr(v_out)[0] if v_out is not None else None
+        pu, pv, on_dev = self._pair(u_out, v_out, ("u_out", "v_out"))
         _check(lib().nrr_get_state(self._h, pu, pv, on_dev))
 
     def set_state(self, u, v=None):
-        pu, on_dev = _ptr(u)
-        pv = _ptr(v)[0] if v is not None else None
+        pu, pv, on_dev = self._pair(u, v, ("u", "v"))
         _check(lib().nrr_set_state(self._h, pu, pv, on_dev))
 
     def rhs(self, u, v, ku, kv, eta: float, mode="fp64"):
+        """ku, kv = the relaxation right-hand side at (u, v): padded FP64
+        device tensors."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        _check(lib().nrr_rhs(self._h, m, eta, _ptr(u)[0], _ptr(v)[0],
-                             _ptr(ku)[0], _ptr(kv)[0]))
+        ptrs = []
+        for name, t in (("u", u), ("v", v), ("ku", ku), ("kv", kv)):
+            p, on_dev = _ptr(t, self.npts, name)
+            if not on_dev:
+                raise ValueError("%s must be a CUDA tensor" % name)
+            ptrs.append(p)
+        _check(lib().nrr_rhs(self._h, m, eta, *ptrs))
 
     def profile_stages(self, steps: int, dt: float, eta: float,
                        mode="fp64") -> float:
@@ -649,16 +689,24 @@ class Batch:
             _check(st)
         return [_result(r) for r in per], _result(tot, st)
 
+    def _solve_npts(self, i: int) -> int:
+        if not 0 <= int(i) < self.n:
+            raise ValueError("solve index %d outside [0, %d)" % (i, self.n))
+        return int(np.prod(self.shapes[int(i)]))
+
     def get_u(self, i: int, out):
-        p, on_dev = _ptr(out)
+        p, on_dev = _ptr(out, self._solve_npts(i), "out")
         _check(lib().nrr_batch_get_u(self._h, int(i), p, on_dev))
 
     def set_u(self, i: int, u):
-        p, on_dev = _ptr(u)
+        p, on_dev = _ptr(u, self._solve_npts(i), "u")
         _check(lib().nrr_batch_set_u(self._h, int(i), p, on_dev))
 
     def get_interior(self, out):
-        """Interior u of every solve (equal sizes) into a float32 tensor."""
+        """Interior u of every solve (equal sizes) into a float32 CUDA
+        tensor of all the solves' interior points."""
+        import torch
+        _require_tensor("out", out, torch.float32, self.interior_points)
         _check(lib().nrr_batch_get_interior(self._h, C.c_void_p(out.data_ptr())))
 
     def set_launch(self, variant: int, zc: int, mode="fp32_dc"):
@@ -709,24 +757,50 @@ class Surrogate:
         except Exception:
             pass
 
+    def _rows(self, name, t, width, rows=None, exact=True):
+        """Rows of a contiguous float32 tensor [rows][width] (rows from t);
+        the device is checked by _on_device once every shape has been."""
+        import torch
+        n = int(t.shape[0]) if rows is None and getattr(t, "ndim", 0) >= 1 else rows
+        _require_tensor(name, t, torch.float32, (n or 0) * width, exact, cuda=False)
+        return n
+
+    @staticmethod
+    def _on_device(**tensors):
+        for name, t in tensors.items():
+            _require_current_device(name, t)
+
     def fit_scaling(self, Y):
-        _check(lib().nrr_surrogate_fit_scaling(self._h, C.c_void_p(Y.data_ptr()),
-                                               Y.shape[0]))
+        n = self._rows("Y", Y, self.dims[-1])
+        self._on_device(Y=Y)
+        _check(lib().nrr_surrogate_fit_scaling(self._h, C.c_void_p(Y.data_ptr()), n))
 
     def train(self, X, Y, order, steps: int, lr: float = 1e-3,
               weight_decay: float = 0.0) -> np.ndarray:
+        import torch
+        n = self._rows("X", X, self.dims[0])
+        self._rows("Y", Y, self.dims[-1], rows=n)
+        _require_tensor("order", order, torch.int32, int(steps) * self.batch,
+                        exact=False, cuda=False)
+        self._on_device(X=X, Y=Y, order=order)
         losses = np.zeros(steps, dtype=np.float32)
         _check(lib().nrr_surrogate_train(
             self._h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
-            X.shape[0], C.c_void_p(order.data_ptr()), steps, lr, weight_decay,
+            n, C.c_void_p(order.data_ptr()), steps, lr, weight_decay,
             losses.ctypes.data_as(C.POINTER(C.c_float))))
         return losses
 
     def predict(self, X, out):
+        n = self._rows("X", X, self.dims[0])
+        self._rows("out", out, self.dims[-1], rows=n)
+        self._on_device(X=X, out=out)
         _check(lib().nrr_surrogate_predict(self._h, C.c_void_p(X.data_ptr()),
-                                           X.shape[0], C.c_void_p(out.data_ptr())))
+                                           n, C.c_void_p(out.data_ptr())))
 
     def gradients(self, X, Y):
+        self._rows("X", X, self.dims[0], rows=self.batch, exact=False)
+        self._rows("Y", Y, self.dims[-1], rows=self.batch, exact=False)
+        self._on_device(X=X, Y=Y)
         g = np.zeros(self.num_params, dtype=np.float32)
         loss = C.c_double()
         _check(lib().nrr_surrogate_gradients(

@@ -178,6 +178,73 @@ def test_noalloc_binding_checks_tensors_before_the_call(lib):
             nrr.residual_noalloc(desc, W.spinning_q4_pair(), u, n, h)
 
 
+def test_binding_checks_buffers_before_the_call(lib):
+    """Every binding call that hands the library a caller's buffer checks
+    its type, size, layout and side (host or device) first: the C side gets
+    bare pointers.  Objects are built without a GPU (no handle); each call
+    below must raise before the library is reached."""
+    import types
+    import torch
+    desc = W.grid_desc("sinhsymtp", (16, 8, 4), 4)
+    npts = int(np.prod(W.padded_shape(desc)))
+    g = nrr.Grid.__new__(nrr.Grid)
+    g._h, g.npts = None, npts
+    bad_padded = [
+        (np.zeros(npts - 1), "float64 array"),
+        (np.zeros(npts, dtype=np.float32), "float64 array"),
+        (np.zeros((npts, 2))[:, 0], "float64 array"),
+        (torch.zeros(npts, dtype=torch.float32), "float64"),
+        (torch.zeros(npts + 1, dtype=torch.float64), "elements"),
+    ]
+    for a, msg in bad_padded:
+        for call in (lambda: g.get_state(a), lambda: g.set_state(a),
+                     lambda: g.residual(100.0, a), lambda: g.relax(u0=a)):
+            with pytest.raises(ValueError, match=msg):
+                call()
+    ok = np.zeros(npts)
+    assert nrr._ptr(ok, npts, "u")[1] == 0
+    assert nrr._ptr(torch.zeros(npts, dtype=torch.float64), npts, "u")[1] == 0
+    with pytest.raises(ValueError, match="CUDA"):
+        g.rhs(ok, ok, ok, ok, 1.0)  # the right-hand side takes device arrays
+
+    b = nrr.Batch.__new__(nrr.Batch)
+    b._h, b.n = None, 2
+    b.shapes = [W.padded_shape(desc)] * 2
+    b.interior_points = 2 * 16 * 8 * 4
+    with pytest.raises(ValueError, match="solve index"):
+        b.get_u(2, ok)
+    with pytest.raises(ValueError, match="float64 array"):
+        b.set_u(1, np.zeros(npts - 1))
+    with pytest.raises(ValueError, match="elements"):
+        b.get_interior(torch.zeros(b.interior_points - 1, dtype=torch.float32))
+
+    s = nrr.Surrogate.__new__(nrr.Surrogate)
+    s._h, s.dims, s.batch = None, [12, 128, 256], 128
+    X, Y = torch.zeros((300, 12)), torch.zeros((300, 256))
+    order = torch.zeros(128 * 4, dtype=torch.int32)
+    cases = [
+        (lambda: s.fit_scaling(torch.zeros((300, 255))), "elements"),
+        (lambda: s.fit_scaling(Y.double()), "float32"),
+        (lambda: s.train(X, torch.zeros((299, 256)), order, 4), "elements"),
+        (lambda: s.train(X, Y, order.long(), 4), "int32"),
+        (lambda: s.train(X, Y, order, 5), "elements"),
+        (lambda: s.predict(X, torch.zeros((300, 128))), "elements"),
+        (lambda: s.gradients(torch.zeros((100, 12)), Y), "elements"),
+        (lambda: s.predict(X, torch.zeros((300, 256))), "CUDA"),
+    ]
+    for call, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            call()
+
+    coarse = W.grid_desc("sinhsymtp", (8, 4, 2), 4)
+    stream = types.SimpleNamespace(cuda_stream=0)
+    uf = torch.zeros(W.padded_shape(desc), dtype=torch.float64)
+    with pytest.raises(ValueError, match="elements"):
+        nrr.prolong(coarse, torch.zeros(63), desc, uf, stream=stream)
+    with pytest.raises(ValueError, match="float64"):
+        nrr.prolong(coarse, torch.zeros(64), desc, uf.float(), stream=stream)
+
+
 @pytest.mark.parametrize("M,N,K,bn,splits", [
     (128, 128, 512, 32, 1),      # tile width not offered
     (128, 128, 512, 256, 1),     # 256 does not divide N
