@@ -606,10 +606,11 @@ nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
 /* Surrogate training (no paper counterpart): `steps` AdamW steps (beta
  * 0.9/0.999, eps 1e-8, decoupled weight decay on
  * weights) on minibatches of `batch` rows: step t uses the sample indices
- * order[t*batch .. (t+1)*batch) (device int32; the caller draws the
- * shuffles).  X: device [n][n_in], Y: device [n][n_out].  loss_out
- * (nullable, host, steps floats) receives each step's mean squared error of
- * the scaled outputs.  With steps >= 2 the first step is launched from the
+ * order[t*batch .. (t+1)*batch) (device int32, each in [0, n), at least
+ * steps*batch of them; the caller draws the shuffles and the library does
+ * not read them back to check).  X: device [n][n_in], Y: device
+ * [n][n_out].  loss_out (nullable, host, steps floats) receives each step's
+ * mean squared error of the scaled outputs.  With steps >= 2 the first step is launched from the
  * host and the others replay it as one captured CUDA graph (a device step
  * counter selects the minibatch, the loss slot and the AdamW bias
  * corrections): the same kernels and arguments, so the same results as
