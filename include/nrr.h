@@ -610,11 +610,11 @@ nrr_status nrr_surrogate_fit_scaling(nrr_surrogate *s, const float *Y,
  * steps*batch of them; the caller draws the shuffles and the library does
  * not read them back to check).  X: device [n][n_in], Y: device
  * [n][n_out].  loss_out (nullable, host, steps floats) receives each step's
- * mean squared error of the scaled outputs.  With steps >= 2 the first step is launched from the
- * host and the others replay it as one captured CUDA graph (a device step
- * counter selects the minibatch, the loss slot and the AdamW bias
- * corrections): the same kernels and arguments, so the same results as
- * one-step calls.
+ * mean squared error of the scaled outputs.  With steps >= 2 the first step
+ * is launched from the host and the others replay it as one captured CUDA
+ * graph (a device step counter selects the minibatch, the loss slot and the
+ * AdamW bias corrections): the same kernels and arguments, so the same
+ * results as one-step calls.
  * Errors: NRR_ERR_INVALID_ARG (null argument, n < batch, lr <= 0),
  * NRR_ERR_TIMEOUT (a GEMM pipeline wait expired), NRR_ERR_CUDA. */
 nrr_status nrr_surrogate_train(nrr_surrogate *s, const float *X, const float *Y,
