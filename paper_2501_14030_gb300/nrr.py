@@ -392,15 +392,17 @@ def kernel_launches() -> int:
     return int(lib().nrr_kernel_launches())
 
 
-def _ptr(x, numel: int, name: str = "array"):
+def _ptr(x, numel: int, name: str = "array", out: bool = False):
     """(pointer, on_device) of a padded FP64 array: a C-contiguous float64
-    numpy array, or a contiguous float64 torch tensor (on the current
-    device if on a GPU), with exactly `numel` elements.  Checked here: the
-    C side receives the bare pointer."""
+    numpy array (writable if `out`), or a contiguous float64 torch tensor
+    (on the current device if on a GPU), with exactly `numel` elements.
+    Checked here: the C side receives the bare pointer."""
     if isinstance(x, np.ndarray):
         if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != numel:
             raise ValueError("%s must be a C-contiguous float64 array of %d "
                              "elements (got %s, %d)" % (name, numel, x.dtype, x.size))
+        if out and not x.flags["WRITEABLE"]:
+            raise ValueError("%s is read-only" % name)
         return C.c_void_p(x.ctypes.data), 0
     import torch
     _require_tensor(name, x, torch.float64, numel, cuda=False)
@@ -481,24 +483,24 @@ class Grid:
         if h_out is None:
             _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), None, 0))
         else:
-            p, on_dev = _ptr(h_out, self.npts, "h_out")
+            p, on_dev = _ptr(h_out, self.npts, "h_out", out=True)
             _check(lib().nrr_residual(self._h, r_int, C.byref(nrm), p, on_dev))
         return nrm.value
 
-    def _pair(self, u, v, names):
+    def _pair(self, u, v, names, out=False):
         """Pointers of u and (nullable) v, both padded FP64 arrays of this
         grid on the same side (host or device)."""
-        pu, on_dev = _ptr(u, self.npts, names[0])
+        pu, on_dev = _ptr(u, self.npts, names[0], out)
         if v is None:
             return pu, None, on_dev
-        pv, on_dev_v = _ptr(v, self.npts, names[1])
+        pv, on_dev_v = _ptr(v, self.npts, names[1], out)
         if on_dev_v != on_dev:
             raise ValueError("%s and %s must both be on the host or both on "
                              "the device" % names)
         return pu, pv, on_dev
 
     def get_state(self, u_out, v_out=None):
-        pu, pv, on_dev = self._pair(u_out, v_out, ("u_out", "v_out"))
+        pu, pv, on_dev = self._pair(u_out, v_out, ("u_out", "v_out"), out=True)
         _check(lib().nrr_get_state(self._h, pu, pv, on_dev))
 
     def set_state(self, u, v=None):
@@ -695,7 +697,7 @@ class Batch:
         return int(np.prod(self.shapes[int(i)]))
 
     def get_u(self, i: int, out):
-        p, on_dev = _ptr(out, self._solve_npts(i), "out")
+        p, on_dev = _ptr(out, self._solve_npts(i), "out", out=True)
         _check(lib().nrr_batch_get_u(self._h, int(i), p, on_dev))
 
     def set_u(self, i: int, u):

@@ -202,6 +202,14 @@ def test_binding_checks_buffers_before_the_call(lib):
             with pytest.raises(ValueError, match=msg):
                 call()
     ok = np.zeros(npts)
+    frozen = np.zeros(npts)
+    frozen.flags.writeable = False
+    with pytest.raises(ValueError, match="read-only"):
+        g.get_state(frozen)
+    # an input may be read-only: the binding passes it on, and the library
+    # refuses the stub's null handle
+    with pytest.raises(nrr.NrrError, match="null grid"):
+        g.set_state(frozen)
     assert nrr._ptr(ok, npts, "u")[1] == 0
     assert nrr._ptr(torch.zeros(npts, dtype=torch.float64), npts, "u")[1] == 0
     with pytest.raises(ValueError, match="CUDA"):
